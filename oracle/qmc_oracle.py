@@ -1,0 +1,254 @@
+"""CPU FP64 oracle for the reduced QMC matrix-vector product.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and
+the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+module.  The library in ``paper_2305_11645_gb300`` never calls it and shares no
+code with it.
+
+What it computes is the plain definition of every quantity, in float64 (exact
+integers where the definition is integer), with no blocking, reuse or
+reordering beyond what the definitions state:
+
+  O1  rank-1 lattice points from the *unreduced* generating vector
+      (b^{w_j} z_j) (Sec. 1.3): x_{k,j} = {k b^{w_j} z_j / N}, in integers.
+      The reduced form (k z_j mod b^{m-w_j}) / b^{m-w_j} is deliberately not
+      used here: it is what the fast method exploits and is checked against
+      this definition by the tests.
+  O2  digital-net points (Sec. 4, eq. def:digital with the reduced generating
+      matrices of eq. reduced_genmat_net2): digits of n least significant
+      first, the last min(w_j, m) rows of C^(j) set to zero, y digits as the
+      matrix-vector product over GF(2), y = sum_p y_p b^-p.
+  O3  random shifts as 32-bit fixed point D_j * 2^-32 (Sec. 2.3):
+      lattice {x + Delta} = (X32 + D) mod 2^32, nets (digital shift)
+      X32 XOR D, with X32 = x * 2^32.
+  O4  coordinate transforms applied elementwise (Sec. 2.3): identity,
+      centring x - 1/2, inverse normal CDF (scipy.special.ndtri), tent
+      1 - |1 - 2x| (Sec. 1.2).
+  O5  the dense product Y = X A (eq. Eq_XA_product), numpy matmul.
+  O6  the QMC rule Q_N(f) = N^-1 sum_k f(x_k^T A) (eq. (2)) per shift, and
+      the mean over the R shifts.
+  O7  the gradient of the shift-averaged estimate with respect to A:
+      (1/(R N)) sum_r X_r^T grad f(Y_r).
+  O8  central finite differences of the estimate in single entries of A.
+
+Parity pins for every function live in tests/test_oracle_pins.py.  Nothing in
+this file is "parity unpinned".
+"""
+from __future__ import annotations
+
+import math
+from typing import Iterable, Optional, Sequence
+
+import numpy as np
+from scipy import special as _sp
+
+LATTICE, DIGITAL_NET = 0, 1
+T_IDENTITY, T_CENTER, T_INV_NORMAL, T_TENT = 0, 1, 2, 3
+F_NONE, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP = range(7)
+
+TWO32 = 1 << 32
+
+
+# ----------------------------------------------------------------------------- O1 lattice points
+
+def lattice_numerators(b: int, m: int, w: Sequence[int], z: Sequence[int],
+                       ks: Optional[np.ndarray] = None) -> np.ndarray:
+    """Integers (k * b^{min(w_j,m)} * z_j) mod b^m, i.e. N * x_{k,j} of the
+    unreduced lattice x_k = {k z / N} with z = (b^{w_1} z_1, ..., b^{w_s} z_s)."""
+    N = b ** m
+    gens = [(b ** min(int(wj), m)) * int(zj) for wj, zj in zip(w, z)]   # unreduced generating vector
+    exact_in_int64 = (N - 1) * max(gens + [1]) < (1 << 63)
+    dt = np.int64 if exact_in_int64 else object
+    ks = np.arange(N, dtype=dt) if ks is None else np.asarray(ks).astype(dt)
+    out = np.empty((len(ks), len(w)), dtype=dt)
+    for j, gen in enumerate(gens):
+        out[:, j] = (ks * gen) % N
+    return out
+
+
+def lattice_x32(m: int, w, z, shift: Optional[np.ndarray] = None, ks=None) -> np.ndarray:
+    """b = 2 lattice points as 32-bit fixed point X32 = x * 2^32 (x exact, m <= 32),
+    optionally shifted: (X32 + D_j) mod 2^32."""
+    num = lattice_numerators(2, m, w, z, ks).astype(np.uint64)      # < 2^m
+    x32 = num * np.uint64(1 << (32 - m))                           # x * 2^32, < 2^32
+    if shift is not None:
+        x32 = (x32 + np.asarray(shift, dtype=np.uint64)[None, :]) % np.uint64(TWO32)
+    return x32.astype(np.uint32)
+
+
+# ----------------------------------------------------------------------------- O2 digital nets
+
+def net_matrix(masks: Sequence[int], m: int) -> np.ndarray:
+    """Column masks -> m x m 0/1 matrix C[p, q] (0-based p, q), row p at bit m-1-p."""
+    C = np.zeros((m, m), dtype=np.int64)
+    for q in range(m):
+        for p in range(m):
+            C[p, q] = (int(masks[q]) >> (m - 1 - p)) & 1
+    return C
+
+
+def reduced_net_matrix(masks: Sequence[int], m: int, wj: int) -> np.ndarray:
+    """eq. reduced_genmat_net2: zero the last min(w_j, m) rows of C^(j)."""
+    C = net_matrix(masks, m)
+    C[m - min(int(wj), m):, :] = 0
+    return C
+
+
+def digits_lsb_first(ks: np.ndarray, m: int) -> np.ndarray:
+    ks = np.asarray(ks, dtype=np.int64)
+    return np.stack([(ks >> q) & 1 for q in range(m)], axis=1)   # n = digits . (1, 2, 4, ...)
+
+
+def net_x32(m: int, w, C: np.ndarray, shift: Optional[np.ndarray] = None, ks=None) -> np.ndarray:
+    """b = 2 reduced digital net (Algorithm 3) as X32 = y * 2^32, optionally XOR-shifted."""
+    N = 1 << m
+    ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
+    dig = digits_lsb_first(ks, m)                         # len(ks) x m
+    out = np.empty((len(ks), len(w)), dtype=np.uint64)
+    place = np.array([1 << (m - 1 - p) for p in range(m)], dtype=np.uint64)   # y_p b^-p, scaled by 2^m
+    for j, wj in enumerate(w):
+        Chat = reduced_net_matrix(C[j], m, int(wj))
+        ydig = (dig @ Chat.T) % 2                          # y digits = Chat n over GF(2)
+        y_int = (ydig.astype(np.uint64) * place[None, :]).sum(axis=1)   # y * 2^m
+        out[:, j] = y_int << np.uint64(32 - m)
+    x32 = out.astype(np.uint32)
+    if shift is not None:
+        x32 = x32 ^ np.asarray(shift, dtype=np.uint32)[None, :]
+    return x32
+
+
+# ----------------------------------------------------------------------------- O3/O4 shifts and transforms
+
+def x32_points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
+    shift = None if problem.shifts is None else problem.shifts[shift_idx]
+    if problem.kind == LATTICE:
+        return lattice_x32(problem.m, problem.w, problem.z, shift, ks)
+    return net_x32(problem.m, problem.w, problem.C, shift, ks)
+
+
+def transform(x32: np.ndarray, kind: int) -> np.ndarray:
+    x = np.asarray(x32, dtype=np.float64) * (1.0 / TWO32)     # exact: 32 bits < 53
+    if kind == T_IDENTITY:
+        return x
+    if kind == T_CENTER:
+        return x - 0.5
+    if kind == T_INV_NORMAL:
+        with np.errstate(divide="ignore"):
+            return _sp.ndtri(x)
+    if kind == T_TENT:
+        return 1.0 - np.abs(1.0 - 2.0 * x)
+    raise ValueError(kind)
+
+
+def points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
+    """Rows x_k^T (after shift and transform) as float64, for k in ks (default all)."""
+    return transform(x32_points(problem, shift_idx, ks), problem.transform)
+
+
+# ----------------------------------------------------------------------------- O5 product
+
+def product(X: np.ndarray, A: np.ndarray) -> np.ndarray:
+    return np.asarray(X, dtype=np.float64) @ np.asarray(A, dtype=np.float64)
+
+
+def row_chunks(N: int, chunk: int) -> Iterable[np.ndarray]:
+    for k0 in range(0, N, chunk):
+        yield np.arange(k0, min(N, k0 + chunk), dtype=np.int64)
+
+
+def reduced_matmul(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
+    """Rows of P = X A for the given shift (all N rows by default)."""
+    return product(points(problem, shift_idx, ks), problem.A)
+
+
+# ----------------------------------------------------------------------------- O6 integrands
+
+def integrand(f_kind: int, params, Y: np.ndarray) -> np.ndarray:
+    """f(y) for every row y of Y (float64)."""
+    Y = np.asarray(Y, dtype=np.float64)
+    tau = Y.shape[1]
+    if f_kind == F_LINEAR_MEAN:
+        return Y.mean(axis=1)
+    if f_kind == F_MEAN_COS:
+        return np.cos(Y).mean(axis=1)
+    if f_kind == F_CALL_MEAN_EXP:
+        c, K = params[0], params[1]
+        return np.maximum(np.exp(c * Y).mean(axis=1) - K, 0.0)
+    if f_kind == F_GAUSS_NORM2:
+        return np.exp(-(Y * Y).sum(axis=1) / (2.0 * tau))
+    if f_kind == F_PDE_INV_SQ:
+        c = params[0]
+        return (1.0 / (1.0 + c * Y) ** 2).mean(axis=1)
+    if f_kind == F_LOGSUMEXP:
+        M = Y.max(axis=1)
+        return M + np.log(np.exp(Y - M[:, None]).sum(axis=1))
+    raise ValueError(f_kind)
+
+
+def integrand_grad(f_kind: int, params, Y: np.ndarray) -> np.ndarray:
+    """df/dy_t for every row (float64), the analytic derivative of integrand()."""
+    Y = np.asarray(Y, dtype=np.float64)
+    tau = Y.shape[1]
+    if f_kind == F_LINEAR_MEAN:
+        return np.full_like(Y, 1.0 / tau)
+    if f_kind == F_MEAN_COS:
+        return -np.sin(Y) / tau
+    if f_kind == F_CALL_MEAN_EXP:
+        c, K = params[0], params[1]
+        E = np.exp(c * Y)
+        active = (E.mean(axis=1) - K) > 0.0
+        return np.where(active[:, None], c * E / tau, 0.0)
+    if f_kind == F_GAUSS_NORM2:
+        f = np.exp(-(Y * Y).sum(axis=1) / (2.0 * tau))
+        return -f[:, None] * Y / tau
+    if f_kind == F_PDE_INV_SQ:
+        c = params[0]
+        return -2.0 * c / (1.0 + c * Y) ** 3 / tau
+    if f_kind == F_LOGSUMEXP:
+        M = Y.max(axis=1)
+        E = np.exp(Y - M[:, None])
+        return E / E.sum(axis=1)[:, None]
+    raise ValueError(f_kind)
+
+
+# ----------------------------------------------------------------------------- O6/O7 estimate and gradient
+
+def estimate(problem, chunk: int = 1 << 16):
+    """Per-shift Q_N(f) (eq. (2)) and their mean; R = 0 counts as one unshifted rule."""
+    Q = np.zeros(problem.R_eff)
+    for r in range(problem.R_eff):
+        acc = 0.0
+        for ks in row_chunks(problem.N, chunk):
+            acc += integrand(problem.f_kind, problem.f_params, reduced_matmul(problem, r, ks)).sum()
+        Q[r] = acc / problem.N
+    return Q, Q.mean()
+
+
+def grad(problem, chunk: int = 1 << 16) -> np.ndarray:
+    """d(mean_r Q_r)/dA = (1/(R N)) sum_r X_r^T grad f(X_r A)."""
+    G = np.zeros((problem.s, problem.tau))
+    for r in range(problem.R_eff):
+        for ks in row_chunks(problem.N, chunk):
+            X = points(problem, r, ks)
+            G += X.T @ integrand_grad(problem.f_kind, problem.f_params, product(X, problem.A))
+    return G / (problem.R_eff * problem.N)
+
+
+def estimate_with_A(problem, A: np.ndarray, chunk: int = 1 << 16) -> float:
+    Q = 0.0
+    for r in range(problem.R_eff):
+        for ks in row_chunks(problem.N, chunk):
+            Q += integrand(problem.f_kind, problem.f_params, product(points(problem, r, ks), A)).sum()
+    return Q / (problem.R_eff * problem.N)
+
+
+def fd_grad(problem, pairs: np.ndarray, h: float) -> np.ndarray:
+    """O8: central differences (Q(A + h e_jt) - Q(A - h e_jt)) / (2h), one full
+    re-evaluation of the estimate per perturbed matrix."""
+    out = np.zeros(len(pairs))
+    A = np.asarray(problem.A, dtype=np.float64)
+    for i, (j, t) in enumerate(pairs):
+        Ap = A.copy(); Ap[j, t] += h
+        Am = A.copy(); Am[j, t] -= h
+        out[i] = (estimate_with_A(problem, Ap) - estimate_with_A(problem, Am)) / (2.0 * h)
+    return out

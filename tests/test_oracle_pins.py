@@ -1,0 +1,329 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself -- hand-worked examples, textbook closed forms, invariants the paper
+states, brute force in exact rational arithmetic, or an independent library
+routine (Python's libm erfc for the normal CDF).  CPU only."""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import qmc_oracle as O
+from paper_2305_11645_gb300 import inputs as I
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return json.load(fh)
+
+
+def lattice_problem(m, w, z, A, shifts=None, transform=I.T_IDENTITY, f_kind=I.F_NONE, f_params=(0, 0, 0, 0)):
+    return I.Problem(I.LATTICE, m, np.array(w, dtype=np.uint32), np.array(A, dtype=np.float64),
+                     z=np.array(z, dtype=np.uint32), shifts=shifts, transform=transform,
+                     f_kind=f_kind, f_params=f_params)
+
+
+def net_problem(m, w, C, A, shifts=None, transform=I.T_IDENTITY, f_kind=I.F_NONE, f_params=(0, 0, 0, 0)):
+    return I.Problem(I.DIGITAL_NET, m, np.array(w, dtype=np.uint32), np.array(A, dtype=np.float64),
+                     C=np.array(C, dtype=np.uint32), shifts=shifts, transform=transform,
+                     f_kind=f_kind, f_params=f_params)
+
+
+# ----------------------------------------------------------------------------- P1-P3 hand-worked examples
+
+def test_p1_lattice_worked_example():
+    g = load("p1_lattice_b2_m3.json")
+    p = lattice_problem(g["m"], g["w"], g["z"], g["A"])
+    X = O.points(p)
+    assert np.array_equal(X * 8, np.array(g["points_times_8"], dtype=float))
+    assert np.array_equal(O.reduced_matmul(p) * 8, np.array(g["XA_times_8"], dtype=float))
+    assert np.array_equal(X.sum(axis=0), np.array(g["column_sums"], dtype=float))
+
+
+def test_p2_net_worked_example():
+    g = load("p2_net_b2_m3.json")
+    p = net_problem(g["m"], g["w"], g["C"], g["A"])
+    X = O.points(p)
+    assert np.array_equal(X * 8, np.array(g["points_times_8"], dtype=float))
+    assert np.array_equal(O.reduced_matmul(p) * 8, np.array(g["XA_times_8"], dtype=float))
+
+
+def test_p3_shifts_worked_example():
+    g = load("p3_shifts_b2_m3.json")
+    D = np.array([[int(d, 16) for d in g["D"]]], dtype=np.uint32)
+    g1, g2 = load("p1_lattice_b2_m3.json"), load("p2_net_b2_m3.json")
+    pl = lattice_problem(g1["m"], g1["w"], g1["z"], g1["A"], shifts=D)
+    pn = net_problem(g2["m"], g2["w"], g2["C"], g2["A"], shifts=D)
+    want_l = np.array([[int(v, 16) for v in row] for row in g["lattice_X32"]], dtype=np.uint32)
+    want_n = np.array([[int(v, 16) for v in row] for row in g["net_X32"]], dtype=np.uint32)
+    assert np.array_equal(O.x32_points(pl, 0), want_l)
+    assert np.array_equal(O.x32_points(pn, 0), want_n)
+
+
+def test_repetition_example_periods():
+    """Sec. 1: with N_1=4, N_2=2, N_3=1 coordinate j takes N_j values and repeats
+    with period N_j (the listed points (y_{1,k}, y_{2,k mod 2}, y_{3,0}))."""
+    p = lattice_problem(2, [0, 1, 2], [1, 1, 1], np.eye(3))
+    X = O.points(p)
+    for j, Nj in enumerate([4, 2, 1]):
+        col = X[:, j]
+        assert len(set(col.tolist())) == Nj
+        assert all(col[k] == col[k % Nj] for k in range(4))
+
+
+# ----------------------------------------------------------------------------- P4 reduced = unreduced (brute force)
+
+@pytest.mark.parametrize("b,mmax", [(2, 9), (3, 5), (5, 3)])
+def test_p4_reduced_form_equals_unreduced_definition(b, mmax):
+    """{k b^w z / b^m} = (k z mod b^(m-w)) / b^(m-w) for every k, every unit z
+    and every w (Sec. 1.3), checked in exact integers for all small cases."""
+    for m in range(1, mmax + 1):
+        N = b ** m
+        for w in range(0, m + 2):
+            q = m - min(w, m)
+            units = [z for z in range(1, max(b ** q, 2)) if math.gcd(z, b) == 1] if q > 0 else [1]
+            for z in units:
+                num = O.lattice_numerators(b, m, [w], [z])[:, 0]
+                for k in range(N):
+                    red = Fraction((k * z) % (b ** q), b ** q) if q > 0 else Fraction(0)
+                    assert Fraction(int(num[k]), N) == red
+
+
+def alg1(p, Afr):
+    """Algorithm 1 (Sec. 3.1) in exact rationals, lattice, b = 2."""
+    m, w, z = p.m, [int(v) for v in p.w], [int(v) for v in p.z]
+    s, tau = len(w), len(Afr[0])
+    sstar = max([j + 1 for j in range(s) if w[j] < m], default=0)
+    P = [[Fraction(0)] * tau]
+    for j in range(sstar - 1, -1, -1):
+        n = 2 ** (m - w[j])
+        wnext = m if j + 1 >= sstar else min(w[j + 1], m)
+        reps = 2 ** (wnext - w[j])
+        assert reps * len(P) == n
+        Xj = [Fraction((k * z[j]) % n, n) for k in range(n)]
+        P = [[P[k % len(P)][t] + Xj[k] * Afr[j][t] for t in range(tau)] for k in range(n)]
+    N = 2 ** m
+    return [[P[k % len(P)][t] for t in range(tau)] for k in range(N)]
+
+
+def alg2(p, Afr):
+    """Algorithm 2 (Sec. 3.2) in exact rationals, lattice, b = 2."""
+    m, w, z = p.m, [int(v) for v in p.w], [int(v) for v in p.z]
+    tau = len(Afr[0])
+    P = [[Fraction(0)] * tau]
+    for Ilev in range(m - 1, -1, -1):
+        cols = [j for j in range(len(w)) if w[j] == Ilev]
+        n = 2 ** (m - Ilev)
+        P = [[P[k % len(P)][t] for t in range(tau)] for k in range(n)]   # b copies of P_{I+1}
+        for j in cols:
+            for k in range(n):
+                x = Fraction((k * z[j]) % n, n)
+                for t in range(tau):
+                    P[k][t] += x * Afr[j][t]
+    return P
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_p4_algorithms_1_and_2_return_XA(seed):
+    """Both algorithms return exactly P = X A (Sec. 3), compared in exact
+    arithmetic with the oracle's dense product of the unreduced points."""
+    g = np.random.default_rng(seed)
+    m = int(g.integers(1, 6)); s = int(g.integers(1, 9)); tau = int(g.integers(1, 4))
+    w = np.sort(g.integers(0, m + 2, size=s)); w[0] = 0
+    z = I.odd_z(g, m, w)
+    A = g.integers(-8, 9, size=(s, tau))
+    p = lattice_problem(m, w, z, A)
+    Afr = [[Fraction(int(v)) for v in row] for row in A]
+    dense = O.reduced_matmul(p)              # exact: dyadic rationals times small integers
+    for P in (alg1(p, Afr), alg2(p, Afr)):
+        assert np.array_equal(np.array([[float(v) for v in row] for row in P]), dense)
+
+
+def test_p4_shift_is_addition_mod_one():
+    """{x + Delta} in exact rationals equals the oracle's 32-bit shift."""
+    g = np.random.default_rng(7)
+    p = lattice_problem(5, [0, 0, 1, 3, 5, 6], I.odd_z(g, 5, np.array([0, 0, 1, 3, 5, 6])), np.eye(6)[:, :1],
+                        shifts=I.random_shifts(g, 1, 6))
+    X32 = O.x32_points(p, 0)
+    base = O.lattice_numerators(2, 5, p.w, p.z)
+    for k in range(32):
+        for j in range(6):
+            v = Fraction(int(base[k, j]), 32) + Fraction(int(p.shifts[0, j]), 2 ** 32)
+            v -= math.floor(v)
+            assert Fraction(int(X32[k, j]), 2 ** 32) == v
+
+
+def test_p4_digital_shift_is_digitwise_addition():
+    """A digital shift adds base-2 digits mod 2 (y_p + Delta_p mod b)."""
+    g = np.random.default_rng(8)
+    w = np.array([0, 1, 2, 4], dtype=np.uint32)
+    C = I.periodic_net_masks(g, 6, w)
+    D = I.random_shifts(g, 1, 4)
+    p = net_problem(6, w, C, np.eye(4)[:, :1], shifts=D)
+    y32 = O.x32_points(net_problem(6, w, C, np.eye(4)[:, :1]), 0)
+    x32 = O.x32_points(p, 0)
+    for k in range(64):
+        for j in range(4):
+            dig_y = [(int(y32[k, j]) >> (31 - p_)) & 1 for p_ in range(32)]
+            dig_d = [(int(D[0, j]) >> (31 - p_)) & 1 for p_ in range(32)]
+            val = sum(((a + b) % 2) * Fraction(1, 2 ** (p_ + 1)) for p_, (a, b) in enumerate(zip(dig_y, dig_d)))
+            assert Fraction(int(x32[k, j]), 2 ** 32) == val
+
+
+def test_van_der_corput_identity_matrix():
+    """C = identity gives the radical inverse of n in base 2 (textbook)."""
+    m = 7
+    C = np.array([[1 << (m - 1 - q) for q in range(m)]], dtype=np.uint32)
+    p = net_problem(m, [0], C, np.eye(1))
+    X = O.points(p)[:, 0]
+    for n in range(2 ** m):
+        rev = int(format(n, f"0{m}b")[::-1], 2)
+        assert X[n] == rev / 2 ** m
+
+
+# ----------------------------------------------------------------------------- P5 permutation, column sums, closed forms
+
+def closed_form_column_sums(p, shift_idx):
+    """sum_k x_{k,j} = 2^{w_j} [ (2^q - 1)/2 + 2^q D_lo 2^-32 ], q = m - min(w_j, m),
+    D_lo = D_j mod 2^(32-q): the period is a permutation of the grid (Sec. 1.3, Sec. 4)."""
+    out = []
+    for j, wj in enumerate(p.w):
+        wj = min(int(wj), p.m); q = p.m - wj
+        D = 0 if p.shifts is None else int(p.shifts[shift_idx, j])
+        Dlo = D % (1 << (32 - q))
+        out.append(Fraction(2 ** wj) * (Fraction(2 ** q - 1, 2) + Fraction(2 ** q * Dlo, 2 ** 32)))
+    return out
+
+
+@pytest.mark.parametrize("kind", [I.LATTICE, I.DIGITAL_NET])
+@pytest.mark.parametrize("seed", range(5))
+def test_p5_permutation_and_exact_column_sums(kind, seed):
+    p = I.random_problem(seed, kind=kind, R=2 if seed % 2 else 0)
+    for r in range(p.R_eff):
+        X32 = O.x32_points(p, r).astype(np.int64)
+        for j, wj in enumerate(p.w):
+            q = p.m - min(int(wj), p.m)
+            period = X32[: 2 ** q, j]
+            D = 0 if p.shifts is None else int(p.shifts[r, j])
+            Dlo = D % (1 << (32 - q))
+            grid = sorted(((v - Dlo) >> (32 - q)) if q > 0 else 0 for v in period)
+            assert grid == list(range(2 ** q))                       # a permutation of the grid
+            assert all(X32[k, j] == X32[k % 2 ** q, j] for k in range(p.N))   # periodic
+        sums = [Fraction(int(v), 2 ** 32) for v in X32.sum(axis=0)]
+        assert sums == closed_form_column_sums(p, r)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_p5_linear_mean_estimate_closed_form(seed):
+    """f = mean_t y_t: Q = (N tau)^-1 sum_j c_j sum_t A_jt with c_j the exact column sums."""
+    p = I.random_problem(seed, kind=I.LATTICE if seed % 2 else I.DIGITAL_NET, R=seed % 3,
+                         f_kind=I.F_LINEAR_MEAN)
+    Q, mean = O.estimate(p)
+    for r in range(p.R_eff):
+        c = closed_form_column_sums(p, r)
+        want = sum(float(cj) * p.A[j].sum() for j, cj in enumerate(c)) / (p.N * p.tau)
+        assert abs(Q[r] - want) <= 1e-13 * max(1.0, abs(want))
+
+
+# ----------------------------------------------------------------------------- transforms
+
+def Phi(x):
+    return 0.5 * math.erfc(-x / math.sqrt(2.0))
+
+
+def test_inverse_normal_round_trip_and_known_values():
+    ps = [2.0 ** -32, 1e-9, 1e-5, 0.01, 0.02425, 0.1, 0.3, 0.5, 0.7, 0.9, 0.97575, 0.99, 1 - 1e-5, 1 - 2.0 ** -32]
+    x32 = np.array([round(p_ * 2 ** 32) for p_ in ps], dtype=np.uint64).astype(np.uint32)
+    xs = O.transform(x32, O.T_INV_NORMAL)
+    for v, x in zip(x32, xs):
+        p_ = int(v) / 2 ** 32
+        if p_ < 0.5:
+            assert abs(Phi(x) - p_) <= 1e-14 * p_
+        else:
+            assert abs(0.5 * math.erfc(x / math.sqrt(2.0)) - (1 - p_)) <= 1e-13 * (1 - p_)
+    # textbook quantiles
+    q975 = O.transform(np.array([int(0.975 * 2 ** 32)], dtype=np.uint32), O.T_INV_NORMAL)[0]
+    assert abs(q975 - 1.959963984540054) < 1e-8
+    assert O.transform(np.array([1 << 31], dtype=np.uint32), O.T_INV_NORMAL)[0] == 0.0
+    assert O.transform(np.array([0], dtype=np.uint32), O.T_INV_NORMAL)[0] == -np.inf
+
+
+def test_center_and_tent_transforms():
+    x32 = np.array([0, 1 << 30, 1 << 31, 3 << 30, 0xFFFFFFFF], dtype=np.uint32)
+    assert np.array_equal(O.transform(x32, O.T_CENTER), np.array([-0.5, -0.25, 0.0, 0.25, 0.5 - 2.0 ** -32]))
+    assert np.array_equal(O.transform(x32, O.T_TENT), np.array([0.0, 0.5, 1.0, 0.5, 2.0 ** -31]))
+
+
+# ----------------------------------------------------------------------------- integrands and gradients
+
+FKINDS = [(I.F_LINEAR_MEAN, (0, 0, 0, 0)), (I.F_MEAN_COS, (0, 0, 0, 0)), (I.F_CALL_MEAN_EXP, (0.2, 1.0, 0, 0)),
+          (I.F_GAUSS_NORM2, (0, 0, 0, 0)), (I.F_PDE_INV_SQ, (0.5, 0, 0, 0)), (I.F_LOGSUMEXP, (0, 0, 0, 0))]
+
+
+def test_integrand_values_at_hand_points():
+    tau = 4
+    Y0 = np.zeros((1, tau))
+    assert O.integrand(I.F_LINEAR_MEAN, (0,) * 4, Y0)[0] == 0.0
+    assert O.integrand(I.F_MEAN_COS, (0,) * 4, Y0)[0] == 1.0
+    assert O.integrand(I.F_CALL_MEAN_EXP, (0.2, 1.0, 0, 0), Y0)[0] == 0.0
+    assert O.integrand(I.F_CALL_MEAN_EXP, (0.2, 0.5, 0, 0), Y0)[0] == 0.5
+    assert O.integrand(I.F_GAUSS_NORM2, (0,) * 4, Y0)[0] == 1.0
+    assert O.integrand(I.F_PDE_INV_SQ, (0.5,) + (0,) * 3, Y0)[0] == 1.0
+    assert abs(O.integrand(I.F_LOGSUMEXP, (0,) * 4, Y0)[0] - math.log(4)) < 1e-15
+    Y = np.array([[1.0, -1.5, 0.5, 3.0]])
+    assert abs(O.integrand(I.F_MEAN_COS, (0,) * 4, Y)[0] - sum(math.cos(v) for v in Y[0]) / 4) < 1e-15
+    assert abs(O.integrand(I.F_GAUSS_NORM2, (0,) * 4, Y)[0] - math.exp(-12.5 / 8)) < 1e-15
+    assert abs(O.integrand(I.F_PDE_INV_SQ, (0.5,) + (0,) * 3, Y)[0] -
+               sum(1 / (1 + 0.5 * v) ** 2 for v in Y[0]) / 4) < 1e-14
+    assert abs(O.integrand(I.F_LOGSUMEXP, (0,) * 4, Y)[0] - math.log(sum(math.exp(v) for v in Y[0]))) < 1e-14
+
+
+@pytest.mark.parametrize("f_kind,params", FKINDS)
+def test_integrand_gradient_matches_finite_differences(f_kind, params):
+    g = np.random.default_rng(11)
+    Y = g.standard_normal((5, 7)) * 0.7
+    G = O.integrand_grad(f_kind, params, Y)
+    h = 1e-6
+    for t in range(7):
+        E = np.zeros_like(Y); E[:, t] = h
+        fd = (O.integrand(f_kind, params, Y + E) - O.integrand(f_kind, params, Y - E)) / (2 * h)
+        assert np.allclose(G[:, t], fd, rtol=1e-6, atol=1e-9)
+
+
+def test_p6_gradient_invariants():
+    """LSE: sum_t dQ/dA_jt = mean_k x_kj = c_j / N; linear f: dQ/dA_jt = c_j / (N tau)."""
+    for kind in (I.LATTICE, I.DIGITAL_NET):
+        p = I.random_problem(3, kind=kind, m=6, s=9, tau=5, R=2, f_kind=I.F_LOGSUMEXP)
+        G = O.grad(p)
+        c = np.mean([[float(v) for v in closed_form_column_sums(p, r)] for r in range(p.R_eff)], axis=0)
+        assert np.allclose(G.sum(axis=1), c / p.N, rtol=1e-13, atol=1e-15)
+        p.f_kind = I.F_LINEAR_MEAN
+        G = O.grad(p)
+        assert np.allclose(G, (c / (p.N * p.tau))[:, None], rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("f_kind,params", FKINDS[1:])
+def test_p6_oracle_gradient_matches_central_differences(f_kind, params):
+    p = I.random_problem(5, kind=I.LATTICE, m=5, s=7, tau=4, R=2, transform=I.T_CENTER,
+                         f_kind=f_kind, f_params=params, a_scale=0.8)
+    G = O.grad(p)
+    pairs = np.array([(j, t) for j in range(7) for t in range(4)])
+    fd = O.fd_grad(p, pairs, 1e-5)
+    want = np.array([G[j, t] for j, t in pairs])
+    assert np.allclose(fd, want, rtol=2e-7, atol=1e-10)
+
+
+def test_p7_gaussian_expectation_closed_form():
+    """Sec. 1: E[mean_t exp(0.2 y_t)] with y = L x, x ~ N(0, I) equals
+    mean_t exp(0.02 Sigma_tt); the shifted, inverse-normal reduced lattice must
+    approach it (integration sanity of the transform and of A = L^T)."""
+    p = I.c2(m=13, s=32)
+    p.f_params = (0.2, 0.0, 0.0, 0.0)                     # K = 0: no kink
+    Q, _ = O.estimate(p)
+    S = p.A.T @ p.A
+    exact = np.exp(0.02 * np.diag(S)).mean()
+    assert abs(Q[0] - exact) < 2e-3 * exact
