@@ -1,0 +1,698 @@
+// Host side of libqmc_gb300: argument validation against the paper's
+// definitions, the block schedule (Algorithm 2's weight blocks split into a
+// register-tree fine band and coarse block products), the workspace layout,
+// and the launch sequences behind the C ABI of include/qmc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/qmc.h"
+#include "qmc_internal.cuh"
+
+using namespace qmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+qmc_status fail(qmc_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define QMC_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) return fail(QMC_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------------------------------
+// kernel tracing: while enabled, every launch is bracketed by CUDA events on its stream
+// ------------------------------------------------------------------------------------------
+struct TraceRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+struct TraceState {
+    std::mutex mu;
+    bool on = false;
+    std::vector<TraceRec> recs;
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::string> names;
+    std::vector<unsigned long long> counts;
+    std::vector<double> ms;
+};
+TraceState& trace_state() {
+    static TraceState t;
+    return t;
+}
+cudaEvent_t trace_event(TraceState& t) {
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+struct TraceScope {
+    cudaStream_t st;
+    const char* name;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on = false;
+    TraceScope(cudaStream_t s, const char* n) : st(s), name(n) {
+        TraceState& t = trace_state();
+        std::lock_guard<std::mutex> g(t.mu);
+        if (!t.on) return;
+        on = true;
+        a = trace_event(t);
+        b = trace_event(t);
+        cudaEventRecord(a, st);
+    }
+    ~TraceScope() {
+        if (!on) return;
+        cudaEventRecord(b, st);
+        TraceState& t = trace_state();
+        std::lock_guard<std::mutex> g(t.mu);
+        t.recs.push_back({name, a, b});
+    }
+};
+#define QMC_LAUNCH(st, name, call)        \
+    do {                                  \
+        TraceScope ts_((st), (name));     \
+        QMC_CUDA(call);                   \
+    } while (0)
+
+// GF(2) rank of q vectors of q bits
+int gf2_rank(std::vector<uint32_t> v) {
+    int rank = 0;
+    for (int bit = 31; bit >= 0; --bit) {
+        int piv = -1;
+        for (size_t i = rank; i < v.size(); ++i)
+            if ((v[i] >> bit) & 1u) { piv = (int)i; break; }
+        if (piv < 0) continue;
+        std::swap(v[rank], v[piv]);
+        for (size_t i = 0; i < v.size(); ++i)
+            if ((int)i != rank && ((v[i] >> bit) & 1u)) v[i] ^= v[rank];
+        ++rank;
+    }
+    return rank;
+}
+
+qmc_status validate(const qmc_rule* r) {
+    if (!r) return fail(QMC_ERR_INVALID_ARG, "rule is NULL");
+    if (r->kind != QMC_LATTICE && r->kind != QMC_DIGITAL_NET)
+        return fail(QMC_ERR_INVALID_ARG, "kind %d is neither QMC_LATTICE nor QMC_DIGITAL_NET", r->kind);
+    if (r->b < 2) return fail(QMC_ERR_INVALID_ARG, "base b=%u must be a prime >= 2", r->b);
+    if (r->b != 2) return fail(QMC_ERR_UNSUPPORTED, "base b=%u: only b=2 is built", r->b);
+    if (r->m < 1) return fail(QMC_ERR_INVALID_ARG, "m=%u: N = b^m needs m >= 1", r->m);
+    if (r->m > 30) return fail(QMC_ERR_UNSUPPORTED, "m=%u: N = 2^m is limited to m <= 30", r->m);
+    if (r->s < 1 || r->s > 65536) return fail(QMC_ERR_INVALID_ARG, "s=%u outside [1, 65536]", r->s);
+    if (!r->w) return fail(QMC_ERR_INVALID_ARG, "w is NULL");
+    for (uint32_t j = 1; j < r->s; ++j)
+        if (r->w[j] < r->w[j - 1])
+            return fail(QMC_ERR_INVALID_ARG, "w must be nondecreasing: w[%u]=%u < w[%u]=%u", j, r->w[j], j - 1,
+                        r->w[j - 1]);
+    if (r->transform < QMC_T_IDENTITY || r->transform > QMC_T_TENT)
+        return fail(QMC_ERR_INVALID_ARG, "transform %d unknown", r->transform);
+    if (r->R > 65535) return fail(QMC_ERR_INVALID_ARG, "R=%u shifts: at most 65535", r->R);
+    if (r->R > 0 && !r->shift) return fail(QMC_ERR_INVALID_ARG, "R=%u but shift is NULL", r->R);
+    if (r->transform == QMC_T_INV_NORMAL && r->R == 0)
+        return fail(QMC_ERR_INVALID_ARG, "the inverse-normal transform needs a random shift (x=0 maps to -inf)");
+    const uint32_t m = r->m;
+    if (r->kind == QMC_LATTICE) {
+        if (!r->z) return fail(QMC_ERR_INVALID_ARG, "lattice rule needs z");
+        for (uint32_t j = 0; j < r->s; ++j) {
+            const uint32_t q = m - std::min(r->w[j], m);
+            const uint32_t z = r->z[j];
+            if (q == 0) {
+                if (z != 1) return fail(QMC_ERR_INVALID_ARG, "z[%u]=%u: U_1 = {1} when w_j >= m", j, z);
+            } else if (z < 1 || (z & 1u) == 0 || (uint64_t)z >= (1ull << q)) {
+                return fail(QMC_ERR_INVALID_ARG, "z[%u]=%u not in U_{2^%u} (odd, < 2^%u)", j, z, q, q);
+            }
+        }
+    } else {
+        if (!r->C) return fail(QMC_ERR_INVALID_ARG, "digital net needs C");
+        for (uint32_t j = 0; j < r->s; ++j) {
+            const uint32_t wcl = std::min(r->w[j], m), q = m - wcl;
+            const uint32_t rowmask = (wcl >= 32) ? 0u : ~((1u << wcl) - 1u);
+            std::vector<uint32_t> lead;
+            for (uint32_t c = 0; c < m; ++c) {
+                const uint32_t word = r->C[(size_t)j * m + c];
+                if (m < 32 && (word >> m) != 0)
+                    return fail(QMC_ERR_INVALID_ARG, "C[%u][%u]=0x%x has bits above row 1 (bit m-1)", j, c, word);
+                const uint32_t red = word & rowmask;      // eq. reduced_genmat_net2
+                if (c >= q && red != 0)
+                    return fail(QMC_ERR_UNSUPPORTED,
+                                "column %u of the reduced C^(%u) is nonzero: the net is not periodic with period "
+                                "2^(m-w_j) (non-periodic reduced nets, Algorithm 4, are not built)",
+                                c + 1, j);
+                if (c < q) lead.push_back(red >> wcl);
+            }
+            if (gf2_rank(lead) != (int)q)
+                return fail(QMC_ERR_INVALID_ARG, "leading %ux%u block of C^(%u) is singular over GF(2)", q, q, j);
+        }
+    }
+    return QMC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// the plan: block schedule and workspace layout of one problem
+// ------------------------------------------------------------------------------------------
+struct Plan {
+    int op = 0;
+    int kind = 0, m = 0, s = 0, transform = 0, R = 0, reff = 1;
+    long long N = 0;
+    int lev_tau[kMaxLevels] = {}, lev_col0[kMaxLevels] = {};
+    long long lev_tab[kMaxLevels + 1] = {};
+    long long T_tot = 0;
+    int tau = 0, tau_pad = 0, precision = 0, elt = 4, fkind = 0;
+    int shape = SHAPE_S0, JF = 0, kf_width = 0, cw_bwd = 4;
+    Chain chf{}, chb{};
+    long long B_per_shift = 0, F_per_shift = 0, partc_elems = 0;
+    int root_blocks = 0, cg_count = 1, cr = 0;
+    int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
+    int nblk = 0;
+    bool need_gen = false, need_shift = false, need_pad = false;
+    size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_rowpart = 0, off_rowmax = 0,
+           off_rowsave = 0, off_fpart = 0, off_F = 0, off_gradpart = 0, off_partc = 0, total = 0;
+};
+
+qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integrand* f, int precision,
+                     const void* d_A, Plan& P) {
+    qmc_status st = validate(r);
+    if (st != QMC_OK) return st;
+    P.op = op;
+    P.kind = r->kind; P.m = (int)r->m; P.s = (int)r->s; P.transform = r->transform;
+    P.R = (int)r->R; P.reff = std::max(P.R, 1);
+    P.N = 1LL << P.m;
+    for (int I = 0; I <= P.m; ++I) { P.lev_tau[I] = 0; P.lev_col0[I] = -1; }
+    for (int j = 0; j < P.s; ++j) {
+        const int I = (int)std::min<uint32_t>(r->w[j], r->m);
+        if (P.lev_col0[I] < 0) P.lev_col0[I] = j;
+        P.lev_tau[I]++;
+    }
+    {   // empty levels get the next column index (never read)
+        int next = P.s;
+        for (int I = P.m; I >= 0; --I) {
+            if (P.lev_col0[I] < 0) P.lev_col0[I] = next;
+            else next = P.lev_col0[I];
+        }
+    }
+    P.lev_tab[0] = 0;
+    for (int I = 0; I <= P.m; ++I) P.lev_tab[I + 1] = P.lev_tab[I] + (long long)P.lev_tau[I] * (1LL << (P.m - I));
+    P.T_tot = P.lev_tab[P.m + 1];
+    P.need_gen = (r->d_gen == nullptr);
+    P.need_shift = (P.R > 0 && r->d_shift == nullptr);
+
+    size_t off = 0;
+    P.off_gen = off;
+    if (P.need_gen) off = align256(off + sizeof(uint32_t) * (size_t)P.s * (P.kind == QMC_DIGITAL_NET ? P.m : 1));
+    P.off_shift = off;
+    if (P.need_shift) off = align256(off + sizeof(uint32_t) * (size_t)P.R * P.s);
+    if (op == QMC_OP_GEN_POINTS) { P.total = off; return QMC_OK; }
+
+    if (precision != QMC_FP64 && precision != QMC_FP32) {
+        if (precision == QMC_SPLIT || precision == QMC_BF16)
+            return fail(QMC_ERR_UNSUPPORTED, "precision %d (tensor-core tiers) is not built", precision);
+        return fail(QMC_ERR_INVALID_ARG, "precision %d unknown", precision);
+    }
+    if (tau < 1 || tau > 65536) return fail(QMC_ERR_INVALID_ARG, "tau=%u outside [1, 65536]", tau);
+    P.precision = precision;
+    P.elt = precision == QMC_FP64 ? 8 : 4;
+    P.tau = (int)tau;
+    P.tau_pad = (int)((tau + 3) / 4 * 4);
+    if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
+        if (!f) return fail(QMC_ERR_INVALID_ARG, "integrand is NULL");
+        if (f->kind < QMC_F_LINEAR_MEAN || f->kind > QMC_F_LOGSUMEXP)
+            return fail(QMC_ERR_INVALID_ARG, "integrand kind %d unknown (QMC_F_NONE is only for the product)", f->kind);
+        P.fkind = f->kind;
+    }
+
+    // fine band shape
+    auto fits = [&](int jf, const int* kmax) {
+        if (P.m < jf) return false;
+        for (int I = 0; I < jf; ++I)
+            if (P.lev_tau[I] > kmax[I]) return false;
+        return true;
+    };
+    const int k4[4] = {1, 2, 4, 8}, k1[1] = {16};
+    if (precision == QMC_FP32 && fits(4, k4)) { P.shape = SHAPE_S4; P.JF = 4; P.kf_width = 15; P.cw_bwd = 4; }
+    else if (fits(1, k1)) { P.shape = SHAPE_S1; P.JF = 1; P.kf_width = 16; P.cw_bwd = precision == QMC_FP64 ? 1 : 2; }
+    else { P.shape = SHAPE_S0; P.JF = 0; P.kf_width = 0; P.cw_bwd = precision == QMC_FP64 ? 2 : 4; }
+    const int logn_root = P.m - P.JF;
+    const long long n_root = 1LL << logn_root;
+
+    // coarse chain: levels JF..m with columns
+    P.chf.count = 0;
+    long long boff = 0;
+    int tiles = 0;
+    for (int I = P.JF; I <= P.m; ++I) {
+        if (P.lev_tau[I] == 0) continue;
+        const int e = P.chf.count++;
+        P.chf.lev[e] = I; P.chf.logn[e] = P.m - I; P.chf.tau[e] = P.lev_tau[I]; P.chf.col0[e] = P.lev_col0[I];
+        P.chf.tab[e] = P.lev_tab[I];
+        P.chf.boff[e] = boff;
+        boff += (1LL << (P.m - I)) * P.tau_pad;
+        P.chf.tile0[e] = tiles;
+        tiles += (int)(((1LL << (P.m - I)) + 63) / 64);
+        P.chf.split[e] = 1; P.chf.poff[e] = 0;
+    }
+    P.chf.tile0[P.chf.count] = tiles;
+    P.B_per_shift = boff;
+
+    // fine forward grid: 128 roots per CTA, column groups to fill the GPU
+    P.root_blocks = (int)((n_root + 127) / 128);
+    {
+        const long long want = 4LL * 152;
+        long long cg = (want + (long long)P.root_blocks * P.reff - 1) / ((long long)P.root_blocks * P.reff);
+        cg = std::max(1LL, std::min(cg, (long long)(P.tau_pad + 15) / 16));
+        int cr = (int)((P.tau_pad + cg - 1) / cg);
+        cr = (cr + 15) / 16 * 16;
+        P.cr = cr;
+        P.cg_count = (P.tau_pad + cr - 1) / cr;
+    }
+    P.nblk = (int)((P.N + 255) / 256);
+
+    // backward schedule
+    if (op == QMC_OP_INTEGRATE_BWD) {
+        const int cols_per_pass = 32 * P.cw_bwd;
+        P.passes = (P.tau_pad + cols_per_pass - 1) / cols_per_pass;
+        long long groups_target = std::max(1LL, 304LL / ((long long)P.passes * P.reff));
+        long long rpc = (n_root + groups_target - 1) / groups_target;
+        rpc = std::max(rpc, (n_root + 511) / 512);
+        rpc = std::max(8LL, (rpc + 7) / 8 * 8);
+        P.roots_per_cta = (int)rpc;
+        P.groups = (int)((n_root + rpc - 1) / rpc);
+        // F area: root folds, then the chain levels above the root
+        P.chb = P.chf;
+        long long foff = 0;
+        long long poff = 0;
+        int bt = 0;
+        for (int e = 0; e < P.chb.count; ++e) {
+            const int I = P.chb.lev[e];
+            if (I == P.JF) P.chb.boff[e] = 0;
+            else { P.chb.boff[e] = foff; foff += (1LL << (P.m - I)) * P.tau_pad; }
+            const long long K = (long long)P.reff << (P.m - I);
+            const int split = (int)std::max(1LL, std::min(64LL, K / 1024));
+            P.chb.split[e] = split;
+            P.chb.poff[e] = poff;
+            poff += (long long)split * P.chb.tau[e] * P.tau_pad;
+            P.chb.tile0[e] = bt;
+            bt += ((P.chb.tau[e] + 15) / 16) * split;
+        }
+        P.chb.tile0[P.chb.count] = bt;
+        P.bwd_tiles = bt;
+        P.F_per_shift = foff;
+        P.partc_elems = poff;
+    }
+
+    // workspace layout
+    const size_t E = (size_t)P.elt;
+    P.need_pad = !((tau % 4) == 0 && d_A != nullptr && (((uintptr_t)d_A) % 16) == 0);
+    P.off_A = off;
+    if (P.need_pad) off = align256(off + E * (size_t)P.s * P.tau_pad);
+    P.off_tab = off;
+    off = align256(off + E * (size_t)P.reff * P.T_tot);
+    P.off_B = off;
+    off = align256(off + E * (size_t)P.reff * P.B_per_shift);
+    if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
+        P.off_rowpart = off;
+        off = align256(off + E * (size_t)P.reff * P.cg_count * P.N);
+        P.off_rowmax = off;
+        if (P.fkind == QMC_F_LOGSUMEXP) off = align256(off + E * (size_t)P.reff * P.cg_count * P.N);
+        P.off_rowsave = off;
+        off = align256(off + sizeof(double) * (size_t)P.reff * P.N);
+        P.off_fpart = off;
+        off = align256(off + sizeof(double) * (size_t)P.reff * P.nblk);
+    }
+    if (op == QMC_OP_INTEGRATE_BWD) {
+        P.off_F = off;
+        off = align256(off + E * (size_t)P.reff * ((size_t)n_root * P.tau_pad + P.F_per_shift));
+        P.off_gradpart = off;
+        off = align256(off + E * (size_t)P.reff * P.groups * std::max(P.kf_width, 1) * P.tau_pad);
+        P.off_partc = off;
+        off = align256(off + E * (size_t)std::max(P.partc_elems, 1LL));
+    }
+    P.total = off;
+    return QMC_OK;
+}
+
+DevRule dev_rule(const Plan& P, const qmc_rule* r, char* ws) {
+    DevRule R{};
+    R.kind = P.kind; R.m = P.m; R.s = P.s; R.transform = P.transform; R.R = P.R;
+    R.gen = P.need_gen ? reinterpret_cast<const uint32_t*>(ws + P.off_gen) : r->d_gen;
+    R.shift = P.R == 0 ? nullptr : (P.need_shift ? reinterpret_cast<const uint32_t*>(ws + P.off_shift) : r->d_shift);
+    R.nlev = P.m + 1;
+    for (int I = 0; I <= P.m; ++I) { R.lev_tau[I] = P.lev_tau[I]; R.lev_col0[I] = P.lev_col0[I]; }
+    for (int I = 0; I <= P.m + 1; ++I) R.lev_tab[I] = P.lev_tab[I];
+    return R;
+}
+
+qmc_status upload_rule(const Plan& P, const qmc_rule* r, char* ws, cudaStream_t st) {
+    if (P.need_gen) {
+        const size_t words = (size_t)P.s * (P.kind == QMC_DIGITAL_NET ? P.m : 1);
+        QMC_CUDA(cudaMemcpyAsync(ws + P.off_gen, P.kind == QMC_DIGITAL_NET ? r->C : r->z, words * 4,
+                                 cudaMemcpyHostToDevice, st));
+    }
+    if (P.need_shift)
+        QMC_CUDA(cudaMemcpyAsync(ws + P.off_shift, r->shift, (size_t)P.R * P.s * 4, cudaMemcpyHostToDevice, st));
+    return QMC_OK;
+}
+
+template <class T>
+FineArgs<T> fine_args(const Plan& P, char* ws, const T* A, int ldA, const qmc_integrand* f) {
+    FineArgs<T> a{};
+    a.tab = reinterpret_cast<const T*>(ws + P.off_tab);
+    a.tab_stride = P.T_tot;
+    a.A = A; a.ldA = ldA;
+    a.tau = P.tau; a.tau_pad = P.tau_pad;
+    a.logn_root = P.m - P.JF;
+    for (int I = 0; I < 4; ++I) {
+        const bool in = I < P.JF;
+        a.lev_tau[I] = in ? P.lev_tau[I] : 0;
+        a.lev_col0[I] = in ? P.lev_col0[I] : 0;
+        a.lev_logn[I] = in ? P.m - I : 0;
+        a.lev_tab[I] = in ? P.lev_tab[I] : 0;
+    }
+    a.B = P.chf.count ? reinterpret_cast<const T*>(ws + P.off_B) : nullptr;
+    a.B_stride = P.B_per_shift;
+    a.chain = P.chf;
+    a.cr = P.cr; a.cg_count = P.cg_count; a.reff = P.reff; a.r0 = 0;
+    a.N = P.N;
+    a.rowpart = reinterpret_cast<T*>(ws + P.off_rowpart);
+    a.rowmax = reinterpret_cast<T*>(ws + P.off_rowmax);
+    a.P = nullptr;
+    a.c0 = f ? (T)f->params[0] : T(0);
+    a.c1 = f ? (T)f->params[1] : T(0);
+    a.tau_d = (double)P.tau;
+    a.K_d = f ? f->params[1] : 0.0;
+    a.fkind = P.fkind;
+    return a;
+}
+
+// forward through the fine kernel (fused or materialised); returns the A pointer/ld used
+template <class T>
+qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, const qmc_integrand* f, int mode,
+                       T* dP, T* rowf, double* est, cudaStream_t st, const T** Aused, int* ldA_used) {
+    qmc_status s0 = upload_rule(P, r, ws, st);
+    if (s0 != QMC_OK) return s0;
+    const DevRule R = dev_rule(P, r, ws);
+    const T* A = dA;
+    int ldA = P.tau;
+    if (P.need_pad) {
+        T* Ap = reinterpret_cast<T*>(ws + P.off_A);
+        QMC_LAUNCH(st, "k_pad_A", launch_pad_A<T>(dA, Ap, P.s, P.tau, P.tau_pad, st));
+        A = Ap;
+        ldA = P.tau_pad;
+    }
+    *Aused = A;
+    *ldA_used = ldA;
+    T* tab = reinterpret_cast<T*>(ws + P.off_tab);
+    QMC_LAUNCH(st, "k_table", launch_table<T>(R, tab, P.T_tot, P.reff, st));
+    if (P.chf.count)
+        QMC_LAUNCH(st, "k_coarse_fwd",
+                   launch_coarse_fwd<T>(tab, P.T_tot, A, ldA, P.tau_pad, P.chf, reinterpret_cast<T*>(ws + P.off_B),
+                                        P.B_per_shift, P.reff, st));
+    FineArgs<T> a = fine_args<T>(P, ws, A, ldA, f);
+    a.P = dP;
+    dim3 grid(P.root_blocks, P.cg_count, P.reff);
+    QMC_LAUNCH(st, mode == MODE_FUSED ? "k_fine_fwd" : "k_fine_fwd_materialize",
+               launch_fine_fwd<T>(a, P.shape, mode == MODE_FUSED ? P.fkind : 0, mode, grid, st));
+    if (mode == MODE_FUSED) {
+        double* rowsave = reinterpret_cast<double*>(ws + P.off_rowsave);
+        double* fpart = reinterpret_cast<double*>(ws + P.off_fpart);
+        QMC_LAUNCH(st, "k_rows_finalize",
+                   launch_rows_finalize<T>(a.rowpart, a.rowmax, P.cg_count, P.N, P.reff, P.fkind, (double)P.tau,
+                                           f->params[0], f->params[1], rowsave, rowf, fpart, P.nblk, st));
+        if (est) QMC_LAUNCH(st, "k_est_finalize", launch_est_finalize(fpart, P.nblk, P.reff, P.N, est, st));
+    }
+    return QMC_OK;
+}
+
+template <class T>
+qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, const qmc_integrand* f,
+                        const double* upstream, T* grad, bool reuse, cudaStream_t st) {
+    const T* A;
+    int ldA;
+    if (!reuse) {
+        qmc_status s0 = run_forward<T>(P, r, dA, ws, f, MODE_FUSED, nullptr, nullptr, nullptr, st, &A, &ldA);
+        if (s0 != QMC_OK) return s0;
+    } else {
+        A = P.need_pad ? reinterpret_cast<const T*>(ws + P.off_A) : dA;
+        ldA = P.need_pad ? P.tau_pad : P.tau;
+    }
+    const long long n_root = 1LL << (P.m - P.JF);
+    const long long root_stride = n_root * P.tau_pad;
+    T* Froot = reinterpret_cast<T*>(ws + P.off_F);
+    T* Fchain = Froot + (long long)P.reff * root_stride;
+    FineArgs<T> a = fine_args<T>(P, ws, A, ldA, f);
+    a.rowsave = reinterpret_cast<const double*>(ws + P.off_rowsave);
+    a.upstream = upstream;
+    a.coef_scale = 1.0 / ((double)P.reff * (double)P.N);
+    a.Froot = Froot;
+    a.gradpart = reinterpret_cast<T*>(ws + P.off_gradpart);
+    a.roots_per_cta = P.roots_per_cta;
+    a.groups = P.groups;
+    a.kf_actual = P.kf_width;
+    dim3 grid(P.groups, P.passes, P.reff);
+    QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.fkind, grid, st));
+    // fold the root gradients onto the distinct rows of each coarser block (ascending levels)
+    const T* src = Froot;
+    long long src_stride = root_stride;
+    int logn_src = P.m - P.JF;
+    for (int e = 0; e < P.chb.count; ++e) {
+        if (P.chb.lev[e] == P.JF) continue;
+        T* dst = Fchain + P.chb.boff[e];
+        QMC_LAUNCH(st, "k_fold",
+                   launch_fold<T>(src, src_stride, logn_src, dst, P.F_per_shift, P.chb.logn[e], P.tau_pad, P.reff, st));
+        src = dst;
+        src_stride = P.F_per_shift;
+        logn_src = P.chb.logn[e];
+    }
+    const T* tab = reinterpret_cast<const T*>(ws + P.off_tab);
+    T* partc = reinterpret_cast<T*>(ws + P.off_partc);
+    if (P.chb.count)
+        QMC_LAUNCH(st, "k_coarse_grad",
+                   launch_coarse_grad<T>(tab, P.T_tot, Froot, root_stride, Fchain, P.F_per_shift, P.JF, P.tau_pad,
+                                         P.chb, partc, P.reff, P.bwd_tiles, st));
+    int koff[4] = {0, 0, 0, 0}, col0[4] = {0, 0, 0, 0}, taul[4] = {0, 0, 0, 0};
+    const int kmax_s4[4] = {1, 2, 4, 8};
+    for (int I = 0, o = 0; I < P.JF; ++I) {
+        koff[I] = o;
+        col0[I] = P.lev_col0[I];
+        taul[I] = P.lev_tau[I];
+        o += P.shape == SHAPE_S4 ? kmax_s4[I] : 16;
+    }
+    QMC_LAUNCH(st, "k_grad_reduce",
+               launch_grad_reduce<T>(a.gradpart, P.reff * P.groups, std::max(P.kf_width, 1), koff, col0, taul, P.JF,
+                                     partc, P.chb, P.tau, P.tau_pad, P.s, grad, st));
+    return QMC_OK;
+}
+
+}  // namespace
+
+// =============================================================================================
+// C ABI
+// =============================================================================================
+extern "C" {
+
+const char* qmc_version(void) { return "qmc_gb300 0.1 (sm_103a)"; }
+const char* qmc_last_error(void) { return g_err.c_str(); }
+
+qmc_status qmc_validate_rule(const qmc_rule* rule) { return validate(rule); }
+
+qmc_status qmc_workspace_size(int op, const qmc_rule* rules, const uint32_t* tau, uint32_t nprob,
+                              const qmc_integrand* f, int precision, size_t* bytes) {
+    if (!bytes) return fail(QMC_ERR_INVALID_ARG, "bytes is NULL");
+    if (!rules) return fail(QMC_ERR_INVALID_ARG, "rules is NULL");
+    if (op < QMC_OP_GEN_POINTS || op > QMC_OP_INTEGRATE_BWD) return fail(QMC_ERR_INVALID_ARG, "op %d unknown", op);
+    if (nprob < 1) return fail(QMC_ERR_INVALID_ARG, "nprob must be >= 1");
+    if (op != QMC_OP_GEN_POINTS && !tau) return fail(QMC_ERR_INVALID_ARG, "tau is NULL");
+    size_t total = 0;
+    for (uint32_t p = 0; p < nprob; ++p) {
+        Plan P;
+        qmc_status st = make_plan(op, &rules[p], op == QMC_OP_GEN_POINTS ? 1u : tau[p], f ? &f[p] : nullptr, precision,
+                                  nullptr, P);
+        if (st != QMC_OK) return st;
+        total += align256(P.total);
+    }
+    *bytes = total;
+    return QMC_OK;
+}
+
+qmc_status qmc_gen_points(const qmc_rule* rule, uint32_t shift_idx, int layout, uint32_t* d_out, size_t out_words,
+                          void* d_ws, size_t ws_bytes, void* stream) {
+    Plan P;
+    qmc_status st = make_plan(QMC_OP_GEN_POINTS, rule, 1, nullptr, QMC_FP32, nullptr, P);
+    if (st != QMC_OK) return st;
+    if (!d_out) return fail(QMC_ERR_INVALID_ARG, "d_out is NULL");
+    if (layout != QMC_LAYOUT_FULL && layout != QMC_LAYOUT_DISTINCT)
+        return fail(QMC_ERR_INVALID_ARG, "layout %d unknown", layout);
+    if (P.R > 0 && shift_idx >= (uint32_t)P.R)
+        return fail(QMC_ERR_INVALID_ARG, "shift_idx=%u but R=%d", shift_idx, P.R);
+    const size_t need = layout == QMC_LAYOUT_FULL ? (size_t)P.N * P.s : (size_t)P.T_tot;
+    if (out_words < need) return fail(QMC_ERR_INVALID_ARG, "d_out holds %zu words, %zu needed", out_words, need);
+    if (P.total > 0 && (!d_ws || ws_bytes < P.total))
+        return fail(QMC_ERR_NO_MEMORY, "workspace of %zu bytes, %zu needed", ws_bytes, P.total);
+    cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = reinterpret_cast<char*>(d_ws);
+    st = upload_rule(P, rule, ws, st_);
+    if (st != QMC_OK) return st;
+    const DevRule R = dev_rule(P, rule, ws);
+    if (layout == QMC_LAYOUT_FULL) QMC_LAUNCH(st_, "k_points_full", launch_points_full(R, d_out, (int)shift_idx, st_));
+    else QMC_LAUNCH(st_, "k_points_distinct", launch_points_distinct(R, d_out, P.T_tot, (int)shift_idx, st_));
+    return QMC_OK;
+}
+
+qmc_status qmc_reduced_matmul(const qmc_rule* rule, const void* d_A, uint32_t tau, int precision, void* d_P,
+                              void* d_ws, size_t ws_bytes, void* stream) {
+    Plan P;
+    qmc_status st = make_plan(QMC_OP_REDUCED_MATMUL, rule, tau, nullptr, precision, d_A, P);
+    if (st != QMC_OK) return st;
+    if (!d_A || !d_P) return fail(QMC_ERR_INVALID_ARG, "d_A or d_P is NULL");
+    if (!d_ws || ws_bytes < P.total) return fail(QMC_ERR_NO_MEMORY, "workspace of %zu bytes, %zu needed", ws_bytes, P.total);
+    if (((uintptr_t)d_ws) % 256) return fail(QMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = reinterpret_cast<char*>(d_ws);
+    if (precision == QMC_FP64) {
+        const double* A; int ld;
+        return run_forward<double>(P, rule, (const double*)d_A, ws, nullptr, MODE_MATERIALIZE, (double*)d_P, nullptr,
+                                   nullptr, st_, &A, &ld);
+    }
+    const float* A; int ld;
+    return run_forward<float>(P, rule, (const float*)d_A, ws, nullptr, MODE_MATERIALIZE, (float*)d_P, nullptr,
+                              nullptr, st_, &A, &ld);
+}
+
+static qmc_status integrate_common(int op, const qmc_rule* rules, const void* const* d_A, const uint32_t* tau,
+                                   uint32_t nprob, const qmc_integrand* f, int precision, double* d_est,
+                                   void* const* d_rowf, const double* d_upstream, void* const* d_gradA,
+                                   uint32_t flags, void* d_ws, size_t ws_bytes, void* stream) {
+    if (!rules || !d_A || !tau || !f) return fail(QMC_ERR_INVALID_ARG, "rules, d_A, tau and f must be non-NULL");
+    if (nprob < 1) return fail(QMC_ERR_INVALID_ARG, "nprob must be >= 1");
+    if (op == QMC_OP_INTEGRATE && !d_est) return fail(QMC_ERR_INVALID_ARG, "d_est is NULL");
+    if (op == QMC_OP_INTEGRATE_BWD && (!d_upstream || !d_gradA))
+        return fail(QMC_ERR_INVALID_ARG, "d_upstream and d_gradA must be non-NULL");
+    if (flags & ~QMC_BWD_REUSE_FORWARD) return fail(QMC_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+    std::vector<Plan> plans(nprob);
+    size_t total = 0;
+    for (uint32_t p = 0; p < nprob; ++p) {
+        qmc_status st = make_plan(op, &rules[p], tau[p], &f[p], precision, d_A[p], plans[p]);
+        if (st != QMC_OK) return st;
+        if (!d_A[p]) return fail(QMC_ERR_INVALID_ARG, "d_A[%u] is NULL", p);
+        if (op == QMC_OP_INTEGRATE_BWD && !d_gradA[p]) return fail(QMC_ERR_INVALID_ARG, "d_gradA[%u] is NULL", p);
+        total += align256(plans[p].total);
+    }
+    if (!d_ws || ws_bytes < total) return fail(QMC_ERR_NO_MEMORY, "workspace of %zu bytes, %zu needed", ws_bytes, total);
+    if (((uintptr_t)d_ws) % 256) return fail(QMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = reinterpret_cast<char*>(d_ws);
+    size_t est_off = 0;
+    for (uint32_t p = 0; p < nprob; ++p) {
+        const Plan& P = plans[p];
+        qmc_status st;
+        if (op == QMC_OP_INTEGRATE) {
+            void* rowf = d_rowf ? d_rowf[p] : nullptr;
+            if (precision == QMC_FP64) {
+                const double* A; int ld;
+                st = run_forward<double>(P, &rules[p], (const double*)d_A[p], ws, &f[p], MODE_FUSED, nullptr,
+                                         (double*)rowf, d_est + est_off, st_, &A, &ld);
+            } else {
+                const float* A; int ld;
+                st = run_forward<float>(P, &rules[p], (const float*)d_A[p], ws, &f[p], MODE_FUSED, nullptr,
+                                        (float*)rowf, d_est + est_off, st_, &A, &ld);
+            }
+        } else {
+            const bool reuse = (flags & QMC_BWD_REUSE_FORWARD) != 0;
+            if (precision == QMC_FP64)
+                st = run_backward<double>(P, &rules[p], (const double*)d_A[p], ws, &f[p], d_upstream + p,
+                                          (double*)d_gradA[p], reuse, st_);
+            else
+                st = run_backward<float>(P, &rules[p], (const float*)d_A[p], ws, &f[p], d_upstream + p,
+                                         (float*)d_gradA[p], reuse, st_);
+        }
+        if (st != QMC_OK) return st;
+        est_off += (size_t)P.reff + 1;
+        ws += align256(P.total);
+    }
+    return QMC_OK;
+}
+
+qmc_status qmc_integrate(const qmc_rule* rules, const void* const* d_A, const uint32_t* tau, uint32_t nprob,
+                         const qmc_integrand* f, int precision, double* d_est, void* const* d_rowf, void* d_ws,
+                         size_t ws_bytes, void* stream) {
+    return integrate_common(QMC_OP_INTEGRATE, rules, d_A, tau, nprob, f, precision, d_est, d_rowf, nullptr, nullptr,
+                            0u, d_ws, ws_bytes, stream);
+}
+
+qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A, const uint32_t* tau, uint32_t nprob,
+                                  const qmc_integrand* f, int precision, const double* d_upstream,
+                                  void* const* d_gradA, uint32_t flags, void* d_ws, size_t ws_bytes, void* stream) {
+    return integrate_common(QMC_OP_INTEGRATE_BWD, rules, d_A, tau, nprob, f, precision, nullptr, nullptr, d_upstream,
+                            d_gradA, flags, d_ws, ws_bytes, stream);
+}
+
+qmc_status qmc_trace_enable(int on) {
+    TraceState& t = trace_state();
+    std::lock_guard<std::mutex> g(t.mu);
+    if (on) {
+        for (auto& r : t.recs) { t.pool.push_back(r.a); t.pool.push_back(r.b); }
+        t.recs.clear();
+        t.names.clear(); t.counts.clear(); t.ms.clear();
+    }
+    t.on = on != 0;
+    return QMC_OK;
+}
+
+qmc_status qmc_trace_collect(uint32_t* n_kernels) {
+    if (!n_kernels) return fail(QMC_ERR_INVALID_ARG, "n_kernels is NULL");
+    TraceState& t = trace_state();
+    std::lock_guard<std::mutex> g(t.mu);
+    std::map<std::string, std::pair<unsigned long long, double>> agg;
+    for (size_t i = 0; i < t.names.size(); ++i) agg[t.names[i]] = {t.counts[i], t.ms[i]};
+    for (auto& r : t.recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return fail(QMC_ERR_CUDA, "cudaEventSynchronize: %s", cudaGetErrorString(e));
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return fail(QMC_ERR_CUDA, "cudaEventElapsedTime: %s", cudaGetErrorString(e));
+        auto& slot = agg[r.name];
+        slot.first += 1;
+        slot.second += ms;
+        t.pool.push_back(r.a);
+        t.pool.push_back(r.b);
+    }
+    t.recs.clear();
+    t.names.clear(); t.counts.clear(); t.ms.clear();
+    for (auto& kv : agg) { t.names.push_back(kv.first); t.counts.push_back(kv.second.first); t.ms.push_back(kv.second.second); }
+    *n_kernels = (uint32_t)t.names.size();
+    return QMC_OK;
+}
+
+qmc_status qmc_trace_entry(uint32_t i, const char** name, uint64_t* launches, double* total_ms) {
+    TraceState& t = trace_state();
+    std::lock_guard<std::mutex> g(t.mu);
+    if (i >= t.names.size() || !name || !launches || !total_ms) return fail(QMC_ERR_INVALID_ARG, "bad trace entry query");
+    *name = t.names[i].c_str();
+    *launches = t.counts[i];
+    *total_ms = t.ms[i];
+    return QMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+// FP32 instantiations of the fine-band kernels (see qmc_fine.cuh).
+#include "qmc_fine.cuh"
+
+namespace qmc {
+
+template <class BandT, int CW>
+static cudaError_t fwd_f(const FineArgs<float>& a, int F, int mode, dim3 grid, cudaStream_t st) {
+    if (mode == MODE_MATERIALIZE) {
+        k_fine_fwd<float, BandT, F_NONE, MODE_MATERIALIZE, CW><<<grid, 128, 0, st>>>(a);
+        return cudaGetLastError();
+    }
+    switch (F) {
+        case F_LINEAR_MEAN: k_fine_fwd<float, BandT, F_LINEAR_MEAN, MODE_FUSED, CW><<<grid, 128, 0, st>>>(a); break;
+        case F_MEAN_COS: k_fine_fwd<float, BandT, F_MEAN_COS, MODE_FUSED, CW><<<grid, 128, 0, st>>>(a); break;
+        case F_CALL_MEAN_EXP: k_fine_fwd<float, BandT, F_CALL_MEAN_EXP, MODE_FUSED, CW><<<grid, 128, 0, st>>>(a); break;
+        case F_GAUSS_NORM2: k_fine_fwd<float, BandT, F_GAUSS_NORM2, MODE_FUSED, CW><<<grid, 128, 0, st>>>(a); break;
+        case F_PDE_INV_SQ: k_fine_fwd<float, BandT, F_PDE_INV_SQ, MODE_FUSED, CW><<<grid, 128, 0, st>>>(a); break;
+        case F_LOGSUMEXP: k_fine_fwd<float, BandT, F_LOGSUMEXP, MODE_FUSED, CW><<<grid, 128, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class BandT, int CW>
+static cudaError_t bwd_f(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
+    switch (F) {
+        case F_LINEAR_MEAN: k_fine_bwd<float, BandT, F_LINEAR_MEAN, CW><<<grid, 256, 0, st>>>(a); break;
+        case F_MEAN_COS: k_fine_bwd<float, BandT, F_MEAN_COS, CW><<<grid, 256, 0, st>>>(a); break;
+        case F_CALL_MEAN_EXP: k_fine_bwd<float, BandT, F_CALL_MEAN_EXP, CW><<<grid, 256, 0, st>>>(a); break;
+        case F_GAUSS_NORM2: k_fine_bwd<float, BandT, F_GAUSS_NORM2, CW><<<grid, 256, 0, st>>>(a); break;
+        case F_PDE_INV_SQ: k_fine_bwd<float, BandT, F_PDE_INV_SQ, CW><<<grid, 256, 0, st>>>(a); break;
+        case F_LOGSUMEXP: k_fine_bwd<float, BandT, F_LOGSUMEXP, CW><<<grid, 256, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_fine_fwd<float>(const FineArgs<float>& a, int shape, int F, int mode, dim3 grid, cudaStream_t st) {
+    switch (shape) {
+        case SHAPE_S4: return fwd_f<BandS4, 4>(a, F, mode, grid, st);
+        case SHAPE_S1: return fwd_f<BandS1, 4>(a, F, mode, grid, st);
+        case SHAPE_S0: return fwd_f<BandS0, 4>(a, F, mode, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_fine_bwd<float>(const FineArgs<float>& a, int shape, int F, dim3 grid, cudaStream_t st) {
+    switch (shape) {
+        case SHAPE_S4: return bwd_f<BandS4, 4>(a, F, grid, st);
+        case SHAPE_S1: return bwd_f<BandS1, 2>(a, F, grid, st);
+        case SHAPE_S0: return bwd_f<BandS0, 4>(a, F, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace qmc

@@ -1,0 +1,155 @@
+"""C ABI checks that need no GPU: the library builds and loads, exports every
+function include/qmc.h declares, and rejects invalid arguments (with an error
+status and a message, never an abort) before any CUDA call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2305_11645_gb300 import _lib as L
+from paper_2305_11645_gb300 import build as B
+from paper_2305_11645_gb300 import inputs as I
+from paper_2305_11645_gb300.api import Integrand, Rule
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "qmc.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(qmc_\w+)\s*\(", text, flags=re.M)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert set(names) == set(L.EXPORTS), names
+    for n in names:
+        assert hasattr(lib, n)
+    assert lib.qmc_version().decode().startswith("qmc_gb300")
+
+
+def status(lib, rule):
+    return lib.qmc_validate_rule(ctypes.byref(rule.struct()))
+
+
+def test_valid_rules_pass(lib):
+    for kind in (I.LATTICE, I.DIGITAL_NET):
+        for seed in range(5):
+            p = I.random_problem(seed, kind=kind)
+            assert status(lib, Rule.from_problem(p)) == L.QMC_OK, lib.qmc_last_error()
+    for p in (I.c1(), I.c2(m=8, s=64)):
+        assert status(lib, Rule.from_problem(p)) == L.QMC_OK
+
+
+def test_invalid_base_and_sizes(lib):
+    p = I.random_problem(1)
+    r = Rule.from_problem(p)
+    r.b = 3
+    assert status(lib, r) == L.QMC_ERR_UNSUPPORTED
+    r.b = 1
+    assert status(lib, r) == L.QMC_ERR_INVALID_ARG
+    r = Rule.from_problem(p)
+    r.m = 0
+    assert status(lib, r) == L.QMC_ERR_INVALID_ARG
+    r.m = 31
+    assert status(lib, r) == L.QMC_ERR_UNSUPPORTED
+    assert "m=31" in lib.qmc_last_error().decode()
+
+
+def test_nonmonotone_weights(lib):
+    r = Rule(I.LATTICE, 5, [0, 2, 1], z=[1, 1, 1])
+    assert status(lib, r) == L.QMC_ERR_INVALID_ARG
+    assert "nondecreasing" in lib.qmc_last_error().decode()
+
+
+@pytest.mark.parametrize("z", [[2, 1, 1], [1, 9, 1], [1, 0, 1], [1, 1, 3]])
+def test_z_outside_units(lib, z):
+    # m=4, w=(0,1,4): z_0 in U_16 (odd < 16), z_1 in U_8 (odd < 8), z_2 in U_1 = {1}
+    assert status(lib, Rule(I.LATTICE, 4, [0, 1, 4], z=z)) == L.QMC_ERR_INVALID_ARG
+
+
+def test_singular_and_nonperiodic_nets(lib):
+    m = 3
+    # singular leading block (two equal columns)
+    C = np.array([[4, 4, 1]], dtype=np.uint32)
+    assert status(lib, Rule(I.DIGITAL_NET, m, [0], C=C)) == L.QMC_ERR_INVALID_ARG
+    assert "singular" in lib.qmc_last_error().decode()
+    # w=1 but column 3 (beyond m-w) nonzero after row reduction: not periodic
+    C = np.array([[4, 2, 4]], dtype=np.uint32)
+    assert status(lib, Rule(I.DIGITAL_NET, m, [1], C=C)) == L.QMC_ERR_UNSUPPORTED
+    # bits above row 1
+    C = np.array([[8, 2, 1]], dtype=np.uint32)
+    assert status(lib, Rule(I.DIGITAL_NET, m, [0], C=C)) == L.QMC_ERR_INVALID_ARG
+    # rows beyond m-w are zeroed by the library (eq. reduced_genmat_net2): accepted
+    C = np.array([[4 | 1, 2, 0]], dtype=np.uint32)
+    assert status(lib, Rule(I.DIGITAL_NET, m, [1], C=C)) == L.QMC_OK
+
+
+def test_null_pointers_and_shift_rules(lib):
+    r = Rule(I.LATTICE, 3, [0, 1], z=[1, 1])
+    st = r.struct()
+    st.z = None
+    assert lib.qmc_validate_rule(ctypes.byref(st)) == L.QMC_ERR_INVALID_ARG
+    st = r.struct()
+    st.w = None
+    assert lib.qmc_validate_rule(ctypes.byref(st)) == L.QMC_ERR_INVALID_ARG
+    assert lib.qmc_validate_rule(None) == L.QMC_ERR_INVALID_ARG
+    st = r.struct()
+    st.R = 2
+    assert lib.qmc_validate_rule(ctypes.byref(st)) == L.QMC_ERR_INVALID_ARG
+    r = Rule(I.LATTICE, 3, [0, 1], z=[1, 1], transform=I.T_INV_NORMAL)
+    assert status(lib, r) == L.QMC_ERR_INVALID_ARG
+    assert "shift" in lib.qmc_last_error().decode()
+
+
+def ws_size(lib, op, rule, tau, f, prec):
+    out = ctypes.c_size_t(0)
+    fa = None if f is None else ctypes.byref(f.struct())
+    st = lib.qmc_workspace_size(op, ctypes.byref(rule.struct()), ctypes.byref(ctypes.c_uint32(tau)), 1, fa, prec,
+                                ctypes.byref(out))
+    return st, out.value
+
+
+def test_workspace_size_and_its_errors(lib):
+    p = I.c2(m=10, s=64)
+    r = Rule.from_problem(p)
+    f = Integrand(I.F_CALL_MEAN_EXP, (0.2, 1.0))
+    st, fwd = ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)
+    assert st == L.QMC_OK and fwd > 0
+    st, bwd = ws_size(lib, L.QMC_OP_INTEGRATE_BWD, r, 64, f, L.QMC_FP32)
+    assert st == L.QMC_OK and bwd > fwd
+    st, _ = ws_size(lib, L.QMC_OP_INTEGRATE, r, 0, f, L.QMC_FP32)
+    assert st == L.QMC_ERR_INVALID_ARG
+    st, _ = ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, Integrand(I.F_NONE), L.QMC_FP32)
+    assert st == L.QMC_ERR_INVALID_ARG
+    st, _ = ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_SPLIT)
+    assert st == L.QMC_ERR_UNSUPPORTED
+    st, _ = ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, 9)
+    assert st == L.QMC_ERR_INVALID_ARG
+
+
+def test_too_small_workspace_rejected_before_any_cuda_call(lib):
+    p = I.random_problem(2, f_kind=I.F_MEAN_COS)
+    r = Rule.from_problem(p)
+    f = Integrand(I.F_MEAN_COS)
+    fake = ctypes.c_void_p(0x1000)          # never dereferenced: the size check fails first
+    st = lib.qmc_integrate(ctypes.byref(r.struct()), ctypes.byref(fake), ctypes.byref(ctypes.c_uint32(p.tau)), 1,
+                           ctypes.byref(f.struct()), L.QMC_FP64, fake, None, None, 0, None)
+    assert st == L.QMC_ERR_NO_MEMORY
+    st = lib.qmc_reduced_matmul(ctypes.byref(r.struct()), fake, p.tau, L.QMC_FP64, fake, None, 0, None)
+    assert st == L.QMC_ERR_NO_MEMORY
+    st = lib.qmc_gen_points(ctypes.byref(r.struct()), 0, L.QMC_LAYOUT_FULL, fake, 1, None, 0, None)
+    assert st == L.QMC_ERR_INVALID_ARG      # output capacity checked
+    st = lib.qmc_integrate_backward(ctypes.byref(r.struct()), ctypes.byref(fake),
+                                    ctypes.byref(ctypes.c_uint32(p.tau)), 1, ctypes.byref(f.struct()), L.QMC_FP64,
+                                    fake, ctypes.byref(fake), 7, fake, 1 << 30, None)
+    assert st == L.QMC_ERR_INVALID_ARG      # unknown flags
