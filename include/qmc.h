@@ -196,6 +196,25 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
                                   void* d_ws, size_t ws_bytes, void* stream);
 
 /*
+ * qmc_integrate_noalloc: qmc_integrate for one problem without a caller workspace and without
+ *  allocating any device memory.  The paper has no counterpart; this entry point serves callers
+ *  that cannot allocate device memory when they call the library (a framework that forbids
+ *  cudaMalloc while it captures a stream, a real-time or embedded host that reserves all device
+ *  memory up front, a foreign-function caller with no device allocator of its own).
+ *  Scratch space is a static 32 MiB array inside the library (present on every GPU that loads
+ *  the library, until the process exits).  Problems whose qmc_workspace_size(QMC_OP_INTEGRATE)
+ *  exceeds it are rejected with QMC_ERR_NO_MEMORY before any work is enqueued.
+ *  Arguments are those of qmc_integrate for nprob = 1, without d_rowf: d_A DEVICE s x tau,
+ *  d_est DEVICE double[R_eff + 1].  The first call on each device looks up the array's device
+ *  address (cudaGetSymbolAddress); make that first call before any stream capture.  All calls
+ *  share the one array: calls whose work overlaps on the GPU (other streams, other host threads)
+ *  race on it and must be serialised by the caller.  The array keeps the last call's contents;
+ *  every value a call reads from it is written earlier in the same call.
+ */
+qmc_status qmc_integrate_noalloc(const qmc_rule* rule, const void* d_A, uint32_t tau,
+                                 const qmc_integrand* f, int precision, double* d_est, void* stream);
+
+/*
  * Kernel tracing (library instrumentation; the paper has no counterpart).
  *  qmc_trace_enable(1) clears earlier records and brackets every kernel the library launches from
  *  then on with two CUDA events recorded on the launch stream; qmc_trace_enable(0) stops recording.

@@ -18,8 +18,8 @@ QMC_OP_GEN_POINTS, QMC_OP_REDUCED_MATMUL, QMC_OP_INTEGRATE, QMC_OP_INTEGRATE_BWD
 QMC_BWD_REUSE_FORWARD = 1
 
 EXPORTS = ["qmc_version", "qmc_last_error", "qmc_validate_rule", "qmc_workspace_size", "qmc_gen_points",
-           "qmc_reduced_matmul", "qmc_integrate", "qmc_integrate_backward", "qmc_trace_enable",
-           "qmc_trace_collect", "qmc_trace_entry"]
+           "qmc_reduced_matmul", "qmc_integrate", "qmc_integrate_backward", "qmc_integrate_noalloc",
+           "qmc_trace_enable", "qmc_trace_collect", "qmc_trace_entry"]
 
 
 class QmcRule(ctypes.Structure):
@@ -68,6 +68,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         lib.qmc_integrate_backward.argtypes = [POINTER(QmcRule), POINTER(c_void_p), POINTER(c_uint32), c_uint32,
                                                POINTER(QmcIntegrand), c_int, c_void_p, POINTER(c_void_p), c_uint32,
                                                c_void_p, c_size_t, c_void_p]
+        lib.qmc_integrate_noalloc.argtypes = [POINTER(QmcRule), c_void_p, c_uint32, POINTER(QmcIntegrand), c_int,
+                                              c_void_p, c_void_p]
         lib.qmc_trace_enable.argtypes = [c_int]
         lib.qmc_trace_collect.argtypes = [POINTER(c_uint32)]
         lib.qmc_trace_entry.argtypes = [c_uint32, POINTER(ctypes.c_char_p), POINTER(ctypes.c_uint64),

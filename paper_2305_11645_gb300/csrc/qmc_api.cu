@@ -648,6 +648,82 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
                             d_gradA, flags, d_ws, ws_bytes, stream);
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free variant of qmc_integrate.
+//
+// Some callers cannot allocate device memory when they call the library: code
+// that runs while a stream is being captured by a framework that forbids
+// cudaMalloc during capture, real-time or embedded hosts that reserve all
+// device memory up front, and foreign-function callers that have no device
+// allocator of their own to make a workspace with.  For them the fused forward
+// runs on a fixed scratch array that is part of the library image: it exists
+// on every GPU that loads the library, from module load until the process
+// exits, whether or not this entry point is ever called.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;   // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address must come from
+// cudaGetSymbolAddress, called once per device with that device current.
+qmc_status noalloc_scratch(void** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(QMC_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(QMC_ERR_CUDA, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return fail(QMC_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return QMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+qmc_status qmc_integrate_noalloc(const qmc_rule* rule, const void* d_A, uint32_t tau, const qmc_integrand* f,
+                                 int precision, double* d_est, void* stream) {
+    if (!d_A || !d_est || !f) return fail(QMC_ERR_INVALID_ARG, "d_A, d_est and f must be non-NULL");
+    Plan P;
+    qmc_status st = make_plan(QMC_OP_INTEGRATE, rule, tau, f, precision, d_A, P);
+    if (st != QMC_OK) return st;
+    if (P.total > kNoAllocScratchBytes)
+        return fail(QMC_ERR_NO_MEMORY,
+                    "qmc_integrate_noalloc: this problem needs %zu bytes of scratch, the static array holds %zu "
+                    "(use qmc_integrate with a caller workspace)",
+                    P.total, kNoAllocScratchBytes);
+    void* scratch = nullptr;
+    st = noalloc_scratch(&scratch);
+    if (st != QMC_OK) return st;
+    // Every area the forward pass reads is written earlier in the same call, so the
+    // array needs no clearing between calls.
+    char* ws = reinterpret_cast<char*>(scratch);
+    cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
+    if (precision == QMC_FP64) {
+        const double* A;
+        int ld;
+        return run_forward<double>(P, rule, (const double*)d_A, ws, f, MODE_FUSED, nullptr, nullptr, d_est, st_, &A,
+                                   &ld);
+    }
+    const float* A;
+    int ld;
+    return run_forward<float>(P, rule, (const float*)d_A, ws, f, MODE_FUSED, nullptr, nullptr, d_est, st_, &A, &ld);
+}
+
 qmc_status qmc_trace_enable(int on) {
     TraceState& t = trace_state();
     std::lock_guard<std::mutex> g(t.mu);
