@@ -30,6 +30,10 @@ sys.path.insert(0, ROOT)
 METRIC = "x_k^T A products/sec (N*tau/s) vs dense X*A on same GB300, at stated rel. error"
 L2_FLUSH_BYTES = 512 << 20        # > 129 MB L2
 SM_COUNT = 152
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on this workload, from the
+# ncu capture summarised in profiles/c2_step_kernels_full.md (cold cache); a kernel missing here
+# has changed since its counters were taken and reports traffic null
+TRAFFIC_BYTES = {"k_fine_bwd": 10.0e6}
 
 
 def parse():
@@ -207,22 +211,19 @@ def run_ours(args, dist, rank, world):
     rule = api.Rule.from_problem(p)
     f = api.Integrand(p.f_kind, p.f_params)
     A = torch.from_numpy(p.A).to(dev)
-    up = torch.ones(1, dtype=torch.float64, device=dev)
-    nbytes = api.workspace_size(L.QMC_OP_INTEGRATE_BWD, [rule], [p.tau], [f], L.QMC_FP32)
-    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        est = api.integrate(rule, A, f, ws=ws)
-        grad = api.integrate_backward(rule, A, f, up, ws=ws, reuse_forward=True)[0]
-        return est, grad
+    # the step as a user runs it repeatedly: one CUDA graph of the forward and backward launches
+    integ = api.Integrator(rule, A, f, backward=True, graph=True)
+    eager = api.Integrator(rule, A, f, backward=True, graph=False)
+    step = integ.run
 
     for _ in range(args.warmup):
         step()
+        eager.run()
     torch.cuda.synchronize()
 
-    def timed(fn, trace=False):
+    def timed(fn, trace=False, prequeue=False):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier(dist)
         torch.cuda.synchronize()
@@ -230,6 +231,8 @@ def run_ours(args, dist, rank, world):
             L.trace_enable(True)
         for a, b in evs:
             flush.zero_()
+            if prequeue:
+                torch.cuda._sleep(3_000_000)    # the host queues the whole step before the GPU reaches it
             a.record(stream)
             fn()
             b.record(stream)
@@ -250,9 +253,11 @@ def run_ours(args, dist, rank, world):
     ms_max = max_over_ranks(dist, ms)
     outputs = p.N * p.tau * p.R_eff
     value = world * outputs / (ms_max / 1e3)
+    eager_ms = statistics.mean(timed(eager.run)[0])
 
-    # second pass of the same steps with the library's per-kernel events (roofline)
-    ttimes, kern = timed(step, trace=True)
+    # the same steps launched eagerly with the library's per-kernel events, the stream pre-queued
+    # so each pair of events brackets device time only (roofline of the dominant kernel)
+    ttimes, kern = timed(eager.run, trace=True, prequeue=True)
     launches = sum(c for c, _ in kern.values())
     top = max(kern.items(), key=lambda kv: kv[1][1])
     mp, peak_src = peaks()
@@ -264,7 +269,7 @@ def run_ours(args, dist, rank, world):
     else:
         w32, wmu = fine_fwd_work(p)
     roof = alu_roofline(w32, wmu, per_launch, clk)
-    roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": None,
+    roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": TRAFFIC_BYTES.get(name),
                  "peak_source": f"derived from {SM_COUNT} SMs x pipe lanes x median SM clock {clk:.0f} MHz "
                                 f"(sampled during the timed region)"})
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in sorted(kern.items())}
@@ -273,12 +278,10 @@ def run_ours(args, dist, rank, world):
     A_host = torch.from_numpy(p.A).pin_memory()
     est_host = torch.empty(p.R_eff + 1, dtype=torch.float64).pin_memory()
     grad_host = torch.empty(p.A.shape, dtype=torch.float32).pin_memory()
-    A_dev = torch.empty_like(A)
 
     def e2e_step():
-        A_dev.copy_(A_host, non_blocking=True)
-        est = api.integrate(rule, A_dev, f, ws=ws)
-        grad = api.integrate_backward(rule, A_dev, f, up, ws=ws, reuse_forward=True)[0]
+        integ.A.copy_(A_host, non_blocking=True)
+        est, grad = integ.run()
         est_host.copy_(est, non_blocking=True)
         grad_host.copy_(grad, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
@@ -298,9 +301,11 @@ def run_ours(args, dist, rank, world):
                                      "s=tau=512, w_j=min(floor(log2(j+1)),10), 1 odd 32-bit shift, inverse-normal "
                                      "transform, A=L^T (exp covariance), f=max(mean exp(0.2y)-1,0)",
                          "N": p.N, "s": p.s, "tau": p.tau, "R": p.R_eff, "precision": "fp32",
-                         "step": "qmc_integrate + qmc_integrate_backward (reuse forward workspace)",
+                         "step": "qmc_integrate + qmc_integrate_backward (reuse forward workspace), "
+                                 "replayed as one CUDA graph (api.Integrator)",
                          "l2": "flushed before every timed step (512 MiB write, untimed)",
                          "parallelism": "replicas" if world > 1 else "single"},
+              "eager_ms_per_step": eager_ms,
               "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clock_info,
               "kernels": kernels, "peaks": peak_src}
 

@@ -201,7 +201,7 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
  *  that cannot allocate device memory when they call the library (a framework that forbids
  *  cudaMalloc while it captures a stream, a real-time or embedded host that reserves all device
  *  memory up front, a foreign-function caller with no device allocator of its own).
- *  Scratch space is a static 32 MiB array inside the library (present on every GPU that loads
+ *  Scratch space is a static 64 MiB array inside the library (present on every GPU that loads
  *  the library, until the process exits).  Problems whose qmc_workspace_size(QMC_OP_INTEGRATE)
  *  exceeds it are rejected with QMC_ERR_NO_MEMORY before any work is enqueued.
  *  Arguments are those of qmc_integrate for nprob = 1, without d_rowf: d_A DEVICE s x tau,

@@ -233,3 +233,61 @@ class QMCEstimate(torch.autograd.Function):
 
 def qmc_estimate(A: torch.Tensor, rule: Rule, f: Integrand) -> torch.Tensor:
     return QMCEstimate.apply(A, rule, f)
+
+
+class Integrator:
+    """A fixed problem (rule, A's shape and dtype, f) evaluated repeatedly: the estimate and,
+    with ``backward=True``, dQ/dA, through one CUDA graph of the library's launches.
+
+    The C structures, the workspace and the input/output buffers are built once; ``A`` is a
+    static device tensor the caller overwrites (``integrator.A.copy_(...)``) before each
+    ``run()``, which replays the graph on the current stream and returns the static outputs
+    ``(est, grad)`` -- est holds the R_eff per-shift estimates and their mean.
+    """
+
+    def __init__(self, rule: Rule, A: torch.Tensor, f: Integrand, backward: bool = True, graph: bool = True):
+        self.rule, self.f, self.backward = rule, f, backward
+        self.device = A.device
+        self.A = A.detach().contiguous().clone()
+        self.prec = _precision(self.A)
+        op = L.QMC_OP_INTEGRATE_BWD if backward else L.QMC_OP_INTEGRATE
+        self.ws = torch.empty(max(workspace_size(op, [rule], [self.A.shape[1]], [f], self.prec), 256),
+                              dtype=torch.uint8, device=self.device)
+        self.est = torch.empty(rule.R_eff + 1, dtype=torch.float64, device=self.device)
+        self.grad = torch.empty_like(self.A)
+        self.upstream = torch.ones(1, dtype=torch.float64, device=self.device)
+        self._rs = L.QmcRule * 1
+        self._r = self._rs(rule.struct(self.device))
+        self._ap = (ctypes.c_void_p * 1)(self.A.data_ptr())
+        self._ts = (ctypes.c_uint32 * 1)(self.A.shape[1])
+        self._fa = (L.QmcIntegrand * 1)(f.struct())
+        self._gp = (ctypes.c_void_p * 1)(self.grad.data_ptr())
+        self._lib = L.load()
+        self.graph = None
+        if graph:
+            self._eager(torch.cuda.current_stream(self.device))          # loads modules, checks arguments
+            torch.cuda.synchronize(self.device)
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream(self.device)
+            s.wait_stream(torch.cuda.current_stream(self.device))
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    self._eager(s)
+            torch.cuda.current_stream(self.device).wait_stream(s)
+            self.graph = g
+
+    def _eager(self, stream) -> None:
+        st = ctypes.c_void_p(stream.cuda_stream)
+        L.check(self._lib.qmc_integrate(self._r, self._ap, self._ts, 1, self._fa, self.prec, self.est.data_ptr(),
+                                        None, self.ws.data_ptr(), self.ws.numel(), st))
+        if self.backward:
+            L.check(self._lib.qmc_integrate_backward(self._r, self._ap, self._ts, 1, self._fa, self.prec,
+                                                     self.upstream.data_ptr(), self._gp, L.QMC_BWD_REUSE_FORWARD,
+                                                     self.ws.data_ptr(), self.ws.numel(), st))
+
+    def run(self):
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._eager(torch.cuda.current_stream(self.device))
+        return self.est, self.grad

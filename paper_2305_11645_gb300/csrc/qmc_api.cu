@@ -183,14 +183,17 @@ struct Plan {
     long long T_tot = 0;
     int tau = 0, tau_pad = 0, precision = 0, elt = 4, fkind = 0;
     int shape = SHAPE_S0, JF = 0, kf_width = 0, cw_bwd = 4;
+    bool exact = false;            // fine band levels hold exactly their maximum column counts
     Chain chf{}, chb{};
-    long long B_per_shift = 0, F_per_shift = 0, partc_elems = 0;
+    long long B_per_shift = 0, S_per_shift = 0, partc_elems = 0, Fchain_per_shift = 0;
+    FoldLevels fold{};
     int root_blocks = 0, cg_count = 1, cr = 0;
     int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
     int nblk = 0;
     bool need_gen = false, need_shift = false, need_pad = false;
-    size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_rowpart = 0, off_rowmax = 0,
-           off_rowsave = 0, off_fpart = 0, off_F = 0, off_gradpart = 0, off_partc = 0, total = 0;
+    size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
+           off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
+           total = 0;
 };
 
 qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integrand* f, int precision,
@@ -252,29 +255,45 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         return true;
     };
     const int k4[4] = {1, 2, 4, 8}, k1[1] = {16};
-    if (precision == QMC_FP32 && fits(4, k4)) { P.shape = SHAPE_S4; P.JF = 4; P.kf_width = 15; P.cw_bwd = 4; }
+    if (precision == QMC_FP32 && fits(4, k4)) {
+        P.shape = SHAPE_S4; P.JF = 4; P.kf_width = 15; P.cw_bwd = 2;
+        P.exact = P.lev_tau[0] == 1 && P.lev_tau[1] == 2 && P.lev_tau[2] == 4 && P.lev_tau[3] == 8;
+    }
     else if (fits(1, k1)) { P.shape = SHAPE_S1; P.JF = 1; P.kf_width = 16; P.cw_bwd = precision == QMC_FP64 ? 1 : 2; }
     else { P.shape = SHAPE_S0; P.JF = 0; P.kf_width = 0; P.cw_bwd = precision == QMC_FP64 ? 2 : 4; }
     const int logn_root = P.m - P.JF;
     const long long n_root = 1LL << logn_root;
 
-    // coarse chain: levels JF..m with columns
+    // coarse chain: levels JF..m with columns.  A level with many columns (a long K for its few
+    // distinct rows) is cut into up to 8 column ranges, each its own entry with its own block
+    // product, so that the levels run in parallel; the chain sum adds the entries' products.
+    int nsplit_tot = 0;
+    for (int I = P.JF; I <= P.m; ++I)
+        if (P.lev_tau[I] > 0) nsplit_tot += std::min(8, (P.lev_tau[I] + 31) / 32);
+    const bool cut = nsplit_tot <= kMaxChain;
     P.chf.count = 0;
     long long boff = 0;
     int tiles = 0;
     for (int I = P.JF; I <= P.m; ++I) {
         if (P.lev_tau[I] == 0) continue;
-        const int e = P.chf.count++;
-        P.chf.lev[e] = I; P.chf.logn[e] = P.m - I; P.chf.tau[e] = P.lev_tau[I]; P.chf.col0[e] = P.lev_col0[I];
-        P.chf.tab[e] = P.lev_tab[I];
-        P.chf.boff[e] = boff;
-        boff += (1LL << (P.m - I)) * P.tau_pad;
-        P.chf.tile0[e] = tiles;
-        tiles += (int)(((1LL << (P.m - I)) + 63) / 64);
-        P.chf.split[e] = 1; P.chf.poff[e] = 0;
+        const int parts = cut ? std::min(8, (P.lev_tau[I] + 31) / 32) : 1;
+        const int width = (P.lev_tau[I] + parts - 1) / parts;
+        for (int pc = 0; pc < parts; ++pc) {
+            const int c0 = pc * width, cw = std::min(width, P.lev_tau[I] - c0);
+            if (cw <= 0) break;
+            const int e = P.chf.count++;
+            P.chf.lev[e] = I; P.chf.logn[e] = P.m - I; P.chf.tau[e] = cw; P.chf.col0[e] = P.lev_col0[I] + c0;
+            P.chf.tab[e] = P.lev_tab[I] + ((long long)c0 << (P.m - I));
+            P.chf.boff[e] = boff;
+            boff += (1LL << (P.m - I)) * P.tau_pad;
+            P.chf.tile0[e] = tiles;
+            tiles += (int)(((1LL << (P.m - I)) + 63) / 64);
+            P.chf.split[e] = 1; P.chf.poff[e] = 0;
+        }
     }
     P.chf.tile0[P.chf.count] = tiles;
     P.B_per_shift = boff;
+    P.S_per_shift = P.chf.count ? n_root * P.tau_pad : 0;
 
     // fine forward grid: 128 roots per CTA, column groups to fill the GPU
     P.root_blocks = (int)((n_root + 127) / 128);
@@ -282,8 +301,9 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         const long long want = 4LL * 152;
         long long cg = (want + (long long)P.root_blocks * P.reff - 1) / ((long long)P.root_blocks * P.reff);
         cg = std::max(1LL, std::min(cg, (long long)(P.tau_pad + 15) / 16));
+        cg = std::max(cg, (long long)(P.tau_pad + kMaxCR - 1) / kMaxCR);
         int cr = (int)((P.tau_pad + cg - 1) / cg);
-        cr = (cr + 15) / 16 * 16;
+        cr = std::min((cr + 15) / 16 * 16, kMaxCR);
         P.cr = cr;
         P.cg_count = (P.tau_pad + cr - 1) / cr;
     }
@@ -299,26 +319,72 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         rpc = std::max(8LL, (rpc + 7) / 8 * 8);
         P.roots_per_cta = (int)rpc;
         P.groups = (int)((n_root + rpc - 1) / rpc);
-        // F area: root folds, then the chain levels above the root
+        // Root gradients are folded level by level (k_fold_tree) up to I_mat = the highest coarse
+        // level below m within kFoldDepth of the root; F of every coarse level up to I_mat is
+        // materialised, the levels above it (the constant level m) fold from F_{I_mat} on the fly.
         P.chb = P.chf;
-        long long foff = 0;
+        const int max_depth = precision == QMC_FP64 ? 5 : 6;
+        int I_mat = P.JF;
+        for (int e = 0; e < P.chb.count; ++e)
+            if (P.chb.lev[e] < P.m && P.chb.lev[e] - P.JF <= max_depth) I_mat = std::max(I_mat, P.chb.lev[e]);
+        P.fold.depth = I_mat - P.JF;
+        P.fold.logn_top = P.m - I_mat;
+        for (int d = 0; d < 8; ++d) { P.fold.want[d] = 0; P.fold.off[d] = 0; }
+        long long fchain = 0;
+        for (int e = 0; e < P.chb.count; ++e) {
+            const int I = P.chb.lev[e];
+            if (I > P.JF && I <= I_mat) {
+                if (!P.fold.want[I - P.JF]) {        // one folded buffer per level, shared by its entries
+                    P.fold.want[I - P.JF] = 1;
+                    P.fold.off[I - P.JF] = fchain;
+                    fchain += (1LL << (P.m - I)) * P.tau_pad;
+                }
+                P.chb.fsel[e] = 1; P.chb.foff[e] = P.fold.off[I - P.JF]; P.chb.flog[e] = 0;
+            }
+        }
+        for (int e = 0; e < P.chb.count; ++e) {
+            const int I = P.chb.lev[e];
+            if (I == P.JF) { P.chb.fsel[e] = 0; P.chb.foff[e] = 0; P.chb.flog[e] = 0; }
+            else if (I > I_mat) {
+                P.chb.fsel[e] = I_mat > P.JF ? 1 : 0;
+                P.chb.foff[e] = I_mat > P.JF ? P.fold.off[I_mat - P.JF] : 0;
+                P.chb.flog[e] = I - I_mat;
+            }
+        }
+        // a level above JF that has no columns but is the fold top still needs its rows
+        if (I_mat > P.JF && !P.fold.want[I_mat - P.JF]) {
+            P.fold.want[I_mat - P.JF] = 1;
+            P.fold.off[I_mat - P.JF] = fchain;
+            fchain += (1LL << (P.m - I_mat)) * P.tau_pad;
+        }
+        P.Fchain_per_shift = fchain;
+        // coarse gradient GEMMs: K = R n_e rows; splits balance the work (16 multiply-adds plus
+        // 4 fold loads per K row and column) over ~4 CTAs per SM
+        const int ttiles = (P.tau_pad + 127) / 128;
+        double wtot = 0.0;
+        for (int e = 0; e < P.chb.count; ++e) {
+            const long long K = (long long)P.reff << (P.m - P.chb.lev[e]);
+            const double fold = (double)(1LL << P.chb.flog[e]);
+            wtot += (double)((P.chb.tau[e] + 15) / 16) * ttiles * K * (16.0 + 4.0 * fold);
+        }
         long long poff = 0;
         int bt = 0;
         for (int e = 0; e < P.chb.count; ++e) {
-            const int I = P.chb.lev[e];
-            if (I == P.JF) P.chb.boff[e] = 0;
-            else { P.chb.boff[e] = foff; foff += (1LL << (P.m - I)) * P.tau_pad; }
-            const long long K = (long long)P.reff << (P.m - I);
-            const int split = (int)std::max(1LL, std::min(64LL, K / 1024));
-            P.chb.split[e] = split;
+            const long long K = (long long)P.reff << (P.m - P.chb.lev[e]);
+            const double fold = (double)(1LL << P.chb.flog[e]);
+            const int jt = (P.chb.tau[e] + 15) / 16;
+            const double we = (double)jt * ttiles * K * (16.0 + 4.0 * fold);
+            long long split = (long long)(we / std::max(wtot, 1.0) * 608.0 / ((double)jt * ttiles) + 0.5);
+            split = std::max(1LL, std::min(split, std::max(1LL, K / 64)));
+            split = std::min(split, 4096LL);
+            P.chb.split[e] = (int)split;
             P.chb.poff[e] = poff;
-            poff += (long long)split * P.chb.tau[e] * P.tau_pad;
+            poff += split * P.chb.tau[e] * P.tau_pad;
             P.chb.tile0[e] = bt;
-            bt += ((P.chb.tau[e] + 15) / 16) * split;
+            bt += jt * (int)split;
         }
         P.chb.tile0[P.chb.count] = bt;
         P.bwd_tiles = bt;
-        P.F_per_shift = foff;
         P.partc_elems = poff;
     }
 
@@ -327,29 +393,48 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.need_pad = !((tau % 4) == 0 && d_A != nullptr && (((uintptr_t)d_A) % 16) == 0);
     P.off_A = off;
     if (P.need_pad) off = align256(off + E * (size_t)P.s * P.tau_pad);
+    // areas that live through a whole forward (and, reused, the backward): the point table,
+    // the root values and the per-row results
     P.off_tab = off;
     off = align256(off + E * (size_t)P.reff * P.T_tot);
-    P.off_B = off;
-    off = align256(off + E * (size_t)P.reff * P.B_per_shift);
+    P.off_S = off;
+    off = align256(off + E * (size_t)P.reff * P.S_per_shift);
     if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
-        P.off_rowpart = off;
-        off = align256(off + E * (size_t)P.reff * P.cg_count * P.N);
-        P.off_rowmax = off;
-        if (P.fkind == QMC_F_LOGSUMEXP) off = align256(off + E * (size_t)P.reff * P.cg_count * P.N);
         P.off_rowsave = off;
-        off = align256(off + sizeof(double) * (size_t)P.reff * P.N);
+        off = align256(off + 2 * E * (size_t)P.reff * P.N);
         P.off_fpart = off;
         off = align256(off + sizeof(double) * (size_t)P.reff * P.nblk);
+        P.off_ticket = off;
+        off = align256(off + sizeof(unsigned int));
+    }
+    // one region shared by areas whose lives do not overlap on the stream: the coarse block
+    // products (dead once summed into S), the row partials of the fused forward, and the
+    // backward's gradient buffers
+    const size_t u0 = off;
+    size_t uend = u0;
+    P.off_B = u0;
+    uend = std::max(uend, align256(u0 + E * (size_t)P.reff * P.B_per_shift));
+    if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
+        size_t o = u0;
+        P.off_rowpart = o;
+        o = align256(o + E * (size_t)P.reff * P.cg_count * P.N);
+        P.off_rowmax = o;
+        if (P.fkind == QMC_F_LOGSUMEXP) o = align256(o + E * (size_t)P.reff * P.cg_count * P.N);
+        uend = std::max(uend, o);
     }
     if (op == QMC_OP_INTEGRATE_BWD) {
-        P.off_F = off;
-        off = align256(off + E * (size_t)P.reff * ((size_t)n_root * P.tau_pad + P.F_per_shift));
-        P.off_gradpart = off;
-        off = align256(off + E * (size_t)P.reff * P.groups * std::max(P.kf_width, 1) * P.tau_pad);
-        P.off_partc = off;
-        off = align256(off + E * (size_t)std::max(P.partc_elems, 1LL));
+        size_t o = u0;
+        P.off_F = o;
+        o = align256(o + E * (size_t)P.reff * (size_t)n_root * P.tau_pad);
+        P.off_Fchain = o;
+        o = align256(o + E * (size_t)P.reff * (size_t)std::max(P.Fchain_per_shift, 1LL));
+        P.off_gradpart = o;
+        o = align256(o + E * (size_t)P.reff * P.groups * std::max(P.kf_width, 1) * P.tau_pad);
+        P.off_partc = o;
+        o = align256(o + E * (size_t)std::max(P.partc_elems, 1LL));
+        uend = std::max(uend, o);
     }
-    P.total = off;
+    P.total = uend;
     return QMC_OK;
 }
 
@@ -375,6 +460,12 @@ qmc_status upload_rule(const Plan& P, const qmc_rule* r, char* ws, cudaStream_t 
     return QMC_OK;
 }
 
+// the integrand's pre-scale kappa (v = kappa y) and derivative factor (see Fn in qmc_internal.cuh)
+double kappa_of(int F, double c) {
+    return F == QMC_F_CALL_MEAN_EXP ? c * kLog2e : F == QMC_F_LOGSUMEXP ? kLog2e : 1.0;
+}
+double gfac_of(int F, double c) { return F == QMC_F_CALL_MEAN_EXP ? c : 1.0; }
+
 template <class T>
 FineArgs<T> fine_args(const Plan& P, char* ws, const T* A, int ldA, const qmc_integrand* f) {
     FineArgs<T> a{};
@@ -390,9 +481,8 @@ FineArgs<T> fine_args(const Plan& P, char* ws, const T* A, int ldA, const qmc_in
         a.lev_logn[I] = in ? P.m - I : 0;
         a.lev_tab[I] = in ? P.lev_tab[I] : 0;
     }
-    a.B = P.chf.count ? reinterpret_cast<const T*>(ws + P.off_B) : nullptr;
-    a.B_stride = P.B_per_shift;
-    a.chain = P.chf;
+    a.S = P.chf.count ? reinterpret_cast<const T*>(ws + P.off_S) : nullptr;
+    a.S_stride = P.S_per_shift;
     a.cr = P.cr; a.cg_count = P.cg_count; a.reff = P.reff; a.r0 = 0;
     a.N = P.N;
     a.rowpart = reinterpret_cast<T*>(ws + P.off_rowpart);
@@ -403,6 +493,7 @@ FineArgs<T> fine_args(const Plan& P, char* ws, const T* A, int ldA, const qmc_in
     a.tau_d = (double)P.tau;
     a.K_d = f ? f->params[1] : 0.0;
     a.fkind = P.fkind;
+    a.kappa = (T)kappa_of(P.fkind, f ? f->params[0] : 0.0);
     return a;
 }
 
@@ -424,23 +515,28 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     *Aused = A;
     *ldA_used = ldA;
     T* tab = reinterpret_cast<T*>(ws + P.off_tab);
-    QMC_LAUNCH(st, "k_table", launch_table<T>(R, tab, P.T_tot, P.reff, st));
-    if (P.chf.count)
-        QMC_LAUNCH(st, "k_coarse_fwd",
-                   launch_coarse_fwd<T>(tab, P.T_tot, A, ldA, P.tau_pad, P.chf, reinterpret_cast<T*>(ws + P.off_B),
-                                        P.B_per_shift, P.reff, st));
-    FineArgs<T> a = fine_args<T>(P, ws, A, ldA, f);
+    unsigned int* ticket = mode == MODE_FUSED ? reinterpret_cast<unsigned int*>(ws + P.off_ticket) : nullptr;
+    QMC_LAUNCH(st, "k_table", launch_table<T>(R, tab, P.T_tot, P.reff, ticket, st));
+    if (P.chf.count) {
+        T* B = reinterpret_cast<T*>(ws + P.off_B);
+        QMC_LAUNCH(st, "k_coarse_fwd", launch_coarse_fwd<T>(tab, P.T_tot, A, ldA, P.tau_pad, P.chf, B, P.B_per_shift,
+                                                            P.reff, st));
+        QMC_LAUNCH(st, "k_chain_sum", launch_chain_sum<T>(B, P.B_per_shift, P.chf, reinterpret_cast<T*>(ws + P.off_S),
+                                                          P.S_per_shift, P.m - P.JF, P.tau_pad, P.reff, st));
+    }
+    FineArgs<T> a = fine_args<T>(P, ws, A, ldA, mode == MODE_FUSED ? f : nullptr);
     a.P = dP;
     dim3 grid(P.root_blocks, P.cg_count, P.reff);
     QMC_LAUNCH(st, mode == MODE_FUSED ? "k_fine_fwd" : "k_fine_fwd_materialize",
-               launch_fine_fwd<T>(a, P.shape, mode == MODE_FUSED ? P.fkind : 0, mode, grid, st));
+               launch_fine_fwd<T>(a, P.shape, P.exact, mode == MODE_FUSED ? P.fkind : 0, mode, grid, st));
     if (mode == MODE_FUSED) {
-        double* rowsave = reinterpret_cast<double*>(ws + P.off_rowsave);
+        T* rowsave = reinterpret_cast<T*>(ws + P.off_rowsave);
         double* fpart = reinterpret_cast<double*>(ws + P.off_fpart);
+        const double coef_scale = gfac_of(P.fkind, f->params[0]) / ((double)P.reff * (double)P.N);
         QMC_LAUNCH(st, "k_rows_finalize",
                    launch_rows_finalize<T>(a.rowpart, a.rowmax, P.cg_count, P.N, P.reff, P.fkind, (double)P.tau,
-                                           f->params[0], f->params[1], rowsave, rowf, fpart, P.nblk, st));
-        if (est) QMC_LAUNCH(st, "k_est_finalize", launch_est_finalize(fpart, P.nblk, P.reff, P.N, est, st));
+                                           f->params[0], f->params[1], coef_scale, rowsave, rowf, fpart, P.nblk,
+                                           ticket, est, st));
     }
     return QMC_OK;
 }
@@ -460,37 +556,30 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
     const long long n_root = 1LL << (P.m - P.JF);
     const long long root_stride = n_root * P.tau_pad;
     T* Froot = reinterpret_cast<T*>(ws + P.off_F);
-    T* Fchain = Froot + (long long)P.reff * root_stride;
     FineArgs<T> a = fine_args<T>(P, ws, A, ldA, f);
-    a.rowsave = reinterpret_cast<const double*>(ws + P.off_rowsave);
+    a.rowsave = reinterpret_cast<const T*>(ws + P.off_rowsave);
     a.upstream = upstream;
-    a.coef_scale = 1.0 / ((double)P.reff * (double)P.N);
     a.Froot = Froot;
     a.gradpart = reinterpret_cast<T*>(ws + P.off_gradpart);
     a.roots_per_cta = P.roots_per_cta;
     a.groups = P.groups;
     a.kf_actual = P.kf_width;
     dim3 grid(P.groups, P.passes, P.reff);
-    QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.fkind, grid, st));
-    // fold the root gradients onto the distinct rows of each coarser block (ascending levels)
-    const T* src = Froot;
-    long long src_stride = root_stride;
-    int logn_src = P.m - P.JF;
-    for (int e = 0; e < P.chb.count; ++e) {
-        if (P.chb.lev[e] == P.JF) continue;
-        T* dst = Fchain + P.chb.boff[e];
-        QMC_LAUNCH(st, "k_fold",
-                   launch_fold<T>(src, src_stride, logn_src, dst, P.F_per_shift, P.chb.logn[e], P.tau_pad, P.reff, st));
-        src = dst;
-        src_stride = P.F_per_shift;
-        logn_src = P.chb.logn[e];
-    }
+    QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.exact, P.fkind, grid, st));
+    // coarse block gradients; each level folds the root gradients onto its distinct rows on the fly
     const T* tab = reinterpret_cast<const T*>(ws + P.off_tab);
     T* partc = reinterpret_cast<T*>(ws + P.off_partc);
     if (P.chb.count)
-        QMC_LAUNCH(st, "k_coarse_grad",
-                   launch_coarse_grad<T>(tab, P.T_tot, Froot, root_stride, Fchain, P.F_per_shift, P.JF, P.tau_pad,
-                                         P.chb, partc, P.reff, P.bwd_tiles, st));
+    {
+        T* Fchain = reinterpret_cast<T*>(ws + P.off_Fchain);
+        if (P.fold.depth > 0)
+            QMC_LAUNCH(st, "k_fold_tree", launch_fold_tree<T>(Froot, root_stride, Fchain, P.Fchain_per_shift, P.fold,
+                                                              P.tau_pad, P.reff, st));
+        if (P.chb.count)
+            QMC_LAUNCH(st, "k_coarse_grad",
+                       launch_coarse_grad<T>(tab, P.T_tot, Froot, root_stride, Fchain, P.Fchain_per_shift,
+                                             P.tau_pad, P.chb, partc, P.reff, P.bwd_tiles, st));
+    }
     int koff[4] = {0, 0, 0, 0}, col0[4] = {0, 0, 0, 0}, taul[4] = {0, 0, 0, 0};
     const int kmax_s4[4] = {1, 2, 4, 8};
     for (int I = 0, o = 0; I < P.JF; ++I) {
@@ -664,7 +753,7 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
 // ------------------------------------------------------------------------------------------
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 32ull << 20;   // 32 MiB
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 256;

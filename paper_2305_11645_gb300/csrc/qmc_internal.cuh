@@ -9,7 +9,7 @@
 namespace qmc {
 
 constexpr int kMaxLevels = 32;     // levels I = 0..m (level m holds the constant columns, w_j >= m)
-constexpr int kMaxChain = 32;
+constexpr int kMaxChain = 48;      // coarse entries (levels, cut into column ranges); keeps Chain < 4 KB
 
 // Kinds, transforms and integrands mirror include/qmc.h.
 enum { KIND_LATTICE = 0, KIND_NET = 1 };
@@ -62,20 +62,43 @@ __device__ __forceinline__ uint32_t apply_shift(int kind, uint32_t x, uint32_t d
 
 // ---------------------------------------------------------------------------------------------
 // Coordinate transforms phi (Sec. 2.3) of x = X32 * 2^-32, rounded once to T.
+// The 32-bit integer conversions are explicit cvt instructions: the unsigned value
+// 2^32 - X32 must be converted as unsigned (2^31 included), never folded into -X32.
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float u32_to_f32(uint32_t v) {
+    float r;
+    asm("cvt.rn.f32.u32 %0, %1;" : "=f"(r) : "r"(v));
+    return r;
+}
+__device__ __forceinline__ float i32_to_f32(int v) {
+    float r;
+    asm("cvt.rn.f32.s32 %0, %1;" : "=f"(r) : "r"(v));
+    return r;
+}
+__device__ __forceinline__ double u32_to_f64(uint32_t v) {
+    double r;
+    asm("cvt.rn.f64.u32 %0, %1;" : "=d"(r) : "r"(v));
+    return r;
+}
+__device__ __forceinline__ double i32_to_f64(int v) {
+    double r;
+    asm("cvt.rn.f64.s32 %0, %1;" : "=d"(r) : "r"(v));
+    return r;
+}
+
 template <class T> struct Tr;
 
 template <> struct Tr<float> {
     static __device__ __forceinline__ float apply(uint32_t x, int tr) {
         const float two_m32 = 2.3283064365386963e-10f, two_m31 = 4.656612873077393e-10f;
-        // 1 - x for x >= 1/2 is (2^32 - X32) 2^-32 <= 1/2, held exactly in 64 bits
-        const unsigned long long cmp = 0x100000000ull - (unsigned long long)x;
+        // 1 - x for x >= 1/2 is (2^32 - X32) 2^-32 <= 1/2; 2^32 - X32 <= 2^31 fits a uint32
+        const uint32_t cmp = 0u - x;
         switch (tr) {
-            case T_CENTER: return (float)((long long)x - 0x80000000ll) * two_m32;
-            case T_TENT: return (x < 0x80000000u) ? (float)x * two_m31 : (float)cmp * two_m31;
+            case T_CENTER: return i32_to_f32((int)(x ^ 0x80000000u)) * two_m32;
+            case T_TENT: return (x < 0x80000000u) ? u32_to_f32(x) * two_m31 : u32_to_f32(cmp) * two_m31;
             case T_INV_NORMAL:
-                return (x < 0x80000000u) ? normcdfinvf((float)x * two_m32) : -normcdfinvf((float)cmp * two_m32);
-            default: return (float)x * two_m32;
+                return (x < 0x80000000u) ? normcdfinvf(u32_to_f32(x) * two_m32) : -normcdfinvf(u32_to_f32(cmp) * two_m32);
+            default: return u32_to_f32(x) * two_m32;
         }
     }
 };
@@ -83,50 +106,59 @@ template <> struct Tr<float> {
 template <> struct Tr<double> {
     static __device__ __forceinline__ double apply(uint32_t x, int tr) {
         const double two_m32 = 2.3283064365386962890625e-10, two_m31 = 4.656612873077392578125e-10;
-        const unsigned long long cmp = 0x100000000ull - (unsigned long long)x;
+        const uint32_t cmp = 0u - x;
         switch (tr) {
-            case T_CENTER: return (double)((long long)x - 0x80000000ll) * two_m32;
-            case T_TENT: return (x < 0x80000000u) ? (double)x * two_m31 : (double)cmp * two_m31;
+            case T_CENTER: return i32_to_f64((int)(x ^ 0x80000000u)) * two_m32;
+            case T_TENT: return (x < 0x80000000u) ? u32_to_f64(x) * two_m31 : u32_to_f64(cmp) * two_m31;
             case T_INV_NORMAL:
-                return (x < 0x80000000u) ? normcdfinv((double)x * two_m32) : -normcdfinv((double)cmp * two_m32);
-            default: return (double)x * two_m32;
+                return (x < 0x80000000u) ? normcdfinv(u32_to_f64(x) * two_m32) : -normcdfinv(u32_to_f64(cmp) * two_m32);
+            default: return u32_to_f64(x) * two_m32;
         }
     }
 };
 
 // ---------------------------------------------------------------------------------------------
-// Integrands, row-separable: f(y) = g(u), u = sum_t h(y_t)   (eq. (2)'s f)
-// For LOGSUMEXP the row state is (max, sum exp(y - max)).
+// Integrands, row-separable: f(y) = g(u), u = sum_t h(y_t)   (eq. (2)'s f).
+// The kernels carry v = kappa * y instead of y: kappa multiplies A's staged
+// columns and the coarse root values once, so that exp(c y) = 2^v costs one
+// ex2 per output (kappa = c log2 e); log-sum-exp works in base 2 (kappa = log2 e).
+// G = dQ/dy_t = coef_k * gfac * hp(v, aux) with coef_k = upstream g'(u_k)/(R N).
 // ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ float ex2f(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2(float x) { return ex2f(x); }
+__device__ __forceinline__ double ex2(double x) { return exp2(x); }
+
+constexpr double kLog2e = 1.4426950408889634;
+constexpr double kLn2 = 0.6931471805599453;
+
 template <int F, class T> struct Fn {
-    static __device__ __forceinline__ T h(T y, T c) {
-        if constexpr (F == F_LINEAR_MEAN) return y;
-        else if constexpr (F == F_MEAN_COS) return cos(y);
-        else if constexpr (F == F_CALL_MEAN_EXP) return exp(c * y);
-        else if constexpr (F == F_GAUSS_NORM2) return y * y;
-        else if constexpr (F == F_PDE_INV_SQ) { T r = T(1) / (T(1) + c * y); return r * r; }
-        else return y;
+    static __host__ __device__ double kappa(double c) {
+        return F == F_CALL_MEAN_EXP ? c * kLog2e : F == F_LOGSUMEXP ? kLog2e : 1.0;
     }
-    // h'(y) (LOGSUMEXP: exp(y - L) with L = log sum exp(y) passed as `aux`)
-    static __device__ __forceinline__ T hprime(T y, T c, T aux) {
+    static __host__ __device__ double gfac(double c) { return F == F_CALL_MEAN_EXP ? c : 1.0; }
+    // contribution of one output to the row sum u (not used for LOGSUMEXP)
+    static __device__ __forceinline__ T h(T v, T c) {
+        if constexpr (F == F_LINEAR_MEAN) return v;
+        else if constexpr (F == F_MEAN_COS) return cos(v);
+        else if constexpr (F == F_CALL_MEAN_EXP) return ex2(v);
+        else if constexpr (F == F_GAUSS_NORM2) return v * v;
+        else if constexpr (F == F_PDE_INV_SQ) { T r = T(1) / (T(1) + c * v); return r * r; }
+        else return v;
+    }
+    // h'(y) / gfac in terms of v (LOGSUMEXP: 2^(v - aux), aux = log2 e * log sum exp(y))
+    static __device__ __forceinline__ T hp(T v, T c, T aux) {
         if constexpr (F == F_LINEAR_MEAN) return T(1);
-        else if constexpr (F == F_MEAN_COS) return -sin(y);
-        else if constexpr (F == F_CALL_MEAN_EXP) return c * exp(c * y);
-        else if constexpr (F == F_GAUSS_NORM2) return T(2) * y;
-        else if constexpr (F == F_PDE_INV_SQ) { T r = T(1) / (T(1) + c * y); return T(-2) * c * r * r * r; }
-        else return exp(y - aux);
+        else if constexpr (F == F_MEAN_COS) return -sin(v);
+        else if constexpr (F == F_CALL_MEAN_EXP) return ex2(v);
+        else if constexpr (F == F_GAUSS_NORM2) return T(2) * v;
+        else if constexpr (F == F_PDE_INV_SQ) { T r = T(1) / (T(1) + c * v); return T(-2) * c * r * r * r; }
+        else return ex2(v - aux);
     }
 };
-
-// float specialisations use the fast single-precision intrinsics where their
-// error (a few ulp over the ranges of these integrands) is inside the FP32 tier.
-template <> __device__ __forceinline__ float Fn<F_CALL_MEAN_EXP, float>::h(float y, float c) { return __expf(c * y); }
-template <> __device__ __forceinline__ float Fn<F_CALL_MEAN_EXP, float>::hprime(float y, float c, float) {
-    return c * __expf(c * y);
-}
-template <> __device__ __forceinline__ float Fn<F_LOGSUMEXP, float>::hprime(float y, float, float aux) {
-    return __expf(y - aux);
-}
 
 // g(u) and g'(u) in double (tau, params as given)
 __device__ __forceinline__ double g_of(int F, double u, double tau, double c, double K) {
@@ -156,11 +188,25 @@ struct Chain {
     int count;
     int lev[kMaxChain], logn[kMaxChain], tau[kMaxChain], col0[kMaxChain];
     long long tab[kMaxChain];        // table offset of the level's first column
-    long long boff[kMaxChain];       // element offset of B_e / F_e inside a shift's area
+    long long boff[kMaxChain];       // element offset of B_e inside a shift's area
     int tile0[kMaxChain + 1];        // prefix sums of work tiles (per kernel)
     int split[kMaxChain];            // k-splits (backward grad GEMM)
     long long poff[kMaxChain];       // partial-buffer offsets (backward grad GEMM)
+    // backward: where level e's folded gradient F_e comes from -- the root folds (fsel 0) or a
+    // folded level (fsel 1) at offset foff, still to be folded 2^flog times on the fly
+    int fsel[kMaxChain], flog[kMaxChain];
+    long long foff[kMaxChain];
 };
+
+// Levels folded by k_fold_tree: F_{JF+d} for d = 1..depth from the root folds, each written at
+// off[d] when want[d] (a coarse level with columns).  Top nodes: 2^logn_top of level JF+depth.
+struct FoldLevels {
+    int depth, logn_top;
+    int want[8];
+    long long off[8];
+};
+
+constexpr int kMaxCR = 256;          // columns per CTA of the fine forward kernel
 
 template <class T> struct FineArgs {
     const T* tab; long long tab_stride;       // distinct-row table, per shift
@@ -169,15 +215,16 @@ template <class T> struct FineArgs {
     int logn_root;                            // root level JF: n_root = 2^(m-JF)
     int lev_tau[4], lev_col0[4], lev_logn[4];
     long long lev_tab[4];
-    const T* B; long long B_stride;           // coarse block products, per shift
-    Chain chain;                               // (only count/logn/boff used here)
+    const T* S; long long S_stride;           // root values S_JF = sum of the coarse block products, per shift
     int cr, cg_count, reff, r0;
     long long N;
     T* rowpart; T* rowmax;                     // FUSED: [r][cg][N]
     T* P;                                      // MATERIALIZE: [r][N][tau]
     T c0, c1;                                  // integrand parameters
+    T kappa;                                   // v = kappa * y
     // backward
-    const double* rowsave; const double* upstream; double coef_scale;   // 1/(R_eff N)
+    const T* rowsave;        // per row: {g'(u_k) gfac/(R_eff N), log2 e * u_k} from the forward finalisation
+    const double* upstream;
     double tau_d, K_d;
     T* Froot;                                  // [r][n_root][tau_pad]
     T* gradpart;                               // [r][group][KF][tau_pad]
@@ -189,7 +236,7 @@ template <class T> struct FineArgs {
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------------------------
 template <class T>
-cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, int reff, cudaStream_t st);
+cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, int reff, unsigned int* ticket, cudaStream_t st);
 cudaError_t launch_points_full(const DevRule& R, uint32_t* out, int shift_idx, cudaStream_t st);
 cudaError_t launch_points_distinct(const DevRule& R, uint32_t* out, long long T_tot, int shift_idx,
                                    cudaStream_t st);
@@ -199,22 +246,24 @@ template <class T>
 cudaError_t launch_coarse_fwd(const T* tab, long long tab_stride, const T* A, int ldA, int tau_pad,
                               const Chain& ch, T* B, long long B_stride, int reff, cudaStream_t st);
 template <class T>
-cudaError_t launch_fine_fwd(const FineArgs<T>& a, int shape, int F, int mode, dim3 grid, cudaStream_t st);
+cudaError_t launch_chain_sum(const T* B, long long B_stride, const Chain& ch, T* S, long long S_stride,
+                             int logn_root, int tau_pad, int reff, cudaStream_t st);
+template <class T>
+cudaError_t launch_fine_fwd(const FineArgs<T>& a, int shape, bool exact, int F, int mode, dim3 grid,
+                            cudaStream_t st);
 template <class T>
 cudaError_t launch_rows_finalize(const T* rowpart, const T* rowmax, int cg_count, long long N, int reff,
-                                 int F, double tau, double c, double K, double* rowsave, T* rowf_out,
-                                 double* fpart, int nblk, cudaStream_t st);
-cudaError_t launch_est_finalize(const double* fpart, int nblk, int reff, long long N, double* est,
-                                cudaStream_t st);
+                                 int F, double tau, double c, double K, double coef_scale, T* rowsave, T* rowf_out,
+                                 double* fpart, int nblk, unsigned int* ticket, double* est, cudaStream_t st);
 template <class T>
-cudaError_t launch_fine_bwd(const FineArgs<T>& a, int shape, int F, dim3 grid, cudaStream_t st);
+cudaError_t launch_fine_bwd(const FineArgs<T>& a, int shape, bool exact, int F, dim3 grid, cudaStream_t st);
 template <class T>
-cudaError_t launch_fold(const T* src, long long src_stride, int logn_src, T* dst, long long dst_stride,
-                        int logn_dst, int tau_pad, int reff, cudaStream_t st);
+cudaError_t launch_fold_tree(const T* Froot, long long root_stride, T* Fchain, long long chain_stride,
+                             const FoldLevels& fl, int tau_pad, int reff, cudaStream_t st);
 template <class T>
 cudaError_t launch_coarse_grad(const T* tab, long long tab_stride, const T* Froot, long long root_stride,
-                               const T* Fchain, long long chain_stride, int jf, int tau_pad, const Chain& ch,
-                               T* part, int reff, int ntiles, cudaStream_t st);
+                               const T* Fchain, long long chain_stride, int tau_pad, const Chain& ch, T* part,
+                               int reff, int ntiles, cudaStream_t st);
 template <class T>
 cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width, const int* koff_lev,
                                const int* col0_lev, const int* tau_lev, int jf, const T* part_c,

@@ -21,8 +21,12 @@ __device__ __forceinline__ int level_of_col(const DevRule& R, int j) {
 }
 
 // Distinct-row table: tab[r*T_tot + lev_tab[I] + (j - col0_I) * n_I + row] = phi(X32 of x_{row,j}, shift r).
+// It is the first kernel of every forward pass and also clears the ticket that the
+// row finalisation uses to elect the block that forms the estimates.
 template <class T>
-__global__ void k_table(DevRule R, T* __restrict__ tab, long long T_tot, int reff) {
+__global__ void k_table(const __grid_constant__ DevRule R, T* __restrict__ tab, long long T_tot, int reff,
+                        unsigned int* ticket) {
+    if (ticket && blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0u;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < T_tot;
          g += (long long)gridDim.x * blockDim.x) {
         const int I = level_of(R, g);
@@ -39,14 +43,14 @@ __global__ void k_table(DevRule R, T* __restrict__ tab, long long T_tot, int ref
 }
 
 template <class T>
-cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, int reff, cudaStream_t st) {
+cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, int reff, unsigned int* ticket, cudaStream_t st) {
     long long blocks = (T_tot + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_table<T><<<(unsigned)blocks, 256, 0, st>>>(R, tab, T_tot, reff);
+    k_table<T><<<(unsigned)blocks, 256, 0, st>>>(R, tab, T_tot, reff, ticket);
     return cudaGetLastError();
 }
-template cudaError_t launch_table<float>(const DevRule&, float*, long long, int, cudaStream_t);
-template cudaError_t launch_table<double>(const DevRule&, double*, long long, int, cudaStream_t);
+template cudaError_t launch_table<float>(const DevRule&, float*, long long, int, unsigned int*, cudaStream_t);
+template cudaError_t launch_table<double>(const DevRule&, double*, long long, int, unsigned int*, cudaStream_t);
 
 // Full layout: out[k*s + j] = X32 of x_{k,j}, row k mod 2^q of column j.
 __global__ void k_points_full(DevRule R, uint32_t* __restrict__ out, int shift_idx) {
