@@ -16,7 +16,8 @@
  *    A random shift Delta_j is D_j * 2^-32 with D_j a uint32: lattices add it
  *    mod 2^32 ({x + Delta}, Sec. 2.3), nets XOR it (digital shift).
  *  - A is s x tau row-major (row j is a_j, Sec. 3.1).  Its element type is
- *    fixed by the precision: QMC_FP64 -> double, QMC_FP32 -> float.
+ *    fixed by the precision: QMC_FP64 -> double; QMC_FP32, QMC_SPLIT and
+ *    QMC_BF16 -> float.
  *  - "HOST" pointers are read during the call only; "DEVICE" pointers must be
  *    device memory of the current CUDA device, and are read or written by
  *    work enqueued on `stream` (the call returns before that work finishes).
@@ -58,8 +59,12 @@ typedef int qmc_status;
 /* arithmetic precision of the product and of the integrand */
 #define QMC_FP64  0               /* double A, double arithmetic */
 #define QMC_FP32  1               /* float A, float arithmetic; estimates reduced in double */
-#define QMC_SPLIT 2               /* reserved: split-precision tensor-core path (not built) */
-#define QMC_BF16  3               /* reserved: plain bf16 tensor-core path (not built) */
+#define QMC_SPLIT 2               /* float A and data; the coarse block products X_I A_I (Algorithm 2)
+                                     and block gradients X_I^T F_I on tensor cores with three bf16
+                                     pieces per operand and six piece products (bf16x6), FP32
+                                     accumulation: FP32-level accuracy; the rest as QMC_FP32 */
+#define QMC_BF16  3               /* as QMC_SPLIT with one bf16 piece per operand (one product):
+                                     relative error ~2^-8 in the block products */
 
 /* row-separable integrands f(y) = g(sum_t h(y_t)), y = x^T A in R^tau */
 #define QMC_F_NONE          0     /* no integrand (qmc_reduced_matmul only) */
@@ -140,6 +145,14 @@ const char* qmc_last_error(void);
 qmc_status qmc_validate_rule(const qmc_rule* rule);
 
 /*
+ * qmc_device_status: synchronises the current device and reads its sticky device error word.
+ *  Returns QMC_ERR_TIMEOUT if a tensor-core kernel (QMC_SPLIT / QMC_BF16) gave up a bounded
+ *  wait on its MMA completion since the word was last cleared (its outputs were then written
+ *  as NaN), QMC_OK otherwise.  clear != 0 resets the word.  Not callable during stream capture.
+ */
+qmc_status qmc_device_status(int clear);
+
+/*
  * qmc_workspace_size: bytes of device workspace `op` needs for these arguments (written to *bytes).
  *  rules/tau/f are arrays of nprob entries (nprob = 1 for GEN_POINTS and REDUCED_MATMUL; f may be
  *  NULL there).  The workspace must be 256-byte aligned.
@@ -162,7 +175,7 @@ qmc_status qmc_gen_points(const qmc_rule* rule, uint32_t shift_idx, int layout, 
 /*
  * qmc_reduced_matmul: the materialised product P = X A of Algorithms 1/2 ("Return P = XA"),
  *  with the shift and transform of the rule applied to X (Sec. 2.3).
- *  d_A   DEVICE s x tau row-major (double for QMC_FP64, float for QMC_FP32).
+ *  d_A   DEVICE s x tau row-major (double for QMC_FP64, float otherwise).
  *  d_P   DEVICE R_eff x N x tau row-major, same element type: d_P[(r*N + k)*tau + t] = (x_k^T A)_t
  *        for shift r.
  */

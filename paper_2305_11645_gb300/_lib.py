@@ -19,7 +19,8 @@ QMC_BWD_REUSE_FORWARD = 1
 
 EXPORTS = ["qmc_version", "qmc_last_error", "qmc_validate_rule", "qmc_workspace_size", "qmc_gen_points",
            "qmc_reduced_matmul", "qmc_integrate", "qmc_integrate_backward", "qmc_integrate_noalloc",
-           "qmc_trace_enable", "qmc_trace_collect", "qmc_trace_entry"]
+           "qmc_trace_enable", "qmc_trace_collect", "qmc_trace_entry", "qmc_device_status"]
+PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "split": QMC_SPLIT, "bf16": QMC_BF16}
 
 
 class QmcRule(ctypes.Structure):
@@ -70,6 +71,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                c_void_p, c_size_t, c_void_p]
         lib.qmc_integrate_noalloc.argtypes = [POINTER(QmcRule), c_void_p, c_uint32, POINTER(QmcIntegrand), c_int,
                                               c_void_p, c_void_p]
+        lib.qmc_device_status.argtypes = [c_int]
         lib.qmc_trace_enable.argtypes = [c_int]
         lib.qmc_trace_collect.argtypes = [POINTER(c_uint32)]
         lib.qmc_trace_entry.argtypes = [c_uint32, POINTER(ctypes.c_char_p), POINTER(ctypes.c_uint64),
@@ -83,6 +85,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 def check(status: int) -> None:
     if status != QMC_OK:
         raise QmcError(status, load().qmc_last_error().decode())
+
+
+def device_status(clear: bool = True) -> None:
+    """Synchronise the device and raise QmcError(QMC_ERR_TIMEOUT) if a tensor-core kernel gave up
+    a bounded wait since the last check (the error word is cleared when `clear`)."""
+    check(load().qmc_device_status(1 if clear else 0))
 
 
 def trace_enable(on: bool) -> None:

@@ -94,12 +94,19 @@ class Rule:
         L.check(L.load().qmc_validate_rule(ctypes.byref(self.struct())))
 
 
-def _precision(A: torch.Tensor) -> int:
-    if A.dtype == torch.float64:
-        return L.QMC_FP64
-    if A.dtype == torch.float32:
-        return L.QMC_FP32
-    raise TypeError(f"A must be float32 or float64 (got {A.dtype})")
+def _precision(A: torch.Tensor, precision: Optional[str] = None) -> int:
+    """The tier of a call: float64 A -> FP64; float32 A -> FP32, or the tensor-core tiers
+    'split' (bf16x6 block products, FP32-level accuracy) and 'bf16' (one bf16 product)."""
+    if A.dtype not in (torch.float32, torch.float64):
+        raise TypeError(f"A must be float32 or float64 (got {A.dtype})")
+    if precision is None:
+        return L.QMC_FP64 if A.dtype == torch.float64 else L.QMC_FP32
+    if precision not in L.PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(L.PRECISIONS)} (got {precision!r})")
+    want = torch.float64 if precision == "fp64" else torch.float32
+    if A.dtype != want:
+        raise TypeError(f"precision {precision!r} takes A as {want} (got {A.dtype})")
+    return L.PRECISIONS[precision]
 
 
 def _stream(device: torch.device) -> ctypes.c_void_p:
@@ -143,10 +150,12 @@ def gen_points(rule: Rule, layout: str = "full", shift_idx: int = 0, device="cud
     return out
 
 
-def reduced_matmul(rule: Rule, A: torch.Tensor, ws: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """P = X A for every shift: (R_eff, N, tau), dtype of A (float64 -> FP64 tier, float32 -> FP32 tier)."""
+def reduced_matmul(rule: Rule, A: torch.Tensor, ws: Optional[torch.Tensor] = None,
+                   precision: Optional[str] = None) -> torch.Tensor:
+    """P = X A for every shift: (R_eff, N, tau), dtype of A (float64 -> FP64 tier, float32 -> FP32
+    tier unless `precision` names a tensor-core tier)."""
     A = A.contiguous()
-    prec = _precision(A)
+    prec = _precision(A, precision)
     tau = A.shape[1]
     nbytes = workspace_size(L.QMC_OP_REDUCED_MATMUL, [rule], [tau], None, prec)
     ws = _workspace(nbytes, A.device, ws)
@@ -158,13 +167,13 @@ def reduced_matmul(rule: Rule, A: torch.Tensor, ws: Optional[torch.Tensor] = Non
 
 
 def integrate(rules: Union[Rule, Sequence[Rule]], As, fs, rowf: bool = False,
-              ws: Optional[torch.Tensor] = None):
+              ws: Optional[torch.Tensor] = None, precision: Optional[str] = None):
     """QMC estimates for one or several problems.  Returns a float64 tensor holding, per problem,
     the R_eff per-shift estimates followed by their mean (and, with rowf=True, the per-point
     integrand values of every problem as (R_eff, N) tensors)."""
     rules, As, fs = _as_list(rules), [a.contiguous() for a in _as_list(As)], _as_list(fs)
     n = len(rules)
-    prec = _precision(As[0])
+    prec = _precision(As[0], precision)
     device = As[0].device
     taus = [a.shape[1] for a in As]
     nbytes = workspace_size(L.QMC_OP_INTEGRATE, rules, taus, fs, prec)
@@ -185,11 +194,11 @@ def integrate(rules: Union[Rule, Sequence[Rule]], As, fs, rowf: bool = False,
 
 
 def integrate_backward(rules, As, fs, upstream: torch.Tensor, ws: Optional[torch.Tensor] = None,
-                       reuse_forward: bool = False) -> List[torch.Tensor]:
+                       reuse_forward: bool = False, precision: Optional[str] = None) -> List[torch.Tensor]:
     """d(upstream_p * mean estimate_p)/dA_p for every problem p."""
     rules, As, fs = _as_list(rules), [a.contiguous() for a in _as_list(As)], _as_list(fs)
     n = len(rules)
-    prec = _precision(As[0])
+    prec = _precision(As[0], precision)
     device = As[0].device
     taus = [a.shape[1] for a in As]
     nbytes = workspace_size(L.QMC_OP_INTEGRATE_BWD, rules, taus, fs, prec)
@@ -214,25 +223,26 @@ class QMCEstimate(torch.autograd.Function):
     The backward reuses the forward's workspace (no recomputation of the forward pass)."""
 
     @staticmethod
-    def forward(ctx, A: torch.Tensor, rule: Rule, f: Integrand):
+    def forward(ctx, A: torch.Tensor, rule: Rule, f: Integrand, precision: Optional[str] = None):
         A = A.contiguous()
-        prec = _precision(A)
+        prec = _precision(A, precision)
         nbytes = workspace_size(L.QMC_OP_INTEGRATE_BWD, [rule], [A.shape[1]], [f], prec)
         ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=A.device)
-        est = integrate(rule, A, f, ws=ws)
+        est = integrate(rule, A, f, ws=ws, precision=precision)
         ctx.save_for_backward(A)
-        ctx.rule, ctx.f, ctx.ws = rule, f, ws
+        ctx.rule, ctx.f, ctx.ws, ctx.precision = rule, f, ws, precision
         return est[-1].to(A.dtype)
 
     @staticmethod
     def backward(ctx, grad_out):
         (A,) = ctx.saved_tensors
-        g = integrate_backward(ctx.rule, A, ctx.f, grad_out.detach().reshape(1), ws=ctx.ws, reuse_forward=True)[0]
-        return g, None, None
+        g = integrate_backward(ctx.rule, A, ctx.f, grad_out.detach().reshape(1), ws=ctx.ws, reuse_forward=True,
+                               precision=ctx.precision)[0]
+        return g, None, None, None
 
 
-def qmc_estimate(A: torch.Tensor, rule: Rule, f: Integrand) -> torch.Tensor:
-    return QMCEstimate.apply(A, rule, f)
+def qmc_estimate(A: torch.Tensor, rule: Rule, f: Integrand, precision: Optional[str] = None) -> torch.Tensor:
+    return QMCEstimate.apply(A, rule, f, precision)
 
 
 class Integrator:
@@ -245,11 +255,12 @@ class Integrator:
     ``(est, grad)`` -- est holds the R_eff per-shift estimates and their mean.
     """
 
-    def __init__(self, rule: Rule, A: torch.Tensor, f: Integrand, backward: bool = True, graph: bool = True):
+    def __init__(self, rule: Rule, A: torch.Tensor, f: Integrand, backward: bool = True, graph: bool = True,
+                 precision: Optional[str] = None):
         self.rule, self.f, self.backward = rule, f, backward
         self.device = A.device
         self.A = A.detach().contiguous().clone()
-        self.prec = _precision(self.A)
+        self.prec = _precision(self.A, precision)
         op = L.QMC_OP_INTEGRATE_BWD if backward else L.QMC_OP_INTEGRATE
         self.ws = torch.empty(max(workspace_size(op, [rule], [self.A.shape[1]], [f], self.prec), 256),
                               dtype=torch.uint8, device=self.device)

@@ -11,6 +11,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/qmc.h"
@@ -180,7 +181,7 @@ struct Plan {
     long long N = 0;
     int lev_tau[kMaxLevels] = {}, lev_col0[kMaxLevels] = {};
     long long lev_tab[kMaxLevels + 1] = {};
-    long long T_tot = 0;
+    long long T_tot = 0, tab_stride = 0;   // table entries per shift, and the per-shift stride (multiple of 4)
     int tau = 0, tau_pad = 0, precision = 0, elt = 4, fkind = 0;
     int shape = SHAPE_S0, JF = 0, kf_width = 0, cw_bwd = 4;
     bool exact = false;            // fine band levels hold exactly their maximum column counts
@@ -190,6 +191,7 @@ struct Plan {
     int root_blocks = 0, cg_count = 1, cr = 0;
     int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
     int nblk = 0;
+    int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
     bool need_gen = false, need_shift = false, need_pad = false;
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
@@ -220,6 +222,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.lev_tab[0] = 0;
     for (int I = 0; I <= P.m; ++I) P.lev_tab[I + 1] = P.lev_tab[I] + (long long)P.lev_tau[I] * (1LL << (P.m - I));
     P.T_tot = P.lev_tab[P.m + 1];
+    P.tab_stride = (P.T_tot + 3) / 4 * 4;
     P.need_gen = (r->d_gen == nullptr);
     P.need_shift = (P.R > 0 && r->d_shift == nullptr);
 
@@ -230,11 +233,10 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     if (P.need_shift) off = align256(off + sizeof(uint32_t) * (size_t)P.R * P.s);
     if (op == QMC_OP_GEN_POINTS) { P.total = off; return QMC_OK; }
 
-    if (precision != QMC_FP64 && precision != QMC_FP32) {
-        if (precision == QMC_SPLIT || precision == QMC_BF16)
-            return fail(QMC_ERR_UNSUPPORTED, "precision %d (tensor-core tiers) is not built", precision);
+    if (precision != QMC_FP64 && precision != QMC_FP32 && precision != QMC_SPLIT && precision != QMC_BF16)
         return fail(QMC_ERR_INVALID_ARG, "precision %d unknown", precision);
-    }
+    // the tensor-core tiers keep FP32 data and FP32 arithmetic outside the coarse block products
+    P.tc_pieces = precision == QMC_SPLIT ? 3 : precision == QMC_BF16 ? 1 : 0;
     if (tau < 1 || tau > 65536) return fail(QMC_ERR_INVALID_ARG, "tau=%u outside [1, 65536]", tau);
     P.precision = precision;
     P.elt = precision == QMC_FP64 ? 8 : 4;
@@ -255,7 +257,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         return true;
     };
     const int k4[4] = {1, 2, 4, 8}, k1[1] = {16};
-    if (precision == QMC_FP32 && fits(4, k4)) {
+    if (precision != QMC_FP64 && fits(4, k4)) {
         P.shape = SHAPE_S4; P.JF = 4; P.kf_width = 15; P.cw_bwd = 2;
         P.exact = P.lev_tau[0] == 1 && P.lev_tau[1] == 2 && P.lev_tau[2] == 4 && P.lev_tau[3] == 8;
     }
@@ -267,16 +269,19 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     // coarse chain: levels JF..m with columns.  A level with many columns (a long K for its few
     // distinct rows) is cut into up to 8 column ranges, each its own entry with its own block
     // product, so that the levels run in parallel; the chain sum adds the entries' products.
+    // (The tensor-core block products run long K well, so their levels are cut more coarsely.)
+    const int cut_cols = P.tc_pieces ? 64 : 32;
+    const int fwd_rows = P.tc_pieces ? tc_fwd_rows() : 64;
     int nsplit_tot = 0;
     for (int I = P.JF; I <= P.m; ++I)
-        if (P.lev_tau[I] > 0) nsplit_tot += std::min(8, (P.lev_tau[I] + 31) / 32);
+        if (P.lev_tau[I] > 0) nsplit_tot += std::min(8, (P.lev_tau[I] + cut_cols - 1) / cut_cols);
     const bool cut = nsplit_tot <= kMaxChain;
     P.chf.count = 0;
     long long boff = 0;
     int tiles = 0;
     for (int I = P.JF; I <= P.m; ++I) {
         if (P.lev_tau[I] == 0) continue;
-        const int parts = cut ? std::min(8, (P.lev_tau[I] + 31) / 32) : 1;
+        const int parts = cut ? std::min(8, (P.lev_tau[I] + cut_cols - 1) / cut_cols) : 1;
         const int width = (P.lev_tau[I] + parts - 1) / parts;
         for (int pc = 0; pc < parts; ++pc) {
             const int c0 = pc * width, cw = std::min(width, P.lev_tau[I] - c0);
@@ -287,7 +292,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             P.chf.boff[e] = boff;
             boff += (1LL << (P.m - I)) * P.tau_pad;
             P.chf.tile0[e] = tiles;
-            tiles += (int)(((1LL << (P.m - I)) + 63) / 64);
+            tiles += (int)(((1LL << (P.m - I)) + fwd_rows - 1) / fwd_rows);
             P.chf.split[e] = 1; P.chf.poff[e] = 0;
         }
     }
@@ -358,25 +363,37 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             fchain += (1LL << (P.m - I_mat)) * P.tau_pad;
         }
         P.Fchain_per_shift = fchain;
-        // coarse gradient GEMMs: K = R n_e rows; splits balance the work (16 multiply-adds plus
-        // 4 fold loads per K row and column) over ~4 CTAs per SM
+        // coarse gradient GEMMs: K = R n_e rows; splits balance the work over the GPU.  FP32/FP64
+        // tiles: 16 columns j, 16 multiply-adds plus 4 fold loads per K row and column, ~4 CTAs
+        // per SM.  Tensor-core tiles: 64 columns j, work ~ the operand loads (2 + fold per K row
+        // and column), ~3 CTAs per SM and at least 128 K rows per split.
+        const bool tc = P.tc_pieces != 0;
+        const int jcols = tc ? tc_grad_cols() : 16;
+        const double fma_w = tc ? 2.0 : 16.0, fold_w = tc ? 1.0 : 4.0, target = tc ? 456.0 : 608.0;
+        const long long kmin = tc ? 128 : 64;
         const int ttiles = (P.tau_pad + 127) / 128;
         double wtot = 0.0;
         for (int e = 0; e < P.chb.count; ++e) {
             const long long K = (long long)P.reff << (P.m - P.chb.lev[e]);
             const double fold = (double)(1LL << P.chb.flog[e]);
-            wtot += (double)((P.chb.tau[e] + 15) / 16) * ttiles * K * (16.0 + 4.0 * fold);
+            wtot += (double)((P.chb.tau[e] + jcols - 1) / jcols) * ttiles * K * (fma_w + fold_w * fold);
         }
         long long poff = 0;
         int bt = 0;
         for (int e = 0; e < P.chb.count; ++e) {
             const long long K = (long long)P.reff << (P.m - P.chb.lev[e]);
             const double fold = (double)(1LL << P.chb.flog[e]);
-            const int jt = (P.chb.tau[e] + 15) / 16;
-            const double we = (double)jt * ttiles * K * (16.0 + 4.0 * fold);
-            long long split = (long long)(we / std::max(wtot, 1.0) * 608.0 / ((double)jt * ttiles) + 0.5);
-            split = std::max(1LL, std::min(split, std::max(1LL, K / 64)));
+            const int jt = (P.chb.tau[e] + jcols - 1) / jcols;
+            const double we = (double)jt * ttiles * K * (fma_w + fold_w * fold);
+            long long split = (long long)(we / std::max(wtot, 1.0) * target / ((double)jt * ttiles) + 0.5);
+            split = std::max(1LL, std::min(split, std::max(1LL, K / kmin)));
             split = std::min(split, 4096LL);
+            long long kper = (K + split - 1) / split;
+            if (tc) {                       // whole chunks of 32 rows per split
+                kper = (kper + 31) / 32 * 32;
+                split = (K + kper - 1) / kper;
+            }
+            P.chb.kper[e] = kper;
             P.chb.split[e] = (int)split;
             P.chb.poff[e] = poff;
             poff += split * P.chb.tau[e] * P.tau_pad;
@@ -396,7 +413,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     // areas that live through a whole forward (and, reused, the backward): the point table,
     // the root values and the per-row results
     P.off_tab = off;
-    off = align256(off + E * (size_t)P.reff * P.T_tot);
+    off = align256(off + E * (size_t)P.reff * P.tab_stride);
     P.off_S = off;
     off = align256(off + E * (size_t)P.reff * P.S_per_shift);
     if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
@@ -470,7 +487,7 @@ template <class T>
 FineArgs<T> fine_args(const Plan& P, char* ws, const T* A, int ldA, const qmc_integrand* f) {
     FineArgs<T> a{};
     a.tab = reinterpret_cast<const T*>(ws + P.off_tab);
-    a.tab_stride = P.T_tot;
+    a.tab_stride = P.tab_stride;
     a.A = A; a.ldA = ldA;
     a.tau = P.tau; a.tau_pad = P.tau_pad;
     a.logn_root = P.m - P.JF;
@@ -516,11 +533,17 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     *ldA_used = ldA;
     T* tab = reinterpret_cast<T*>(ws + P.off_tab);
     unsigned int* ticket = mode == MODE_FUSED ? reinterpret_cast<unsigned int*>(ws + P.off_ticket) : nullptr;
-    QMC_LAUNCH(st, "k_table", launch_table<T>(R, tab, P.T_tot, P.reff, ticket, st));
+    QMC_LAUNCH(st, "k_table", launch_table<T>(R, tab, P.T_tot, P.tab_stride, P.reff, ticket, st));
     if (P.chf.count) {
         T* B = reinterpret_cast<T*>(ws + P.off_B);
-        QMC_LAUNCH(st, "k_coarse_fwd", launch_coarse_fwd<T>(tab, P.T_tot, A, ldA, P.tau_pad, P.chf, B, P.B_per_shift,
-                                                            P.reff, st));
+        if (P.tc_pieces) {
+            if constexpr (std::is_same<T, float>::value)
+                QMC_LAUNCH(st, "k_coarse_fwd_tc", launch_coarse_fwd_tc(tab, P.tab_stride, A, ldA, P.tau_pad, P.chf, B,
+                                                                       P.B_per_shift, P.reff, P.tc_pieces, st));
+        } else {
+            QMC_LAUNCH(st, "k_coarse_fwd", launch_coarse_fwd<T>(tab, P.tab_stride, A, ldA, P.tau_pad, P.chf, B,
+                                                                P.B_per_shift, P.reff, st));
+        }
         QMC_LAUNCH(st, "k_chain_sum", launch_chain_sum<T>(B, P.B_per_shift, P.chf, reinterpret_cast<T*>(ws + P.off_S),
                                                           P.S_per_shift, P.m - P.JF, P.tau_pad, P.reff, st));
     }
@@ -575,10 +598,16 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
         if (P.fold.depth > 0)
             QMC_LAUNCH(st, "k_fold_tree", launch_fold_tree<T>(Froot, root_stride, Fchain, P.Fchain_per_shift, P.fold,
                                                               P.tau_pad, P.reff, st));
-        if (P.chb.count)
+        if (P.tc_pieces) {
+            if constexpr (std::is_same<T, float>::value)
+                QMC_LAUNCH(st, "k_coarse_grad_tc",
+                           launch_coarse_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
+                                                 P.tau_pad, P.chb, partc, P.reff, P.bwd_tiles, P.tc_pieces, st));
+        } else {
             QMC_LAUNCH(st, "k_coarse_grad",
-                       launch_coarse_grad<T>(tab, P.T_tot, Froot, root_stride, Fchain, P.Fchain_per_shift,
+                       launch_coarse_grad<T>(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
                                              P.tau_pad, P.chb, partc, P.reff, P.bwd_tiles, st));
+        }
     }
     int koff[4] = {0, 0, 0, 0}, col0[4] = {0, 0, 0, 0}, taul[4] = {0, 0, 0, 0};
     const int kmax_s4[4] = {1, 2, 4, 8};
@@ -601,10 +630,18 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
 // =============================================================================================
 extern "C" {
 
-const char* qmc_version(void) { return "qmc_gb300 0.1 (sm_103a)"; }
+const char* qmc_version(void) { return "qmc_gb300 0.2 (sm_103a)"; }
 const char* qmc_last_error(void) { return g_err.c_str(); }
 
 qmc_status qmc_validate_rule(const qmc_rule* rule) { return validate(rule); }
+
+qmc_status qmc_device_status(int clear) {
+    unsigned int word = 0;
+    QMC_CUDA(cudaDeviceSynchronize());
+    QMC_CUDA(tc_error_word(&word, clear != 0));
+    if (word) return fail(QMC_ERR_TIMEOUT, "a tensor-core kernel's bounded wait ran out (error word 0x%x)", word);
+    return QMC_OK;
+}
 
 qmc_status qmc_workspace_size(int op, const qmc_rule* rules, const uint32_t* tau, uint32_t nprob,
                               const qmc_integrand* f, int precision, size_t* bytes) {

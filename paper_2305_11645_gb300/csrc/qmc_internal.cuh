@@ -9,7 +9,7 @@
 namespace qmc {
 
 constexpr int kMaxLevels = 32;     // levels I = 0..m (level m holds the constant columns, w_j >= m)
-constexpr int kMaxChain = 48;      // coarse entries (levels, cut into column ranges); keeps Chain < 4 KB
+constexpr int kMaxChain = 48;      // coarse entries (levels, cut into column ranges); Chain stays ~4 KB
 
 // Kinds, transforms and integrands mirror include/qmc.h.
 enum { KIND_LATTICE = 0, KIND_NET = 1 };
@@ -191,6 +191,7 @@ struct Chain {
     long long boff[kMaxChain];       // element offset of B_e inside a shift's area
     int tile0[kMaxChain + 1];        // prefix sums of work tiles (per kernel)
     int split[kMaxChain];            // k-splits (backward grad GEMM)
+    long long kper[kMaxChain];       // K rows per split (tensor-core backward: a multiple of 32)
     long long poff[kMaxChain];       // partial-buffer offsets (backward grad GEMM)
     // backward: where level e's folded gradient F_e comes from -- the root folds (fsel 0) or a
     // folded level (fsel 1) at offset foff, still to be folded 2^flog times on the fly
@@ -236,7 +237,8 @@ template <class T> struct FineArgs {
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------------------------
 template <class T>
-cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, int reff, unsigned int* ticket, cudaStream_t st);
+cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, long long stride, int reff, unsigned int* ticket,
+                         cudaStream_t st);
 cudaError_t launch_points_full(const DevRule& R, uint32_t* out, int shift_idx, cudaStream_t st);
 cudaError_t launch_points_distinct(const DevRule& R, uint32_t* out, long long T_tot, int shift_idx,
                                    cudaStream_t st);
@@ -268,5 +270,16 @@ template <class T>
 cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width, const int* koff_lev,
                                const int* col0_lev, const int* tau_lev, int jf, const T* part_c,
                                const Chain& ch, int tau, int tau_pad, int s, T* grad, cudaStream_t st);
+
+// tensor-core block products (split tier: pieces = 3, bf16 tier: pieces = 1); FP32 data
+int tc_fwd_rows();        // rows of a forward tile (the chain's tile0 counts tiles of this many rows)
+int tc_grad_cols();       // block-gradient columns of a backward tile
+cudaError_t launch_coarse_fwd_tc(const float* tab, long long tab_stride, const float* A, int ldA, int tau_pad,
+                                 const Chain& ch, float* B, long long B_stride, int reff, int pieces,
+                                 cudaStream_t st);
+cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
+                                  const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
+                                  float* part, int reff, int ntiles, int pieces, cudaStream_t st);
+cudaError_t tc_error_word(unsigned int* value, bool clear);
 
 }  // namespace qmc

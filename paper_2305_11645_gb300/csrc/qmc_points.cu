@@ -24,8 +24,8 @@ __device__ __forceinline__ int level_of_col(const DevRule& R, int j) {
 // It is the first kernel of every forward pass and also clears the ticket that the
 // row finalisation uses to elect the block that forms the estimates.
 template <class T>
-__global__ void k_table(const __grid_constant__ DevRule R, T* __restrict__ tab, long long T_tot, int reff,
-                        unsigned int* ticket) {
+__global__ void k_table(const __grid_constant__ DevRule R, T* __restrict__ tab, long long T_tot, long long stride,
+                        int reff, unsigned int* ticket) {
     if (ticket && blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0u;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < T_tot;
          g += (long long)gridDim.x * blockDim.x) {
@@ -37,20 +37,22 @@ __global__ void k_table(const __grid_constant__ DevRule R, T* __restrict__ tab, 
         const uint32_t x0 = unshifted_x32(R, j, row, q);
         for (int r = 0; r < reff; ++r) {
             const uint32_t x = R.shift ? apply_shift(R.kind, x0, R.shift[(size_t)r * R.s + j]) : x0;
-            tab[(long long)r * T_tot + g] = Tr<T>::apply(x, R.transform);
+            tab[(long long)r * stride + g] = Tr<T>::apply(x, R.transform);
         }
     }
 }
 
 template <class T>
-cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, int reff, unsigned int* ticket, cudaStream_t st) {
+cudaError_t launch_table(const DevRule& R, T* tab, long long T_tot, long long stride, int reff, unsigned int* ticket,
+                         cudaStream_t st) {
     long long blocks = (T_tot + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_table<T><<<(unsigned)blocks, 256, 0, st>>>(R, tab, T_tot, reff, ticket);
+    k_table<T><<<(unsigned)blocks, 256, 0, st>>>(R, tab, T_tot, stride, reff, ticket);
     return cudaGetLastError();
 }
-template cudaError_t launch_table<float>(const DevRule&, float*, long long, int, unsigned int*, cudaStream_t);
-template cudaError_t launch_table<double>(const DevRule&, double*, long long, int, unsigned int*, cudaStream_t);
+template cudaError_t launch_table<float>(const DevRule&, float*, long long, long long, int, unsigned int*, cudaStream_t);
+template cudaError_t launch_table<double>(const DevRule&, double*, long long, long long, int, unsigned int*,
+                                          cudaStream_t);
 
 // Full layout: out[k*s + j] = X32 of x_{k,j}, row k mod 2^q of column j.
 __global__ void k_points_full(DevRule R, uint32_t* __restrict__ out, int shift_idx) {

@@ -1,0 +1,553 @@
+// Tensor-core block products for the split and bf16 tiers: the coarse block products
+// B_e = X_e A_e of Algorithm 2 (X~_I A~_I on the b^(m-I) distinct rows of weight block I)
+// and the block gradients dA_e = X_e^T F_e of the adjoint, on tcgen05.mma (kind::f16,
+// bf16 operands, FP32 accumulation in tensor memory).
+//
+// Split tier.  Every FP32 operand v is written as three bf16 pieces
+//     v = v0 + v1 + v2,   v0 = bf16(v), v1 = bf16(v - v0), v2 = bf16(v - v0 - v1)
+// (each difference is exact in FP32, so the three pieces hold all 24 bits of v), and a
+// product keeps the six piece products with i + j <= 2:
+//     v w ~ v0 w0 + v0 w1 + v1 w0 + v0 w2 + v1 w1 + v2 w0,
+// the bf16x6 scheme of Henry, Tang and Heinecke (ARITH 2019).  The dropped terms are
+// below 2^-23 |v w|.  All six products accumulate into one FP32 accumulator (bf16 keeps
+// the FP32 exponent range, so no operand scaling is needed).
+// Bf16 tier.  One piece, one product: v w ~ bf16(v) bf16(w).
+//
+// Structure of both kernels.  One CTA of 128 threads owns a 128-row tile of the MMA's M
+// dimension.  K runs in chunks of 32 through two shared-memory stages.  Every thread
+// loads its share of chunk c + 1 from global memory into registers (coalesced along
+// the rows of the operand tiles) before it splits chunk c into bf16 pieces and stores
+// them, so the loads of one chunk overlap the conversion of the previous one.  The
+// pieces sit in K-major tiles with the 64-byte swizzle (rows of 32 bf16 = 64 bytes;
+// the 16-byte group g of row r is stored at group g ^ ((r >> 1) & 3)), which keeps the
+// threads' 16-byte stores and the tensor core's reads free of bank conflicts.  One
+// thread issues a chunk's MMAs and commits them to the stage's mbarrier; the stage is
+// refilled once that barrier has completed.  After the last chunk the threads read
+// their rows of the accumulator (tcgen05.ld, TMEM lane = tile row) and store them.
+// Every mbarrier wait is bounded; a wait that runs out sets the device error word, the
+// tile's outputs are written as NaN and the kernel releases its tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "qmc_internal.cuh"
+
+namespace qmc {
+
+__device__ unsigned int g_tc_error;      // sticky: bit 0 = a bounded mbarrier wait ran out
+
+namespace {
+
+constexpr int TM = 128;            // tile rows = MMA M = TMEM lanes
+constexpr int KC = 32;             // K per chunk: two MMA K-steps of 16
+constexpr int NJ = 64;             // backward: block-gradient columns j per tile (MMA N <= 64)
+constexpr uint32_t ROWB = KC * 2;  // bytes of one tile row (32 bf16)
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor of a K-major tile with the 64-byte swizzle: 8-row
+// groups 512 bytes apart (stride-dimension offset), K-step ks of 16 bf16 starts 32 * ks
+// bytes into the rows (the swizzle is applied to the final address, so the start
+// address moves inside the swizzle atom).  The leading-dimension offset is not used by
+// swizzled K-major layouts and is set to 16 bytes.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);            // start address
+    d |= (uint64_t)1 << 16;                              // leading-dimension byte offset 16 (unused)
+    d |= (uint64_t)(512 >> 4) << 32;                     // stride-dimension byte offset: 8 rows x 64 B
+    d |= (uint64_t)1 << 46;                              // descriptor version for tcgen05
+    d |= (uint64_t)4 << 61;                              // 64-byte swizzle
+    return d;
+}
+
+// byte offset of the 16-byte group g (k = 8g..8g+7) of row r in a swizzled tile
+__device__ __forceinline__ uint32_t sw64_off(int r, int g) {
+    return (uint32_t)r * ROWB + ((uint32_t)(g ^ ((r >> 1) & 3)) << 4);
+}
+
+// instruction descriptor: D = F32, A = B = BF16, both K-major, dense, M = 128, N = n
+__device__ __forceinline__ uint32_t idesc_bf16(uint32_t n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long long it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(slot), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t tmem, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(ncols));
+}
+
+__device__ __forceinline__ void mbar_init2(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar[0])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&bar[1])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane (no wait)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Split 8 consecutive k of one row into P bf16 pieces and store each piece's 16 bytes
+// (group g of row r) into the tiles tile0 + p * piece_stride.
+template <int P>
+__device__ __forceinline__ void store_group(unsigned char* tile0, uint32_t piece_stride, int r, int g,
+                                            const float* v) {
+    uint32_t w[P][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float a = v[2 * i], b = v[2 * i + 1];
+        const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
+        w[0][i] = *reinterpret_cast<const uint32_t*>(&h0);
+        if constexpr (P == 3) {
+            const float2 f0 = __bfloat1622float2(h0);
+            a -= f0.x; b -= f0.y;                              // exact residuals
+            const __nv_bfloat162 h1 = __floats2bfloat162_rn(a, b);
+            w[1][i] = *reinterpret_cast<const uint32_t*>(&h1);
+            const float2 f1 = __bfloat1622float2(h1);
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(a - f1.x, b - f1.y);
+            w[2][i] = *reinterpret_cast<const uint32_t*>(&h2);
+        }
+    }
+    const uint32_t off = sw64_off(r, g);
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+        *reinterpret_cast<uint4*>(tile0 + p * piece_stride + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+}
+
+// The piece products of one K-step, smallest first: A piece i times B piece j.
+template <int P>
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_base, uint32_t a_piece, uint32_t b_base,
+                                            uint32_t b_piece, uint32_t idesc, bool& first) {
+    constexpr int NP = P == 3 ? 6 : 1;
+    constexpr int pi[6] = {2, 1, 0, 1, 0, 0};
+    constexpr int pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        const int i = P == 3 ? pi[q] : 0, j = P == 3 ? pj[q] : 0;
+        mma_bf16(tmem, smem_desc_sw64(a_base + i * a_piece), smem_desc_sw64(b_base + j * b_piece), idesc,
+                 first ? 0u : 1u);
+        first = false;
+    }
+}
+
+__device__ __forceinline__ int entry_of(const Chain& ch, int bx) {
+    int e = 0;
+    while (e + 1 < ch.count && bx >= ch.tile0[e + 1]) ++e;
+    return e;
+}
+
+__device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
+
+__device__ __forceinline__ unsigned char* align_1k(unsigned char* p) {
+    return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
+}
+
+// Thread-block prologue / epilogue shared by both kernels.
+__device__ __forceinline__ uint32_t tc_setup(uint64_t* bar, uint32_t* tmem_slot, uint32_t ncols) {
+    if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(tmem_slot), ncols);
+    if (threadIdx.x == 0) mbar_init2(bar);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    return *tmem_slot;
+}
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols) {
+    fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        fence_after_sync();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+// Publish the stage to the tensor core; returns false (in every thread) if any thread's
+// wait ran out.
+__device__ __forceinline__ bool publish_stage(bool ok) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    fence_before_sync();
+    ok = __syncthreads_and(ok);
+    fence_after_sync();
+    return ok;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// Forward: B_e[r][t/4][rho][t%4] = sum_{k < tau_e} tab[r][tab_e + k n_e + rho] A[col0_e + k][t].
+// Tile: 128 rows rho x 128 columns t; M = rho, N = t, K = k.  Both operands are contiguous
+// along the tile's rows in global memory (rho for X, t for A), so thread i loads row i of
+// X and row i (column t0 + i) of A for the 32 k of a chunk; every load instruction of a
+// warp reads 128 contiguous bytes.
+// Shared memory per stage: X and A tiles, P pieces x 128 rows x 64 B each.
+// ------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__ tab, long long tab_stride,
+                                                       const float* __restrict__ A, int ldA, int tau_pad,
+                                                       const __grid_constant__ Chain ch, float* __restrict__ B,
+                                                       long long B_stride) {
+    constexpr uint32_t TILE = TM * ROWB;              // one piece of one operand: 8 KB
+    constexpr uint32_t OPND = P * TILE;
+    constexpr uint32_t STAGE = 2 * OPND;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = align_1k(smem_raw);          // the swizzle pattern follows address bits 7-8
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int e = entry_of(ch, blockIdx.x);
+    const long long rho0 = (long long)(blockIdx.x - ch.tile0[e]) * TM;
+    const int logn = ch.logn[e], tau_e = ch.tau[e];
+    const long long n_e = 1LL << logn;
+    const int t0 = blockIdx.y * TM;
+    const int r = blockIdx.z;
+    const int nchunks = (tau_e + KC - 1) / KC;
+    const uint32_t tmem = tc_setup(bar, tmem_slot, TM);
+
+    const long long rho = rho0 + tid;                 // = TMEM lane tid of the accumulator
+    const int t = t0 + tid;
+    const bool row_ok = rho < n_e, col_ok = t < tau_pad;
+    const float* xr = tab + (long long)r * tab_stride + ch.tab[e] + (row_ok ? rho : 0);
+    const float* ac = A + (long long)ch.col0[e] * ldA + (col_ok ? t : 0);
+    float xv[KC], av[KC];
+    bool ok = true, first = true;
+    // Iteration it loads chunk it and converts chunk it - 1 (one load site keeps the code small).
+    for (int it = 0; it <= nchunks; ++it) {
+        float xc[KC], ac_[KC];
+#pragma unroll
+        for (int i = 0; i < KC; ++i) { xc[i] = xv[i]; ac_[i] = av[i]; }
+        if (it < nchunks) {
+#pragma unroll
+            for (int i = 0; i < KC; ++i) {
+                const int k = it * KC + i;
+                const bool kv = k < tau_e;
+                xv[i] = (kv && row_ok) ? __ldg(xr + (long long)k * n_e) : 0.0f;
+                av[i] = (kv && col_ok) ? __ldg(ac + (long long)k * ldA) : 0.0f;
+            }
+        }
+        if (it == 0) continue;
+        const int c = it - 1;
+        const int s = c & 1;
+        unsigned char* Xs = smem + s * STAGE;
+        unsigned char* As = Xs + OPND;
+        const int ksteps = min(2, (tau_e - c * KC + 15) >> 4);
+        if (c >= 2) ok = mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1);
+        if (ok) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                if (g < 2 * ksteps) {
+                    store_group<P>(Xs, TILE, tid, g, xc + 8 * g);
+                    store_group<P>(As, TILE, tid, g, ac_ + 8 * g);
+                }
+            }
+        }
+        ok = publish_stage(ok);
+        if (!ok) break;
+        if (tid == 0) {
+            const uint32_t idesc = idesc_bf16(TM);
+            for (int ks = 0; ks < ksteps; ++ks)
+                issue_kstep<P>(tmem, smem_u32(Xs) + 32 * ks, TILE, smem_u32(As) + 32 * ks, TILE, idesc, first);
+            mma_commit(smem_u32(&bar[s]));
+        }
+    }
+    if (ok) ok = mbar_wait(smem_u32(&bar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
+    fence_after_sync();
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicOr(&g_tc_error, 1u);
+
+    float* Be = B + (long long)r * B_stride + ch.boff[e];
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        uint32_t d[2][32];
+        if (ok) {
+            tmem_ld32(lane_addr + half * 64, d[0]);
+            tmem_ld32(lane_addr + half * 64 + 32, d[1]);
+            tmem_wait_ld();
+        }
+        if (row_ok) {
+#pragma unroll
+            for (int g = 0; g < 16; ++g) {
+                const int tt = t0 + half * 64 + 4 * g;
+                const uint32_t* q = &d[g >> 3][(g & 7) * 4];
+                const float4 v = ok ? make_float4(__uint_as_float(q[0]), __uint_as_float(q[1]),
+                                                  __uint_as_float(q[2]), __uint_as_float(q[3]))
+                                    : make_float4(qnan(), qnan(), qnan(), qnan());
+                if (tt < tau_pad) *reinterpret_cast<float4*>(Be + (((long long)(tt >> 2) << logn) << 2) + (rho << 2)) = v;
+            }
+        }
+    }
+    tc_teardown(tmem, TM);
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward: part[e][sp][j][t] = sum over k = (r, rho) in split sp of
+//           tab[r][tab_e + j n_e + rho] * F_e[r][rho][t],
+// F_e[rho] = sum_{q < 2^flog} Fsrc[rho + q n_e] (the adjoint of the periodic tiling).
+// Computed transposed, D[t][j] = sum_k F_e[k][t] X[k][j]: M = t (128 rows), N = j (a tile
+// of up to 64 columns of the entry), K = k.  F is contiguous along t, so thread i loads
+// column t0 + i of F for the 32 k of a chunk (coalesced over the warp); X is contiguous
+// along k, so each thread loads 16 consecutive k of one row j (float4 loads when the
+// chunk lies inside one shift's rows, n_e >= 32).  A split covers a multiple of 32 rows.
+// Shared memory per stage: F^T (P pieces x 128 rows x 64 B) and X (P x 64 rows x 64 B).
+// ------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict__ tab, long long tab_stride,
+                                                        const float* __restrict__ Froot, long long root_stride,
+                                                        const float* __restrict__ Fchain, long long chain_stride,
+                                                        int tau_pad, const __grid_constant__ Chain ch,
+                                                        float* __restrict__ part, int reff) {
+    constexpr uint32_t TILEA = TM * ROWB, TILEB = NJ * ROWB;
+    constexpr uint32_t OPA = P * TILEA, OPB = P * TILEB;
+    constexpr uint32_t STAGE = OPA + OPB;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = align_1k(smem_raw);          // the swizzle pattern follows address bits 7-8
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int e = entry_of(ch, blockIdx.x);
+    const int local = blockIdx.x - ch.tile0[e];
+    const int tau_e = ch.tau[e], logn = ch.logn[e], nsplit = ch.split[e];
+    const int jt = local / nsplit, sp = local - jt * nsplit;
+    const int j0 = jt * NJ;
+    const int nj = min(NJ, tau_e - j0);
+    const uint32_t nmma = (uint32_t)((nj + 15) & ~15);
+    const long long n_e = 1LL << logn;
+    const int fold = 1 << ch.flog[e];
+    const float* Fsrc = (ch.fsel[e] ? Fchain : Froot) + ch.foff[e];
+    const long long F_stride = ch.fsel[e] ? chain_stride : root_stride;
+    const long long rstep = n_e * tau_pad;
+    const long long Ktot = (long long)reff * n_e;
+    const long long kb = (long long)sp * ch.kper[e], ke = min(Ktot, kb + ch.kper[e]);
+    const int nchunks = ke > kb ? (int)((ke - kb + KC - 1) / KC) : 0;
+    const int t0 = blockIdx.y * TM;
+    const uint32_t tmem = tc_setup(bar, tmem_slot, NJ);
+
+    const int t = t0 + tid;                            // = TMEM lane tid of the accumulator
+    const bool col_ok = t < tau_pad;
+    const int jrow = tid & (NJ - 1), khalf = tid >> 6; // X: row j0 + jrow, one half of the chunk
+    const bool jrow_ok = jrow < nj;
+    const float* xcol = tab + ch.tab[e] + (long long)(j0 + (jrow_ok ? jrow : 0)) * n_e;
+    const float* Fcol = Fsrc + (col_ok ? t : 0);
+    const bool whole = n_e >= KC;                      // a chunk never crosses a shift boundary
+    float fv[KC], xw[16];
+    bool ok = true, first = true;
+    // Iteration it loads chunk it and converts chunk it - 1 (one load site keeps the code small).
+    for (int it = 0; it <= nchunks; ++it) {
+        float fc[KC], xc[16];
+#pragma unroll
+        for (int i = 0; i < KC; ++i) fc[i] = fv[i];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) xc[i] = xw[i];
+        if (it < nchunks) {
+            const long long k0 = kb + (long long)it * KC;
+            if (whole) {
+                const long long rr = k0 >> logn, rho0 = k0 & (n_e - 1);
+                const float* fp = Fcol + rr * F_stride + rho0 * tau_pad;
+#pragma unroll
+                for (int i = 0; i < KC; ++i) {
+                    float v = 0.0f;
+                    if (k0 + i < ke && col_ok) {
+                        const float* q = fp + (long long)i * tau_pad;
+                        v = __ldg(q);
+#pragma unroll 1
+                        for (int f = 1; f < fold; ++f) v += __ldg(q + f * rstep);
+                    }
+                    fv[i] = v;
+                }
+                const float* xp = xcol + rr * tab_stride + rho0 + 16 * khalf;
+                const long long kx = k0 + 16 * khalf;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float4 v4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (jrow_ok && kx + 4 * i + 4 <= ke) v4 = __ldg(reinterpret_cast<const float4*>(xp) + i);
+                    else if (jrow_ok) {
+                        v4.x = kx + 4 * i + 0 < ke ? __ldg(xp + 4 * i + 0) : 0.f;
+                        v4.y = kx + 4 * i + 1 < ke ? __ldg(xp + 4 * i + 1) : 0.f;
+                        v4.z = kx + 4 * i + 2 < ke ? __ldg(xp + 4 * i + 2) : 0.f;
+                    }
+                    xw[4 * i] = v4.x; xw[4 * i + 1] = v4.y; xw[4 * i + 2] = v4.z; xw[4 * i + 3] = v4.w;
+                }
+            } else {
+                // levels with fewer than 32 distinct rows: a chunk spans several shifts
+                const long long r0 = k0 >> logn;
+                const int rho0 = (int)(k0 & (n_e - 1));
+#pragma unroll
+                for (int i = 0; i < KC; ++i) {
+                    const int q = rho0 + i;
+                    float v = 0.0f;
+                    if (k0 + i < ke && col_ok) {
+                        const float* fq = Fcol + (r0 + (q >> logn)) * F_stride + (long long)(q & (n_e - 1)) * tau_pad;
+                        v = __ldg(fq);
+#pragma unroll 1
+                        for (int f = 1; f < fold; ++f) v += __ldg(fq + f * rstep);
+                    }
+                    fv[i] = v;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int q = rho0 + 16 * khalf + i;
+                    xw[i] = (k0 + 16 * khalf + i < ke && jrow_ok)
+                                ? __ldg(xcol + (r0 + (q >> logn)) * tab_stride + (q & (n_e - 1))) : 0.0f;
+                }
+            }
+        }
+        if (it == 0) continue;
+        const int c = it - 1;
+        const int s = c & 1;
+        unsigned char* Fs = smem + s * STAGE;
+        unsigned char* Xs = Fs + OPA;
+        const int ksteps = (int)min(2LL, (ke - kb - (long long)c * KC + 15) >> 4);
+        if (c >= 2) ok = mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1);
+        if (ok) {
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+                if (g < 2 * ksteps) store_group<P>(Fs, TILEA, tid, g, fc + 8 * g);
+            if (khalf < ksteps) {
+                store_group<P>(Xs, TILEB, jrow, 2 * khalf, xc);
+                store_group<P>(Xs, TILEB, jrow, 2 * khalf + 1, xc + 8);
+            }
+        }
+        ok = publish_stage(ok);
+        if (!ok) break;
+        if (tid == 0) {
+            const uint32_t idesc = idesc_bf16(nmma);
+            for (int ks = 0; ks < ksteps; ++ks)
+                issue_kstep<P>(tmem, smem_u32(Fs) + 32 * ks, TILEA, smem_u32(Xs) + 32 * ks, TILEB, idesc, first);
+            mma_commit(smem_u32(&bar[s]));
+        }
+    }
+    if (ok && nchunks > 0) ok = mbar_wait(smem_u32(&bar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
+    fence_after_sync();
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicOr(&g_tc_error, 1u);
+
+    // D[t][j]: TMEM lane = t - t0, column = j - j0
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    float* pe = part + ch.poff[e] + ((long long)sp * tau_e + j0) * tau_pad + t;
+    uint32_t d[2][32];
+    const bool have = ok && nchunks > 0;
+    if (have) {
+        tmem_ld32(lane_addr, d[0]);
+        if (nmma > 32) tmem_ld32(lane_addr + 32, d[1]);
+        tmem_wait_ld();
+    }
+    if (col_ok) {
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            if (i < nj) {
+                const float v = have ? __uint_as_float(d[i >> 5][i & 31]) : (ok ? 0.0f : qnan());
+                pe[(long long)i * tau_pad] = v;
+            }
+        }
+    }
+    tc_teardown(tmem, NJ);
+}
+
+// ------------------------------------------------------------------------------------------
+// launchers.  The shared-memory requests also cap the CTAs per SM so that their tensor
+// memory (128 columns forward, 64 backward) fits in the SM's 512 columns.
+// ------------------------------------------------------------------------------------------
+namespace {
+template <int P> constexpr size_t fwd_smem() {
+    const size_t need = 2 * (2 * P * TM * ROWB) + 1024 + 64;
+    return need < 58 * 1024 ? 58 * 1024 : need;         // <= 3 CTAs per SM
+}
+template <int P> constexpr size_t bwd_smem() {
+    const size_t need = 2 * (P * TM * ROWB + P * NJ * ROWB) + 1024 + 64;
+    return need < 30 * 1024 ? 30 * 1024 : need;         // <= 7 CTAs per SM
+}
+}  // namespace
+
+int tc_fwd_rows() { return TM; }
+int tc_grad_cols() { return NJ; }
+
+cudaError_t launch_coarse_fwd_tc(const float* tab, long long tab_stride, const float* A, int ldA, int tau_pad,
+                                 const Chain& ch, float* B, long long B_stride, int reff, int pieces,
+                                 cudaStream_t st) {
+    if (ch.count == 0) return cudaSuccess;
+    if (pieces != 1 && pieces != 3) return cudaErrorInvalidValue;
+    dim3 grid(ch.tile0[ch.count], (tau_pad + TM - 1) / TM, reff);
+    if (pieces == 3) {
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)fwd_smem<3>());
+        if (e != cudaSuccess) return e;
+        k_coarse_fwd_tc<3><<<grid, 128, fwd_smem<3>(), st>>>(tab, tab_stride, A, ldA, tau_pad, ch, B, B_stride);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_fwd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)fwd_smem<1>());
+        if (e != cudaSuccess) return e;
+        k_coarse_fwd_tc<1><<<grid, 128, fwd_smem<1>(), st>>>(tab, tab_stride, A, ldA, tau_pad, ch, B, B_stride);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
+                                  const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
+                                  float* part, int reff, int ntiles, int pieces, cudaStream_t st) {
+    if (ch.count == 0 || ntiles == 0) return cudaSuccess;
+    if (pieces != 1 && pieces != 3) return cudaErrorInvalidValue;
+    dim3 grid(ntiles, (tau_pad + TM - 1) / TM);
+    if (pieces == 3) {
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_grad_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bwd_smem<3>());
+        if (e != cudaSuccess) return e;
+        k_coarse_grad_tc<3><<<grid, 128, bwd_smem<3>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
+                                                              chain_stride, tau_pad, ch, part, reff);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_coarse_grad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)bwd_smem<1>());
+        if (e != cudaSuccess) return e;
+        k_coarse_grad_tc<1><<<grid, 128, bwd_smem<1>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
+                                                              chain_stride, tau_pad, ch, part, reff);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t tc_error_word(unsigned int* value, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(value, g_tc_error, sizeof(unsigned int));
+    if (e != cudaSuccess || !clear) return e;
+    const unsigned int zero = 0;
+    return cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(unsigned int));
+}
+
+}  // namespace qmc

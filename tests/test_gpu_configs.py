@@ -55,17 +55,36 @@ def test_c1_full():
     assert norm_rel(G.cpu().numpy(), O.grad(p)) <= 1e-11
 
 
-@pytest.mark.parametrize("dtype", [np.float32, np.float64])
-def test_c2_full(dtype):
+_C2_ORACLE = {}
+
+
+def c2_oracle(dtype):
+    """The full-size oracle estimate and gradient of the c2 workload (cached per dtype of A)."""
+    key = np.dtype(dtype).name
+    if key not in _C2_ORACLE:
+        p = I.c2(dtype=dtype)
+        _C2_ORACLE[key] = (O.estimate(p), O.grad(p))
+    return _C2_ORACLE[key]
+
+
+# estimate and gradient tolerances per tier: FP64 1e-12 / 1e-11; FP32 2e-5; split 1e-6 on the
+# estimate (the split path's stated tolerance); plain bf16 2e-3 on the estimate
+C2_TIERS = [(np.float64, None, 1e-12, 1e-11), (np.float32, None, 2e-5, 2e-5),
+            (np.float32, "split", 1e-6, 2e-5), (np.float32, "bf16", 2e-3, 2e-2)]
+
+
+@pytest.mark.parametrize("tier", range(len(C2_TIERS)))
+def test_c2_full(tier):
+    dtype, precision, tol, gtol = C2_TIERS[tier]
     p = I.c2(dtype=dtype)
     rule = api.Rule.from_problem(p)
     A = torch.from_numpy(p.A).to(DEV)
-    est = api.integrate(rule, A, integrand(p)).cpu().numpy()
-    Q, mean = O.estimate(p)
-    tol = 1e-12 if dtype == np.float64 else 2e-5
+    est = api.integrate(rule, A, integrand(p), precision=precision).cpu().numpy()
+    (Q, mean), grad = c2_oracle(dtype)
     assert rel(est[0], Q[0]) <= tol, (est, Q)
-    G = api.integrate_backward(rule, A, integrand(p), torch.ones(1, dtype=torch.float64, device=DEV))[0]
-    assert norm_rel(G.cpu().numpy(), O.grad(p)) <= (1e-11 if dtype == np.float64 else 2e-5)
+    G = api.integrate_backward(rule, A, integrand(p), torch.ones(1, dtype=torch.float64, device=DEV),
+                               precision=precision)[0]
+    assert norm_rel(G.cpu().numpy(), grad) <= gtol
 
 
 def sampled_rows_check(p, rowf, nsample=96, tol=2e-5):
