@@ -192,6 +192,8 @@ struct Plan {
     int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
+    bool fine_tc = false;          // fused forward of the fine band on tensor cores
+    int cg_tc = 0;                 // its row-partial column groups
     bool need_gen = false, need_shift = false, need_pad = false;
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
@@ -313,6 +315,9 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.cg_count = (P.tau_pad + cr - 1) / cr;
     }
     P.nblk = (int)((P.N + 255) / 256);
+    // tensor-core tiers: the fused forward of the dyadic band runs on tensor cores (8 roots per tile)
+    P.fine_tc = P.tc_pieces != 0 && P.shape == SHAPE_S4 && logn_root >= 3;
+    P.cg_tc = (P.tau + fine_tc_group_cols() - 1) / fine_tc_group_cols();
 
     // backward schedule
     if (op == QMC_OP_INTEGRATE_BWD) {
@@ -433,10 +438,11 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     uend = std::max(uend, align256(u0 + E * (size_t)P.reff * P.B_per_shift));
     if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
         size_t o = u0;
+        const int cgmax = std::max(P.cg_count, P.fine_tc ? P.cg_tc : 0);
         P.off_rowpart = o;
-        o = align256(o + E * (size_t)P.reff * P.cg_count * P.N);
+        o = align256(o + E * (size_t)P.reff * cgmax * P.N);
         P.off_rowmax = o;
-        if (P.fkind == QMC_F_LOGSUMEXP) o = align256(o + E * (size_t)P.reff * P.cg_count * P.N);
+        if (P.fkind == QMC_F_LOGSUMEXP) o = align256(o + E * (size_t)P.reff * cgmax * P.N);
         uend = std::max(uend, o);
     }
     if (op == QMC_OP_INTEGRATE_BWD) {
@@ -549,15 +555,24 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     }
     FineArgs<T> a = fine_args<T>(P, ws, A, ldA, mode == MODE_FUSED ? f : nullptr);
     a.P = dP;
-    dim3 grid(P.root_blocks, P.cg_count, P.reff);
-    QMC_LAUNCH(st, mode == MODE_FUSED ? "k_fine_fwd" : "k_fine_fwd_materialize",
-               launch_fine_fwd<T>(a, P.shape, P.exact, mode == MODE_FUSED ? P.fkind : 0, mode, grid, st));
+    const bool fine_tc = mode == MODE_FUSED && P.fine_tc;
+    if (fine_tc) {
+        if constexpr (std::is_same<T, float>::value) {
+            a.cg_count = P.cg_tc;
+            QMC_LAUNCH(st, "k_fine_fwd_tc", launch_fine_fwd_tc(a, P.fkind, P.tc_pieces, st));
+        }
+    } else {
+        dim3 grid(P.root_blocks, P.cg_count, P.reff);
+        QMC_LAUNCH(st, mode == MODE_FUSED ? "k_fine_fwd" : "k_fine_fwd_materialize",
+                   launch_fine_fwd<T>(a, P.shape, P.exact, mode == MODE_FUSED ? P.fkind : 0, mode, grid, st));
+    }
     if (mode == MODE_FUSED) {
         T* rowsave = reinterpret_cast<T*>(ws + P.off_rowsave);
         double* fpart = reinterpret_cast<double*>(ws + P.off_fpart);
         const double coef_scale = gfac_of(P.fkind, f->params[0]) / ((double)P.reff * (double)P.N);
         QMC_LAUNCH(st, "k_rows_finalize",
-                   launch_rows_finalize<T>(a.rowpart, a.rowmax, P.cg_count, P.N, P.reff, P.fkind, (double)P.tau,
+                   launch_rows_finalize<T>(a.rowpart, a.rowmax, fine_tc ? P.cg_tc : P.cg_count, P.N, P.reff,
+                                           P.fkind, (double)P.tau,
                                            f->params[0], f->params[1], coef_scale, rowsave, rowf, fpart, P.nblk,
                                            ticket, est, st));
     }
@@ -636,9 +651,11 @@ const char* qmc_last_error(void) { return g_err.c_str(); }
 qmc_status qmc_validate_rule(const qmc_rule* rule) { return validate(rule); }
 
 qmc_status qmc_device_status(int clear) {
-    unsigned int word = 0;
+    unsigned int word = 0, word2 = 0;
     QMC_CUDA(cudaDeviceSynchronize());
     QMC_CUDA(tc_error_word(&word, clear != 0));
+    QMC_CUDA(fine_tc_error_word(&word2, clear != 0));
+    word |= word2 << 1;
     if (word) return fail(QMC_ERR_TIMEOUT, "a tensor-core kernel's bounded wait ran out (error word 0x%x)", word);
     return QMC_OK;
 }

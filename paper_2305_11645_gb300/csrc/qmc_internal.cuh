@@ -281,5 +281,9 @@ cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const 
                                   const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
                                   float* part, int reff, int ntiles, int pieces, cudaStream_t st);
 cudaError_t tc_error_word(unsigned int* value, bool clear);
+// fused forward of the S4 fine band on tensor cores; row partials per 128-column group
+int fine_tc_group_cols();
+cudaError_t launch_fine_fwd_tc(const FineArgs<float>& a, int F, int pieces, cudaStream_t st);
+cudaError_t fine_tc_error_word(unsigned int* value, bool clear);
 
 }  // namespace qmc
