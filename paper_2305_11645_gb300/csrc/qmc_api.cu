@@ -192,8 +192,9 @@ struct Plan {
     int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
-    bool fine_tc = false;          // fused forward of the fine band on tensor cores
+    bool fine_tc = false;          // fused forward and adjoint of the fine band on tensor cores
     int cg_tc = 0;                 // its row-partial column groups
+    long long fine_parts_tc = 0;   // band-gradient partials of its adjoint
     bool need_gen = false, need_shift = false, need_pad = false;
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
@@ -318,6 +319,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     // tensor-core tiers: the fused forward of the dyadic band runs on tensor cores (8 roots per tile)
     P.fine_tc = P.tc_pieces != 0 && P.shape == SHAPE_S4 && logn_root >= 3;
     P.cg_tc = (P.tau + fine_tc_group_cols() - 1) / fine_tc_group_cols();
+    P.fine_parts_tc = P.fine_tc ? bwd_tc_partials(P.tau_pad, P.reff, logn_root) : 0;
 
     // backward schedule
     if (op == QMC_OP_INTEGRATE_BWD) {
@@ -452,7 +454,8 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.off_Fchain = o;
         o = align256(o + E * (size_t)P.reff * (size_t)std::max(P.Fchain_per_shift, 1LL));
         P.off_gradpart = o;
-        o = align256(o + E * (size_t)P.reff * P.groups * std::max(P.kf_width, 1) * P.tau_pad);
+        const size_t nparts = std::max<size_t>((size_t)P.reff * P.groups, (size_t)P.fine_parts_tc);
+        o = align256(o + E * nparts * std::max(P.kf_width, 1) * P.tau_pad);
         P.off_partc = o;
         o = align256(o + E * (size_t)std::max(P.partc_elems, 1LL));
         uend = std::max(uend, o);
@@ -602,8 +605,16 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
     a.roots_per_cta = P.roots_per_cta;
     a.groups = P.groups;
     a.kf_actual = P.kf_width;
-    dim3 grid(P.groups, P.passes, P.reff);
-    QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.exact, P.fkind, grid, st));
+    int nfine_part = P.reff * P.groups;
+    if (P.fine_tc) {
+        if constexpr (std::is_same<T, float>::value) {
+            QMC_LAUNCH(st, "k_fine_bwd_tc", launch_fine_bwd_tc(a, P.fkind, P.tc_pieces, st));
+            nfine_part = (int)P.fine_parts_tc;
+        }
+    } else {
+        dim3 grid(P.groups, P.passes, P.reff);
+        QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.exact, P.fkind, grid, st));
+    }
     // coarse block gradients; each level folds the root gradients onto its distinct rows on the fly
     const T* tab = reinterpret_cast<const T*>(ws + P.off_tab);
     T* partc = reinterpret_cast<T*>(ws + P.off_partc);
@@ -633,7 +644,7 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
         o += P.shape == SHAPE_S4 ? kmax_s4[I] : 16;
     }
     QMC_LAUNCH(st, "k_grad_reduce",
-               launch_grad_reduce<T>(a.gradpart, P.reff * P.groups, std::max(P.kf_width, 1), koff, col0, taul, P.JF,
+               launch_grad_reduce<T>(a.gradpart, nfine_part, std::max(P.kf_width, 1), koff, col0, taul, P.JF,
                                      partc, P.chb, P.tau, P.tau_pad, P.s, grad, st));
     return QMC_OK;
 }

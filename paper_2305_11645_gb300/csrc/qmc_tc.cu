@@ -3,13 +3,14 @@
 // and the block gradients dA_e = X_e^T F_e of the adjoint, on tcgen05.mma (kind::f16,
 // bf16 operands, FP32 accumulation in tensor memory).
 //
-// Split tier.  Every FP32 operand v is written as three bf16 pieces
-//     v = v0 + v1 + v2,   v0 = bf16(v), v1 = bf16(v - v0), v2 = bf16(v - v0 - v1)
+// Split tier.  Every FP32 operand v is written exactly as three bf16 pieces
+//     v = v0 + v1 + v2,   v0 = bf16(v) (nearest), v1 = the top 8 bits of v - v0,
+//     v2 = v - v0 - v1,   |v1| <= 2^-9 |v|, |v2| <= 2^-16 |v|
 // (each difference is exact in FP32, so the three pieces hold all 24 bits of v), and a
 // product keeps the six piece products with i + j <= 2:
 //     v w ~ v0 w0 + v0 w1 + v1 w0 + v0 w2 + v1 w1 + v2 w0,
 // the bf16x6 scheme of Henry, Tang and Heinecke (ARITH 2019).  The dropped terms are
-// below 2^-23 |v w|.  All six products accumulate into one FP32 accumulator (bf16 keeps
+// below 2^-24 |v w|.  All six products accumulate into one FP32 accumulator (bf16 keeps
 // the FP32 exponent range, so no operand scaling is needed).
 // Bf16 tier.  One piece, one product: v w ~ bf16(v) bf16(w).
 //

@@ -101,24 +101,39 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 // Split 8 consecutive k of one row into P bf16 pieces and store each piece's 16 bytes
 // (group g of row r) into the tiles tile0 + p * piece_stride.
+// The bf16 pieces of two FP32 values (a in the low, b in the high half of each word).
+// Piece 0 is the round-to-nearest bf16 (one conversion per pair); in the split tier the
+// residual r1 = v - v0 (exact, |r1| <= 2^-9 |v|, at most 16 significant bits) is cut into
+// its top 8 bits v1 (truncation: keep the upper half of the FP32 word) and the exact rest
+// v2 = r1 - v1 (at most 8 significant bits), so v = v0 + v1 + v2 exactly with |v1| <=
+// 2^-9 |v| and |v2| <= 2^-16 |v|.  The truncations are integer byte permutes, which keeps
+// the conversion pipe to one instruction per pair.
+template <int P>
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t (&w)[P]) {
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
+    const uint32_t p0 = *reinterpret_cast<const uint32_t*>(&h0);
+    w[0] = p0;
+    if constexpr (P == 3) {
+        const float ra = a - __uint_as_float(p0 << 16), rb = b - __uint_as_float(p0 & 0xFFFF0000u);
+        const uint32_t ua = __float_as_uint(ra), ub = __float_as_uint(rb);
+        w[1] = __byte_perm(ua, ub, 0x7632);
+        const float sa = ra - __uint_as_float(ua & 0xFFFF0000u), sb = rb - __uint_as_float(ub & 0xFFFF0000u);
+        w[2] = __byte_perm(__float_as_uint(sa), __float_as_uint(sb), 0x7632);
+    }
+}
+
+// Split 8 consecutive k of one row into P bf16 pieces and store each piece's 16 bytes
+// (group g of row r) into the tiles tile0 + p * piece_stride.
 template <int P>
 __device__ __forceinline__ void store_group(unsigned char* tile0, uint32_t piece_stride, int r, int g,
                                             const float* v) {
     uint32_t w[P][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        float a = v[2 * i], b = v[2 * i + 1];
-        const __nv_bfloat162 h0 = __floats2bfloat162_rn(a, b);
-        w[0][i] = *reinterpret_cast<const uint32_t*>(&h0);
-        if constexpr (P == 3) {
-            const float2 f0 = __bfloat1622float2(h0);
-            a -= f0.x; b -= f0.y;                              // exact residuals
-            const __nv_bfloat162 h1 = __floats2bfloat162_rn(a, b);
-            w[1][i] = *reinterpret_cast<const uint32_t*>(&h1);
-            const float2 f1 = __bfloat1622float2(h1);
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(a - f1.x, b - f1.y);
-            w[2][i] = *reinterpret_cast<const uint32_t*>(&h2);
-        }
+        uint32_t q[P];
+        split_pair<P>(v[2 * i], v[2 * i + 1], q);
+#pragma unroll
+        for (int p = 0; p < P; ++p) w[p][i] = q[p];
     }
     const uint32_t off = sw64_off(r, g);
 #pragma unroll
