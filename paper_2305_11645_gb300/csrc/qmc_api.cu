@@ -315,7 +315,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.cr = cr;
         P.cg_count = (P.tau_pad + cr - 1) / cr;
     }
-    P.nblk = (int)((P.N + 255) / 256);
+    P.nblk = (int)((P.N + 255) / 256);          // row blocks of the finalisation (256 rows each)
     // tensor-core tiers: the fused forward of the dyadic band runs on tensor cores (8 roots per tile)
     P.fine_tc = P.tc_pieces != 0 && P.shape == SHAPE_S4 && logn_root >= 3;
     P.cg_tc = (P.tau + fine_tc_group_cols() - 1) / fine_tc_group_cols();

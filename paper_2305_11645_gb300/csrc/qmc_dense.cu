@@ -102,38 +102,112 @@ template cudaError_t launch_coarse_fwd<float>(const float*, long long, const flo
 template cudaError_t launch_coarse_fwd<double>(const double*, long long, const double*, int, int, const Chain&,
                                                double*, long long, int, cudaStream_t);
 
-// S[r][t/4][rho][t%4] = sum_e B_e[r][t/4][rho mod n_e][t%4], rho < n_root
+// S[r][t/4][rho][t%4] = sum_e B_e[r][t/4][rho mod n_e][t%4], rho < n_root (Algorithm 2's
+// periodic tiling of the coarse block products onto the root rows).
+// A thread owns one group of four columns and one node rho' < n_top = n_root / 2^D: the
+// 2^D root rows rho' + q n_top of its subtree share their rows in every coarse entry with
+// n_e >= n_top (rho' + (q mod n_e/n_top) n_top, 2^D n_e / n_root distinct rows), and one
+// row rho' mod n_e of every coarser entry.  Each entry row is loaded once per thread and
+// added to all the root rows it tiles; consecutive threads take consecutive rho', so
+// every load and store of a warp is contiguous.
+template <class T> struct V4 { T x, y, z, w; };
+
 template <class T>
-__global__ void k_chain_sum(const T* __restrict__ B, long long B_stride, const __grid_constant__ Chain ch,
-                            T* __restrict__ S, long long S_stride, int logn_root, int tau_pad) {
-    // one group of four columns of one root row per thread; the entries' loads are independent
-    const int r = blockIdx.y;
-    const long long n_root = 1LL << logn_root;
-    const long long total = n_root * (tau_pad >> 2);
-    const long long e4 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e4 >= total) return;
-    const T* Br = B + (long long)r * B_stride;
-    const long long t4 = e4 >> logn_root, rho = e4 & (n_root - 1);
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll 4
-    for (int e = 0; e < ch.count; ++e) {
-        const T* p = Br + ch.boff[e] + ((t4 << ch.logn[e]) << 2) + ((rho & ((1LL << ch.logn[e]) - 1)) << 2);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[c] += __ldg(p + c);
+__device__ __forceinline__ V4<T> ld4(const T* p) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        return {v.x, v.y, v.z, v.w};
+    } else {
+        const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+        return {a.x, a.y, b.x, b.y};
     }
-    T* o = S + (long long)r * S_stride + (e4 << 2);
+}
+template <class T>
+__device__ __forceinline__ void st4(T* p, const V4<T>& v) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(v.x, v.y, v.z, v.w);
+    } else {
+        reinterpret_cast<double2*>(p)[0] = make_double2(v.x, v.y);
+        reinterpret_cast<double2*>(p)[1] = make_double2(v.z, v.w);
+    }
+}
+template <class T>
+__device__ __forceinline__ void add4(V4<T>& a, const V4<T>& b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
+
+// add an entry at depth d < D below the top (2^(D-d) distinct rows) to the subtree's root rows
+template <class T, int D, int d>
+__device__ __forceinline__ void tile_entry(V4<T> (&v)[1 << D], const T* rowp, long long rstep) {
+    constexpr int nd = 1 << (D - d);
+    V4<T> w[nd];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) o[c] = acc[c];
+    for (int q = 0; q < nd; ++q) w[q] = ld4<T>(rowp + q * rstep);
+#pragma unroll
+    for (int q = 0; q < (1 << D); ++q) add4(v[q], w[q & (nd - 1)]);
+}
+
+template <class T, int D>
+__global__ void __launch_bounds__(128) k_chain_sum(const T* __restrict__ B, long long B_stride,
+                                                   const __grid_constant__ Chain ch, T* __restrict__ S,
+                                                   long long S_stride, int logn_root, int tau_pad) {
+    const int logn_top = logn_root - D;
+    const long long n_top = 1LL << logn_top;
+    const long long rho = (long long)blockIdx.x * 128 + threadIdx.x;
+    const long long t4 = blockIdx.y;
+    const int r = blockIdx.z;
+    if (rho >= n_top) return;
+    const T* Br = B + (long long)r * B_stride;
+    V4<T> v[1 << D];
+#pragma unroll
+    for (int q = 0; q < (1 << D); ++q) v[q] = {T(0), T(0), T(0), T(0)};
+    for (int e = 0; e < ch.count; ++e) {
+        const int logn = ch.logn[e];
+        const T* be = Br + ch.boff[e] + ((t4 << logn) << 2);
+        const int d = logn_root - logn;                 // depth of the entry below the root level
+        if (d >= D) {                                   // at or above the subtree's top: one row
+            const V4<T> w = ld4<T>(be + ((rho & ((1LL << logn) - 1)) << 2));
+#pragma unroll
+            for (int q = 0; q < (1 << D); ++q) add4(v[q], w);
+            continue;
+        }
+        const T* rowp = be + (rho << 2);
+        const long long rstep = n_top << 2;
+        switch (d) {                                    // 2^(D-d) distinct rows below the top
+            case 0: tile_entry<T, D, 0>(v, rowp, rstep); break;
+            case 1: if constexpr (D > 1) tile_entry<T, D, 1>(v, rowp, rstep); break;
+            case 2: if constexpr (D > 2) tile_entry<T, D, 2>(v, rowp, rstep); break;
+            case 3: if constexpr (D > 3) tile_entry<T, D, 3>(v, rowp, rstep); break;
+            default: break;
+        }
+    }
+    T* o = S + (long long)r * S_stride + ((t4 << logn_root) << 2) + (rho << 2);
+#pragma unroll
+    for (int q = 0; q < (1 << D); ++q) st4<T>(o + ((long long)q << logn_top << 2), v[q]);
 }
 
 template <class T>
 cudaError_t launch_chain_sum(const T* B, long long B_stride, const Chain& ch, T* S, long long S_stride, int logn_root,
                              int tau_pad, int reff, cudaStream_t st) {
-    const long long total = (1LL << logn_root) * (tau_pad / 4);
-    const long long blocks = (total + 255) / 256;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)blocks, reff);
-    k_chain_sum<T><<<grid, 256, 0, st>>>(B, B_stride, ch, S, S_stride, logn_root, tau_pad);
+    // 2^D groups of 4 values per thread in registers: the deepest subtree that still leaves
+    // about a thousand threads per SM to hide the loads' latency
+    constexpr int DMAX = sizeof(T) == 4 ? 4 : 3;
+    int D = logn_root < DMAX ? logn_root : DMAX;
+    while (D > 0 && ((1LL << (logn_root - D)) * (tau_pad / 4) * reff) < 152LL * 1024) --D;
+    const long long n_top = 1LL << (logn_root - D);
+    dim3 grid((unsigned)((n_top + 127) / 128), (unsigned)(tau_pad / 4), (unsigned)reff);
+    switch (D) {
+        case 0: k_chain_sum<T, 0><<<grid, 128, 0, st>>>(B, B_stride, ch, S, S_stride, logn_root, tau_pad); break;
+        case 1: k_chain_sum<T, 1><<<grid, 128, 0, st>>>(B, B_stride, ch, S, S_stride, logn_root, tau_pad); break;
+        case 2: k_chain_sum<T, 2><<<grid, 128, 0, st>>>(B, B_stride, ch, S, S_stride, logn_root, tau_pad); break;
+        case 3: k_chain_sum<T, 3><<<grid, 128, 0, st>>>(B, B_stride, ch, S, S_stride, logn_root, tau_pad); break;
+        case 4:
+            if constexpr (DMAX >= 4) {
+                k_chain_sum<T, 4><<<grid, 128, 0, st>>>(B, B_stride, ch, S, S_stride, logn_root, tau_pad);
+                break;
+            }
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 template cudaError_t launch_chain_sum<float>(const float*, long long, const Chain&, float*, long long, int, int, int,
@@ -157,21 +231,41 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return s;
 }
 
+// sum over the CTA in a fixed order: warp shuffles in T, then the 8 warp sums in double
+template <class T>
+__device__ __forceinline__ double block_sum_t(T v, double* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[warp] = (double)v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    __syncthreads();
+    return s;
+}
+
+constexpr int kRowsPerThread = 1;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ rowpart, const T* __restrict__ rowmax,
                                                        int cg_count, long long N, int F, double tau, double c,
                                                        double K, double coef_scale, T* __restrict__ rowsave,
                                                        T* __restrict__ rowf, double* __restrict__ fpart, int nblk,
                                                        unsigned int* ticket, double* __restrict__ est) {
-    // Per-row arithmetic in T (the row sums are T partials); only the sum over rows is kept in
-    // double.  The call payoff's kink test u/tau > K is taken in double, without a division.
+    // Per-row arithmetic in T (the row sums are T partials).  The CTA's rows are summed with
+    // warp shuffles in T and the warp sums in double; the mean over the CTAs is in double.
+    // The call payoff's kink test u/tau > K is taken in double, without a division.
     __shared__ double sh[32];
     const int r = blockIdx.y;
-    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const T inv_tau = (T)(1.0 / tau);
-    double f = 0.0;
-    if (k < N) {
-        T u;
+    T fsum = T(0);
+#pragma unroll
+    for (int i = 0; i < kRowsPerThread; ++i) {
+        const long long k = ((long long)blockIdx.x * kRowsPerThread + i) * blockDim.x + threadIdx.x;
+        if (k >= N) break;
+        T u, fv;
         const T* rp = rowpart + (long long)r * cg_count * N + k;
         if (F == F_LOGSUMEXP) {
             // the partials hold (max, sum 2^(v - max)) of v = y log2 e
@@ -188,7 +282,7 @@ __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ row
 #pragma unroll 8
             for (int g = 0; g < cg_count; ++g) u += rp[(long long)g * N];
         }
-        T fv, gp;
+        T gp;
         switch (F) {
             case F_LINEAR_MEAN: case F_MEAN_COS: case F_PDE_INV_SQ: fv = u * inv_tau; gp = inv_tau; break;
             case F_CALL_MEAN_EXP: {
@@ -200,15 +294,15 @@ __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ row
             case F_GAUSS_NORM2: fv = exp(T(-0.5) * u * inv_tau); gp = T(-0.5) * inv_tau * fv; break;
             default: fv = u; gp = T(1); break;     // log-sum-exp: u is log sum exp(y)
         }
-        f = (double)fv;
         if (rowsave) {
             // what the backward needs of this row: g'(u) gfac/(R N) and log2 e * u
             rowsave[2 * ((long long)r * N + k)] = gp * (T)coef_scale;
             rowsave[2 * ((long long)r * N + k) + 1] = u * (T)kLog2e;
         }
         if (rowf) rowf[(long long)r * N + k] = fv;
+        fsum += fv;
     }
-    const double s = block_sum(f, sh);
+    const double s = block_sum_t<T>(fsum, sh);
     if (!est) {
         if (threadIdx.x == 0) fpart[(long long)r * nblk + blockIdx.x] = s;
         return;
@@ -377,44 +471,45 @@ template cudaError_t launch_coarse_grad<double>(const double*, long long, const 
                                                 long long, int, const Chain&, double*, int, int, cudaStream_t);
 
 // Hierarchical fold of the root gradients (the adjoint of Algorithm 2's tiling):
-// F_{I+1}[rho] = F_I[rho] + F_I[rho + n_{I+1}].  A CTA (one warp) owns a top node
-// rho' < n_top of level JF+depth and 128 columns; the 2^depth root rows
-// rho' + q n_top of its subtree are held in shared memory, each lane folds its own
-// four columns level by level and writes the folded rows of every coarse level.
-template <class T>
-__global__ void __launch_bounds__(32) k_fold_tree(const T* __restrict__ Froot, long long root_stride,
-                                                  T* __restrict__ Fchain, long long chain_stride,
-                                                  const FoldLevels fl, int tau_pad) {
-    constexpr int kMaxDepth = sizeof(T) == 8 ? 5 : 6;     // 32 KB of shared memory either way
-    __shared__ __align__(16) T S[(1 << kMaxDepth) * 32 * 4];
-    const int lane = threadIdx.x;
+// F_{I+1}[rho] = F_I[rho] + F_I[rho + n_{I+1}].  A thread owns one column t and one top
+// node rho' < n_top of level JF+D: it loads the 2^D root rows rho' + q n_top of its subtree
+// (coalesced over the warp's consecutive columns, all loads in flight at once), folds them
+// level by level in registers and writes the folded rows of every wanted level.
+// one level of the fold, d = 1..D (a compile-time recursion keeps every index static)
+template <class T, int D, int d>
+struct FoldStep {
+    static __device__ __forceinline__ void run(T (&v)[1 << D], T* Fchain, const FoldLevels& fl, long long base,
+                                               long long rstep) {
+        constexpr int half = 1 << (D - d);
+        T* dst = Fchain + fl.off[d] + base;
+        const bool want = fl.want[d] != 0;
+#pragma unroll
+        for (int q = 0; q < half; ++q) {
+            v[q] += v[q + half];
+            if (want) dst[q * rstep] = v[q];
+        }
+        FoldStep<T, D, d + 1>::run(v, Fchain, fl, base, rstep);
+    }
+};
+template <class T, int D>
+struct FoldStep<T, D, D + 1> {
+    static __device__ __forceinline__ void run(T (&)[1 << D], T*, const FoldLevels&, long long, long long) {}
+};
+
+template <class T, int D>
+__global__ void __launch_bounds__(128) k_fold_tree(const T* __restrict__ Froot, long long root_stride,
+                                                   T* __restrict__ Fchain, long long chain_stride,
+                                                   const FoldLevels fl, int tau_pad) {
     const long long rho = blockIdx.x;
-    const int t = blockIdx.y * 128 + lane * 4;
+    const int t = blockIdx.y * 128 + threadIdx.x;
     const int r = blockIdx.z;
     if (t >= tau_pad) return;
-    const int rows = 1 << fl.depth;
-    T* Sl = S + lane * 4;
+    const long long rstep = ((long long)1 << fl.logn_top) * tau_pad;     // row stride of the subtree
     const T* src = Froot + (long long)r * root_stride + rho * tau_pad + t;
-#pragma unroll 8
-    for (int q = 0; q < rows; ++q) {
-        const T* p = src + (((long long)q << fl.logn_top) * tau_pad);
+    T v[1 << D];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Sl[q * 128 + c] = p[c];
-    }
-    int cur = rows;
-    for (int d = 1; d <= fl.depth; ++d) {
-        const int half = cur >> 1;
-        T* dst = Fchain + fl.off[d] + (long long)r * chain_stride + rho * tau_pad + t;
-        for (int q = 0; q < half; ++q) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const T v = Sl[q * 128 + c] + Sl[(q + half) * 128 + c];
-                Sl[q * 128 + c] = v;
-                if (fl.want[d]) dst[(((long long)q << fl.logn_top) * tau_pad) + c] = v;
-            }
-        }
-        cur = half;
-    }
+    for (int q = 0; q < (1 << D); ++q) v[q] = __ldg(src + q * rstep);
+    FoldStep<T, D, 1>::run(v, Fchain, fl, (long long)r * chain_stride + rho * tau_pad + t, rstep);
 }
 
 template <class T>
@@ -422,7 +517,20 @@ cudaError_t launch_fold_tree(const T* Froot, long long root_stride, T* Fchain, l
                              const FoldLevels& fl, int tau_pad, int reff, cudaStream_t st) {
     if (fl.depth <= 0) return cudaSuccess;
     dim3 grid((unsigned)(1LL << fl.logn_top), (tau_pad + 127) / 128, reff);
-    k_fold_tree<T><<<grid, 32, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad);
+    switch (fl.depth) {
+        case 1: k_fold_tree<T, 1><<<grid, 128, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad); break;
+        case 2: k_fold_tree<T, 2><<<grid, 128, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad); break;
+        case 3: k_fold_tree<T, 3><<<grid, 128, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad); break;
+        case 4: k_fold_tree<T, 4><<<grid, 128, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad); break;
+        case 5: k_fold_tree<T, 5><<<grid, 128, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad); break;
+        case 6:
+            if constexpr (sizeof(T) == 4) {
+                k_fold_tree<T, 6><<<grid, 128, 0, st>>>(Froot, root_stride, Fchain, chain_stride, fl, tau_pad);
+                break;
+            }
+            return cudaErrorInvalidValue;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 template cudaError_t launch_fold_tree<float>(const float*, long long, float*, long long, const FoldLevels&, int, int,
@@ -435,35 +543,68 @@ struct FineCols {
     int koff[4], col0[4], tau[4];
 };
 
+// dA[j][t] = sum of column j's gradient partials (the fine band's, or the coarse entry's
+// k-splits).  A CTA owns column j: warp w sums the partials p = w, w + 8, ... for 512
+// columns t at a time (16 per lane, coalesced, all loads of a partial in flight together),
+// and the eight warp sums are added in a fixed order.
 template <class T>
-__global__ void k_grad_reduce(const T* __restrict__ gradpart_f, const FineCols fc, const T* __restrict__ part_c,
-                              const __grid_constant__ Chain ch, int tau, int tau_pad, int s, T* __restrict__ grad) {
-    const long long total = (long long)s * tau;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(e / tau);
-        const int t = (int)(e - (long long)j * tau);
-        T v = T(0);
-        bool done = false;
-        for (int I = 0; I < fc.jf && !done; ++I) {
-            if (fc.tau[I] > 0 && j >= fc.col0[I] && j < fc.col0[I] + fc.tau[I]) {
-                const int jl = fc.koff[I] + (j - fc.col0[I]);
-#pragma unroll 8
-                for (int p = 0; p < fc.nfine_part; ++p)
-                    v += gradpart_f[((long long)p * fc.kf_width + jl) * tau_pad + t];
-                done = true;
+__global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradpart_f, const FineCols fc,
+                                                     const T* __restrict__ part_c, const __grid_constant__ Chain ch,
+                                                     int tau, int tau_pad, int s, T* __restrict__ grad) {
+    __shared__ T red[8][512];
+    const int j = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // where column j's partials are: base + p * stride, p < count
+    const T* base = nullptr;
+    long long stride = 0;
+    int count = 0;
+    for (int I = 0; I < fc.jf; ++I)
+        if (fc.tau[I] > 0 && j >= fc.col0[I] && j < fc.col0[I] + fc.tau[I]) {
+            base = gradpart_f + (long long)(fc.koff[I] + (j - fc.col0[I])) * tau_pad;
+            stride = (long long)fc.kf_width * tau_pad;
+            count = fc.nfine_part;
+        }
+    for (int q = 0; q < ch.count; ++q)
+        if (j >= ch.col0[q] && j < ch.col0[q] + ch.tau[q]) {
+            base = part_c + ch.poff[q] + (long long)(j - ch.col0[q]) * tau_pad;
+            stride = (long long)ch.tau[q] * tau_pad;
+            count = ch.split[q];
+        }
+    for (int t0 = 0; t0 < tau; t0 += 512) {
+        T v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = T(0);
+        // four partials per round: 64 loads in flight per lane
+        int p = warp;
+        for (; p + 24 < count; p += 32) {
+            T w[4][16];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const T* bp = base + (long long)(p + 8 * h) * stride + t0 + lane;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) w[h][c] = t0 + 32 * c + lane < tau ? __ldg(bp + 32 * c) : T(0);
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) v[c] += (w[0][c] + w[1][c]) + (w[2][c] + w[3][c]);
+        }
+        for (; p < count; p += 8) {
+            const T* bp = base + (long long)p * stride + t0 + lane;
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                if (t0 + 32 * c + lane < tau) v[c] += __ldg(bp + 32 * c);
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) red[warp][32 * c + lane] = v[c];
+        __syncthreads();
+        for (int i = threadIdx.x; i < 512; i += 256) {
+            if (t0 + i < tau) {
+                T acc = T(0);
+#pragma unroll
+                for (int w = 0; w < 8; ++w) acc += red[w][i];
+                grad[(long long)j * tau + t0 + i] = acc;
             }
         }
-        for (int q = 0; q < ch.count && !done; ++q) {
-            if (j >= ch.col0[q] && j < ch.col0[q] + ch.tau[q]) {
-                const int jj = j - ch.col0[q];
-#pragma unroll 8
-                for (int sp = 0; sp < ch.split[q]; ++sp)
-                    v += part_c[ch.poff[q] + ((long long)sp * ch.tau[q] + jj) * tau_pad + t];
-                done = true;
-            }
-        }
-        grad[e] = v;
+        __syncthreads();
     }
 }
 
@@ -480,10 +621,7 @@ cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width
         fc.col0[i] = i < jf ? col0_lev[i] : 0;
         fc.tau[i] = i < jf ? tau_lev[i] : 0;
     }
-    long long total = (long long)s * tau;
-    long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_grad_reduce<T><<<(unsigned)blocks, 256, 0, st>>>(gradpart_f, fc, part_c, ch, tau, tau_pad, s, grad);
+    k_grad_reduce<T><<<(unsigned)s, 256, 0, st>>>(gradpart_f, fc, part_c, ch, tau, tau_pad, s, grad);
     return cudaGetLastError();
 }
 template cudaError_t launch_grad_reduce<float>(const float*, int, int, const int*, const int*, const int*, int,

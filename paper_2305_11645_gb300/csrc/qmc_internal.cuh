@@ -96,8 +96,11 @@ template <> struct Tr<float> {
         switch (tr) {
             case T_CENTER: return i32_to_f32((int)(x ^ 0x80000000u)) * two_m32;
             case T_TENT: return (x < 0x80000000u) ? u32_to_f32(x) * two_m31 : u32_to_f32(cmp) * two_m31;
-            case T_INV_NORMAL:
-                return (x < 0x80000000u) ? normcdfinvf(u32_to_f32(x) * two_m32) : -normcdfinvf(u32_to_f32(cmp) * two_m32);
+            case T_INV_NORMAL: {      // one quantile call on the half nearer 0, then the sign
+                const bool low = x < 0x80000000u;
+                const float z = normcdfinvf(u32_to_f32(low ? x : cmp) * two_m32);
+                return low ? z : -z;
+            }
             default: return u32_to_f32(x) * two_m32;
         }
     }
@@ -110,8 +113,11 @@ template <> struct Tr<double> {
         switch (tr) {
             case T_CENTER: return i32_to_f64((int)(x ^ 0x80000000u)) * two_m32;
             case T_TENT: return (x < 0x80000000u) ? u32_to_f64(x) * two_m31 : u32_to_f64(cmp) * two_m31;
-            case T_INV_NORMAL:
-                return (x < 0x80000000u) ? normcdfinv(u32_to_f64(x) * two_m32) : -normcdfinv(u32_to_f64(cmp) * two_m32);
+            case T_INV_NORMAL: {
+                const bool low = x < 0x80000000u;
+                const double z = normcdfinv(u32_to_f64(low ? x : cmp) * two_m32);
+                return low ? z : -z;
+            }
             default: return u32_to_f64(x) * two_m32;
         }
     }

@@ -6,10 +6,16 @@
 namespace qmc {
 
 // Level of table index g (levels are few; linear scan over the prefix sums).
+// the level I with lev_tab[I] <= g < lev_tab[I + 1] (binary search; empty levels have
+// lev_tab[I] == lev_tab[I + 1] and are never returned for a valid g)
 __device__ __forceinline__ int level_of(const DevRule& R, long long g) {
-    int I = 0;
-    while (I + 1 < R.nlev && g >= R.lev_tab[I + 1]) ++I;
-    return I;
+    int lo = 0, hi = R.nlev - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (g >= R.lev_tab[mid]) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // Column j's level: the largest I with lev_col0[I] <= j among non-empty levels.
