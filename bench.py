@@ -3,11 +3,14 @@
 A step is one pass of the whole hot path over the Gaussian-expectation workload
 (reduced rank-1 lattice, b=2, m=16 -> N=65536, s=tau=512, w_j=min(floor(log2(j+1)),10),
 one random shift, inverse-normal transform, A=L^T of the exp(-|t_i-t_j|/0.1) covariance,
-f=max(mean_t exp(0.2 y_t)-1,0), FP32 tier): point generation, transform, coarse block
-products, the fused periodic broadcast-accumulate with f and the mean, and the folded
-adjoint dQ/dA.  Metric: x_k^T A outputs per second, N*tau*R / step time.
+f=max(mean_t exp(0.2 y_t)-1,0)): point generation, transform, coarse block products, the
+fused periodic broadcast-accumulate with f and the mean, and the folded adjoint dQ/dA.
+Metric: x_k^T A outputs per second, N*tau*R / step time.  The headline tier is the split
+tier (bf16x6 tensor-core products, FP32 elsewhere); the FP32 and plain-bf16 tiers are
+timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision split|fp32|bf16]
 """
 from __future__ import annotations
 
@@ -31,9 +34,10 @@ METRIC = "x_k^T A products/sec (N*tau/s) vs dense X*A on same GB300, at stated r
 L2_FLUSH_BYTES = 512 << 20        # > 129 MB L2
 SM_COUNT = 152
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on this workload, from the
-# ncu capture summarised in profiles/c2_step_kernels_full.md (cold cache); a kernel missing here
-# has changed since its counters were taken and reports traffic null
-TRAFFIC_BYTES = {"k_fine_bwd": 10.0e6}
+# ncu captures summarised under profiles/ (cold cache); a kernel missing here has changed since
+# its counters were taken and reports traffic null
+TRAFFIC_BYTES = {}
+TIERS = ("split", "fp32", "bf16")
 
 
 def parse():
@@ -42,6 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=list(TIERS), default="split")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense X*A comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     return ap.parse_args()
@@ -175,6 +180,39 @@ def fine_bwd_work(p):
     return fp32, outs * mufu_h
 
 
+def tc_work(p, name, pieces):
+    """Tensor-core work of one launch of a fine-band kernel of the split (pieces=3) or bf16
+    (pieces=1) tier: MMA flops as issued (the piece products included) and MUFU ops.
+    Forward: per 128-row x 256-column tile, NP+P MMAs of 128x256x16 (NP = 6 / 1 piece products
+    of X_f A_f, P products E S).  Adjoint: per 128 x 128 tile, the same recomputation with
+    N = 128 plus 8 K-steps x P MMAs of 128 x 32P x 16 (G^T [W_0|W_1|W_2])."""
+    n_root = p.N // 16
+    outs = p.N * p.tau * p.R_eff
+    np_ = 6 if pieces == 3 else 1
+    tau_pad = (p.tau + 3) // 4 * 4
+    if name == "k_fine_fwd_tc":
+        nt = 256
+        tiles = p.R_eff * (n_root // 8) * math.ceil(tau_pad / nt)
+        fma = tiles * (np_ + pieces) * 128 * nt * 16
+    else:
+        nt = 128
+        tiles = p.R_eff * (n_root // 8) * math.ceil(tau_pad / nt)
+        fma = tiles * ((np_ + pieces) * 128 * nt * 16 + 8 * pieces * 128 * 32 * pieces * 16)
+    _, mufu_h = H_OPS[p.f_kind]
+    return 2.0 * fma, outs * mufu_h
+
+
+def tc_roofline(flops, mufu_ops, seconds, clock_mhz, peak_tflops):
+    """Tensor pipe (measured dense bf16 peak) or MUFU (16 lanes/SM/clk), whichever bounds."""
+    p_mufu = SM_COUNT * 16 * clock_mhz * 1e6
+    t_tc, t_mufu = flops / (peak_tflops * 1e12), mufu_ops / p_mufu
+    if t_tc >= t_mufu:
+        return {"bound": "tensor", "achieved": flops / seconds / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": t_tc / seconds}
+    return {"bound": "alu", "pipe": "mufu", "achieved": mufu_ops / seconds / 1e9, "peak": p_mufu / 1e9,
+            "unit": "Gop/s", "frac": t_mufu / seconds}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -214,13 +252,17 @@ def run_ours(args, dist, rank, world):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     # the step as a user runs it repeatedly: one CUDA graph of the forward and backward launches
-    integ = api.Integrator(rule, A, f, backward=True, graph=True)
-    eager = api.Integrator(rule, A, f, backward=True, graph=False)
+    prec = args.precision
+    integ = api.Integrator(rule, A, f, backward=True, graph=True, precision=prec)
+    eager = api.Integrator(rule, A, f, backward=True, graph=False, precision=prec)
+    others = {t: api.Integrator(rule, A, f, backward=True, graph=True, precision=t) for t in TIERS if t != prec}
     step = integ.run
 
     for _ in range(args.warmup):
         step()
         eager.run()
+        for o in others.values():
+            o.run()
     torch.cuda.synchronize()
 
     def timed(fn, trace=False, prequeue=False):
@@ -254,6 +296,9 @@ def run_ours(args, dist, rank, world):
     outputs = p.N * p.tau * p.R_eff
     value = world * outputs / (ms_max / 1e3)
     eager_ms = statistics.mean(timed(eager.run)[0])
+    tier_ms = {prec: ms}
+    for t, o in others.items():
+        tier_ms[t] = statistics.mean(timed(o.run)[0])
 
     # the same steps launched eagerly with the library's per-kernel events, the stream pre-queued
     # so each pair of events brackets device time only (roofline of the dominant kernel)
@@ -264,14 +309,21 @@ def run_ours(args, dist, rank, world):
     clk = clock_info["sm_mhz"] or mp.get("sm_max_mhz", 2070.0)
     name, (cnt, tot) = top
     per_launch = tot / cnt / 1e3
-    if name == "k_fine_bwd":
-        w32, wmu = fine_bwd_work(p)
+    if name.endswith("_tc"):
+        fl, wmu = tc_work(p, name, 3 if prec == "split" else 1)
+        roof = tc_roofline(fl, wmu, per_launch, clk, mp["bf16_tflops"])
+        roof["peak_source"] = (f"{peak_src} dense bf16 burst peak (MEASURED_PEAKS.json bf16_tflops) for the tensor "
+                               f"pipe; MUFU from {SM_COUNT} SMs x 16 lanes x median SM clock {clk:.0f} MHz")
+        roof["work"] = {"mma_flops": fl, "mufu_ops": wmu}
     else:
-        w32, wmu = fine_fwd_work(p)
-    roof = alu_roofline(w32, wmu, per_launch, clk)
-    roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": TRAFFIC_BYTES.get(name),
-                 "peak_source": f"derived from {SM_COUNT} SMs x pipe lanes x median SM clock {clk:.0f} MHz "
-                                f"(sampled during the timed region)"})
+        if name == "k_fine_bwd":
+            w32, wmu = fine_bwd_work(p)
+        else:
+            w32, wmu = fine_fwd_work(p)
+        roof = alu_roofline(w32, wmu, per_launch, clk)
+        roof["peak_source"] = (f"derived from {SM_COUNT} SMs x pipe lanes x median SM clock {clk:.0f} MHz "
+                               f"(sampled during the timed region)")
+    roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": TRAFFIC_BYTES.get(name)})
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in sorted(kern.items())}
 
     # end to end through the public API with host buffers: H2D of A, D2H of the estimates and dQ/dA
@@ -296,11 +348,12 @@ def run_ours(args, dist, rank, world):
 
     result = {"metric": METRIC, "value": value, "unit": "outputs/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-              "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "vs_baseline": None, "dtype": {"split": "bf16x6+f32", "fp32": "f32", "bf16": "bf16+f32"}[prec],
+              "data": "synthetic",
               "config": {"workload": "c2 Gaussian expectation: reduced rank-1 lattice b=2 m=16 (N=65536), "
                                      "s=tau=512, w_j=min(floor(log2(j+1)),10), 1 odd 32-bit shift, inverse-normal "
                                      "transform, A=L^T (exp covariance), f=max(mean exp(0.2y)-1,0)",
-                         "N": p.N, "s": p.s, "tau": p.tau, "R": p.R_eff, "precision": "fp32",
+                         "N": p.N, "s": p.s, "tau": p.tau, "R": p.R_eff, "precision": prec,
                          "step": "qmc_integrate + qmc_integrate_backward (reuse forward workspace), "
                                  "replayed as one CUDA graph (api.Integrator)",
                          "l2": "flushed before every timed step (512 MiB write, untimed)",
@@ -312,7 +365,14 @@ def run_ours(args, dist, rank, world):
     est, grad = step()
     torch.cuda.synchronize()
     if rank == 0:
-        result["accuracy"] = accuracy(p, est, grad, args)
+        result["accuracy"] = accuracy(p, est, grad, args, prec)
+        tiers = {}
+        for t in TIERS:
+            e_t, g_t = (est, grad) if t == prec else others[t].run()
+            torch.cuda.synchronize()
+            tiers[t] = {"ms_per_step": tier_ms[t], "value": outputs / (tier_ms[t] / 1e3),
+                        **accuracy(p, e_t, g_t, args, t)}
+        result["tiers"] = tiers
         if not args.no_dense:
             result["dense_xa"] = dense_baseline(p, rule, A, args, flush, stream)
         if not args.no_cpu:
@@ -331,12 +391,17 @@ def oracle_full(p):
     return _ORACLE_CACHE["full"]
 
 
-def accuracy(p, est, grad, args):
+# stated tolerances on the estimate (relative) and the gradient (max-norm relative) per tier
+TOLERANCE = {"split": (1e-6, 2e-5), "fp32": (2e-5, 2e-5), "bf16": (2e-3, 2e-2)}
+
+
+def accuracy(p, est, grad, args, tier):
     mean, G = oracle_full(p)
     e = est.cpu().numpy()[-1]
     g = grad.double().cpu().numpy()
     return {"estimate": float(e), "oracle_estimate": float(mean), "estimate_rel_err": float(abs(e - mean) / abs(mean)),
-            "grad_rel_err": float(np.max(np.abs(g - G)) / np.max(np.abs(G))), "tolerance": 2e-5}
+            "grad_rel_err": float(np.max(np.abs(g - G)) / np.max(np.abs(G))),
+            "tolerance": {"estimate": TOLERANCE[tier][0], "grad": TOLERANCE[tier][1]}}
 
 
 def dense_baseline(p, rule, A, args, flush, stream):
