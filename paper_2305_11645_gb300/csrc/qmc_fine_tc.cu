@@ -48,7 +48,8 @@ namespace {
 constexpr int EPI_WARPS = 8, PROD_WARPS = 4;                 // forward
 constexpr int THREADS = (EPI_WARPS + PROD_WARPS + 1) * 32;
 constexpr int EPI_WARPS_B = 16;                               // adjoint: 4 warps per TMEM lane quarter
-constexpr int THREADS_B = (EPI_WARPS_B + PROD_WARPS + 1) * 32;
+constexpr int DRAIN_WARPS = 4;                                // adjoint: one per lane quarter
+constexpr int THREADS_B = (EPI_WARPS_B + DRAIN_WARPS + PROD_WARPS + 1) * 32;
 constexpr int kRootsPerTile = 8;        // x 16 leaves = 128 rows per tile
 constexpr int NT_FWD = 256, NT_BWD = 128;
 
@@ -63,9 +64,6 @@ struct Stages {
     static constexpr uint32_t SST = XST + 64 * 8 * 4;         // NTT columns x 8 roots
     static constexpr uint32_t END = SST + NTT * 8 * 4;
 };
-
-// bits 15/16 of the instruction descriptor: A / B read as MN-major
-__device__ __forceinline__ uint32_t idesc_bf16_mn(uint32_t n) { return idesc_bf16(n) | (1u << 15) | (1u << 16); }
 
 // descriptor of a 64-byte-swizzled MN-major operand: atoms of 8 K-rows x 32 MN-elements
 // (512 B), K-groups sbo bytes apart, MN-groups of 32 elements lbo bytes apart
@@ -86,6 +84,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+// MMA with the A operand in tensor memory (16-bit elements packed two per 32-bit column)
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// 8 consecutive 32-bit columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                    "r"(r[7]) : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
@@ -95,6 +109,22 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 // The producers' barrier (named barrier 1) with an OR over the threads: every producer takes
 // the same decision to stop, so none is left waiting at a barrier the others have quit.
 __device__ __forceinline__ void prod_sync() { asm volatile("bar.sync 1, %0;" :: "n"(PROD_WARPS * 32) : "memory"); }
+
+// The four epilogue warps of one TMEM lane quarter (named barriers 2..5) with an OR of a flag.
+__device__ __forceinline__ bool quarter_sync_or(int quarter, bool v) {
+    uint32_t r;
+    const uint32_t x = (uint32_t)v;
+    switch (quarter) {
+#define QMC_QSYNC(Q) \
+        case Q: asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t" \
+                             "bar.red.or.pred q, " #Q " + 2, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}" \
+                             : "=r"(r) : "r"(x) : "memory"); break;
+        QMC_QSYNC(0) QMC_QSYNC(1) QMC_QSYNC(2) QMC_QSYNC(3)
+#undef QMC_QSYNC
+        default: r = 1;
+    }
+    return r != 0;
+}
 __device__ __forceinline__ bool prod_sync_or(bool v) {
     uint32_t r;
     asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
@@ -365,43 +395,49 @@ __global__ void __launch_bounds__(THREADS, 1) k_fine_fwd_tc(const FineArgs<float
 }
 
 // ==========================================================================================
-// Adjoint: 128 columns per tile.
-// TMEM: forward accumulators at columns 0 and 128 (128 each), backward accumulators at 256
-// and 256 + 32 P (32 P each: block j of 32 columns holds G W_j, m < 16 the band gradient,
-// 16 + i the root gradient of root rho0 + i).
-// G^T tile (A operand of D' = G^T W), MN-major with the 64-byte swizzle: element (t, l) at
-//   (t / 32) 8192 + (l / 8) 512 + (l % 8) 64 + (((t % 32) / 8) ^ ((l % 8) / 2)) 16 + (t % 8) 2.
-// Barriers (phases per tile): full/empty (producer stages), accf/acce (forward accumulators),
-// gready (G^T written, count 256), bwdf/bwde (backward accumulators).
-// The MMA thread issues the forward pair of tile i+1 before it waits for G^T of tile i, so
-// the recomputation runs under the epilogue's work on the previous tile.  A stage is
-// released only after the backward MMAs, which read its W as well.
+// Adjoint: 128 columns per tile, the recomputed product transposed and G kept in tensor memory.
+// The forward pair is issued with the operands swapped, D^T[t][l] = [A_f ; S]^T W^T, so the
+// accumulator's lanes are columns t and its columns are the tile's rows l.  The epilogue
+// thread of lane t forms G[l][t] = coef_l h'(v_lt) for its rows, splits it into bf16 pieces
+// and stores them back into the same tensor-memory buffer (piece p of row pair (2i, 2i+1)
+// in column 64 p + i, low half the even row).  That buffer is the A operand of
+//     D'[t][m] = sum_l G^T[t][l] [W_0 | W_1 | W_2][l][m]     (A from tensor memory, W MN-major),
+// so G never passes through shared memory.
+// TMEM: two buffers of 192 columns (y as FP32 in 0..127, then the P pieces of G in
+// 64 p .. 64 p + 63) at 0 and 192, the backward accumulator (32 P columns) at 384.  In the
+// split tier piece i of G multiplies W_0 .. W_{2-i} (N = 96, 64, 32): block j of the
+// accumulator collects G_0 W_j + ... + G_{2-j} W_j, the six products with i + j <= 2.
+// Barriers (phases per tile): full/empty (producer stages), accf[2] (forward product in
+// buffer b), gready (G of the tile stored, count 512), bwdf (backward MMAs complete: the
+// buffer's G consumed, the backward accumulator ready), bwde (accumulator drained, count 128).
+// Roles: 16 epilogue warps form G; 4 drain warps (one per lane quarter) read the backward
+// accumulator after bwdf, add the band gradient and store the root gradients, then arrive
+// on bwde, which the next tile's backward MMAs wait for.  An epilogue thread signals gready
+// of tile i only after gready of tile i-1 has completed (its next phase needs this thread),
+// which keeps every phase count exact.  Buffer i & 1 last held G of tile i-2, consumed
+// before the MMA thread issued the forward of tile i.
 // ==========================================================================================
 template <int P, int F>
 __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<float> a, int ntn, long long units) {
     using L = Stages<P, NT_BWD>;
-    constexpr uint32_t GT_PIECE = NT_BWD * TM * 2;                      // 32 KB
-    constexpr uint32_t GT = L::END;                                      // G^T pieces
-    constexpr uint32_t BAR = GT + P * GT_PIECE;
+    constexpr uint32_t BUF = 192, BWD = 384;                            // TMEM columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = align_1k(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + BAR);
+    float2* coefs = reinterpret_cast<float2*>(smem + L::END);            // [epilogue warp][32 rows]
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::END + EPI_WARPS_B * 32 * sizeof(float2));
     uint64_t* empty = full + 2;
     uint64_t* accf = full + 4;
-    uint64_t* acce = full + 6;
-    uint64_t* bwdf = full + 8;
-    uint64_t* bwde = full + 10;
-    uint64_t* gready = full + 12;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 13);
-    volatile int* abort = reinterpret_cast<volatile int*>(full + 14);
+    uint64_t* gready = full + 6;
+    uint64_t* bwdf = full + 7;
+    uint64_t* bwde = full + 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 9);
+    volatile int* abort = reinterpret_cast<volatile int*>(full + 10);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nt = blockIdx.x % ntn;
     const long long u0 = blockIdx.x / ntn, ustep = gridDim.x / ntn;
     const long long ntiles = units > u0 ? (units - u0 + ustep - 1) / ustep : 0;   // tiles of this CTA
     const int t0 = nt * NT_BWD;
-    const int ncols = min(NT_BWD, a.tau_pad - t0);
-    const uint32_t nmma = (uint32_t)((ncols + 15) & ~15);
     const long long n_root = 1LL << a.logn_root;
     const int lmt = a.logn_root - 3;
 
@@ -410,10 +446,9 @@ __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<flo
         mbar_init(&full[0], PROD_WARPS * 32); mbar_init(&full[1], PROD_WARPS * 32);
         mbar_init(&empty[0], 1); mbar_init(&empty[1], 1);
         mbar_init(&accf[0], 1); mbar_init(&accf[1], 1);
-        mbar_init(&acce[0], EPI_WARPS_B * 32); mbar_init(&acce[1], EPI_WARPS_B * 32);
-        mbar_init(&bwdf[0], 1); mbar_init(&bwdf[1], 1);
-        mbar_init(&bwde[0], EPI_WARPS_B * 32); mbar_init(&bwde[1], EPI_WARPS_B * 32);
         mbar_init(gready, EPI_WARPS_B * 32);
+        mbar_init(bwdf, 1);
+        mbar_init(bwde, DRAIN_WARPS * 32);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -422,162 +457,162 @@ __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<flo
     fence_after_sync();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= EPI_WARPS_B && warp < EPI_WARPS_B + PROD_WARPS) {
-        producer_loop<P, NT_BWD>(a, smem, full, empty, abort, tid - EPI_WARPS_B * 32, u0, ustep, units, t0, lmt);
-    } else if (warp == EPI_WARPS_B + PROD_WARPS) {
+    constexpr int PROD0 = EPI_WARPS_B + DRAIN_WARPS, MMAW = PROD0 + PROD_WARPS;
+    if (warp >= PROD0 && warp < MMAW) {
+        producer_loop<P, NT_BWD>(a, smem, full, empty, abort, tid - PROD0 * 32, u0, ustep, units, t0, lmt);
+    } else if (warp >= EPI_WARPS_B && warp < PROD0) {
+        // ---------------------------------------------------------------- drain
+        const int quarter = warp - EPI_WARPS_B;
+        const int t = t0 + quarter * 32 + (tid & 31);
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + BWD;
+        float gacc[15];
+#pragma unroll
+        for (int j = 0; j < 15; ++j) gacc[j] = 0.0f;
+        for (long long it = 0; it < ntiles; ++it) {
+            if (!__all_sync(0xffffffffu, mbar_wait_abort(bwdf, (uint32_t)(it & 1), abort))) break;
+            fence_after_sync();
+            uint32_t d[P][16], rr[8];
+#pragma unroll
+            for (int j = 0; j < P; ++j) tmem_ld16(ta + 32 * j, d[j]);
+            tmem_ld8(ta + 16, rr);
+            tmem_wait_ld();
+            fence_before_sync();
+            mbar_arrive(bwde);
+#pragma unroll
+            for (int m = 0; m < 15; ++m) {
+                float v = 0.0f;
+#pragma unroll
+                for (int j = P - 1; j >= 0; --j) v += __uint_as_float(d[j][m]);     // small blocks first
+                gacc[m] += v;
+            }
+            const long long u = u0 + it * ustep;
+            const long long r = u >> lmt, rho0 = (u & ((1LL << lmt) - 1)) * kRootsPerTile;
+            if (t < a.tau_pad) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) a.Froot[(r * n_root + rho0 + i) * a.tau_pad + t] = __uint_as_float(rr[i]);
+            }
+        }
+        if (t < a.tau_pad) {
+            // this CTA's partial of the band gradient: partial p = blockIdx.x / ntn
+            float* out = a.gradpart + (long long)(blockIdx.x / ntn) * 15 * a.tau_pad + t;
+#pragma unroll
+            for (int j = 0; j < 15; ++j) out[(long long)j * a.tau_pad] = gacc[j];
+        }
+    } else if (warp == MMAW) {
         // ---------------------------------------------------------------- MMA issue
         if ((tid & 31) == 0) {
-            const uint32_t idesc_f = idesc_bf16(nmma);
-            const uint32_t idesc_b = idesc_bf16_mn(32 * P);
-            const uint32_t gt = smem_u32(smem + GT);
-            auto forward = [&](long long it) -> bool {           // forward pair of tile it
+            const uint32_t idesc_f = idesc_bf16(TM);                      // D^T: M = t, N = l = 128
+            auto forward = [&](long long it) -> bool {                    // D^T of tile it into buffer it & 1
                 const int s = (int)(it & 1), b = (int)(it & 1);
                 if (!mbar_wait_abort(&full[s], (uint32_t)((it >> 1) & 1), abort)) return false;
-                if (it >= 2 && !mbar_wait_abort(&acce[b], (uint32_t)(((it - 2) >> 1) & 1), abort)) return false;
                 fence_after_sync();
-                issue_forward<P, NT_BWD>(tmem + (uint32_t)(b * NT_BWD), smem_u32(smem + s * L::STAGE), idesc_f);
+                const uint32_t W = smem_u32(smem + s * L::STAGE);
+                const uint32_t Bt = W + P * L::TILE_A;
+                const uint32_t d = tmem + (uint32_t)(b * BUF);
+                bool first = true;
+                issue_kstep<P>(d, Bt, L::TILE_B, W, L::TILE_A, idesc_f, first);         // A_f^T X_f^T
+#pragma unroll
+                for (int j = 0; j < P; ++j)                                             // S_j^T E^T
+                    mma_bf16(d, smem_desc_sw64(Bt + 32 + j * L::TILE_B), smem_desc_sw64(W + 32), idesc_f, 1u);
                 mma_commit(smem_u32(&accf[b]));
                 return true;
             };
             if (ntiles > 0 && forward(0)) {
                 for (long long it = 0; it < ntiles; ++it) {
-                    if (it + 1 < ntiles && !forward(it + 1)) break;
+                    if (it + 1 < ntiles) {
+                        // buffer (it + 1) & 1 held G of tile it - 1: its backward MMAs must be done
+                        if (it >= 1 && !mbar_wait_abort(bwdf, (uint32_t)((it - 1) & 1), abort)) break;
+                        if (!forward(it + 1)) break;
+                    }
                     const int s = (int)(it & 1), b = (int)(it & 1);
                     if (!mbar_wait_abort(gready, (uint32_t)(it & 1), abort)) break;
-                    if (it >= 2 && !mbar_wait_abort(&bwde[b], (uint32_t)(((it - 2) >> 1) & 1), abort)) break;
+                    // the drain warps have read the backward accumulator of tile it - 1
+                    if (it >= 1 && !mbar_wait_abort(bwde, (uint32_t)((it - 1) & 1), abort)) break;
                     fence_after_sync();
-                    // D' = G^T [W_0 | W_1 | W_2] over the tile's 128 rows: 8 K-steps of 16 rows, one
-                    // MMA per piece of G (the pieces of W are MN-groups TILE_A bytes apart)
-                    const uint32_t d = tmem + 256u + (uint32_t)(b * 32 * P);
+                    // D' = G^T [W_0 | W_1 | W_2]: 8 K-steps of 16 rows; piece i of G multiplies the
+                    // pieces W_0 .. W_{P-1-i} (N = 32 (P - i)), the six products with i + j <= 2
                     const uint32_t W = smem_u32(smem + s * L::STAGE);
+                    const uint32_t gbuf = tmem + (uint32_t)(b * BUF);
                     bool first = true;
 #pragma unroll 1
                     for (int ks = 0; ks < TM / 16; ++ks) {
 #pragma unroll
                         for (int i = 0; i < P; ++i) {
-                            mma_bf16(d, smem_desc_sw64_mn(gt + i * GT_PIECE + ks * 1024, 8192, 512),
-                                     smem_desc_sw64_mn(W + ks * 1024, L::TILE_A, 512), idesc_b, first ? 0u : 1u);
+                            mma_bf16_tmem_a(tmem + BWD, gbuf + 64u * i + 8u * ks,
+                                            smem_desc_sw64_mn(W + ks * 1024, L::TILE_A, 512),
+                                            idesc_bf16(32u * (P - i)) | (1u << 16), first ? 0u : 1u);
                             first = false;
                         }
                     }
-                    mma_commit(smem_u32(&bwdf[b]));
+                    mma_commit(smem_u32(bwdf));
                     mma_commit(smem_u32(&empty[s]));
                 }
             }
         }
     } else if (warp < EPI_WARPS_B) {
         // ---------------------------------------------------------------- epilogue
-        // warp w: TMEM lane quarter w % 4, columns 32 (w / 4) .. + 31 of the tile
-        const int quarter = warp & 3, cq = warp >> 2;
-        const int l = quarter * 32 + (tid & 31);         // forward: row of the tile; backward: column t0 + l
-        const int rl = l >> 4, q = l & 15;
-        const int c_beg = cq * 32;
+        // warp w: lanes 32 (w % 4) + i = columns t0 + 32 (w % 4) + i, rows l = 32 (w / 4) .. + 31
+        const int quarter = warp & 3, rq = warp >> 2;
+        const int lt = quarter * 32 + (tid & 31);         // column of the tile = TMEM lane
+        const int t = t0 + lt;
+        const int lane = tid & 31;
         const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
         const float upstream = (float)a.upstream[0];
-        unsigned char* gtile = smem + GT;
-        float gacc[15];
-#pragma unroll
-        for (int j = 0; j < 15; ++j) gacc[j] = 0.0f;
-        // read the backward accumulator of tile jt: the warps of column quarter 0 add the band
-        // gradient of column t0 + l, those of quarter 1 write the root gradients of the tile's
-        // 8 roots at column t0 + l
-        auto drain = [&](long long jt) {
-            const long long u = u0 + jt * ustep;
-            const int b = (int)(jt & 1);
-            const uint32_t ta = tmem + lane_base + 256u + (uint32_t)(b * 32 * P);
-            if (cq == 0) {
-                uint32_t d[P][16];
-#pragma unroll
-                for (int j = 0; j < P; ++j) tmem_ld16(ta + 32 * j, d[j]);
-                tmem_wait_ld();
-#pragma unroll
-                for (int m = 0; m < 15; ++m) {
-                    float v = 0.0f;
-#pragma unroll
-                    for (int j = P - 1; j >= 0; --j) v += __uint_as_float(d[j][m]);     // small blocks first
-                    gacc[m] += v;
-                }
-            } else if (cq == 1) {
-                uint32_t d[8];
-                tmem_ld8(ta + 16, d);
-                tmem_wait_ld();
-                const long long r = u >> lmt, rho0 = (u & ((1LL << lmt) - 1)) * kRootsPerTile;
-                if (t0 + l < a.tau_pad) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        a.Froot[(r * n_root + rho0 + i) * a.tau_pad + t0 + l] = __uint_as_float(d[i]);
-                }
-            }
-        };
-        // the row's saved {g'(u) gfac / (R N), log2 e u} (one float2), loaded a tile ahead
+        float2* wcoef = coefs + warp * 32;
+        // the saved {g'(u) gfac / (R N), log2 e u} of row l = 32 rq + lane of tile jt
         auto row_coef = [&](long long jt) {
             const long long u = u0 + jt * ustep;
             const long long r = u >> lmt, rho0 = (u & ((1LL << lmt) - 1)) * kRootsPerTile;
-            const long long k = rho0 + rl + (long long)q * n_root;
+            const int l = rq * 32 + lane;
+            const long long k = rho0 + (l >> 4) + (long long)(l & 15) * n_root;
             return __ldg(reinterpret_cast<const float2*>(a.rowsave) + r * a.N + k);
         };
         float2 coef_next = ntiles > 0 ? row_coef(0) : make_float2(0.f, 0.f);
         bool ok = true;
         for (long long it = 0; it < ntiles; ++it) {
             const int b = (int)(it & 1);
-            const float cf = upstream * coef_next.x, aux = coef_next.y;
+            const float2 coef_mine = coef_next;
             if (it + 1 < ntiles) coef_next = row_coef(it + 1);
-            if (!mbar_wait_abort(&accf[b], (uint32_t)((it >> 1) & 1), abort)) { ok = false; break; }
-            // G^T of the previous tile has been consumed once its backward MMAs are done
-            if (it >= 1 && !mbar_wait_abort(&bwdf[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1), abort)) {
-                ok = false;
-                break;
+            // the waits' outcome is made uniform over the warp (for the aligned tensor-memory
+            // accesses) and over the lane quarter (for its named barrier) before anything depends on it
+            bool okl = mbar_wait_abort(&accf[b], (uint32_t)((it >> 1) & 1), abort);
+            okl = __all_sync(0xffffffffu, okl);
+            const uint32_t ybuf = tmem + lane_base + (uint32_t)(b * BUF);
+            uint32_t y[32];
+            if (okl) {
+                fence_after_sync();
+                __syncwarp();
+                wcoef[lane] = make_float2(upstream * coef_mine.x, coef_mine.y);
+                tmem_ld32(ybuf + 32 * rq, y);
+                tmem_wait_ld();
+                __syncwarp();
             }
-            fence_after_sync();
-            uint32_t d[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)(b * NT_BWD + c_beg), d);
-            tmem_wait_ld();
+            // every warp of this lane quarter has read its y before any G piece overwrites them
+            if (quarter_sync_or(quarter, !okl)) { ok = false; break; }
 #pragma unroll
-            for (int g8 = 0; g8 < 4; ++g8) {
-                float gv[8];
+            for (int h = 0; h < 2; ++h) {
+                uint32_t w[P][8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const int t = t0 + c_beg + 8 * g8 + i;
-                    gv[i] = t < a.tau ? cf * Fn<F, float>::hp(__uint_as_float(d[8 * g8 + i]), a.c0, aux) : 0.0f;
-                }
-                // MN-major G^T: row l of K, columns t = c_beg + 8 g8 .. + 7 of M
-                const int tl = c_beg + 8 * g8;
-                const uint32_t off = (uint32_t)(tl >> 5) * 8192u + (uint32_t)(l >> 3) * 512u + (uint32_t)(l & 7) * 64u +
-                                     ((uint32_t)(((tl & 31) >> 3) ^ ((l & 7) >> 1)) << 4);
-                uint32_t w[P][4];
+                    float g2[2];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                    for (int e = 0; e < 2; ++e) {
+                        const int c = 16 * h + 2 * i + e;                // row l = 32 rq + c
+                        const float2 cf = wcoef[c];
+                        g2[e] = t < a.tau ? cf.x * Fn<F, float>::hp(__uint_as_float(y[c]), a.c0, cf.y) : 0.0f;
+                    }
                     uint32_t qp[P];
-                    split_pair<P>(gv[2 * i], gv[2 * i + 1], qp);
+                    split_pair<P>(g2[0], g2[1], qp);
 #pragma unroll
                     for (int pp = 0; pp < P; ++pp) w[pp][i] = qp[pp];
                 }
 #pragma unroll
-                for (int pp = 0; pp < P; ++pp)
-                    *reinterpret_cast<uint4*>(gtile + pp * GT_PIECE + off) = make_uint4(w[pp][0], w[pp][1], w[pp][2], w[pp][3]);
+                for (int pp = 0; pp < P; ++pp) tmem_st8(ybuf + 64u * pp + 16u * rq + 8u * h, w[pp]);
             }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             fence_before_sync();
-            mbar_arrive(&acce[b]);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (it >= 1 && !mbar_wait_abort(gready, (uint32_t)((it - 1) & 1), abort)) { ok = false; break; }
             mbar_arrive(gready);
-            if (it >= 1) {                               // the previous tile's backward accumulator
-                drain(it - 1);
-                fence_before_sync();
-                mbar_arrive(&bwde[(it - 1) & 1]);
-            }
-        }
-        if (ok && ntiles > 0) {
-            const long long last = ntiles - 1;
-            if (mbar_wait_abort(&bwdf[last & 1], (uint32_t)((last >> 1) & 1), abort)) {
-                fence_after_sync();
-                drain(last);
-            }
-        }
-        if (cq == 0 && t0 + l < a.tau_pad) {
-            // this CTA's partial of the band gradient: partial p = blockIdx.x / ntn
-            float* out = a.gradpart + (long long)(blockIdx.x / ntn) * 15 * a.tau_pad + t0 + l;
-#pragma unroll
-            for (int j = 0; j < 15; ++j) out[(long long)j * a.tau_pad] = gacc[j];
         }
     }
     if (*abort && tid == 0) atomicOr(&g_fine_tc_error, 1u);
@@ -617,7 +652,7 @@ cudaError_t bwd_tc_launch(const FineArgs<float>& a, cudaStream_t st) {
     const int ntn = (a.tau_pad + NT_BWD - 1) / NT_BWD;
     const long long units = (long long)a.reff * ((1LL << a.logn_root) / kRootsPerTile);
     const long long per = bwd_tc_partials(a.tau_pad, a.reff, a.logn_root);
-    const size_t smem = at_least_120k(1024 + Stages<P, NT_BWD>::END + P * NT_BWD * TM * 2 + 128);
+    const size_t smem = at_least_120k(1024 + Stages<P, NT_BWD>::END + EPI_WARPS_B * 32 * sizeof(float2) + 128);
     cudaError_t e = cudaFuncSetAttribute(k_fine_bwd_tc<P, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_fine_bwd_tc<P, F><<<(unsigned)(per * ntn), THREADS_B, smem, st>>>(a, ntn, units);
