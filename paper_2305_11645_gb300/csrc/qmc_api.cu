@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -192,6 +193,7 @@ struct Plan {
     int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
+    bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
     bool fine_tc = false;          // fused forward and adjoint of the fine band on tensor cores
     int cg_tc = 0;                 // its row-partial column groups
     long long fine_parts_tc = 0;   // band-gradient partials of its adjoint
@@ -315,22 +317,62 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.cr = cr;
         P.cg_count = (P.tau_pad + cr - 1) / cr;
     }
-    P.nblk = (int)((P.N + 255) / 256);          // row blocks of the finalisation (256 rows each)
+    // the S4 band of the float tiers: forward CTAs of 64 roots x 2 branches, column groups picked
+    // by a per-SM cost model (CTAs per SM, at least 5 resident, times columns per CTA plus a fixed
+    // setup cost); the adjoint below.  m <= 27 keeps the adjoint's 32-bit staging offsets (4 * 2^m
+    // table entries, 2 * 2^m row-save floats) below 2^30.
+    P.fine_s4 = (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) && P.shape == SHAPE_S4 &&
+                precision != QMC_FP64 && P.m <= 27 && !getenv("QMC_FINE_TC");
+    if (P.fine_s4) {
+        const int rows = fine_s4_fwd_roots();
+        P.root_blocks = (int)((n_root + rows - 1) / rows);
+        const long long rbr = (long long)P.root_blocks * P.reff;
+        const int quads = P.tau_pad / 4, qmax = 512 / 4;
+        long long best = -1;
+        for (int cg = (quads + qmax - 1) / qmax; cg <= quads; ++cg) {
+            const int qpg = (quads + cg - 1) / cg;
+            if ((long long)(cg - 1) * qpg >= quads) continue;       // an empty last group
+            const long long per_sm = (rbr * cg + 151) / 152;
+            const long long cost = std::max(per_sm, 5LL) * (qpg + 2);
+            if (best < 0 || cost < best) { best = cost; P.cr = 4 * qpg; P.cg_count = (quads + qpg - 1) / qpg; }
+        }
+    }
+    // partials of the estimate: row blocks of the finalisation (256 rows each)
+    P.nblk = (int)((P.N + 255) / 256);
     // tensor-core tiers: the fused forward of the dyadic band runs on tensor cores (8 roots per tile)
-    P.fine_tc = P.tc_pieces != 0 && P.shape == SHAPE_S4 && logn_root >= 3;
+    P.fine_tc = !P.fine_s4 && P.tc_pieces != 0 && P.shape == SHAPE_S4 && logn_root >= 3;
     P.cg_tc = (P.tau + fine_tc_group_cols() - 1) / fine_tc_group_cols();
     P.fine_parts_tc = P.fine_tc ? bwd_tc_partials(P.tau_pad, P.reff, logn_root) : 0;
 
     // backward schedule
+    if (op == QMC_OP_INTEGRATE_BWD && P.fine_s4) {
+        // 256 columns per CTA; an even number of roots per CTA (the two halves take alternate
+        // roots), chosen by the same kind of cost model (at least 2 CTAs of 8 warps resident per
+        // SM, a fixed setup cost of about 8 roots per CTA)
+        const int cols = fine_s4_bwd_cols(), rb = fine_s4_bwd_batch();
+        P.passes = (P.tau_pad + cols - 1) / cols;
+        long long best = -1;
+        const long long gmax = std::min<long long>((n_root + 1) / 2, 152LL * 16);
+        for (long long G = 1; G <= gmax; ++G) {
+            const long long rpc = ((n_root + G - 1) / G + 1) / 2 * 2;
+            const long long g = (n_root + rpc - 1) / rpc;
+            if (g != G) continue;
+            const long long per_sm = ((long long)P.passes * g * P.reff + 151) / 152;
+            const long long cost = std::max(per_sm, 2LL) * (rpc + rb);
+            if (best < 0 || cost < best) { best = cost; P.roots_per_cta = (int)rpc; P.groups = (int)g; }
+        }
+    }
     if (op == QMC_OP_INTEGRATE_BWD) {
-        const int cols_per_pass = 32 * P.cw_bwd;
-        P.passes = (P.tau_pad + cols_per_pass - 1) / cols_per_pass;
-        long long groups_target = std::max(1LL, 304LL / ((long long)P.passes * P.reff));
-        long long rpc = (n_root + groups_target - 1) / groups_target;
-        rpc = std::max(rpc, (n_root + 511) / 512);
-        rpc = std::max(8LL, (rpc + 7) / 8 * 8);
-        P.roots_per_cta = (int)rpc;
-        P.groups = (int)((n_root + rpc - 1) / rpc);
+        if (!P.fine_s4) {
+            const int cols_per_pass = 32 * P.cw_bwd;
+            P.passes = (P.tau_pad + cols_per_pass - 1) / cols_per_pass;
+            long long groups_target = std::max(1LL, 304LL / ((long long)P.passes * P.reff));
+            long long rpc = (n_root + groups_target - 1) / groups_target;
+            rpc = std::max(rpc, (n_root + 511) / 512);
+            rpc = std::max(8LL, (rpc + 7) / 8 * 8);
+            P.roots_per_cta = (int)rpc;
+            P.groups = (int)((n_root + rpc - 1) / rpc);
+        }
         // Root gradients are folded level by level (k_fold_tree) up to I_mat = the highest coarse
         // level below m within kFoldDepth of the root; F of every coarse level up to I_mat is
         // materialised, the levels above it (the constant level m) fold from F_{I_mat} on the fly.
@@ -564,6 +606,10 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
             a.cg_count = P.cg_tc;
             QMC_LAUNCH(st, "k_fine_fwd_tc", launch_fine_fwd_tc(a, P.fkind, P.tc_pieces, st));
         }
+    } else if (mode == MODE_FUSED && P.fine_s4) {
+        if constexpr (std::is_same<T, float>::value) {
+            QMC_LAUNCH(st, "k_fine_fwd_s4", launch_fine_fwd_s4(a, P.fkind, dim3(P.root_blocks, P.cg_count, P.reff), st));
+        }
     } else {
         dim3 grid(P.root_blocks, P.cg_count, P.reff);
         QMC_LAUNCH(st, mode == MODE_FUSED ? "k_fine_fwd" : "k_fine_fwd_materialize",
@@ -611,6 +657,9 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
             QMC_LAUNCH(st, "k_fine_bwd_tc", launch_fine_bwd_tc(a, P.fkind, P.tc_pieces, st));
             nfine_part = (int)P.fine_parts_tc;
         }
+    } else if (P.fine_s4) {
+        if constexpr (std::is_same<T, float>::value)
+            QMC_LAUNCH(st, "k_fine_bwd_s4", launch_fine_bwd_s4(a, P.fkind, dim3(P.groups, P.passes, P.reff), st));
     } else {
         dim3 grid(P.groups, P.passes, P.reff);
         QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.exact, P.fkind, grid, st));

@@ -17,6 +17,7 @@
 //                  (the adjoint of the periodic tiling), split over K = R n_e.
 //  k_grad_reduce   fixed-order sum of all gradient partials into dA.
 #include "qmc_internal.cuh"
+#include "qmc_finalize.cuh"
 
 namespace qmc {
 
@@ -218,34 +219,6 @@ template cudaError_t launch_chain_sum<double>(const double*, long long, const Ch
 // ------------------------------------------------------------------------------------------
 // row finalisation and the mean
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    __syncthreads();
-    return s;
-}
-
-// sum over the CTA in a fixed order: warp shuffles in T, then the 8 warp sums in double
-template <class T>
-__device__ __forceinline__ double block_sum_t(T v, double* sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[warp] = (double)v;
-    __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
-    __syncthreads();
-    return s;
-}
-
 constexpr int kRowsPerThread = 1;
 
 template <class T>
@@ -256,7 +229,6 @@ __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ row
                                                        unsigned int* ticket, double* __restrict__ est) {
     // Per-row arithmetic in T (the row sums are T partials).  The CTA's rows are summed with
     // warp shuffles in T and the warp sums in double; the mean over the CTAs is in double.
-    // The call payoff's kink test u/tau > K is taken in double, without a division.
     __shared__ double sh[32];
     const int r = blockIdx.y;
     const T inv_tau = (T)(1.0 / tau);
@@ -265,7 +237,7 @@ __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ row
     for (int i = 0; i < kRowsPerThread; ++i) {
         const long long k = ((long long)blockIdx.x * kRowsPerThread + i) * blockDim.x + threadIdx.x;
         if (k >= N) break;
-        T u, fv;
+        T u;
         const T* rp = rowpart + (long long)r * cg_count * N + k;
         if (F == F_LOGSUMEXP) {
             // the partials hold (max, sum 2^(v - max)) of v = y log2 e
@@ -276,61 +248,16 @@ __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ row
             T S = T(0);
 #pragma unroll 8
             for (int g = 0; g < cg_count; ++g) S += rp[(long long)g * N] * exp2(rm[(long long)g * N] - M);
-            u = (M + log2(S)) * (T)kLn2;
+            u = lse_row(M, S);
         } else {
             u = T(0);
 #pragma unroll 8
             for (int g = 0; g < cg_count; ++g) u += rp[(long long)g * N];
         }
-        T gp;
-        switch (F) {
-            case F_LINEAR_MEAN: case F_MEAN_COS: case F_PDE_INV_SQ: fv = u * inv_tau; gp = inv_tau; break;
-            case F_CALL_MEAN_EXP: {
-                const bool active = (double)u * (1.0 / tau) - K > 0.0;
-                fv = active ? u * inv_tau - (T)K : T(0);
-                gp = active ? inv_tau : T(0);
-                break;
-            }
-            case F_GAUSS_NORM2: fv = exp(T(-0.5) * u * inv_tau); gp = T(-0.5) * inv_tau * fv; break;
-            default: fv = u; gp = T(1); break;     // log-sum-exp: u is log sum exp(y)
-        }
-        if (rowsave) {
-            // what the backward needs of this row: g'(u) gfac/(R N) and log2 e * u
-            rowsave[2 * ((long long)r * N + k)] = gp * (T)coef_scale;
-            rowsave[2 * ((long long)r * N + k) + 1] = u * (T)kLog2e;
-        }
-        if (rowf) rowf[(long long)r * N + k] = fv;
-        fsum += fv;
+        fsum += finalize_row<T>(F, u, inv_tau, tau, K, coef_scale, rowsave, rowf, (long long)r * N + k);
     }
     const double s = block_sum_t<T>(fsum, sh);
-    if (!est) {
-        if (threadIdx.x == 0) fpart[(long long)r * nblk + blockIdx.x] = s;
-        return;
-    }
-    // the last block to finish forms Q_r = N^-1 sum_k f for every shift and their mean,
-    // summing the block partials in a fixed order (deterministic whichever block is last)
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        fpart[(long long)r * nblk + blockIdx.x] = s;
-        __threadfence();
-        const unsigned int total = gridDim.x * gridDim.y;
-        last = atomicAdd(ticket, 1u) == total - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double mean = 0.0;
-    const int reff = gridDim.y;
-    for (int rr = 0; rr < reff; ++rr) {
-        double v = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += __ldcg(fpart + (long long)rr * nblk + b);
-        const double sr = block_sum(v, sh);
-        if (threadIdx.x == 0) {
-            est[rr] = sr / (double)N;
-            mean += sr / (double)N;
-        }
-    }
-    if (threadIdx.x == 0) est[reff] = mean / reff;
+    finalize_estimate(s, r, blockIdx.x, nblk, gridDim.y, N, gridDim.x * gridDim.y, ticket, fpart, est, sh);
 }
 
 template <class T>
@@ -544,15 +471,17 @@ struct FineCols {
 };
 
 // dA[j][t] = sum of column j's gradient partials (the fine band's, or the coarse entry's
-// k-splits).  A CTA owns column j: warp w sums the partials p = w, w + 8, ... for 512
-// columns t at a time (16 per lane, coalesced, all loads of a partial in flight together),
+// k-splits).  A CTA owns column j and kGradCols columns t: warp w sums the partials
+// p = w, w + 8, ... (8 columns per lane, coalesced, four partials' loads in flight together),
 // and the eight warp sums are added in a fixed order.
+constexpr int kGradCols = 256;
+
 template <class T>
 __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradpart_f, const FineCols fc,
                                                      const T* __restrict__ part_c, const __grid_constant__ Chain ch,
                                                      int tau, int tau_pad, int s, T* __restrict__ grad) {
-    __shared__ T red[8][512];
-    const int j = blockIdx.x;
+    __shared__ T red[8][kGradCols];
+    const int j = blockIdx.x, t0 = blockIdx.y * kGradCols;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // where column j's partials are: base + p * stride, p < count
     const T* base = nullptr;
@@ -570,41 +499,38 @@ __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradp
             stride = (long long)ch.tau[q] * tau_pad;
             count = ch.split[q];
         }
-    for (int t0 = 0; t0 < tau; t0 += 512) {
-        T v[16];
+    constexpr int C = kGradCols / 32;
+    T v[C];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = T(0);
-        // four partials per round: 64 loads in flight per lane
-        int p = warp;
-        for (; p + 24 < count; p += 32) {
-            T w[4][16];
+    for (int c = 0; c < C; ++c) v[c] = T(0);
+    int p = warp;
+    for (; p + 24 < count; p += 32) {
+        T w[4][C];
 #pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const T* bp = base + (long long)(p + 8 * h) * stride + t0 + lane;
+        for (int h = 0; h < 4; ++h) {
+            const T* bp = base + (long long)(p + 8 * h) * stride + t0 + lane;
 #pragma unroll
-                for (int c = 0; c < 16; ++c) w[h][c] = t0 + 32 * c + lane < tau ? __ldg(bp + 32 * c) : T(0);
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) v[c] += (w[0][c] + w[1][c]) + (w[2][c] + w[3][c]);
-        }
-        for (; p < count; p += 8) {
-            const T* bp = base + (long long)p * stride + t0 + lane;
-#pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (t0 + 32 * c + lane < tau) v[c] += __ldg(bp + 32 * c);
+            for (int c = 0; c < C; ++c) w[h][c] = t0 + 32 * c + lane < tau ? __ldg(bp + 32 * c) : T(0);
         }
 #pragma unroll
-        for (int c = 0; c < 16; ++c) red[warp][32 * c + lane] = v[c];
-        __syncthreads();
-        for (int i = threadIdx.x; i < 512; i += 256) {
-            if (t0 + i < tau) {
-                T acc = T(0);
+        for (int c = 0; c < C; ++c) v[c] += (w[0][c] + w[1][c]) + (w[2][c] + w[3][c]);
+    }
+    for (; p < count; p += 8) {
+        const T* bp = base + (long long)p * stride + t0 + lane;
 #pragma unroll
-                for (int w = 0; w < 8; ++w) acc += red[w][i];
-                grad[(long long)j * tau + t0 + i] = acc;
-            }
+        for (int c = 0; c < C; ++c)
+            if (t0 + 32 * c + lane < tau) v[c] += __ldg(bp + 32 * c);
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) red[warp][32 * c + lane] = v[c];
+    __syncthreads();
+    for (int i = threadIdx.x; i < kGradCols; i += 256) {
+        if (t0 + i < tau) {
+            T acc = T(0);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) acc += red[w][i];
+            grad[(long long)j * tau + t0 + i] = acc;
         }
-        __syncthreads();
     }
 }
 
@@ -621,7 +547,8 @@ cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width
         fc.col0[i] = i < jf ? col0_lev[i] : 0;
         fc.tau[i] = i < jf ? tau_lev[i] : 0;
     }
-    k_grad_reduce<T><<<(unsigned)s, 256, 0, st>>>(gradpart_f, fc, part_c, ch, tau, tau_pad, s, grad);
+    const dim3 grid((unsigned)s, (unsigned)((tau + kGradCols - 1) / kGradCols));
+    k_grad_reduce<T><<<grid, 256, 0, st>>>(gradpart_f, fc, part_c, ch, tau, tau_pad, s, grad);
     return cudaGetLastError();
 }
 template cudaError_t launch_grad_reduce<float>(const float*, int, int, const int*, const int*, const int*, int,

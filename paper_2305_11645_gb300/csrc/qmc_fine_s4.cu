@@ -1,0 +1,502 @@
+// Fine band S4 in FP32 on the CUDA cores: the levels w = 0..3 (at most 1, 2, 4 and 8 columns)
+// expanded as the binary tree of Sec. 3.2, fused with the integrand (forward) or with the
+// folded adjoint (backward).
+//
+// Notation as in qmc_fine.cuh: a root rho < n_root = 2^(m-4) of level 4 has the descendants
+// rho + c n_root at level I (c < 2^(4-I)); node c at level I has the children c and c + 2^(4-I)
+// at level I - 1, and leaf q is the output row k = rho + q n_root.  A root costs 64 multiply-
+// adds per column for its 16 outputs (Algorithm 1's count for these levels: sum_I 2^(4-I) tau_I),
+// 4 per output, against the 15 + 1 a dense row would take.  That is why the band stays on the
+// FP32 pipes in every float tier: a tensor-core tile of the band multiplies 16 padded columns
+// plus the root per output, six times over in the three-piece split, and its adjoint is bounded
+// by the tensor pipe well above the 11 FP32 operations per output the tree takes here.
+//
+// Forward: a CTA holds 64 roots x 2 branches.  Thread (rho, b) owns the 8 leaves q = b + 2i under
+// level-3 node b (the tree splits there without shared work), keeps their 32 x values in
+// registers and walks the CTA's columns; the kappa-scaled fine columns of A are staged in shared
+// memory and read as four broadcast 16-byte loads per column.
+//
+// Backward: a CTA covers 256 columns (4 warps x 32 lanes x 2 columns) of a range of roots, in
+// two halves of 4 warps that take alternate roots.  The x values and row coefficients of 8 roots
+// at a time are staged in shared memory (double-buffered, coalesced along the roots) and read as
+// broadcast 16-byte loads; each lane holds its columns of A and its gradient accumulators in
+// registers for every root it visits, so the only reductions are the two halves' at the end.
+#include "qmc_internal.cuh"
+
+namespace qmc {
+namespace {
+
+constexpr int kFwdRoots = 64;
+constexpr int kFwdThreads = 2 * kFwdRoots;
+constexpr int kBwdThreads = 256;
+constexpr int kBwdCols = 256;                // columns per CTA: 4 warps x 32 lanes x 2
+constexpr int kRB = 8;                       // roots per staged batch
+constexpr int kSlots = 96;                   // staged floats per root
+constexpr int kFwdMinBlocks = 5, kBwdMinBlocks = 2;
+constexpr int kMaxCRS4 = 512;                // forward columns per CTA (dynamic shared memory 48 KB)
+
+// ------------------------------------------------------------------------------------------
+// Forward
+// ------------------------------------------------------------------------------------------
+
+// Shared-memory layout of the staged fine columns of A, 24 floats per column:
+//   [a3 0..7 | a2 0, a2 0, a2 1, a2 1, a2 2, a2 2, a2 3, a2 3 | a1 0, a1 0, a1 1, a1 1 | a0, a0, 0, 0]
+// The paired FP32 instructions (two lanes of one register pair per instruction) then take their
+// operands straight from the 16-byte loads: the level-3 dot product runs as two interleaved
+// partial sums over (a3 2k, a3 2k+1), and the two sibling nodes of each lower level share an a.
+constexpr int kAQuads = 6;
+
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Row accumulator of u = sum_t h(v_t); log-sum-exp keeps (max, sum 2^(v - max)) and takes one
+// ex2 per output: with d = v - max, 2^-|d| is either the new term (d <= 0) or the rescale of
+// the old sum when v becomes the maximum (d > 0, new term 2^0 = 1).
+template <int F>
+struct RowAcc {
+    float s, mx;
+    __device__ __forceinline__ void init() { s = 0.0f; mx = -INFINITY; }
+    __device__ __forceinline__ void add(float v, float c0) {
+        if constexpr (F == F_LOGSUMEXP) {
+            const float d = v - mx;
+            const float e = ex2f(-fabsf(d));
+            const bool up = d > 0.0f;
+            s = up ? fmaf(s, e, 1.0f) : s + e;
+            mx = up ? v : mx;
+        } else {
+            s += Fn<F, float>::h(v, c0);
+        }
+    }
+};
+
+// The row accumulators of two sibling leaves; the row-sum integrands add their two terms with
+// one paired add.
+template <int F>
+struct RowAcc2 {
+    float2 s, mx;
+    __device__ __forceinline__ void init() { s = f2(0.0f, 0.0f); mx = f2(-INFINITY, -INFINITY); }
+    __device__ __forceinline__ void add(float2 v, float c0) {
+        if constexpr (F == F_LOGSUMEXP) {
+            RowAcc<F> a{s.x, mx.x}, b{s.y, mx.y};
+            a.add(v.x, c0);
+            b.add(v.y, c0);
+            s = f2(a.s, b.s);
+            mx = f2(a.mx, b.mx);
+        } else {
+            s = __fadd2_rn(s, f2(Fn<F, float>::h(v.x, c0), Fn<F, float>::h(v.y, c0)));
+        }
+    }
+};
+
+template <int F>
+__global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) k_fine_fwd_s4(const __grid_constant__ FineArgs<float> a) {
+    extern __shared__ __align__(16) float4 As_dyn[];                  // [a.cr][kAQuads]
+    float4 (*As)[kAQuads] = reinterpret_cast<float4 (*)[kAQuads]>(As_dyn);
+    const int tid = threadIdx.x, b = tid / kFwdRoots;
+    const long long n_root = 1LL << a.logn_root;
+    const long long rho = (long long)blockIdx.x * kFwdRoots + (tid % kFwdRoots);
+    const int cg = blockIdx.y, r = blockIdx.z;
+    const int t_beg = cg * a.cr, t_end = min(t_beg + a.cr, a.tau);
+    const int ncol = (t_end - t_beg + 3) & ~3;
+
+    // x of the subtree (level-3 node b, level-2 nodes b + 2 i2, level-1 nodes b + 2 i1, leaves
+    // b + 2 i), as register pairs: the level-3 columns (2k, 2k+1), and for the lower levels the
+    // sibling nodes (i2 = 0, 1), (i1 = 0, 1), (i1 = 2, 3), (i = 2k, 2k+1)
+    // (the loads of x and of the first root values are issued before the staging of A, so that
+    // their latency overlaps it)
+    const bool valid = rho < n_root;
+    const float* tab = a.tab + (long long)r * a.tab_stride + (valid ? rho : 0) + ((long long)b << a.logn_root);
+    const long long step2 = 2LL << a.logn_root;                  // from node c to node c + 2
+    float2 x3p[4], x2p[4], x1p[2][2], x0p[4];
+    {
+        const float* p3 = tab + a.lev_tab[3];
+        float x3[8];
+#pragma unroll
+        for (int jj = 0; jj < 8; ++jj) x3[jj] = jj < a.lev_tau[3] ? __ldg(p3 + ((long long)jj << a.lev_logn[3])) : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x3p[k] = f2(x3[2 * k], x3[2 * k + 1]);
+        const float* p2 = tab + a.lev_tab[2];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            const bool on = jj < a.lev_tau[2];
+            const float* q = p2 + ((long long)jj << a.lev_logn[2]);
+            x2p[jj] = on ? f2(__ldg(q), __ldg(q + step2)) : f2(0.0f, 0.0f);
+        }
+        const float* p1 = tab + a.lev_tab[1];
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+            const bool on = jj < a.lev_tau[1];
+            const float* q = p1 + ((long long)jj << a.lev_logn[1]);
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+                x1p[p][jj] = on ? f2(__ldg(q + (2 * p) * step2), __ldg(q + (2 * p + 1) * step2)) : f2(0.0f, 0.0f);
+        }
+        const float* p0 = tab + a.lev_tab[0];
+        const bool on0 = a.lev_tau[0] > 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            x0p[k] = on0 ? f2(__ldg(p0 + (2 * k) * step2), __ldg(p0 + (2 * k + 1) * step2)) : f2(0.0f, 0.0f);
+    }
+
+    RowAcc2<F> acc[4];                                    // leaves (2k, 2k+1)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k].init();
+    const float kap = a.kappa, c0 = a.c0;
+    // one column: the subtree's 8 outputs and their row accumulators
+    auto column = [&](const float4* ac, float vroot) {
+        const float4 A0 = ac[0], A1 = ac[1], A2 = ac[2], A3 = ac[3], A4 = ac[4], A5 = ac[5];
+        float2 s3 = ffma2(x3p[0], f2(A0.x, A0.y), f2(vroot, 0.0f));
+        s3 = ffma2(x3p[1], f2(A0.z, A0.w), s3);
+        s3 = ffma2(x3p[2], f2(A1.x, A1.y), s3);
+        s3 = ffma2(x3p[3], f2(A1.z, A1.w), s3);
+        const float v3 = s3.x + s3.y;
+        float2 v2 = ffma2(x2p[0], f2(A2.x, A2.y), f2(v3, v3));            // level-2 nodes i2 = 0, 1
+        v2 = ffma2(x2p[1], f2(A2.z, A2.w), v2);
+        v2 = ffma2(x2p[2], f2(A3.x, A3.y), v2);
+        v2 = ffma2(x2p[3], f2(A3.z, A3.w), v2);
+        // level-1 nodes (0, 1) and (2, 3): parents (0, 1), i.e. v2 itself
+        const float2 v1a = ffma2(x1p[0][1], f2(A4.z, A4.w), ffma2(x1p[0][0], f2(A4.x, A4.y), v2));
+        const float2 v1b = ffma2(x1p[1][1], f2(A4.z, A4.w), ffma2(x1p[1][0], f2(A4.x, A4.y), v2));
+        // leaves (0, 1), (4, 5) below (0, 1) and (2, 3), (6, 7) below (2, 3)
+        const float2 a0 = f2(A5.x, A5.y);
+        acc[0].add(ffma2(x0p[0], a0, v1a), c0);
+        acc[1].add(ffma2(x0p[1], a0, v1b), c0);
+        acc[2].add(ffma2(x0p[2], a0, v1a), c0);
+        acc[3].add(ffma2(x0p[3], a0, v1b), c0);
+    };
+    // root values S_4 (layout [t/4][rho][4]), two quads of columns ahead
+    const float* S = (a.S && valid) ? a.S + (long long)r * a.S_stride + rho * 4 : nullptr;
+    const long long squad = 4LL << a.logn_root;
+    auto lds4 = [&](int t) -> float4 {
+        return (S && t < t_end) ? __ldg(reinterpret_cast<const float4*>(S + (long long)(t >> 2) * squad))
+                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    };
+    float4 snext = lds4(t_beg), snext2 = lds4(t_beg + 4);
+    {
+        // threads tid < 120 stage position jp = tid % 24 of the columns tid / 24, tid / 24 + 5, ...
+        constexpr int W = 4 * kAQuads, STEP = kFwdThreads / W;
+        const int jp = tid % W;
+        int lev = 0, jj = 0;
+        bool on = tid < STEP * W;
+        if (jp < 8) { lev = 3; jj = jp; }
+        else if (jp < 16) { lev = 2; jj = (jp - 8) >> 1; }
+        else if (jp < 20) { lev = 1; jj = (jp - 16) >> 1; }
+        else if (jp < 22) { lev = 0; jj = 0; }
+        else on = false;
+        on = on && jj < a.lev_tau[lev];
+        const float* arow = a.A + (long long)(a.lev_col0[lev] + jj) * a.ldA;
+        float* Asf = reinterpret_cast<float*>(As);
+        if (tid < STEP * W)
+            for (int c = tid / W; c < ncol; c += STEP)
+                Asf[c * W + jp] = (on && t_beg + c < a.tau) ? a.kappa * __ldg(arow + t_beg + c) : 0.0f;
+    }
+    __syncthreads();
+    const int t_full = t_beg + ((t_end - t_beg) & ~3);
+    int t0 = valid ? t_beg : t_end;
+    for (; t0 < t_full; t0 += 4) {                        // whole quads: four independent columns
+        const float4 sq = snext;
+        snext = snext2;
+        snext2 = lds4(t0 + 8);
+        const float4* ac = As[t0 - t_beg];
+        column(ac, kap * sq.x);
+        column(ac + kAQuads, kap * sq.y);
+        column(ac + 2 * kAQuads, kap * sq.z);
+        column(ac + 3 * kAQuads, kap * sq.w);
+    }
+    if (t0 < t_end) {                                     // the ragged last quad
+        const float sv[4] = {snext.x, snext.y, snext.z, snext.w};
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (t0 + c < t_end) column(As[t0 - t_beg + c], kap * sv[c]);
+    }
+
+    // row partials of this column group: rowpart[r][cg][k] (log-sum-exp: also rowmax)
+    if (valid) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const long long o = ((long long)r * gridDim.y + cg) * a.N + rho + ((long long)(b + 2 * i) << a.logn_root);
+            a.rowpart[o] = (i & 1) ? acc[i >> 1].s.y : acc[i >> 1].s.x;
+            if constexpr (F == F_LOGSUMEXP) a.rowmax[o] = (i & 1) ? acc[i >> 1].mx.y : acc[i >> 1].mx.x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Backward
+// ------------------------------------------------------------------------------------------
+
+// Staged values of one root, each stored twice ({v, v}, one register pair for the paired
+// instructions over the thread's two columns), in slot order:
+//   slots  0..15   x of the level-3 nodes (c3 = 0: columns 0..7, c3 = 1: columns 0..7)
+//   slots 16..31   x of the level-2 nodes c2 = 0..3 (columns 0..3)
+//   slots 32..63   per level-1 node c1: x columns 0, 1 and the x of its leaves c1, c1 + 8
+//   slots 64..79   per level-2 node c2: coefficients of the leaves c2, c2 + 8, c2 + 4, c2 + 12
+//   slots 80..95   the same leaves' -aux (log-sum-exp only)
+// A root's row is kRowPad floats long: the 8 roots of a batch then start 16 bytes apart modulo
+// 128, so that the staging stores hit distinct banks, and the reads are 16-byte aligned at
+// fixed offsets.
+constexpr int kRowPad = 2 * kSlots + 4;
+
+// Where slot s of every root comes from, as a 32-bit code: bit 31 set for no value (0), else
+// bit 30 for the row coefficients (rowsave, float offset code & 0x3fffffff + 2 rho; the aux
+// slots read the second float of the pair and are negated) or the point table (tab, offset
+// code + rho).  Offsets are within one shift's table or one shift's rowsave.
+template <int F>
+__device__ __forceinline__ unsigned bwd_slot_code(const FineArgs<float>& a, int s) {
+    int lev, c, jj;
+    if (s < 16) { lev = 3; c = s >> 3; jj = s & 7; }
+    else if (s < 32) { lev = 2; c = (s - 16) >> 2; jj = s & 3; }
+    else if (s < 64) {
+        const int u = s - 32, e = u & 3;
+        c = u >> 2;
+        if (e < 2) { lev = 1; jj = e; } else { lev = 0; jj = 0; c += (e - 2) * 8; }
+    } else {
+        if (F != F_LOGSUMEXP && s >= 80) return 1u << 31;
+        const int u = (s - 64) & 15, c2 = u >> 2, e = u & 3;
+        const int q = c2 + ((e & 1) ? 8 : 0) + ((e & 2) ? 4 : 0);
+        return (1u << 30) | (unsigned)(2 * ((long long)q << a.logn_root) + (s < 80 ? 0 : 1));
+    }
+    if (jj >= a.lev_tau[lev]) return 1u << 31;
+    return (unsigned)(a.lev_tab[lev] + ((long long)jj << a.lev_logn[lev]) + ((long long)c << a.logn_root));
+}
+
+// h'(v) / gfac for the two columns of a lane (log-sum-exp: nax = -aux)
+template <int F>
+__device__ __forceinline__ float2 hp2(float2 v, float c0, float2 nax) {
+    if constexpr (F == F_LOGSUMEXP) {
+        const float2 w = __fadd2_rn(v, nax);
+        return f2(ex2f(w.x), ex2f(w.y));
+    } else {
+        return f2(Fn<F, float>::hp(v.x, c0, 0.0f), Fn<F, float>::hp(v.y, c0, 0.0f));
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(const __grid_constant__ FineArgs<float> a) {
+    __shared__ __align__(16) float xs[2][kRB][kRowPad];
+    __shared__ __align__(16) float2 red[15][kBwdCols / 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int half = warp >> 2, colw = (warp & 3) * 32 + lane;   // column pair of this lane
+    const int grp = blockIdx.x, pass = blockIdx.y, r = blockIdx.z;
+    const long long n_root = 1LL << a.logn_root;
+    const int t = pass * kBwdCols + 2 * colw;
+    const bool active = t < a.tau_pad;                          // then t + 1 < tau_pad too
+    const float* tab = a.tab + (long long)r * a.tab_stride;
+    const float upstream = (float)a.upstream[0];
+    const float kap = a.kappa, c0 = a.c0;
+
+    // kappa * A of the thread's two columns and the band-gradient accumulators, as column pairs
+    float2 ah3[8], ah2[4], ah1[2], ah0;
+    float2 g3[8], g2[4], g1[2], g0;
+    auto lda = [&](int lev, int jj) -> float2 {
+        if (!active || jj >= a.lev_tau[lev]) return f2(0.0f, 0.0f);
+        const float* p = a.A + (long long)(a.lev_col0[lev] + jj) * a.ldA + t;
+        return f2(kap * __ldg(p), kap * __ldg(p + 1));
+    };
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) { ah3[jj] = lda(3, jj); g3[jj] = f2(0.0f, 0.0f); }
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) { ah2[jj] = lda(2, jj); g2[jj] = f2(0.0f, 0.0f); }
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) { ah1[jj] = lda(1, jj); g1[jj] = f2(0.0f, 0.0f); }
+    ah0 = lda(0, 0);
+    g0 = f2(0.0f, 0.0f);
+
+    const long long rho_beg = (long long)grp * a.roots_per_cta;
+    const long long rho_end = min(rho_beg + (long long)a.roots_per_cta, n_root);
+    const int nb = rho_end > rho_beg ? (int)((rho_end - rho_beg + kRB - 1) / kRB) : 0;
+    // staging: thread tid fills slots tid / 8 + 32 u of batch root tid % 8
+    constexpr int PER = kRB * kSlots / kBwdThreads;
+    const int jst = tid & 7;
+    const float* rsave = a.rowsave + 2 * (long long)r * a.N;
+    unsigned code[PER];
+    float pre[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) code[u] = bwd_slot_code<F>(a, (tid >> 3) + 32 * u);
+    auto fetch = [&](long long rb0) {
+        const long long rho = rb0 + jst;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            float v = 0.0f;
+            if (!(code[u] >> 31) && rho < rho_end) {
+                if (code[u] >> 30) {
+                    v = __ldg(rsave + (code[u] & 0x3fffffffu) + 2 * rho);
+                    v = (code[u] & 1u) ? -v : upstream * v;
+                } else {
+                    v = __ldg(tab + code[u] + rho);
+                }
+            }
+            pre[u] = v;
+        }
+    };
+    auto put = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+            *reinterpret_cast<float2*>(&xs[buf][jst][2 * ((tid >> 3) + 32 * u)]) = f2(pre[u], pre[u]);
+    };
+    // root values S_4 (layout [t/4][rho][4]) of the thread's columns, and its root-gradient column
+    const float* Sb = (a.S && active) ? a.S + (long long)r * a.S_stride + ((long long)(t >> 2) << a.logn_root) * 4 + (t & 3)
+                                      : nullptr;
+    float* Fb = a.Froot + (long long)r * n_root * a.tau_pad + t;
+    auto lds2 = [&](long long rho) -> float2 {
+        return Sb ? __ldg(reinterpret_cast<const float2*>(Sb + rho * 4)) : make_float2(0.0f, 0.0f);
+    };
+
+    if (nb > 0) { fetch(rho_beg); put(0); }
+    __syncthreads();
+    float2 snext = rho_beg + half < rho_end ? lds2(rho_beg + half) : make_float2(0.0f, 0.0f);
+    for (int kb = 0; kb < nb; ++kb) {
+        const long long rb0 = rho_beg + (long long)kb * kRB;
+        if (kb + 1 < nb) fetch(rb0 + kRB);                        // in flight during this batch
+        for (int j = half; j < kRB; j += 2) {
+            const long long rho = rb0 + j;
+            if (rho >= rho_end) break;
+            const float2 sr = snext;
+            if (rho + 2 < rho_end) snext = lds2(rho + 2);
+            const float* xr = xs[kb & 1][j];
+            // slots 2g and 2g + 1, each a {v, v} pair
+            auto pairs = [&](int g, float2& p0, float2& p1) {
+                const float4 q = *reinterpret_cast<const float4*>(xr + 4 * g);
+                p0 = f2(q.x, q.y);
+                p1 = f2(q.z, q.w);
+            };
+            float2 Fr = f2(0.0f, 0.0f);
+#pragma unroll
+            for (int c3 = 0; c3 < 2; ++c3) {
+                // (x of the level-3 and level-2 nodes is read again for the gradient updates
+                // instead of being held in registers across the subtree)
+                // (two interleaved partial sums shorten the dependent chain)
+                float2 v3 = f2(kap * sr.x, kap * sr.y), w3 = f2(0.0f, 0.0f), F3 = f2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float2 xa, xb;
+                    pairs(4 * c3 + k, xa, xb);
+                    v3 = ffma2(xa, ah3[2 * k], v3);
+                    w3 = ffma2(xb, ah3[2 * k + 1], w3);
+                }
+                v3 = __fadd2_rn(v3, w3);
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int c2 = c3 + 2 * k2;
+                    float2 v2 = v3, w2 = f2(0.0f, 0.0f), F2 = f2(0.0f, 0.0f);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        float2 xa, xb;
+                        pairs(8 + 2 * c2 + k, xa, xb);
+                        v2 = ffma2(xa, ah2[2 * k], v2);
+                        w2 = ffma2(xb, ah2[2 * k + 1], w2);
+                    }
+                    v2 = __fadd2_rn(v2, w2);
+#pragma unroll
+                    for (int k1 = 0; k1 < 2; ++k1) {             // level-1 node c1 = c2 + 4 k1
+                        const int c1 = c2 + 4 * k1;
+                        float2 x10, x11, x0a, x0b;
+                        pairs(16 + 2 * c1, x10, x11);
+                        pairs(17 + 2 * c1, x0a, x0b);
+                        const float2 v1 = ffma2(x11, ah1[1], ffma2(x10, ah1[0], v2));
+                        // leaves c1 and c1 + 8: coefficients (and -aux) in slots 64 + 4 c2 + 2 k1 + (0, 1)
+                        float2 cfa, cfb, naa = f2(0.0f, 0.0f), nab = f2(0.0f, 0.0f);
+                        pairs(32 + 2 * c2 + k1, cfa, cfb);
+                        if constexpr (F == F_LOGSUMEXP) pairs(40 + 2 * c2 + k1, naa, nab);
+                        const float2 Ga = __fmul2_rn(cfa, hp2<F>(ffma2(x0a, ah0, v1), c0, naa));
+                        const float2 Gb = __fmul2_rn(cfb, hp2<F>(ffma2(x0b, ah0, v1), c0, nab));
+                        g0 = ffma2(x0b, Gb, ffma2(x0a, Ga, g0));
+                        const float2 F1 = __fadd2_rn(Ga, Gb);
+                        g1[0] = ffma2(x10, F1, g1[0]);
+                        g1[1] = ffma2(x11, F1, g1[1]);
+                        F2 = __fadd2_rn(F2, F1);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        float2 xa, xb;
+                        pairs(8 + 2 * c2 + k, xa, xb);
+                        g2[2 * k] = ffma2(xa, F2, g2[2 * k]);
+                        g2[2 * k + 1] = ffma2(xb, F2, g2[2 * k + 1]);
+                    }
+                    F3 = __fadd2_rn(F3, F2);
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float2 xa, xb;
+                    pairs(4 * c3 + k, xa, xb);
+                    g3[2 * k] = ffma2(xa, F3, g3[2 * k]);
+                    g3[2 * k + 1] = ffma2(xb, F3, g3[2 * k + 1]);
+                }
+                Fr = __fadd2_rn(Fr, F3);
+            }
+            if (active) {
+                // columns at or beyond tau carry no gradient
+                *reinterpret_cast<float2*>(Fb + rho * a.tau_pad) =
+                    make_float2(t < a.tau ? Fr.x : 0.0f, t + 1 < a.tau ? Fr.y : 0.0f);
+            }
+        }
+        if (kb + 1 < nb) put((kb + 1) & 1);
+        __syncthreads();
+    }
+
+    // the two root halves' accumulators, in a fixed order; gradient rows in the band's column
+    // order: level 0, level 1 (2), level 2 (4), level 3 (8)
+    auto row = [&](int j) -> float2 { return j == 0 ? g0 : j < 3 ? g1[j - 1] : j < 7 ? g2[j - 3] : g3[j - 7]; };
+    if (half == 1) {
+#pragma unroll
+        for (int j = 0; j < 15; ++j) red[j][colw] = row(j);
+    }
+    __syncthreads();
+    if (half == 0 && active) {
+        float* out = a.gradpart + ((long long)r * a.groups + grp) * 15 * a.tau_pad + t;
+#pragma unroll
+        for (int j = 0; j < 15; ++j) {
+            const float2 o = __fadd2_rn(row(j), red[j][colw]);
+            *reinterpret_cast<float2*>(out + (long long)j * a.tau_pad) =
+                make_float2(t < a.tau ? o.x : 0.0f, t + 1 < a.tau ? o.y : 0.0f);
+        }
+    }
+}
+
+}  // namespace
+
+int fine_s4_fwd_roots() { return kFwdRoots; }
+int fine_s4_bwd_cols() { return kBwdCols; }
+int fine_s4_bwd_batch() { return kRB; }
+
+template <int F>
+static cudaError_t fwd_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {
+    const size_t smem = (size_t)a.cr * kAQuads * sizeof(float4);
+    static bool opted_in = false;                  // dynamic + static shared memory may exceed 48 KB
+    if (!opted_in) {
+        const cudaError_t e = cudaFuncSetAttribute(k_fine_fwd_s4<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(kMaxCRS4 * kAQuads * sizeof(float4)));
+        if (e != cudaSuccess) return e;
+        opted_in = true;
+    }
+    k_fine_fwd_s4<F><<<grid, kFwdThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
+    if (a.cr < 4 || a.cr > kMaxCRS4 || (a.cr & 3)) return cudaErrorInvalidValue;
+    switch (F) {
+        case F_LINEAR_MEAN: return fwd_s4<F_LINEAR_MEAN>(a, grid, st);
+        case F_MEAN_COS: return fwd_s4<F_MEAN_COS>(a, grid, st);
+        case F_CALL_MEAN_EXP: return fwd_s4<F_CALL_MEAN_EXP>(a, grid, st);
+        case F_GAUSS_NORM2: return fwd_s4<F_GAUSS_NORM2>(a, grid, st);
+        case F_PDE_INV_SQ: return fwd_s4<F_PDE_INV_SQ>(a, grid, st);
+        case F_LOGSUMEXP: return fwd_s4<F_LOGSUMEXP>(a, grid, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
+    switch (F) {
+        case F_LINEAR_MEAN: k_fine_bwd_s4<F_LINEAR_MEAN><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_MEAN_COS: k_fine_bwd_s4<F_MEAN_COS><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_CALL_MEAN_EXP: k_fine_bwd_s4<F_CALL_MEAN_EXP><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_GAUSS_NORM2: k_fine_bwd_s4<F_GAUSS_NORM2><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_PDE_INV_SQ: k_fine_bwd_s4<F_PDE_INV_SQ><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_LOGSUMEXP: k_fine_bwd_s4<F_LOGSUMEXP><<<grid, kBwdThreads, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace qmc

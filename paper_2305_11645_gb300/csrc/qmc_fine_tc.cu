@@ -54,13 +54,14 @@ constexpr int kRootsPerTile = 8;        // x 16 leaves = 128 rows per tile
 constexpr int NT_FWD = 256, NT_BWD = 128;
 
 // Shared-memory map of the producer stages: per stage, P pieces of W (128 rows x 64 B) and
-// P pieces of [A_f ; S]^T (NTT rows x 64 B); FP32 staging of the coalesced loads.
-template <int P, int NTT>
+// P pieces of [A_f ; S]^T (NTT rows x 64 B), NS stages; FP32 staging of the coalesced loads.
+template <int P, int NTT, int NS = 2>
 struct Stages {
+    static constexpr int NSTAGE = NS;
     static constexpr uint32_t TILE_A = TM * ROWB;
     static constexpr uint32_t TILE_B = NTT * ROWB;
     static constexpr uint32_t STAGE = P * (TILE_A + TILE_B);
-    static constexpr uint32_t XST = 2 * STAGE;                // 64 fine nodes x 8 roots
+    static constexpr uint32_t XST = NS * STAGE;               // 64 fine nodes x 8 roots
     static constexpr uint32_t SST = XST + 64 * 8 * 4;         // NTT columns x 8 roots
     static constexpr uint32_t END = SST + NTT * 8 * 4;
 };
@@ -144,13 +145,13 @@ __device__ __forceinline__ bool prod_sync_or(bool v) {
 // The loads of tile i+1 are in flight while tile i is converted.  A stage is refilled
 // after the MMA thread's commit on empty[s] (all MMAs that read it have completed).
 // ------------------------------------------------------------------------------------------
-template <int P, int NTT>
+template <int P, int NTT, int NS>
 __device__ __forceinline__ void producer_loop(const FineArgs<float>& a, unsigned char* smem, uint64_t* full,
                                               uint64_t* empty, volatile int* abort, int p, long long u0,
                                               long long ustep, long long units, int t0, int lmt) {
-    using L = Stages<P, NTT>;
+    using L = Stages<P, NTT, NS>;
     constexpr int H = NTT / 128;                 // B rows per thread
-    constexpr int NS = NTT / 128 * 2;            // S float4 loads per thread
+    constexpr int NSL = NTT / 128 * 2;           // S float4 loads per thread
     const long long n_root = 1LL << a.logn_root;
     float* Xst = reinterpret_cast<float*>(smem + L::XST);
     float* Sst = reinterpret_cast<float*>(smem + L::SST);
@@ -159,14 +160,14 @@ __device__ __forceinline__ void producer_loop(const FineArgs<float>& a, unsigned
     const bool item_live = jj_i < a.lev_tau[lev_i];
     const long long item_off = a.lev_tab[lev_i] + ((long long)jj_i << a.lev_logn[lev_i]) +
                                (long long)c_i * n_root + 4 * (p & 1);
-    float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), sr[NS];
+    float4 xr = make_float4(0.f, 0.f, 0.f, 0.f), sr[NSL];
     auto load_tile = [&](long long u) {
         const long long r = u >> lmt, rho0 = (u & ((1LL << lmt) - 1)) * kRootsPerTile;
         xr = item_live ? __ldg(reinterpret_cast<const float4*>(a.tab + r * a.tab_stride + item_off + rho0))
                        : make_float4(0.f, 0.f, 0.f, 0.f);
         const float* S = a.S + r * a.S_stride;
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
+        for (int i = 0; i < NSL; ++i) {
             const int f = p + 128 * i, t4 = f >> 3, ri = f & 7;
             sr[i] = (S && t0 + 4 * t4 < a.tau_pad)
                         ? __ldg(reinterpret_cast<const float4*>(
@@ -192,7 +193,7 @@ __device__ __forceinline__ void producer_loop(const FineArgs<float>& a, unsigned
         float e[8], z[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) { e[i] = (i == (p >> 4)) ? 1.0f : 0.0f; z[i] = 0.0f; }
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < NS; ++s) {
             unsigned char* As_ = smem + s * L::STAGE;
             unsigned char* Bs_ = As_ + P * L::TILE_A;
             store_group<P>(As_, L::TILE_A, p, 2, e);
@@ -213,7 +214,7 @@ __device__ __forceinline__ void producer_loop(const FineArgs<float>& a, unsigned
         if (prod_sync_or(u >= units || *abort || !ok)) break;
         *reinterpret_cast<float4*>(Xst + item * 8 + 4 * (p & 1)) = xr;
 #pragma unroll
-        for (int i = 0; i < NS; ++i) {
+        for (int i = 0; i < NSL; ++i) {
             const int f = p + 128 * i, t4 = f >> 3, ri = f & 7;
             Sst[(4 * t4 + 0) * 8 + ri] = sr[i].x;
             Sst[(4 * t4 + 1) * 8 + ri] = sr[i].y;
@@ -237,8 +238,8 @@ __device__ __forceinline__ void producer_loop(const FineArgs<float>& a, unsigned
             sv[h][0] = a.kappa * lo.x; sv[h][1] = a.kappa * lo.y; sv[h][2] = a.kappa * lo.z; sv[h][3] = a.kappa * lo.w;
             sv[h][4] = a.kappa * hi.x; sv[h][5] = a.kappa * hi.y; sv[h][6] = a.kappa * hi.z; sv[h][7] = a.kappa * hi.w;
         }
-        const int s = (int)(it & 1);
-        if (it >= 2) ok = mbar_wait_abort(&empty[s], (uint32_t)(((it - 2) >> 1) & 1), abort);
+        const int s = (int)(it % NS);
+        if (it >= NS) ok = mbar_wait_abort(&empty[s], (uint32_t)(((it - NS) / NS) & 1), abort);
         if (ok) {                                      // (a failed wait stops all producers at the loop top)
             unsigned char* As_ = smem + s * L::STAGE;
             unsigned char* Bs_ = As_ + P * L::TILE_A;
@@ -258,10 +259,11 @@ __device__ __forceinline__ void issue_forward(uint32_t d, uint32_t As_, uint32_t
     using L = Stages<P, NTT>;
     const uint32_t Bs_ = As_ + P * L::TILE_A;
     bool first = true;
-    issue_kstep<P>(d, As_, L::TILE_A, Bs_, L::TILE_B, idesc, first);                     // X_f A_f
+    const uint64_t da = smem_desc_sw64(As_), db = smem_desc_sw64(Bs_);
+    issue_kstep<P, L::TILE_A, L::TILE_B>(d, da, db, idesc, first);                         // X_f A_f
 #pragma unroll
     for (int j = 0; j < P; ++j)                                                          // E S_j
-        mma_bf16(d, smem_desc_sw64(As_ + 32), smem_desc_sw64(Bs_ + 32 + j * L::TILE_B), idesc, 1u);
+        mma_bf16(d, desc_add(da, 32), desc_add(db, 32 + j * L::TILE_B), idesc, 1u);
 }
 
 }  // namespace
@@ -307,7 +309,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_fine_fwd_tc(const FineArgs<float
     const uint32_t tmem = *tmem_slot;
 
     if (warp >= EPI_WARPS && warp < EPI_WARPS + PROD_WARPS) {
-        producer_loop<P, NT_FWD>(a, smem, full, empty, abort, tid - EPI_WARPS * 32, u0, ustep, units, t0, lmt);
+        producer_loop<P, NT_FWD, 2>(a, smem, full, empty, abort, tid - EPI_WARPS * 32, u0, ustep, units, t0, lmt);
     } else if (warp == EPI_WARPS + PROD_WARPS) {
         // ---------------------------------------------------------------- MMA issue
         if ((tid & 31) == 0) {
@@ -419,19 +421,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_fine_fwd_tc(const FineArgs<float
 // ==========================================================================================
 template <int P, int F>
 __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<float> a, int ntn, long long units) {
-    using L = Stages<P, NT_BWD>;
+    using L = Stages<P, NT_BWD, 3>;
+    constexpr int NS = L::NSTAGE;
     constexpr uint32_t BUF = 192, BWD = 384;                            // TMEM columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = align_1k(smem_raw);
     float2* coefs = reinterpret_cast<float2*>(smem + L::END);            // [epilogue warp][32 rows]
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L::END + EPI_WARPS_B * 32 * sizeof(float2));
-    uint64_t* empty = full + 2;
-    uint64_t* accf = full + 4;
-    uint64_t* gready = full + 6;
-    uint64_t* bwdf = full + 7;
-    uint64_t* bwde = full + 8;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(full + 9);
-    volatile int* abort = reinterpret_cast<volatile int*>(full + 10);
+    uint64_t* empty = full + NS;
+    uint64_t* accf = full + 2 * NS;
+    uint64_t* gready = accf + 2;
+    uint64_t* bwdf = accf + 3;
+    uint64_t* bwde = accf + 4;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 5);
+    volatile int* abort = reinterpret_cast<volatile int*>(accf + 6);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nt = blockIdx.x % ntn;
@@ -443,8 +446,10 @@ __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<flo
 
     if (warp == 0) tmem_alloc(smem_u32(tmem_slot), 512);
     if (tid == 0) {
-        mbar_init(&full[0], PROD_WARPS * 32); mbar_init(&full[1], PROD_WARPS * 32);
-        mbar_init(&empty[0], 1); mbar_init(&empty[1], 1);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(&full[i], PROD_WARPS * 32);
+            mbar_init(&empty[i], 1);
+        }
         mbar_init(&accf[0], 1); mbar_init(&accf[1], 1);
         mbar_init(gready, EPI_WARPS_B * 32);
         mbar_init(bwdf, 1);
@@ -459,7 +464,7 @@ __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<flo
 
     constexpr int PROD0 = EPI_WARPS_B + DRAIN_WARPS, MMAW = PROD0 + PROD_WARPS;
     if (warp >= PROD0 && warp < MMAW) {
-        producer_loop<P, NT_BWD>(a, smem, full, empty, abort, tid - PROD0 * 32, u0, ustep, units, t0, lmt);
+        producer_loop<P, NT_BWD, NS>(a, smem, full, empty, abort, tid - PROD0 * 32, u0, ustep, units, t0, lmt);
     } else if (warp >= EPI_WARPS_B && warp < PROD0) {
         // ---------------------------------------------------------------- drain
         const int quarter = warp - EPI_WARPS_B;
@@ -502,18 +507,22 @@ __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<flo
         // ---------------------------------------------------------------- MMA issue
         if ((tid & 31) == 0) {
             const uint32_t idesc_f = idesc_bf16(TM);                      // D^T: M = t, N = l = 128
+            uint32_t idesc_bwd[P];                                        // A in TMEM, B (W) MN-major
+#pragma unroll
+            for (int i = 0; i < P; ++i) idesc_bwd[i] = idesc_bf16(32u * (P - i)) | (1u << 16);
             auto forward = [&](long long it) -> bool {                    // D^T of tile it into buffer it & 1
-                const int s = (int)(it & 1), b = (int)(it & 1);
-                if (!mbar_wait_abort(&full[s], (uint32_t)((it >> 1) & 1), abort)) return false;
+                const int s = (int)(it % NS), b = (int)(it & 1);
+                if (!mbar_wait_abort(&full[s], (uint32_t)((it / NS) & 1), abort)) return false;
                 fence_after_sync();
                 const uint32_t W = smem_u32(smem + s * L::STAGE);
                 const uint32_t Bt = W + P * L::TILE_A;
                 const uint32_t d = tmem + (uint32_t)(b * BUF);
                 bool first = true;
-                issue_kstep<P>(d, Bt, L::TILE_B, W, L::TILE_A, idesc_f, first);         // A_f^T X_f^T
+                const uint64_t dbt = smem_desc_sw64(Bt), dw = smem_desc_sw64(W);
+                issue_kstep<P, L::TILE_B, L::TILE_A>(d, dbt, dw, idesc_f, first);       // A_f^T X_f^T
 #pragma unroll
                 for (int j = 0; j < P; ++j)                                             // S_j^T E^T
-                    mma_bf16(d, smem_desc_sw64(Bt + 32 + j * L::TILE_B), smem_desc_sw64(W + 32), idesc_f, 1u);
+                    mma_bf16(d, desc_add(dbt, 32 + j * L::TILE_B), desc_add(dw, 32), idesc_f, 1u);
                 mma_commit(smem_u32(&accf[b]));
                 return true;
             };
@@ -524,25 +533,21 @@ __global__ void __launch_bounds__(THREADS_B, 1) k_fine_bwd_tc(const FineArgs<flo
                         if (it >= 1 && !mbar_wait_abort(bwdf, (uint32_t)((it - 1) & 1), abort)) break;
                         if (!forward(it + 1)) break;
                     }
-                    const int s = (int)(it & 1), b = (int)(it & 1);
+                    const int s = (int)(it % NS), b = (int)(it & 1);
                     if (!mbar_wait_abort(gready, (uint32_t)(it & 1), abort)) break;
                     // the drain warps have read the backward accumulator of tile it - 1
                     if (it >= 1 && !mbar_wait_abort(bwde, (uint32_t)((it - 1) & 1), abort)) break;
                     fence_after_sync();
                     // D' = G^T [W_0 | W_1 | W_2]: 8 K-steps of 16 rows; piece i of G multiplies the
                     // pieces W_0 .. W_{P-1-i} (N = 32 (P - i)), the six products with i + j <= 2
-                    const uint32_t W = smem_u32(smem + s * L::STAGE);
+                    const uint64_t dw = smem_desc_sw64_mn(smem_u32(smem + s * L::STAGE), L::TILE_A, 512);
                     const uint32_t gbuf = tmem + (uint32_t)(b * BUF);
-                    bool first = true;
-#pragma unroll 1
+#pragma unroll
                     for (int ks = 0; ks < TM / 16; ++ks) {
 #pragma unroll
-                        for (int i = 0; i < P; ++i) {
-                            mma_bf16_tmem_a(tmem + BWD, gbuf + 64u * i + 8u * ks,
-                                            smem_desc_sw64_mn(W + ks * 1024, L::TILE_A, 512),
-                                            idesc_bf16(32u * (P - i)) | (1u << 16), first ? 0u : 1u);
-                            first = false;
-                        }
+                        for (int i = 0; i < P; ++i)
+                            mma_bf16_tmem_a(tmem + BWD, gbuf + 64u * i + 8u * ks, desc_add(dw, ks * 1024),
+                                            idesc_bwd[i], (ks == 0 && i == 0) ? 0u : 1u);
                     }
                     mma_commit(smem_u32(bwdf));
                     mma_commit(smem_u32(&empty[s]));
@@ -652,7 +657,7 @@ cudaError_t bwd_tc_launch(const FineArgs<float>& a, cudaStream_t st) {
     const int ntn = (a.tau_pad + NT_BWD - 1) / NT_BWD;
     const long long units = (long long)a.reff * ((1LL << a.logn_root) / kRootsPerTile);
     const long long per = bwd_tc_partials(a.tau_pad, a.reff, a.logn_root);
-    const size_t smem = at_least_120k(1024 + Stages<P, NT_BWD>::END + EPI_WARPS_B * 32 * sizeof(float2) + 128);
+    const size_t smem = at_least_120k(1024 + Stages<P, NT_BWD, 3>::END + EPI_WARPS_B * 32 * sizeof(float2) + 128);
     cudaError_t e = cudaFuncSetAttribute(k_fine_bwd_tc<P, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_fine_bwd_tc<P, F><<<(unsigned)(per * ntn), THREADS_B, smem, st>>>(a, ntn, units);

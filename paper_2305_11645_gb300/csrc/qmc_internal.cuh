@@ -287,6 +287,15 @@ cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const 
                                   const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
                                   float* part, int reff, int ntiles, int pieces, cudaStream_t st);
 cudaError_t tc_error_word(unsigned int* value, bool clear);
+// the S4 fine band in FP32 on the CUDA cores: forward CTAs of fine_s4_fwd_roots() roots (grid:
+// root blocks x column groups of a.cr <= 512 columns x shifts), adjoint CTAs of fine_s4_bwd_cols()
+// columns (grid: root groups of a.roots_per_cta roots, a multiple of fine_s4_bwd_batch() x
+// column passes x shifts)
+int fine_s4_fwd_roots();
+int fine_s4_bwd_cols();
+int fine_s4_bwd_batch();
+cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
+cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
 // fused forward of the S4 fine band on tensor cores; row partials per 128-column group
 int fine_tc_group_cols();
 cudaError_t launch_fine_fwd_tc(const FineArgs<float>& a, int F, int pieces, cudaStream_t st);

@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__
         if (tid == 0) {
             const uint32_t idesc = idesc_bf16(TM);
             for (int ks = 0; ks < ksteps; ++ks)
-                issue_kstep<P>(tmem, smem_u32(Xs) + 32 * ks, TILE, smem_u32(As) + 32 * ks, TILE, idesc, first);
+                issue_kstep<P, TILE, TILE>(tmem, smem_desc_sw64(smem_u32(Xs) + 32 * ks),
+                                           smem_desc_sw64(smem_u32(As) + 32 * ks), idesc, first);
             mma_commit(smem_u32(&bar[s]));
         }
     }
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict_
         if (tid == 0) {
             const uint32_t idesc = idesc_bf16(nmma);
             for (int ks = 0; ks < ksteps; ++ks)
-                issue_kstep<P>(tmem, smem_u32(Fs) + 32 * ks, TILEA, smem_u32(Xs) + 32 * ks, TILEB, idesc, first);
+                issue_kstep<P, TILEA, TILEB>(tmem, smem_desc_sw64(smem_u32(Fs) + 32 * ks),
+                                             smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, first);
             mma_commit(smem_u32(&bar[s]));
         }
     }

@@ -141,18 +141,25 @@ __device__ __forceinline__ void store_group(unsigned char* tile0, uint32_t piece
         *reinterpret_cast<uint4*>(tile0 + p * piece_stride + off) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
-// The piece products of one K-step, smallest first: A piece i times B piece j.
-template <int P>
-__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint32_t a_base, uint32_t a_piece, uint32_t b_base,
-                                            uint32_t b_piece, uint32_t idesc, bool& first) {
+// Descriptor arithmetic: the start address sits in the low 14 bits as address / 16, so a
+// descriptor of addr + bytes is the descriptor of addr plus bytes / 16 (shared-memory
+// addresses stay below 256 KB, so the field never carries).  The issuing thread then spends
+// one add per MMA instead of building a descriptor: the MMA issue rate of a single thread is
+// otherwise the bound of these kernels.
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
+// The piece products of one K-step, smallest first: A piece i times B piece j; adesc, bdesc
+// describe piece 0 of each operand at this K-step, the pieces A_PIECE / B_PIECE bytes apart.
+template <int P, uint32_t A_PIECE, uint32_t B_PIECE>
+__device__ __forceinline__ void issue_kstep(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            bool& first) {
     constexpr int NP = P == 3 ? 6 : 1;
     constexpr int pi[6] = {2, 1, 0, 1, 0, 0};
     constexpr int pj[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
         const int i = P == 3 ? pi[q] : 0, j = P == 3 ? pj[q] : 0;
-        mma_bf16(tmem, smem_desc_sw64(a_base + i * a_piece), smem_desc_sw64(b_base + j * b_piece), idesc,
-                 first ? 0u : 1u);
+        mma_bf16(tmem, desc_add(adesc, i * A_PIECE), desc_add(bdesc, j * B_PIECE), idesc, first ? 0u : 1u);
         first = false;
     }
 }
