@@ -6,8 +6,8 @@ one random shift, inverse-normal transform, A=L^T of the exp(-|t_i-t_j|/0.1) cov
 f=max(mean_t exp(0.2 y_t)-1,0)): point generation, transform, coarse block products, the
 fused periodic broadcast-accumulate with f and the mean, and the folded adjoint dQ/dA.
 Metric: x_k^T A outputs per second, N*tau*R / step time.  The headline tier is the split
-tier (bf16x6 tensor-core products, FP32 elsewhere); the FP32 and plain-bf16 tiers are
-timed beside it.
+tier (bf16x6 tensor-core coarse block products, FP32 elsewhere); the FP32 and plain-bf16
+tiers are timed beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision split|fp32|bf16]
@@ -155,62 +155,37 @@ def band_of(p):
 
 
 H_OPS = {1: (0, 0), 2: (1, 1), 3: (1, 1), 4: (1, 0), 5: (3, 1), 6: (1, 1)}   # (fp32 ops, mufu ops) per h(y)
+# MUFU (ex2, sin, cos, rcp) lanes per SM per clock: ncu's peak for the XU pipe is one warp
+# instruction per 4 cycles per SM sub-partition (measured: an ex2 loop reaches 27.6 per clock)
+MUFU_LANES = 32
 
 
-def fine_fwd_work(p):
-    """Algorithmic work of one fused fine-band launch (all shifts): per output element,
-    the tree's multiply-adds sum_{I<JF} tau_I 2^-I, the chain of coarse adds (count/2^JF),
-    h(y) and the row accumulation.  Returns (fp32 pipe ops, MUFU ops)."""
-    jf, tau_I, chain = band_of(p)
+def fine_work(p, name):
+    """Algorithmic work of one launch of the fine-band (S4) kernel, counted per output of all
+    shifts: the tree's multiply-adds sum_{I<4} tau_I 2^-I (4 for a full band), h(y) and the row
+    accumulation (forward); the recomputed tree, G = coef h'(y) (h' and a multiply), the fold
+    (one add per output amortised) and the gradient multiply-adds (adjoint).  Returns (FP32
+    pipe operations, an FMA counted once, MUFU operations)."""
+    jf, tau_I, _ = band_of(p)
     outs = p.N * p.tau * p.R_eff
     fma = sum(tau_I[I] / 2.0 ** I for I in range(jf))
     fp_h, mufu_h = H_OPS[p.f_kind]
-    fp32 = outs * (fma + len(chain) / 2.0 ** jf + fp_h + 1)
-    return fp32, outs * mufu_h
+    per = (fma + fp_h + 1) if "fwd" in name else (2 * fma + fp_h + 2)
+    return outs * per, outs * mufu_h
 
 
-def fine_bwd_work(p):
-    """Fine backward per output: recompute (tree FMAs + chain adds), G = coef h'(y) (h' and a
-    multiply), the fold (one add per output amortised) and the gradient multiply-adds."""
+def coarse_mma_flops(p, pieces):
+    """MMA flops of a coarse block-product launch (forward X_I A_I or adjoint X_I^T F_I, the
+    same contraction sizes): 2 n_I tau tau_I per level I >= 4 (n_I = 2^(m-I) distinct rows),
+    times the piece products (6 in the split tier, 1 in the bf16 tier)."""
     jf, tau_I, chain = band_of(p)
-    outs = p.N * p.tau * p.R_eff
-    fma = sum(tau_I[I] / 2.0 ** I for I in range(jf))
-    fp_h, mufu_h = H_OPS[p.f_kind]
-    fp32 = outs * (2 * fma + len(chain) / 2.0 ** jf + fp_h + 2)
-    return fp32, outs * mufu_h
-
-
-def tc_work(p, name, pieces):
-    """Tensor-core work of one launch of a fine-band kernel of the split (pieces=3) or bf16
-    (pieces=1) tier: MMA flops as issued (the piece products included) and MUFU ops.
-    Forward: per 128-row x 256-column tile, NP+P MMAs of 128x256x16 (NP = 6 / 1 piece products
-    of X_f A_f, P products E S).  Adjoint: per 128 x 128 tile, the same recomputation with
-    N = 128 plus 8 K-steps x P MMAs of 128 x 32P x 16 (G^T [W_0|W_1|W_2])."""
-    n_root = p.N // 16
-    outs = p.N * p.tau * p.R_eff
     np_ = 6 if pieces == 3 else 1
-    tau_pad = (p.tau + 3) // 4 * 4
-    if name == "k_fine_fwd_tc":
-        nt = 256
-        tiles = p.R_eff * (n_root // 8) * math.ceil(tau_pad / nt)
-        fma = tiles * (np_ + pieces) * 128 * nt * 16
-    else:
-        nt = 128
-        tiles = p.R_eff * (n_root // 8) * math.ceil(tau_pad / nt)
-        fma = tiles * ((np_ + pieces) * 128 * nt * 16 + 8 * pieces * 128 * 32 * pieces * 16)
-    _, mufu_h = H_OPS[p.f_kind]
-    return 2.0 * fma, outs * mufu_h
+    return sum(2.0 * 2 ** (p.m - I) * p.tau * tau_I[I] for I in chain if I < p.m + 1) * p.R_eff * np_
 
 
-def tc_roofline(flops, mufu_ops, seconds, clock_mhz, peak_tflops):
-    """Tensor pipe (measured dense bf16 peak) or MUFU (16 lanes/SM/clk), whichever bounds."""
-    p_mufu = SM_COUNT * 16 * clock_mhz * 1e6
-    t_tc, t_mufu = flops / (peak_tflops * 1e12), mufu_ops / p_mufu
-    if t_tc >= t_mufu:
-        return {"bound": "tensor", "achieved": flops / seconds / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": t_tc / seconds}
-    return {"bound": "alu", "pipe": "mufu", "achieved": mufu_ops / seconds / 1e9, "peak": p_mufu / 1e9,
-            "unit": "Gop/s", "frac": t_mufu / seconds}
+def tensor_roofline(flops, seconds, peak_tflops):
+    return {"bound": "tensor", "achieved": flops / seconds / 1e12, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": flops / seconds / 1e12 / peak_tflops}
 
 
 def peaks():
@@ -223,10 +198,11 @@ def peaks():
 
 
 def alu_roofline(fp32_ops, mufu_ops, seconds, clock_mhz):
-    """FP32 FMA pipe: 128 lanes/SM/clk; MUFU (ex2, sin, cos, rcp): 16 lanes/SM/clk."""
+    """FP32 pipe: 128 FMA lanes/SM/clk (the paired FFMA2 does two per lane in two cycles); MUFU:
+    MUFU_LANES/SM/clk.  The bound is the pipe with the larger time at full rate."""
     clk = clock_mhz * 1e6
     p_fp32 = SM_COUNT * 128 * clk
-    p_mufu = SM_COUNT * 16 * clk
+    p_mufu = SM_COUNT * MUFU_LANES * clk
     t_fp32, t_mufu = fp32_ops / p_fp32, mufu_ops / p_mufu
     if t_mufu > t_fp32:
         return {"bound": "alu", "pipe": "mufu", "achieved": mufu_ops / seconds / 1e9, "peak": p_mufu / 1e9,
@@ -310,19 +286,16 @@ def run_ours(args, dist, rank, world):
     name, (cnt, tot) = top
     per_launch = tot / cnt / 1e3
     if name.endswith("_tc"):
-        fl, wmu = tc_work(p, name, 3 if prec == "split" else 1)
-        roof = tc_roofline(fl, wmu, per_launch, clk, mp["bf16_tflops"])
-        roof["peak_source"] = (f"{peak_src} dense bf16 burst peak (MEASURED_PEAKS.json bf16_tflops) for the tensor "
-                               f"pipe; MUFU from {SM_COUNT} SMs x 16 lanes x median SM clock {clk:.0f} MHz")
-        roof["work"] = {"mma_flops": fl, "mufu_ops": wmu}
+        fl = coarse_mma_flops(p, 3 if prec == "split" else 1)
+        roof = tensor_roofline(fl, per_launch, mp["bf16_tflops"])
+        roof["peak_source"] = f"{peak_src} dense bf16 burst peak (MEASURED_PEAKS.json bf16_tflops)"
+        roof["work"] = {"mma_flops": fl}
     else:
-        if name == "k_fine_bwd":
-            w32, wmu = fine_bwd_work(p)
-        else:
-            w32, wmu = fine_fwd_work(p)
+        w32, wmu = fine_work(p, name)
         roof = alu_roofline(w32, wmu, per_launch, clk)
-        roof["peak_source"] = (f"derived from {SM_COUNT} SMs x pipe lanes x median SM clock {clk:.0f} MHz "
-                               f"(sampled during the timed region)")
+        roof["peak_source"] = (f"derived: {SM_COUNT} SMs x pipe lanes (FP32 128, MUFU {MUFU_LANES}) x median SM "
+                               f"clock {clk:.0f} MHz sampled during the timed region")
+        roof["work"] = {"fp32_ops": w32, "mufu_ops": wmu}
     roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": TRAFFIC_BYTES.get(name)})
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in sorted(kern.items())}
 

@@ -6,7 +6,6 @@
 
 #include <algorithm>
 #include <cstdarg>
-#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -194,9 +193,6 @@ struct Plan {
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
-    bool fine_tc = false;          // fused forward and adjoint of the fine band on tensor cores
-    int cg_tc = 0;                 // its row-partial column groups
-    long long fine_parts_tc = 0;   // band-gradient partials of its adjoint
     bool need_gen = false, need_shift = false, need_pad = false;
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
@@ -322,7 +318,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     // setup cost); the adjoint below.  m <= 27 keeps the adjoint's 32-bit staging offsets (4 * 2^m
     // table entries, 2 * 2^m row-save floats) below 2^30.
     P.fine_s4 = (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) && P.shape == SHAPE_S4 &&
-                precision != QMC_FP64 && P.m <= 27 && !getenv("QMC_FINE_TC");
+                precision != QMC_FP64 && P.m <= 27;
     if (P.fine_s4) {
         const int rows = fine_s4_fwd_roots();
         P.root_blocks = (int)((n_root + rows - 1) / rows);
@@ -339,10 +335,6 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     }
     // partials of the estimate: row blocks of the finalisation (256 rows each)
     P.nblk = (int)((P.N + 255) / 256);
-    // tensor-core tiers: the fused forward of the dyadic band runs on tensor cores (8 roots per tile)
-    P.fine_tc = !P.fine_s4 && P.tc_pieces != 0 && P.shape == SHAPE_S4 && logn_root >= 3;
-    P.cg_tc = (P.tau + fine_tc_group_cols() - 1) / fine_tc_group_cols();
-    P.fine_parts_tc = P.fine_tc ? bwd_tc_partials(P.tau_pad, P.reff, logn_root) : 0;
 
     // backward schedule
     if (op == QMC_OP_INTEGRATE_BWD && P.fine_s4) {
@@ -482,11 +474,10 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     uend = std::max(uend, align256(u0 + E * (size_t)P.reff * P.B_per_shift));
     if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
         size_t o = u0;
-        const int cgmax = std::max(P.cg_count, P.fine_tc ? P.cg_tc : 0);
         P.off_rowpart = o;
-        o = align256(o + E * (size_t)P.reff * cgmax * P.N);
+        o = align256(o + E * (size_t)P.reff * P.cg_count * P.N);
         P.off_rowmax = o;
-        if (P.fkind == QMC_F_LOGSUMEXP) o = align256(o + E * (size_t)P.reff * cgmax * P.N);
+        if (P.fkind == QMC_F_LOGSUMEXP) o = align256(o + E * (size_t)P.reff * P.cg_count * P.N);
         uend = std::max(uend, o);
     }
     if (op == QMC_OP_INTEGRATE_BWD) {
@@ -496,8 +487,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.off_Fchain = o;
         o = align256(o + E * (size_t)P.reff * (size_t)std::max(P.Fchain_per_shift, 1LL));
         P.off_gradpart = o;
-        const size_t nparts = std::max<size_t>((size_t)P.reff * P.groups, (size_t)P.fine_parts_tc);
-        o = align256(o + E * nparts * std::max(P.kf_width, 1) * P.tau_pad);
+        o = align256(o + E * (size_t)P.reff * P.groups * std::max(P.kf_width, 1) * P.tau_pad);
         P.off_partc = o;
         o = align256(o + E * (size_t)std::max(P.partc_elems, 1LL));
         uend = std::max(uend, o);
@@ -600,13 +590,7 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     }
     FineArgs<T> a = fine_args<T>(P, ws, A, ldA, mode == MODE_FUSED ? f : nullptr);
     a.P = dP;
-    const bool fine_tc = mode == MODE_FUSED && P.fine_tc;
-    if (fine_tc) {
-        if constexpr (std::is_same<T, float>::value) {
-            a.cg_count = P.cg_tc;
-            QMC_LAUNCH(st, "k_fine_fwd_tc", launch_fine_fwd_tc(a, P.fkind, P.tc_pieces, st));
-        }
-    } else if (mode == MODE_FUSED && P.fine_s4) {
+    if (mode == MODE_FUSED && P.fine_s4) {
         if constexpr (std::is_same<T, float>::value) {
             QMC_LAUNCH(st, "k_fine_fwd_s4", launch_fine_fwd_s4(a, P.fkind, dim3(P.root_blocks, P.cg_count, P.reff), st));
         }
@@ -620,7 +604,7 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
         double* fpart = reinterpret_cast<double*>(ws + P.off_fpart);
         const double coef_scale = gfac_of(P.fkind, f->params[0]) / ((double)P.reff * (double)P.N);
         QMC_LAUNCH(st, "k_rows_finalize",
-                   launch_rows_finalize<T>(a.rowpart, a.rowmax, fine_tc ? P.cg_tc : P.cg_count, P.N, P.reff,
+                   launch_rows_finalize<T>(a.rowpart, a.rowmax, P.cg_count, P.N, P.reff,
                                            P.fkind, (double)P.tau,
                                            f->params[0], f->params[1], coef_scale, rowsave, rowf, fpart, P.nblk,
                                            ticket, est, st));
@@ -651,13 +635,8 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
     a.roots_per_cta = P.roots_per_cta;
     a.groups = P.groups;
     a.kf_actual = P.kf_width;
-    int nfine_part = P.reff * P.groups;
-    if (P.fine_tc) {
-        if constexpr (std::is_same<T, float>::value) {
-            QMC_LAUNCH(st, "k_fine_bwd_tc", launch_fine_bwd_tc(a, P.fkind, P.tc_pieces, st));
-            nfine_part = (int)P.fine_parts_tc;
-        }
-    } else if (P.fine_s4) {
+    const int nfine_part = P.reff * P.groups;
+    if (P.fine_s4) {
         if constexpr (std::is_same<T, float>::value)
             QMC_LAUNCH(st, "k_fine_bwd_s4", launch_fine_bwd_s4(a, P.fkind, dim3(P.groups, P.passes, P.reff), st));
     } else {
@@ -705,17 +684,15 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
 // =============================================================================================
 extern "C" {
 
-const char* qmc_version(void) { return "qmc_gb300 0.2 (sm_103a)"; }
+const char* qmc_version(void) { return "qmc_gb300 0.3 (sm_103a)"; }
 const char* qmc_last_error(void) { return g_err.c_str(); }
 
 qmc_status qmc_validate_rule(const qmc_rule* rule) { return validate(rule); }
 
 qmc_status qmc_device_status(int clear) {
-    unsigned int word = 0, word2 = 0;
+    unsigned int word = 0;
     QMC_CUDA(cudaDeviceSynchronize());
     QMC_CUDA(tc_error_word(&word, clear != 0));
-    QMC_CUDA(fine_tc_error_word(&word2, clear != 0));
-    word |= word2 << 1;
     if (word) return fail(QMC_ERR_TIMEOUT, "a tensor-core kernel's bounded wait ran out (error word 0x%x)", word);
     return QMC_OK;
 }

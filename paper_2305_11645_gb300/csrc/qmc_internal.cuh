@@ -296,12 +296,5 @@ int fine_s4_bwd_cols();
 int fine_s4_bwd_batch();
 cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
 cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
-// fused forward of the S4 fine band on tensor cores; row partials per 128-column group
-int fine_tc_group_cols();
-cudaError_t launch_fine_fwd_tc(const FineArgs<float>& a, int F, int pieces, cudaStream_t st);
-// its adjoint: root gradients into Froot, band-gradient partials (15 x tau_pad each) into gradpart
-long long bwd_tc_partials(int tau_pad, int reff, int logn_root);
-cudaError_t launch_fine_bwd_tc(const FineArgs<float>& a, int F, int pieces, cudaStream_t st);
-cudaError_t fine_tc_error_word(unsigned int* value, bool clear);
 
 }  // namespace qmc

@@ -166,33 +166,6 @@ __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint64_t adesc, uint6
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}"
-                 :: "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
-    return done != 0;
-}
-// Bounded wait shared by the roles of a warp-specialised kernel: gives up when the CTA's
-// abort flag is raised by another role, and raises it when its own limit runs out.
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kWaitLimit; ++it) {
-        if (mbar_try(a, parity)) return true;
-        if (*abort) return false;
-    }
-    *abort = 1;
-    return false;
-}
-
 __device__ __forceinline__ unsigned char* align_1k(unsigned char* p) {
     return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
 }
