@@ -275,6 +275,7 @@ template <int F>
 __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(const __grid_constant__ FineArgs<float> a) {
     __shared__ __align__(16) float xs[2][kRB][kRowPad];
     __shared__ __align__(16) float2 red[15][kBwdCols / 2];
+    __shared__ unsigned codes[kSlots];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int half = warp >> 2, colw = (warp & 3) * 32 + lane;   // column pair of this lane
     const int grp = blockIdx.x, pass = blockIdx.y, r = blockIdx.z;
@@ -309,21 +310,20 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
     constexpr int PER = kRB * kSlots / kBwdThreads;
     const int jst = tid & 7;
     const float* rsave = a.rowsave + 2 * (long long)r * a.N;
-    unsigned code[PER];
+    if (tid < kSlots) codes[tid] = bwd_slot_code<F>(a, tid);    // (read after the first barrier)
     float pre[PER];
-#pragma unroll
-    for (int u = 0; u < PER; ++u) code[u] = bwd_slot_code<F>(a, (tid >> 3) + 32 * u);
     auto fetch = [&](long long rb0) {
         const long long rho = rb0 + jst;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
+            const unsigned code = codes[(tid >> 3) + 32 * u];
             float v = 0.0f;
-            if (!(code[u] >> 31) && rho < rho_end) {
-                if (code[u] >> 30) {
-                    v = __ldg(rsave + (code[u] & 0x3fffffffu) + 2 * rho);
-                    v = (code[u] & 1u) ? -v : upstream * v;
+            if (!(code >> 31) && rho < rho_end) {
+                if (code >> 30) {
+                    v = __ldg(rsave + (code & 0x3fffffffu) + 2 * rho);
+                    v = (code & 1u) ? -v : upstream * v;
                 } else {
-                    v = __ldg(tab + code[u] + rho);
+                    v = __ldg(tab + code + rho);
                 }
             }
             pre[u] = v;
@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
         return Sb ? __ldg(reinterpret_cast<const float2*>(Sb + rho * 4)) : make_float2(0.0f, 0.0f);
     };
 
+    __syncthreads();                                            // the slot codes
     if (nb > 0) { fetch(rho_beg); put(0); }
     __syncthreads();
     float2 snext = rho_beg + half < rho_end ? lds2(rho_beg + half) : make_float2(0.0f, 0.0f);
