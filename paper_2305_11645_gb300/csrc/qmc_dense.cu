@@ -105,12 +105,11 @@ template cudaError_t launch_coarse_fwd<double>(const double*, long long, const d
 
 // S[r][t/4][rho][t%4] = sum_e B_e[r][t/4][rho mod n_e][t%4], rho < n_root (Algorithm 2's
 // periodic tiling of the coarse block products onto the root rows).
-// A thread owns one group of four columns and one node rho' < n_top = n_root / 2^D: the
-// 2^D root rows rho' + q n_top of its subtree share their rows in every coarse entry with
-// n_e >= n_top (rho' + (q mod n_e/n_top) n_top, 2^D n_e / n_root distinct rows), and one
-// row rho' mod n_e of every coarser entry.  Each entry row is loaded once per thread and
-// added to all the root rows it tiles; consecutive threads take consecutive rho', so
-// every load and store of a warp is contiguous.
+// A thread owns one group of four columns and the 2^D root rows rho' + q n_top of the subtree
+// of node rho' < n_top = n_root / 2^D; an entry row is (rho' + q n_top) mod n_e.  The entries
+// are taken in batches whose loads (about 16 float4 per thread) are all issued before any of
+// their adds, and added in entry order; consecutive threads take consecutive rho', so every
+// load and store of a warp is contiguous.
 template <class T> struct V4 { T x, y, z, w; };
 
 template <class T>
@@ -136,54 +135,44 @@ __device__ __forceinline__ void st4(T* p, const V4<T>& v) {
 template <class T>
 __device__ __forceinline__ void add4(V4<T>& a, const V4<T>& b) { a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w; }
 
-// add an entry at depth d < D below the top (2^(D-d) distinct rows) to the subtree's root rows
-template <class T, int D, int d>
-__device__ __forceinline__ void tile_entry(V4<T> (&v)[1 << D], const T* rowp, long long rstep) {
-    constexpr int nd = 1 << (D - d);
-    V4<T> w[nd];
-#pragma unroll
-    for (int q = 0; q < nd; ++q) w[q] = ld4<T>(rowp + q * rstep);
-#pragma unroll
-    for (int q = 0; q < (1 << D); ++q) add4(v[q], w[q & (nd - 1)]);
-}
-
 template <class T, int D>
 __global__ void __launch_bounds__(128) k_chain_sum(const T* __restrict__ B, long long B_stride,
                                                    const __grid_constant__ Chain ch, T* __restrict__ S,
                                                    long long S_stride, int logn_root, int tau_pad) {
+    constexpr int NQ = 1 << D, NB = NQ >= 16 ? 1 : 16 / NQ;       // rows per thread, entries per batch
     const int logn_top = logn_root - D;
-    const long long n_top = 1LL << logn_top;
     const long long rho = (long long)blockIdx.x * 128 + threadIdx.x;
     const long long t4 = blockIdx.y;
     const int r = blockIdx.z;
-    if (rho >= n_top) return;
+    if (rho >= (1LL << logn_top)) return;
     const T* Br = B + (long long)r * B_stride;
-    V4<T> v[1 << D];
+    V4<T> v[NQ];
 #pragma unroll
-    for (int q = 0; q < (1 << D); ++q) v[q] = {T(0), T(0), T(0), T(0)};
-    for (int e = 0; e < ch.count; ++e) {
-        const int logn = ch.logn[e];
-        const T* be = Br + ch.boff[e] + ((t4 << logn) << 2);
-        const int d = logn_root - logn;                 // depth of the entry below the root level
-        if (d >= D) {                                   // at or above the subtree's top: one row
-            const V4<T> w = ld4<T>(be + ((rho & ((1LL << logn) - 1)) << 2));
+    for (int q = 0; q < NQ; ++q) v[q] = {T(0), T(0), T(0), T(0)};
+    for (int e0 = 0; e0 < ch.count; e0 += NB) {
+        V4<T> w[NB][NQ];
 #pragma unroll
-            for (int q = 0; q < (1 << D); ++q) add4(v[q], w);
-            continue;
+        for (int i = 0; i < NB; ++i) {
+            const int e = e0 + i;
+            if (e < ch.count) {
+                const int logn = ch.logn[e];
+                const long long mask = (1LL << logn) - 1;
+                const T* be = Br + ch.boff[e] + ((t4 << logn) << 2);
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) w[i][q] = ld4<T>(be + (((rho + ((long long)q << logn_top)) & mask) << 2));
+            } else {
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) w[i][q] = {T(0), T(0), T(0), T(0)};
+            }
         }
-        const T* rowp = be + (rho << 2);
-        const long long rstep = n_top << 2;
-        switch (d) {                                    // 2^(D-d) distinct rows below the top
-            case 0: tile_entry<T, D, 0>(v, rowp, rstep); break;
-            case 1: if constexpr (D > 1) tile_entry<T, D, 1>(v, rowp, rstep); break;
-            case 2: if constexpr (D > 2) tile_entry<T, D, 2>(v, rowp, rstep); break;
-            case 3: if constexpr (D > 3) tile_entry<T, D, 3>(v, rowp, rstep); break;
-            default: break;
-        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) add4(v[q], w[i][q]);
     }
     T* o = S + (long long)r * S_stride + ((t4 << logn_root) << 2) + (rho << 2);
 #pragma unroll
-    for (int q = 0; q < (1 << D); ++q) st4<T>(o + ((long long)q << logn_top << 2), v[q]);
+    for (int q = 0; q < NQ; ++q) st4<T>(o + ((long long)q << logn_top << 2), v[q]);
 }
 
 template <class T>
