@@ -314,7 +314,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.cg_count = (P.tau_pad + cr - 1) / cr;
     }
     // the S4 band of the float tiers: forward CTAs of 64 roots x 2 branches, column groups picked
-    // by a per-SM cost model (CTAs per SM, at least 5 resident, times columns per CTA plus a fixed
+    // by a per-SM cost model (CTAs per SM, at least the resident count, times columns per CTA plus a fixed
     // setup cost); the adjoint below.  m <= 27 keeps the adjoint's 32-bit staging offsets (4 * 2^m
     // table entries, 2 * 2^m row-save floats) below 2^30.
     P.fine_s4 = (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) && P.shape == SHAPE_S4 &&
@@ -324,12 +324,13 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.root_blocks = (int)((n_root + rows - 1) / rows);
         const long long rbr = (long long)P.root_blocks * P.reff;
         const int quads = P.tau_pad / 4, qmax = 512 / 4;
+        const long long resident = fine_s4_fwd_resident(P.fkind);
         long long best = -1;
         for (int cg = (quads + qmax - 1) / qmax; cg <= quads; ++cg) {
             const int qpg = (quads + cg - 1) / cg;
             if ((long long)(cg - 1) * qpg >= quads) continue;       // an empty last group
             const long long per_sm = (rbr * cg + 151) / 152;
-            const long long cost = std::max(per_sm, 5LL) * (qpg + 2);
+            const long long cost = std::max(per_sm, resident) * (qpg + 2);
             if (best < 0 || cost < best) { best = cost; P.cr = 4 * qpg; P.cg_count = (quads + qpg - 1) / qpg; }
         }
     }

@@ -32,7 +32,12 @@ constexpr int kBwdThreads = 256;
 constexpr int kBwdCols = 256;                // columns per CTA: 4 warps x 32 lanes x 2
 constexpr int kRB = 8;                       // roots per staged batch
 constexpr int kSlots = 96;                   // staged floats per root
-constexpr int kFwdMinBlocks = 5, kBwdMinBlocks = 2;
+constexpr int kBwdMinBlocks = 2;
+// forward CTAs resident per SM: 7 (72 registers) where the integrand's h fits without spilling,
+// else 5 (cos, the inverse square's reciprocal and log-sum-exp's running maximum need more)
+__host__ __device__ constexpr int fwd_min_blocks(int F) {
+    return (F == F_LINEAR_MEAN || F == F_CALL_MEAN_EXP || F == F_GAUSS_NORM2) ? 7 : 5;
+}
 constexpr int kMaxCRS4 = 512;                // forward columns per CTA (dynamic shared memory 48 KB)
 
 // ------------------------------------------------------------------------------------------
@@ -89,7 +94,7 @@ struct RowAcc2 {
 };
 
 template <int F>
-__global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) k_fine_fwd_s4(const __grid_constant__ FineArgs<float> a) {
+__global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F)) k_fine_fwd_s4(const __grid_constant__ FineArgs<float> a) {
     extern __shared__ __align__(16) float4 As_dyn[];                  // [a.cr][kAQuads]
     float4 (*As)[kAQuads] = reinterpret_cast<float4 (*)[kAQuads]>(As_dyn);
     const int tid = threadIdx.x, b = tid / kFwdRoots;
@@ -200,6 +205,7 @@ __global__ void __launch_bounds__(kFwdThreads, kFwdMinBlocks) k_fine_fwd_s4(cons
         const float4* ac = As[t0 - t_beg];
         column(ac, kap * sq.x);
         column(ac + kAQuads, kap * sq.y);
+        asm volatile("" ::: "memory");                 // (caps the columns' loads held at once)
         column(ac + 2 * kAQuads, kap * sq.z);
         column(ac + 3 * kAQuads, kap * sq.w);
     }
@@ -457,6 +463,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
 }  // namespace
 
 int fine_s4_fwd_roots() { return kFwdRoots; }
+int fine_s4_fwd_resident(int F) { return fwd_min_blocks(F); }
 int fine_s4_bwd_cols() { return kBwdCols; }
 int fine_s4_bwd_batch() { return kRB; }
 

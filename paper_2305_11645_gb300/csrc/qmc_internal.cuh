@@ -292,6 +292,7 @@ cudaError_t tc_error_word(unsigned int* value, bool clear);
 // columns (grid: root groups of a.roots_per_cta roots, a multiple of fine_s4_bwd_batch() x
 // column passes x shifts)
 int fine_s4_fwd_roots();
+int fine_s4_fwd_resident(int F);       // forward CTAs resident per SM for integrand F
 int fine_s4_bwd_cols();
 int fine_s4_bwd_batch();
 cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
