@@ -411,7 +411,8 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         // and column), ~3 CTAs per SM and at least 128 K rows per split.
         const bool tc = P.tc_pieces != 0;
         const int jcols = tc ? tc_grad_cols() : 16;
-        const double fma_w = tc ? 2.0 : 16.0, fold_w = tc ? 1.0 : 4.0, target = tc ? 456.0 : 608.0;
+        // (the tensor-core kernel runs one CTA per SM: about one wave of 152 CTAs)
+        const double fma_w = tc ? 2.0 : 16.0, fold_w = tc ? 1.0 : 4.0, target = tc ? 152.0 : 608.0;
         const long long kmin = tc ? 128 : 64;
         const int ttiles = (P.tau_pad + 127) / 128;
         double wtot = 0.0;

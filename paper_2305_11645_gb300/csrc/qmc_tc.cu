@@ -77,6 +77,16 @@ __device__ __forceinline__ bool publish_stage(bool ok) {
     return ok;
 }
 
+// 16-byte asynchronous copy global -> shared (zero-filled when !valid; src must still be a
+// valid address), and the per-thread copy groups
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -198,19 +208,33 @@ __global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__
 // chunk lies inside one shift's rows, n_e >= 32).  A split covers a multiple of 32 rows.
 // Shared memory per stage: F^T (P pieces x 128 rows x 64 B) and X (P x 64 rows x 64 B).
 // ------------------------------------------------------------------------------------------
+// Main path (levels with at least 32 distinct rows whose F is read without an on-the-fly fold):
+// the raw FP32 chunks of F (32 rows x 128 columns t) and X (64 rows j x 32 k) are copied into
+// RAWS shared-memory stages with 16-byte cp.async, RAWS - 1 chunks ahead of the one being
+// converted, so the copies need no registers and their latency is hidden behind the
+// conversion and the MMAs; each thread then converts its row of F^T and its half row of X from
+// shared memory into the bf16 pieces.  Other levels take the register path below (one chunk of
+// loads in flight).
+constexpr int RAWS = 4;
+constexpr uint32_t RAW_F = KC * TM * 4;              // F chunk: [k][t], 512 B rows
+constexpr uint32_t RAW_XROW = (KC + 4) * 4;          // X chunk rows padded to 144 B (bank spread)
+constexpr uint32_t RAW_X = NJ * RAW_XROW;
+constexpr uint32_t RAW_STAGE = RAW_F + RAW_X;
+
 template <int P>
-__global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict__ tab, long long tab_stride,
-                                                        const float* __restrict__ Froot, long long root_stride,
-                                                        const float* __restrict__ Fchain, long long chain_stride,
-                                                        int tau_pad, const __grid_constant__ Chain ch,
-                                                        float* __restrict__ part, int reff) {
+__global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restrict__ tab, long long tab_stride,
+                                                           const float* __restrict__ Froot, long long root_stride,
+                                                           const float* __restrict__ Fchain, long long chain_stride,
+                                                           int tau_pad, const __grid_constant__ Chain ch,
+                                                           float* __restrict__ part, int reff) {
     constexpr uint32_t TILEA = TM * ROWB, TILEB = NJ * ROWB;
     constexpr uint32_t OPA = P * TILEA, OPB = P * TILEB;
     constexpr uint32_t STAGE = OPA + OPB;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = align_1k(smem_raw);          // the swizzle pattern follows address bits 7-8
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * STAGE + 16);
+    unsigned char* raw = smem + 2 * STAGE;             // RAWS raw FP32 stages (main path)
+    uint64_t* bar = reinterpret_cast<uint64_t*>(raw + RAWS * RAW_STAGE);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(raw + RAWS * RAW_STAGE + 16);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int e = entry_of(ch, blockIdx.x);
@@ -231,15 +255,90 @@ __global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict_
     const int t0 = blockIdx.y * TM;
     const uint32_t tmem = tc_setup(bar, tmem_slot, NJ);
 
-    const int t = t0 + tid;                            // = TMEM lane tid of the accumulator
+    // 256 threads: thread tq = tid % 128 owns column t = t0 + tq (TMEM lane tq); in the main path
+    // warps 0-3 convert F^T, warps 4-7 convert X, and both groups share the copies and the epilogue
+    const int tq = tid & (TM - 1);
+    const bool lower = tid < TM;
+    const int t = t0 + tq;
     const bool col_ok = t < tau_pad;
-    const int jrow = tid & (NJ - 1), khalf = tid >> 6; // X: row j0 + jrow, one half of the chunk
+    const int jrow = tq & (NJ - 1), khalf = tq >> 6;  // X: row j0 + jrow, one half of the chunk
     const bool jrow_ok = jrow < nj;
     const float* xcol = tab + ch.tab[e] + (long long)(j0 + (jrow_ok ? jrow : 0)) * n_e;
     const float* Fcol = Fsrc + (col_ok ? t : 0);
     const bool whole = n_e >= KC;                      // a chunk never crosses a shift boundary
-    float fv[KC], xw[16];
     bool ok = true, first = true;
+    if (whole && fold == 1) {
+        // ------------------------------------------------------------ main path
+        const int lane = tid & 31;
+        auto copy_chunk = [&](int c) {
+            if (c < nchunks) {
+                const long long k0 = kb + (long long)c * KC;
+                const long long rr = k0 >> logn, rho0 = k0 & (n_e - 1);
+                const uint32_t rs = smem_u32(raw + (c % RAWS) * RAW_STAGE);
+                // F: warp w copies rows 4w .. 4w + 3, lane l the columns t0 + 4l .. + 3
+                const bool tin = t0 + 4 * lane < tau_pad;
+                const float* fsrc = Fsrc + rr * F_stride + rho0 * tau_pad + (tin ? t0 + 4 * lane : 0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int row = warp * 4 + i;
+                    cp_async16(rs + row * (TM * 4) + lane * 16, fsrc + (long long)row * tau_pad, tin);
+                }
+                // X: 64 rows j x 8 groups of 4 k, two per thread
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int idx = tid + 256 * u, jr = idx >> 3, q = idx & 7;
+                    const bool jin = jr < nj;
+                    const float* xsrc = tab + ch.tab[e] + (long long)(j0 + (jin ? jr : 0)) * n_e + rr * tab_stride +
+                                        rho0 + 4 * q;
+                    cp_async16(rs + RAW_F + jr * RAW_XROW + q * 16, xsrc, jin);
+                }
+            }
+            cp_async_commit();                          // (one group per chunk, possibly empty)
+        };
+#pragma unroll
+        for (int c = 0; c < RAWS - 1; ++c) copy_chunk(c);
+        for (int c = 0; c < nchunks; ++c) {
+            copy_chunk(c + RAWS - 1);                   // into the stage chunk c - 1 was converted from
+            cp_async_wait<RAWS - 1>();                  // this thread's copies of chunk c have landed
+            __syncthreads();                            // and every thread's
+            const unsigned char* rs = raw + (c % RAWS) * RAW_STAGE;
+            const int s = c & 1;
+            unsigned char* Fs = smem + s * STAGE;
+            unsigned char* Xs = Fs + OPA;
+            if (c >= 2) ok = mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1);
+            if (ok && lower) {
+                float fc[KC];
+                const float* fr = reinterpret_cast<const float*>(rs) + tq;
+#pragma unroll
+                for (int i = 0; i < KC; ++i) fc[i] = fr[i * TM];
+#pragma unroll
+                for (int g = 0; g < 4; ++g) store_group<P>(Fs, TILEA, tq, g, fc + 8 * g);
+            } else if (ok) {
+                if (jrow < (int)nmma) {
+                    const float4* xr = reinterpret_cast<const float4*>(rs + RAW_F + jrow * RAW_XROW) + 4 * khalf;
+                    float xc[16];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 v = xr[q];
+                        xc[4 * q] = v.x; xc[4 * q + 1] = v.y; xc[4 * q + 2] = v.z; xc[4 * q + 3] = v.w;
+                    }
+                    store_group<P>(Xs, TILEB, jrow, 2 * khalf, xc);
+                    store_group<P>(Xs, TILEB, jrow, 2 * khalf + 1, xc + 8);
+                }
+            }
+            ok = publish_stage(ok);
+            if (!ok) break;
+            if (tid == 0) {
+                const uint32_t idesc = idesc_bf16(nmma);
+                for (int ks = 0; ks < 2; ++ks)
+                    issue_kstep<P, TILEA, TILEB>(tmem, smem_desc_sw64(smem_u32(Fs) + 32 * ks),
+                                                 smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, first);
+                mma_commit(smem_u32(&bar[s]));
+            }
+        }
+        cp_async_wait<0>();
+    } else {
+    float fv[KC], xw[16];
     // Iteration it loads chunk it and converts chunk it - 1 (one load site keeps the code small).
     for (int it = 0; it <= nchunks; ++it) {
         float fc[KC], xc[16];
@@ -247,7 +346,7 @@ __global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict_
         for (int i = 0; i < KC; ++i) fc[i] = fv[i];
 #pragma unroll
         for (int i = 0; i < 16; ++i) xc[i] = xw[i];
-        if (it < nchunks) {
+        if (it < nchunks && lower) {                   // (warps 4-7 only join the barriers here)
             const long long k0 = kb + (long long)it * KC;
             if (whole) {
                 const long long rr = k0 >> logn, rho0 = k0 & (n_e - 1);
@@ -307,10 +406,10 @@ __global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict_
         unsigned char* Xs = Fs + OPA;
         const int ksteps = (int)min(2LL, (ke - kb - (long long)c * KC + 15) >> 4);
         if (c >= 2) ok = mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1);
-        if (ok) {
+        if (ok && lower) {
 #pragma unroll
             for (int g = 0; g < 4; ++g)
-                if (g < 2 * ksteps) store_group<P>(Fs, TILEA, tid, g, fc + 8 * g);
+                if (g < 2 * ksteps) store_group<P>(Fs, TILEA, tq, g, fc + 8 * g);
             if (khalf < ksteps) {
                 store_group<P>(Xs, TILEB, jrow, 2 * khalf, xc);
                 store_group<P>(Xs, TILEB, jrow, 2 * khalf + 1, xc + 8);
@@ -326,26 +425,28 @@ __global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict_
             mma_commit(smem_u32(&bar[s]));
         }
     }
+    }
     if (ok && nchunks > 0) ok = mbar_wait(smem_u32(&bar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
     fence_after_sync();
     ok = __syncthreads_and(ok);
     if (!ok && tid == 0) atomicOr(&g_tc_error, 1u);
 
-    // D[t][j]: TMEM lane = t - t0, column = j - j0
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    float* pe = part + ch.poff[e] + ((long long)sp * tau_e + j0) * tau_pad + t;
-    uint32_t d[2][32];
+    // D[t][j]: TMEM lane = t - t0, column = j - j0; warps w and w + 4 share lanes 32 (w % 4) ..,
+    // the lower ones store columns 0..31, the upper ones 32..63
+    const int cb = lower ? 0 : 32;
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb;
+    float* pe = part + ch.poff[e] + ((long long)sp * tau_e + j0 + cb) * tau_pad + t;
+    uint32_t d[32];
     const bool have = ok && nchunks > 0;
-    if (have) {
-        tmem_ld32(lane_addr, d[0]);
-        if (nmma > 32) tmem_ld32(lane_addr + 32, d[1]);
+    if (have && (int)nmma > cb) {
+        tmem_ld32(lane_addr, d);
         tmem_wait_ld();
     }
     if (col_ok) {
 #pragma unroll
-        for (int i = 0; i < NJ; ++i) {
-            if (i < nj) {
-                const float v = have ? __uint_as_float(d[i >> 5][i & 31]) : (ok ? 0.0f : qnan());
+        for (int i = 0; i < 32; ++i) {
+            if (cb + i < nj) {
+                const float v = have ? __uint_as_float(d[i]) : (ok ? 0.0f : qnan());
                 pe[(long long)i * tau_pad] = v;
             }
         }
@@ -354,8 +455,8 @@ __global__ void __launch_bounds__(128) k_coarse_grad_tc(const float* __restrict_
 }
 
 // ------------------------------------------------------------------------------------------
-// launchers.  The shared-memory requests also cap the CTAs per SM so that their tensor
-// memory (128 columns forward, 64 backward) fits in the SM's 512 columns.
+// launchers.  The forward's shared-memory request also caps its CTAs per SM so that their
+// tensor memory (128 columns each) fits in the SM's 512 columns.
 // ------------------------------------------------------------------------------------------
 namespace {
 template <int P> constexpr size_t fwd_smem() {
@@ -363,8 +464,7 @@ template <int P> constexpr size_t fwd_smem() {
     return need < 58 * 1024 ? 58 * 1024 : need;         // <= 3 CTAs per SM
 }
 template <int P> constexpr size_t bwd_smem() {
-    const size_t need = 2 * (P * TM * ROWB + P * NJ * ROWB) + 1024 + 64;
-    return need < 30 * 1024 ? 30 * 1024 : need;         // <= 7 CTAs per SM
+    return 2 * (P * TM * ROWB + P * NJ * ROWB) + RAWS * RAW_STAGE + 1024 + 64;   // one CTA per SM
 }
 }  // namespace
 
@@ -401,13 +501,13 @@ cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const 
         cudaError_t e = cudaFuncSetAttribute(k_coarse_grad_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bwd_smem<3>());
         if (e != cudaSuccess) return e;
-        k_coarse_grad_tc<3><<<grid, 128, bwd_smem<3>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
+        k_coarse_grad_tc<3><<<grid, 256, bwd_smem<3>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
                                                               chain_stride, tau_pad, ch, part, reff);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_coarse_grad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bwd_smem<1>());
         if (e != cudaSuccess) return e;
-        k_coarse_grad_tc<1><<<grid, 128, bwd_smem<1>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
+        k_coarse_grad_tc<1><<<grid, 256, bwd_smem<1>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
                                                               chain_stride, tau_pad, ch, part, reff);
     }
     return cudaGetLastError();
