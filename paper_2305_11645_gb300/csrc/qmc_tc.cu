@@ -98,7 +98,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // Shared memory per stage: X and A tiles, P pieces x 128 rows x 64 B each.
 // ------------------------------------------------------------------------------------------
 template <int P>
-__global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__ tab, long long tab_stride,
+__global__ void __launch_bounds__(256) k_coarse_fwd_tc(const float* __restrict__ tab, long long tab_stride,
                                                        const float* __restrict__ A, int ldA, int tau_pad,
                                                        const __grid_constant__ Chain ch, float* __restrict__ B,
                                                        long long B_stride) {
@@ -120,25 +120,30 @@ __global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__
     const int nchunks = (tau_e + KC - 1) / KC;
     const uint32_t tmem = tc_setup(bar, tmem_slot, TM);
 
-    const long long rho = rho0 + tid;                 // = TMEM lane tid of the accumulator
-    const int t = t0 + tid;
+    // 256 threads: thread tq = tid % 128 of warps 0-3 loads and converts row rho0 + tq of X (its
+    // TMEM lane), of warps 4-7 row t0 + tq of A^T; the two halves store the accumulator's
+    // columns 0-63 and 64-127 of their lanes
+    const int tq = tid & (TM - 1);
+    const bool lower = tid < TM;
+    const long long rho = rho0 + tq;
+    const int t = t0 + tq;
     const bool row_ok = rho < n_e, col_ok = t < tau_pad;
-    const float* xr = tab + (long long)r * tab_stride + ch.tab[e] + (row_ok ? rho : 0);
-    const float* ac = A + (long long)ch.col0[e] * ldA + (col_ok ? t : 0);
-    float xv[KC], av[KC];
+    const bool src_ok = lower ? row_ok : col_ok;
+    const float* src = lower ? tab + (long long)r * tab_stride + ch.tab[e] + (row_ok ? rho : 0)
+                             : A + (long long)ch.col0[e] * ldA + (col_ok ? t : 0);
+    const long long kstride = lower ? n_e : (long long)ldA;
+    float vv[KC];
     bool ok = true, first = true;
     // Iteration it loads chunk it and converts chunk it - 1 (one load site keeps the code small).
     for (int it = 0; it <= nchunks; ++it) {
-        float xc[KC], ac_[KC];
+        float vc[KC];
 #pragma unroll
-        for (int i = 0; i < KC; ++i) { xc[i] = xv[i]; ac_[i] = av[i]; }
+        for (int i = 0; i < KC; ++i) vc[i] = vv[i];
         if (it < nchunks) {
 #pragma unroll
             for (int i = 0; i < KC; ++i) {
                 const int k = it * KC + i;
-                const bool kv = k < tau_e;
-                xv[i] = (kv && row_ok) ? __ldg(xr + (long long)k * n_e) : 0.0f;
-                av[i] = (kv && col_ok) ? __ldg(ac + (long long)k * ldA) : 0.0f;
+                vv[i] = (k < tau_e && src_ok) ? __ldg(src + (long long)k * kstride) : 0.0f;
             }
         }
         if (it == 0) continue;
@@ -149,13 +154,10 @@ __global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__
         const int ksteps = min(2, (tau_e - c * KC + 15) >> 4);
         if (c >= 2) ok = mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1);
         if (ok) {
+            unsigned char* dst = lower ? Xs : As;
 #pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                if (g < 2 * ksteps) {
-                    store_group<P>(Xs, TILE, tid, g, xc + 8 * g);
-                    store_group<P>(As, TILE, tid, g, ac_ + 8 * g);
-                }
-            }
+            for (int g = 0; g < 4; ++g)
+                if (g < 2 * ksteps) store_group<P>(dst, TILE, tq, g, vc + 8 * g);
         }
         ok = publish_stage(ok);
         if (!ok) break;
@@ -173,9 +175,9 @@ __global__ void __launch_bounds__(128) k_coarse_fwd_tc(const float* __restrict__
     if (!ok && tid == 0) atomicOr(&g_tc_error, 1u);
 
     float* Be = B + (long long)r * B_stride + ch.boff[e];
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    {
+        const int half = lower ? 0 : 1;
         uint32_t d[2][32];
         if (ok) {
             tmem_ld32(lane_addr + half * 64, d[0]);
@@ -481,12 +483,12 @@ cudaError_t launch_coarse_fwd_tc(const float* tab, long long tab_stride, const f
         cudaError_t e = cudaFuncSetAttribute(k_coarse_fwd_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)fwd_smem<3>());
         if (e != cudaSuccess) return e;
-        k_coarse_fwd_tc<3><<<grid, 128, fwd_smem<3>(), st>>>(tab, tab_stride, A, ldA, tau_pad, ch, B, B_stride);
+        k_coarse_fwd_tc<3><<<grid, 256, fwd_smem<3>(), st>>>(tab, tab_stride, A, ldA, tau_pad, ch, B, B_stride);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_coarse_fwd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)fwd_smem<1>());
         if (e != cudaSuccess) return e;
-        k_coarse_fwd_tc<1><<<grid, 128, fwd_smem<1>(), st>>>(tab, tab_stride, A, ldA, tau_pad, ch, B, B_stride);
+        k_coarse_fwd_tc<1><<<grid, 256, fwd_smem<1>(), st>>>(tab, tab_stride, A, ldA, tau_pad, ch, B, B_stride);
     }
     return cudaGetLastError();
 }
