@@ -36,8 +36,7 @@ SM_COUNT = 152
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on this workload, from the
 # ncu captures summarised under profiles/ (cold cache); a kernel missing here has changed since
 # its counters were taken and reports traffic null
-TRAFFIC_BYTES = {"k_fine_bwd_s4": 10012928, "k_fine_fwd_s4": 9487616, "k_coarse_grad_tc": 17904896,
-                 "k_coarse_fwd_tc": 2371328}
+TRAFFIC_BYTES = {"k_fine_bwd_s4": 10012928}
 TIERS = ("split", "fp32", "bf16")
 
 
@@ -366,7 +365,7 @@ def oracle_full(p):
 
 
 # stated tolerances on the estimate (relative) and the gradient (max-norm relative) per tier
-TOLERANCE = {"split": (1e-6, 2e-5), "fp32": (2e-5, 2e-5), "bf16": (2e-3, 2e-2)}
+TOLERANCE = {"split": (1e-6, 1e-6), "fp32": (2e-5, 2e-5), "bf16": (2e-3, 2e-2)}
 
 
 def accuracy(p, est, grad, args, tier):

@@ -218,6 +218,10 @@ __global__ void __launch_bounds__(256) k_coarse_fwd_tc(const float* __restrict__
 // shared memory into the bf16 pieces.  Other levels take the register path below (one chunk of
 // loads in flight).
 constexpr int RAWS = 4;
+// Chunk c accumulates into tensor-memory accumulator c % NACC (64 columns each), summed in FP32
+// in a fixed order at the end: an FP32 accumulation chain inside the tensor core is then at
+// most kper / NACC rows long, which keeps the split tier's gradient error near 2^-24 sqrt(64).
+constexpr int NACC = 4;
 constexpr uint32_t RAW_F = KC * TM * 4;              // F chunk: [k][t], 512 B rows
 constexpr uint32_t RAW_XROW = (KC + 4) * 4;          // X chunk rows padded to 144 B (bank spread)
 constexpr uint32_t RAW_X = NJ * RAW_XROW;
@@ -255,7 +259,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
     const long long kb = (long long)sp * ch.kper[e], ke = min(Ktot, kb + ch.kper[e]);
     const int nchunks = ke > kb ? (int)((ke - kb + KC - 1) / KC) : 0;
     const int t0 = blockIdx.y * TM;
-    const uint32_t tmem = tc_setup(bar, tmem_slot, NJ);
+    const uint32_t tmem = tc_setup(bar, tmem_slot, NACC * NJ);
 
     // 256 threads: thread tq = tid % 128 owns column t = t0 + tq (TMEM lane tq); in the main path
     // warps 0-3 convert F^T, warps 4-7 convert X, and both groups share the copies and the epilogue
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
     const float* xcol = tab + ch.tab[e] + (long long)(j0 + (jrow_ok ? jrow : 0)) * n_e;
     const float* Fcol = Fsrc + (col_ok ? t : 0);
     const bool whole = n_e >= KC;                      // a chunk never crosses a shift boundary
-    bool ok = true, first = true;
+    bool ok = true;
     if (whole && fold == 1) {
         // ------------------------------------------------------------ main path
         const int lane = tid & 31;
@@ -332,9 +336,11 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
             if (!ok) break;
             if (tid == 0) {
                 const uint32_t idesc = idesc_bf16(nmma);
+                bool fresh = c < NACC;                  // the accumulator's first chunk
                 for (int ks = 0; ks < 2; ++ks)
-                    issue_kstep<P, TILEA, TILEB>(tmem, smem_desc_sw64(smem_u32(Fs) + 32 * ks),
-                                                 smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, first);
+                    issue_kstep<P, TILEA, TILEB>(tmem + (uint32_t)((c % NACC) * NJ),
+                                                 smem_desc_sw64(smem_u32(Fs) + 32 * ks),
+                                                 smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, fresh);
                 mma_commit(smem_u32(&bar[s]));
             }
         }
@@ -421,9 +427,11 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
         if (!ok) break;
         if (tid == 0) {
             const uint32_t idesc = idesc_bf16(nmma);
+            bool fresh = c < NACC;                      // the accumulator's first chunk
             for (int ks = 0; ks < ksteps; ++ks)
-                issue_kstep<P, TILEA, TILEB>(tmem, smem_desc_sw64(smem_u32(Fs) + 32 * ks),
-                                             smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, first);
+                issue_kstep<P, TILEA, TILEB>(tmem + (uint32_t)((c % NACC) * NJ),
+                                             smem_desc_sw64(smem_u32(Fs) + 32 * ks),
+                                             smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, fresh);
             mma_commit(smem_u32(&bar[s]));
         }
     }
@@ -438,22 +446,29 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
     const int cb = lower ? 0 : 32;
     const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)cb;
     float* pe = part + ch.poff[e] + ((long long)sp * tau_e + j0 + cb) * tau_pad + t;
-    uint32_t d[32];
+    float sum[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) sum[i] = 0.0f;
     const bool have = ok && nchunks > 0;
     if (have && (int)nmma > cb) {
-        tmem_ld32(lane_addr, d);
-        tmem_wait_ld();
+        for (int a = 0; a < NACC && a < nchunks; ++a) {   // accumulators in order
+            uint32_t d[32];
+            tmem_ld32(lane_addr + (uint32_t)(a * NJ), d);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sum[i] += __uint_as_float(d[i]);
+        }
     }
     if (col_ok) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
             if (cb + i < nj) {
-                const float v = have ? __uint_as_float(d[i]) : (ok ? 0.0f : qnan());
+                const float v = have ? sum[i] : (ok ? 0.0f : qnan());
                 pe[(long long)i * tau_pad] = v;
             }
         }
     }
-    tc_teardown(tmem, NJ);
+    tc_teardown(tmem, NACC * NJ);
 }
 
 // ------------------------------------------------------------------------------------------
