@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
     const uint32_t tmem = tc_setup(bar, tmem_slot, NACC * NJ);
 
     // 256 threads: thread tq = tid % 128 owns column t = t0 + tq (TMEM lane tq); in the main path
-    // warps 0-3 convert F^T, warps 4-7 convert X, and both groups share the copies and the epilogue
+    // every thread converts half a row of F^T and a quarter row of X, and all share the copies
+    // and the epilogue
     const int tq = tid & (TM - 1);
     const bool lower = tid < TM;
     const int t = t0 + tq;
@@ -312,24 +313,22 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
             unsigned char* Fs = smem + s * STAGE;
             unsigned char* Xs = Fs + OPA;
             if (c >= 2) ok = mbar_wait(smem_u32(&bar[s]), ((c - 2) >> 1) & 1);
-            if (ok && lower) {
-                float fc[KC];
-                const float* fr = reinterpret_cast<const float*>(rs) + tq;
+            if (ok) {
+                // every thread: k 16h .. 16h + 15 of row tq of F^T (h = tid / 128), and k 8q .. 8q + 7
+                // of row tid % 64 of X (q = tid / 64)
+                const int h = tid >> 7;
+                float fc[16];
+                const float* fr = reinterpret_cast<const float*>(rs) + 16 * h * TM + tq;
 #pragma unroll
-                for (int i = 0; i < KC; ++i) fc[i] = fr[i * TM];
-#pragma unroll
-                for (int g = 0; g < 4; ++g) store_group<P>(Fs, TILEA, tq, g, fc + 8 * g);
-            } else if (ok) {
-                if (jrow < (int)nmma) {
-                    const float4* xr = reinterpret_cast<const float4*>(rs + RAW_F + jrow * RAW_XROW) + 4 * khalf;
-                    float xc[16];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 v = xr[q];
-                        xc[4 * q] = v.x; xc[4 * q + 1] = v.y; xc[4 * q + 2] = v.z; xc[4 * q + 3] = v.w;
-                    }
-                    store_group<P>(Xs, TILEB, jrow, 2 * khalf, xc);
-                    store_group<P>(Xs, TILEB, jrow, 2 * khalf + 1, xc + 8);
+                for (int i = 0; i < 16; ++i) fc[i] = fr[i * TM];
+                store_group<P>(Fs, TILEA, tq, 2 * h, fc);
+                store_group<P>(Fs, TILEA, tq, 2 * h + 1, fc + 8);
+                const int xj = tid & (NJ - 1), xq = tid >> 6;
+                if (xj < (int)nmma) {
+                    const float4* xr = reinterpret_cast<const float4*>(rs + RAW_F + xj * RAW_XROW) + 2 * xq;
+                    const float4 a = xr[0], b = xr[1];
+                    const float xc[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+                    store_group<P>(Xs, TILEB, xj, xq, xc);
                 }
             }
             ok = publish_stage(ok);
