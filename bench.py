@@ -36,7 +36,8 @@ SM_COUNT = 152
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on this workload, from the
 # ncu captures summarised under profiles/ (cold cache); a kernel missing here has changed since
 # its counters were taken and reports traffic null
-TRAFFIC_BYTES = {"k_fine_bwd_s4": 10012928}
+TRAFFIC_BYTES = {"k_fine_bwd_s4": 10012928, "k_fine_fwd_s4": 9484544, "k_coarse_grad_tc": 17909248,
+                 "k_coarse_fwd_tc": 2355712}
 TIERS = ("split", "fp32", "bf16")
 
 
