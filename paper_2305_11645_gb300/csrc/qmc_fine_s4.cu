@@ -13,14 +13,16 @@
 //
 // Forward: a CTA holds 64 roots x 2 branches.  Thread (rho, b) owns the 8 leaves q = b + 2i under
 // level-3 node b (the tree splits there without shared work), keeps their 32 x values in
-// registers and walks the CTA's columns; the kappa-scaled fine columns of A are staged in shared
-// memory and read as four broadcast 16-byte loads per column.
+// registers (as pairs of sibling nodes) and walks the CTA's columns; the kappa-scaled fine
+// columns of A are staged in shared memory and read as six broadcast 16-byte loads per column,
+// and the paired FP32 instructions (FFMA2, FADD2) take two siblings per instruction.
 //
 // Backward: a CTA covers 256 columns (4 warps x 32 lanes x 2 columns) of a range of roots, in
 // two halves of 4 warps that take alternate roots.  The x values and row coefficients of 8 roots
-// at a time are staged in shared memory (double-buffered, coalesced along the roots) and read as
-// broadcast 16-byte loads; each lane holds its columns of A and its gradient accumulators in
-// registers for every root it visits, so the only reductions are the two halves' at the end.
+// at a time are staged in shared memory (double-buffered, coalesced along the roots, each value
+// stored twice) and read as broadcast 16-byte loads; each lane holds its two columns of A and its
+// gradient accumulators in registers for every root it visits, the paired FP32 instructions
+// taking both columns at once, so the only reductions are the two halves' at the end.
 #include "qmc_internal.cuh"
 
 namespace qmc {
