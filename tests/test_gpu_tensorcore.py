@@ -43,13 +43,16 @@ def product_bound(X, A, precision):
 
 # Shapes for the tensor-core tiles on top of the band shapes: a coarse level with fewer
 # distinct rows than a 128-row tile and a K of 100 (four K chunks, both stages reused), a
-# level whose K is cut into two entries, 128-column tiles with a ragged last tile, and
-# levels with several 128-row tiles.
+# level whose K is cut into two entries, 128-column tiles with a ragged last tile, levels
+# with several 128-row tiles, and a level eight above the band (m = 14, w = 12: its root
+# gradients are folded on the fly while the block gradient loads them).
 TC_SHAPES = SHAPES + [
     dict(m=10, w=np.array([0] + [4] * 100 + [6] * 70 + [10] * 3), tau=200),
     dict(m=13, w=np.array([0, 1, 1] + [5] * 40 + [7] * 300), tau=136),
     dict(m=14, w=I.log2_weights(600, 14), tau=64),
+    dict(m=14, w=np.array([0, 1, 1, 2, 2, 2, 2] + [3] * 8 + [6] * 40 + [12] * 5), tau=72),
 ]
+FOLD_SHAPE = len(TC_SHAPES) - 1
 
 
 @pytest.mark.parametrize("precision", ["split", "bf16"])
@@ -81,7 +84,7 @@ def test_split_is_at_least_as_accurate_as_bf16_and_close_to_fp32():
 
 @pytest.mark.parametrize("precision", ["split", "bf16"])
 @pytest.mark.parametrize("fk", range(len(FKINDS)))
-@pytest.mark.parametrize("shape", [0, 3, 4, 5])
+@pytest.mark.parametrize("shape", [0, 3, 4, 5, FOLD_SHAPE])
 def test_integrate_and_backward(precision, fk, shape):
     f_kind, f_params = FKINDS[fk]
     kind = I.LATTICE if (fk + shape) % 2 == 0 else I.DIGITAL_NET
