@@ -106,10 +106,14 @@ template cudaError_t launch_coarse_fwd<double>(const double*, long long, const d
 // S[r][t/4][rho][t%4] = sum_e B_e[r][t/4][rho mod n_e][t%4], rho < n_root (Algorithm 2's
 // periodic tiling of the coarse block products onto the root rows).
 // A thread owns one group of four columns and the 2^D root rows rho' + q n_top of the subtree
-// of node rho' < n_top = n_root / 2^D; an entry row is (rho' + q n_top) mod n_e.  The entries
-// are taken in batches whose loads (about 16 float4 per thread) are all issued before any of
-// their adds, and added in entry order; consecutive threads take consecutive rho', so every
-// load and store of a warp is contiguous.
+// of node rho' < n_top = n_root / 2^D.  An entry of level JF + d (n_e = n_root / 2^d) has
+// 2^(D-d) distinct rows among the thread's 2^D (root row q uses row q mod 2^(D-d)) and one row
+// for d >= D, so every distinct block row is loaded once per thread, not once per root row.
+// The entries at or above the subtree's top go into one sum (batches of 8 loads, all issued
+// before their adds), which every root row adds at the end; the first batch's loads are in
+// flight while the entries below the top (the chain's first ones: it comes in ascending level
+// order) add their rows into the root rows.  Consecutive threads take consecutive rho', so
+// every load and store of a warp is contiguous.
 template <class T> struct V4 { T x, y, z, w; };
 
 template <class T>
@@ -139,50 +143,71 @@ template <class T, int D>
 __global__ void __launch_bounds__(128) k_chain_sum(const T* __restrict__ B, long long B_stride,
                                                    const __grid_constant__ Chain ch, T* __restrict__ S,
                                                    long long S_stride, int logn_root, int tau_pad) {
-    constexpr int NQ = 1 << D, NB = NQ >= 16 ? 1 : 16 / NQ;       // rows per thread, entries per batch
+    constexpr int NQ = 1 << D;
     const int logn_top = logn_root - D;
     const long long rho = (long long)blockIdx.x * 128 + threadIdx.x;
     const long long t4 = blockIdx.y;
     const int r = blockIdx.z;
     if (rho >= (1LL << logn_top)) return;
     const T* Br = B + (long long)r * B_stride;
+    const V4<T> zero = {T(0), T(0), T(0), T(0)};
+    auto ent = [&](int e, long long row) { return ld4<T>(Br + ch.boff[e] + ((t4 << ch.logn[e]) << 2) + (row << 2)); };
+    auto is_top = [&](int e) { return logn_root - ch.logn[e] >= D; };
+    // up to 8 entries at or above the top, from the last one down (their rows rho' mod n_e)
+    V4<T> w[8];
+    int e = ch.count - 1;
+    auto batch = [&]() {
+        int n = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int ei = e - i;
+            const bool on = ei >= 0 && is_top(ei);
+            w[i] = on ? ent(ei, rho & ((1LL << ch.logn[ei]) - 1)) : zero;
+            n += on ? 1 : 0;
+        }
+        return n;
+    };
+    int n = batch();
+    // the entries below the top, level JF + d for d = 0 .. D - 1: rows rho' + q n_top, q < 2^(D-d)
     V4<T> v[NQ];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) v[q] = {T(0), T(0), T(0), T(0)};
-    for (int e0 = 0; e0 < ch.count; e0 += NB) {
-        V4<T> w[NB][NQ];
+    for (int q = 0; q < NQ; ++q) v[q] = zero;
+    int f = 0;
 #pragma unroll
-        for (int i = 0; i < NB; ++i) {
-            const int e = e0 + i;
-            if (e < ch.count) {
-                const int logn = ch.logn[e];
-                const long long mask = (1LL << logn) - 1;
-                const T* be = Br + ch.boff[e] + ((t4 << logn) << 2);
+    for (int d = 0; d < D; ++d) {
+        for (; f < ch.count && logn_root - ch.logn[f] == d; ++f) {
+            V4<T> x[NQ];
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) w[i][q] = ld4<T>(be + (((rho + ((long long)q << logn_top)) & mask) << 2));
-            } else {
+            for (int q = 0; q < NQ; ++q)
+                if (q < (1 << (D - d))) x[q] = ent(f, rho + ((long long)q << logn_top));
 #pragma unroll
-                for (int q = 0; q < NQ; ++q) w[i][q] = {T(0), T(0), T(0), T(0)};
-            }
+            for (int q = 0; q < NQ; ++q) add4(v[q], x[q & ((1 << (D - d)) - 1)]);
         }
+    }
+    V4<T> top = zero;
+    for (;;) {
 #pragma unroll
-        for (int i = 0; i < NB; ++i)
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) add4(v[q], w[i][q]);
+        for (int i = 0; i < 8; ++i) add4(top, w[i]);
+        e -= n;
+        if (n < 8 || e < 0 || !is_top(e)) break;
+        n = batch();
     }
     T* o = S + (long long)r * S_stride + ((t4 << logn_root) << 2) + (rho << 2);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) st4<T>(o + ((long long)q << logn_top << 2), v[q]);
+    for (int q = 0; q < NQ; ++q) {
+        add4(v[q], top);
+        st4<T>(o + ((long long)q << logn_top << 2), v[q]);
+    }
 }
 
 template <class T>
 cudaError_t launch_chain_sum(const T* B, long long B_stride, const Chain& ch, T* S, long long S_stride, int logn_root,
                              int tau_pad, int reff, cudaStream_t st) {
     // 2^D groups of 4 values per thread in registers: the deepest subtree that still leaves
-    // about a thousand threads per SM to hide the loads' latency
+    // about 512 threads per SM to hide the loads' latency
     constexpr int DMAX = sizeof(T) == 4 ? 4 : 3;
     int D = logn_root < DMAX ? logn_root : DMAX;
-    while (D > 0 && ((1LL << (logn_root - D)) * (tau_pad / 4) * reff) < 152LL * 1024) --D;
+    while (D > 0 && ((1LL << (logn_root - D)) * (tau_pad / 4) * reff) < 152LL * 512) --D;
     const long long n_top = 1LL << (logn_root - D);
     dim3 grid((unsigned)((n_top + 127) / 128), (unsigned)(tau_pad / 4), (unsigned)reff);
     switch (D) {
