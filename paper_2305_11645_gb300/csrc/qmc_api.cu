@@ -193,6 +193,7 @@ struct Plan {
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
+    bool fine_mat = false;         // materialised S4 band of the float tiers (column-pair lanes)
     bool need_gen = false, need_shift = false, need_pad = false;
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
@@ -333,6 +334,19 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             const long long cost = std::max(per_sm, resident) * (qpg + 2);
             if (best < 0 || cost < best) { best = cost; P.cr = 4 * qpg; P.cg_count = (quads + qpg - 1) / qpg; }
         }
+    }
+    // the materialised product of the float tiers with the S4 band: CTAs of 256 columns over a
+    // range of roots (a multiple of 8), about 5 CTAs per SM in all; the band's 32-bit staging
+    // offsets (below 4 * 2^m) need m <= 27
+    P.fine_mat = op == QMC_OP_REDUCED_MATMUL && P.shape == SHAPE_S4 && precision != QMC_FP64 && P.m <= 27;
+    if (P.fine_mat) {
+        const int cols = fine_s4_mat_cols();
+        P.passes = (P.tau_pad + cols - 1) / cols;
+        const long long want = std::max(1LL, 152LL * 5 / ((long long)P.passes * P.reff));
+        long long rpc = (n_root + want - 1) / want;
+        rpc = std::max(8LL, (rpc + 7) / 8 * 8);
+        P.roots_per_cta = (int)rpc;
+        P.groups = (int)((n_root + rpc - 1) / rpc);
     }
     // partials of the estimate: row blocks of the finalisation (256 rows each)
     P.nblk = (int)((P.N + 255) / 256);
@@ -595,6 +609,11 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     if (mode == MODE_FUSED && P.fine_s4) {
         if constexpr (std::is_same<T, float>::value) {
             QMC_LAUNCH(st, "k_fine_fwd_s4", launch_fine_fwd_s4(a, P.fkind, dim3(P.root_blocks, P.cg_count, P.reff), st));
+        }
+    } else if (mode == MODE_MATERIALIZE && P.fine_mat) {
+        if constexpr (std::is_same<T, float>::value) {
+            a.roots_per_cta = P.roots_per_cta;
+            QMC_LAUNCH(st, "k_fine_mat_s4", launch_fine_mat_s4(a, dim3(P.groups, P.passes, P.reff), st));
         }
     } else {
         dim3 grid(P.root_blocks, P.cg_count, P.reff);

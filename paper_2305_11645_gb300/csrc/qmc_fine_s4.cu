@@ -462,12 +462,174 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// Materialised product P = X A (Algorithms 1-2's output, no integrand)
+// ------------------------------------------------------------------------------------------
+// The product is bound by its 4-byte output writes, so the layout is chosen for them: a CTA
+// covers 256 columns (4 warps x 32 lanes x 2) of a range of roots, and every lane walks the
+// same roots with its two columns of A in registers.  A leaf's two outputs per lane then make
+// one 256-byte contiguous segment of output row k = rho + q n_root per warp store (a thread per
+// root would write 32 rows 4 tau bytes apart).  The x values of 8 roots at a time are staged
+// in shared memory (double-buffered, each value stored twice for the paired instructions).
+constexpr int kMatThreads = 128;
+constexpr int kMatCols = 2 * kMatThreads;
+constexpr int kMatSlots = 64;                  // x values per root
+constexpr int kMatRowPad = 2 * kMatSlots + 4;
+
+// Slot s of a root: level 3 (s < 16: node s / 8, column s % 8), level 2 (node (s-16) / 4,
+// column s % 4), level 1 (node (s-32) / 2, column s % 2), level 0 (s >= 48: leaf c1 + 8 k0 for
+// u = s - 48 = 2 c1 + k0, so that the two leaves under level-1 node c1 are adjacent).  As a
+// code: bit 31 for no value (0), else the point-table offset (+ rho).
+__device__ __forceinline__ unsigned mat_slot_code(const FineArgs<float>& a, int s) {
+    int lev, c, jj;
+    if (s < 16) { lev = 3; c = s >> 3; jj = s & 7; }
+    else if (s < 32) { lev = 2; c = (s - 16) >> 2; jj = s & 3; }
+    else if (s < 48) { lev = 1; c = (s - 32) >> 1; jj = s & 1; }
+    else { const int u = s - 48; lev = 0; c = (u >> 1) + 8 * (u & 1); jj = 0; }
+    if (jj >= a.lev_tau[lev]) return 1u << 31;
+    return (unsigned)(a.lev_tab[lev] + ((long long)jj << a.lev_logn[lev]) + ((long long)c << a.logn_root));
+}
+
+__global__ void __launch_bounds__(kMatThreads, 5) k_fine_mat_s4(const __grid_constant__ FineArgs<float> a) {
+    __shared__ __align__(16) float xs[2][kRB][kMatRowPad];
+    __shared__ unsigned codes[kMatSlots];
+    const int tid = threadIdx.x;
+    const int grp = blockIdx.x, pass = blockIdx.y, r = blockIdx.z;
+    const long long n_root = 1LL << a.logn_root;
+    const int t = pass * kMatCols + 2 * tid;
+    const bool active = t < a.tau_pad;                          // then t + 1 < tau_pad too
+    const bool on0 = t < a.tau, on1 = t + 1 < a.tau;            // the columns written
+    const float* tab = a.tab + (long long)r * a.tab_stride;
+    const float kap = a.kappa;
+
+    float2 ah3[8], ah2[4], ah1[2], ah0;
+    auto lda = [&](int lev, int jj) -> float2 {
+        if (!active || jj >= a.lev_tau[lev]) return f2(0.0f, 0.0f);
+        const float* p = a.A + (long long)(a.lev_col0[lev] + jj) * a.ldA + t;
+        return f2(kap * __ldg(p), kap * __ldg(p + 1));
+    };
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) ah3[jj] = lda(3, jj);
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) ah2[jj] = lda(2, jj);
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) ah1[jj] = lda(1, jj);
+    ah0 = lda(0, 0);
+
+    const long long rho_beg = (long long)grp * a.roots_per_cta;
+    const long long rho_end = min(rho_beg + (long long)a.roots_per_cta, n_root);
+    const int nb = rho_end > rho_beg ? (int)((rho_end - rho_beg + kRB - 1) / kRB) : 0;
+    // staging: thread tid fills slots tid / 8 + 16 u of batch root tid % 8
+    constexpr int PER = kRB * kMatSlots / kMatThreads;
+    const int jst = tid & 7;
+    if (tid < kMatSlots) codes[tid] = mat_slot_code(a, tid);    // (read after the first barrier)
+    float pre[PER];
+    auto fetch = [&](long long rb0) {
+        const long long rho = rb0 + jst;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const unsigned code = codes[(tid >> 3) + 16 * u];
+            pre[u] = (!(code >> 31) && rho < rho_end) ? __ldg(tab + code + rho) : 0.0f;
+        }
+    };
+    auto put = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u)
+            *reinterpret_cast<float2*>(&xs[buf][jst][2 * ((tid >> 3) + 16 * u)]) = f2(pre[u], pre[u]);
+    };
+    // root values S_4 (layout [t/4][rho][4]) of the thread's columns
+    const float* Sb = (a.S && active) ? a.S + (long long)r * a.S_stride + ((long long)(t >> 2) << a.logn_root) * 4 + (t & 3)
+                                      : nullptr;
+    auto lds2 = [&](long long rho) -> float2 {
+        return Sb ? __ldg(reinterpret_cast<const float2*>(Sb + rho * 4)) : f2(0.0f, 0.0f);
+    };
+    // output rows of shift r: P[r][k][t]; with tau even, (k tau + t) is even and a lane's two
+    // columns are one aligned 8-byte store
+    float* Pr = a.P + (long long)r * a.N * a.tau + t;
+    const long long qstride = n_root * a.tau;
+    const bool pair_store = (a.tau & 1) == 0;
+    auto out = [&](float* p, float2 y) {
+        if (pair_store) {
+            if (on1) *reinterpret_cast<float2*>(p) = y;
+        } else {
+            if (on0) p[0] = y.x;
+            if (on1) p[1] = y.y;
+        }
+    };
+
+    __syncthreads();                                            // the slot codes
+    if (nb > 0) { fetch(rho_beg); put(0); }
+    __syncthreads();
+    float2 snext = rho_beg < rho_end ? lds2(rho_beg) : f2(0.0f, 0.0f);
+    for (int kb = 0; kb < nb; ++kb) {
+        const long long rb0 = rho_beg + (long long)kb * kRB;
+        if (kb + 1 < nb) fetch(rb0 + kRB);                        // in flight during this batch
+        for (int j = 0; j < kRB; ++j) {
+            const long long rho = rb0 + j;
+            if (rho >= rho_end) break;
+            const float2 sr = snext;
+            if (rho + 1 < rho_end) snext = lds2(rho + 1);
+            const float* xr = xs[kb & 1][j];
+            auto pairs = [&](int g, float2& p0, float2& p1) {
+                const float4 q = *reinterpret_cast<const float4*>(xr + 4 * g);
+                p0 = f2(q.x, q.y);
+                p1 = f2(q.z, q.w);
+            };
+            float* prow = Pr + rho * a.tau;
+#pragma unroll
+            for (int c3 = 0; c3 < 2; ++c3) {
+                float2 v3 = f2(kap * sr.x, kap * sr.y), w3 = f2(0.0f, 0.0f);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float2 xa, xb;
+                    pairs(4 * c3 + k, xa, xb);
+                    v3 = ffma2(xa, ah3[2 * k], v3);
+                    w3 = ffma2(xb, ah3[2 * k + 1], w3);
+                }
+                v3 = __fadd2_rn(v3, w3);
+#pragma unroll
+                for (int k2 = 0; k2 < 2; ++k2) {
+                    const int c2 = c3 + 2 * k2;
+                    float2 v2 = v3, w2 = f2(0.0f, 0.0f);
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        float2 xa, xb;
+                        pairs(8 + 2 * c2 + k, xa, xb);
+                        v2 = ffma2(xa, ah2[2 * k], v2);
+                        w2 = ffma2(xb, ah2[2 * k + 1], w2);
+                    }
+                    v2 = __fadd2_rn(v2, w2);
+#pragma unroll
+                    for (int k1 = 0; k1 < 2; ++k1) {             // level-1 node c1 = c2 + 4 k1
+                        const int c1 = c2 + 4 * k1;
+                        float2 x10, x11, x0a, x0b;
+                        pairs(16 + c1, x10, x11);
+                        pairs(24 + c1, x0a, x0b);
+                        const float2 v1 = ffma2(x11, ah1[1], ffma2(x10, ah1[0], v2));
+                        out(prow + c1 * qstride, ffma2(x0a, ah0, v1));            // leaf c1
+                        out(prow + (c1 + 8) * qstride, ffma2(x0b, ah0, v1));      // leaf c1 + 8
+                    }
+                }
+            }
+        }
+        if (kb + 1 < nb) put((kb + 1) & 1);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int fine_s4_fwd_roots() { return kFwdRoots; }
 int fine_s4_fwd_resident(int F) { return fwd_min_blocks(F); }
 int fine_s4_bwd_cols() { return kBwdCols; }
 int fine_s4_bwd_batch() { return kRB; }
+int fine_s4_mat_cols() { return kMatCols; }
+
+cudaError_t launch_fine_mat_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {
+    if (a.roots_per_cta < 1 || !a.P) return cudaErrorInvalidValue;
+    k_fine_mat_s4<<<grid, kMatThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 template <int F>
 static cudaError_t fwd_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {

@@ -297,5 +297,9 @@ int fine_s4_bwd_cols();
 int fine_s4_bwd_batch();
 cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
 cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
+// the materialised S4 band (P = X A, float tiers): CTAs of fine_s4_mat_cols() columns over
+// a.roots_per_cta roots (grid: root groups x column passes x shifts)
+int fine_s4_mat_cols();
+cudaError_t launch_fine_mat_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st);
 
 }  // namespace qmc

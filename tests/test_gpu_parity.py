@@ -128,6 +128,21 @@ def test_reduced_matmul_band_shapes(shape, kind, dtype):
             assert np.all(np.abs(P[r] - want) <= fp32_product_bound(X, p.A))
 
 
+@pytest.mark.parametrize("kind", [I.LATTICE, I.DIGITAL_NET])
+@pytest.mark.parametrize("tau", [600, 601])
+def test_reduced_matmul_fp32_passes_and_groups(kind, tau):
+    """The materialised S4 band over several 256-column passes and many root groups, with a
+    ragged last pass; an even tau takes the paired 8-byte stores, an odd one the scalar ones."""
+    sh = dict(m=14, w=I.log2_weights(300, 14), tau=tau)
+    p = shaped_problem(sh, kind, 31 + tau, transform=I.T_CENTER, R=2, dtype=np.float32)
+    P = api.reduced_matmul(api.Rule.from_problem(p), torch.from_numpy(p.A).to(DEV)).cpu().numpy()
+    assert P.shape == (2, 1 << 14, tau)
+    for r in range(p.R_eff):
+        X = O.points(p, r)
+        want = O.product(X, p.A)
+        assert np.all(np.abs(P[r] - want) <= fp32_product_bound(X, p.A))
+
+
 # ----------------------------------------------------------------------------- estimates and gradients
 
 FKINDS = [(I.F_LINEAR_MEAN, (0, 0, 0, 0)), (I.F_MEAN_COS, (0, 0, 0, 0)), (I.F_CALL_MEAN_EXP, (0.2, 1.0, 0, 0)),
