@@ -300,6 +300,33 @@ def run_ours(args, dist, rank, world):
     roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": TRAFFIC_BYTES.get(name)})
     kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in sorted(kern.items())}
 
+    # the materialised product P = X A of the same workload and tier (qmc_reduced_matmul): its
+    # band kernel is bound by the output writes, 4 bytes per output (the root values and the
+    # point table it reads are under 5 % of that)
+    mws = torch.empty(max(api.workspace_size(L.QMC_OP_REDUCED_MATMUL, [rule], [p.tau], None,
+                                             api._precision(A, prec)), 256), dtype=torch.uint8, device=dev)
+
+    def materialize():
+        api.reduced_matmul(rule, A, ws=mws, precision=prec)
+
+    for _ in range(3):
+        materialize()
+    mat_ms = statistics.mean(timed(materialize)[0])
+    _, mkern = timed(materialize, trace=True, prequeue=True)
+    out_bytes = outputs * 4
+    materialized = {"op": "qmc_reduced_matmul (P = X A, R x N x tau float32)", "ms_per_call": mat_ms,
+                    "value": outputs / (mat_ms / 1e3), "unit": "outputs/s",
+                    "kernels": {k: {"launches": c, "ms_per_call": t / args.steps} for k, (c, t) in sorted(mkern.items())}}
+    band = "k_fine_mat_s4" if "k_fine_mat_s4" in mkern else "k_fine_fwd_materialize"
+    if band in mkern:
+        cnt, tot = mkern[band]
+        sec = tot / cnt / 1e3
+        materialized["roofline"] = {"bound": "hbm", "kernel": band, "achieved": out_bytes / sec / 1e9,
+                                    "peak": mp["hbm_gbs"], "unit": "GB/s", "frac": out_bytes / sec / 1e9 / mp["hbm_gbs"],
+                                    "bytes_per_launch": out_bytes, "launch_ms": sec * 1e3, "traffic": None,
+                                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    del mws
+
     # end to end through the public API with host buffers: H2D of A, D2H of the estimates and dQ/dA
     A_host = torch.from_numpy(p.A).pin_memory()
     est_host = torch.empty(p.R_eff + 1, dtype=torch.float64).pin_memory()
@@ -334,7 +361,7 @@ def run_ours(args, dist, rank, world):
                          "parallelism": "replicas" if world > 1 else "single"},
               "eager_ms_per_step": eager_ms,
               "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clock_info,
-              "kernels": kernels, "peaks": peak_src}
+              "kernels": kernels, "materialized": materialized, "peaks": peak_src}
 
     est, grad = step()
     torch.cuda.synchronize()

@@ -336,15 +336,15 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         }
     }
     // the materialised product of the float tiers with the S4 band: CTAs of 256 columns over a
-    // range of roots (a multiple of 8), about 5 CTAs per SM in all; the band's 32-bit staging
-    // offsets (below 4 * 2^m) need m <= 27
+    // range of roots, as many as fill 5 CTAs per SM once (the band is bound by its output writes;
+    // an even spread over the SMs matters more than whole batches of 8 roots); the band's 32-bit
+    // staging offsets (below 4 * 2^m) need m <= 27
     P.fine_mat = op == QMC_OP_REDUCED_MATMUL && P.shape == SHAPE_S4 && precision != QMC_FP64 && P.m <= 27;
     if (P.fine_mat) {
         const int cols = fine_s4_mat_cols();
         P.passes = (P.tau_pad + cols - 1) / cols;
         const long long want = std::max(1LL, 152LL * 5 / ((long long)P.passes * P.reff));
-        long long rpc = (n_root + want - 1) / want;
-        rpc = std::max(8LL, (rpc + 7) / 8 * 8);
+        const long long rpc = std::max(1LL, (n_root + want - 1) / want);
         P.roots_per_cta = (int)rpc;
         P.groups = (int)((n_root + rpc - 1) / rpc);
     }
