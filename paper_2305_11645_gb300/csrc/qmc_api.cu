@@ -348,8 +348,12 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.roots_per_cta = (int)rpc;
         P.groups = (int)((n_root + rpc - 1) / rpc);
     }
-    // partials of the estimate: row blocks of the finalisation (256 rows each)
-    P.nblk = (int)((P.N + 255) / 256);
+    // partials of the estimate: row blocks of the finalisation, 256 threads of rpt rows each (one
+    // row per thread up to about four waves of 8 CTAs per SM, then up to 16 rows per thread)
+    {
+        const long long rpt = std::max(1LL, std::min(16LL, P.N * P.reff / (152LL * 8 * 256 * 4)));
+        P.nblk = (int)((P.N + 256 * rpt - 1) / (256 * rpt));
+    }
 
     // backward schedule
     if (op == QMC_OP_INTEGRATE_BWD && P.fine_s4) {

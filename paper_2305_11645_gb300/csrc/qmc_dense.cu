@@ -228,42 +228,76 @@ template cudaError_t launch_chain_sum<double>(const double*, long long, const Ch
 // ------------------------------------------------------------------------------------------
 // row finalisation and the mean
 // ------------------------------------------------------------------------------------------
-constexpr int kRowsPerThread = 1;
-
+// A CTA of 256 threads takes rpt rows per thread (consecutive threads, consecutive rows), so
+// that large problems run in a few waves instead of one CTA per 256 rows; with rpt > 1 rows are
+// taken two at a time, the loads of both rows' partials issued before their sums.
 template <class T>
 __global__ void __launch_bounds__(256) k_rows_finalize(const T* __restrict__ rowpart, const T* __restrict__ rowmax,
                                                        int cg_count, long long N, int F, double tau, double c,
                                                        double K, double coef_scale, T* __restrict__ rowsave,
                                                        T* __restrict__ rowf, double* __restrict__ fpart, int nblk,
-                                                       unsigned int* ticket, double* __restrict__ est) {
+                                                       int rpt, unsigned int* ticket, double* __restrict__ est) {
     // Per-row arithmetic in T (the row sums are T partials).  The CTA's rows are summed with
     // warp shuffles in T and the warp sums in double; the mean over the CTAs is in double.
     __shared__ double sh[32];
     const int r = blockIdx.y;
     const T inv_tau = (T)(1.0 / tau);
+    const T* rp0 = rowpart + (long long)r * cg_count * N;
+    const T* rm0 = rowmax ? rowmax + (long long)r * cg_count * N : nullptr;
     T fsum = T(0);
-#pragma unroll
-    for (int i = 0; i < kRowsPerThread; ++i) {
-        const long long k = ((long long)blockIdx.x * kRowsPerThread + i) * blockDim.x + threadIdx.x;
-        if (k >= N) break;
-        T u;
-        const T* rp = rowpart + (long long)r * cg_count * N + k;
+    if (rpt == 1) {
+        // one row per thread (problems of up to about four waves)
+        const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+        if (k < N) {
+            T u;
+            if (F == F_LOGSUMEXP) {
+                T M = -INFINITY;
+#pragma unroll 8
+                for (int g = 0; g < cg_count; ++g) M = fmax(M, rm0[(long long)g * N + k]);
+                T S = T(0);
+#pragma unroll 8
+                for (int g = 0; g < cg_count; ++g) S += rp0[(long long)g * N + k] * exp2(rm0[(long long)g * N + k] - M);
+                u = lse_row(M, S);
+            } else {
+                u = T(0);
+#pragma unroll 8
+                for (int g = 0; g < cg_count; ++g) u += rp0[(long long)g * N + k];
+            }
+            fsum = finalize_row<T>(F, u, inv_tau, tau, K, coef_scale, rowsave, rowf, (long long)r * N + k);
+        }
+    }
+    for (int i = 0; rpt > 1 && i < rpt; i += 2) {
+        const long long k0 = ((long long)blockIdx.x * rpt + i) * blockDim.x + threadIdx.x;
+        const long long k1 = k0 + blockDim.x;
+        const bool on0 = k0 < N, on1 = i + 1 < rpt && k1 < N;
+        if (!on0) break;
+        T u0, u1 = T(0);
         if (F == F_LOGSUMEXP) {
             // the partials hold (max, sum 2^(v - max)) of v = y log2 e
-            const T* rm = rowmax + (long long)r * cg_count * N + k;
-            T M = -INFINITY;
+            T M0 = -INFINITY, M1 = -INFINITY;
 #pragma unroll 8
-            for (int g = 0; g < cg_count; ++g) M = fmax(M, rm[(long long)g * N]);
-            T S = T(0);
+            for (int g = 0; g < cg_count; ++g) {
+                M0 = fmax(M0, rm0[(long long)g * N + k0]);
+                if (on1) M1 = fmax(M1, rm0[(long long)g * N + k1]);
+            }
+            T S0 = T(0), S1 = T(0);
 #pragma unroll 8
-            for (int g = 0; g < cg_count; ++g) S += rp[(long long)g * N] * exp2(rm[(long long)g * N] - M);
-            u = lse_row(M, S);
+            for (int g = 0; g < cg_count; ++g) {
+                S0 += rp0[(long long)g * N + k0] * exp2(rm0[(long long)g * N + k0] - M0);
+                if (on1) S1 += rp0[(long long)g * N + k1] * exp2(rm0[(long long)g * N + k1] - M1);
+            }
+            u0 = lse_row(M0, S0);
+            if (on1) u1 = lse_row(M1, S1);
         } else {
-            u = T(0);
+            u0 = T(0);
 #pragma unroll 8
-            for (int g = 0; g < cg_count; ++g) u += rp[(long long)g * N];
+            for (int g = 0; g < cg_count; ++g) {
+                u0 += rp0[(long long)g * N + k0];
+                if (on1) u1 += rp0[(long long)g * N + k1];
+            }
         }
-        fsum += finalize_row<T>(F, u, inv_tau, tau, K, coef_scale, rowsave, rowf, (long long)r * N + k);
+        fsum += finalize_row<T>(F, u0, inv_tau, tau, K, coef_scale, rowsave, rowf, (long long)r * N + k0);
+        if (on1) fsum += finalize_row<T>(F, u1, inv_tau, tau, K, coef_scale, rowsave, rowf, (long long)r * N + k1);
     }
     const double s = block_sum_t<T>(fsum, sh);
     finalize_estimate(s, r, blockIdx.x, nblk, gridDim.y, N, gridDim.x * gridDim.y, ticket, fpart, est, sh);
@@ -273,9 +307,11 @@ template <class T>
 cudaError_t launch_rows_finalize(const T* rowpart, const T* rowmax, int cg_count, long long N, int reff, int F,
                                  double tau, double c, double K, double coef_scale, T* rowsave, T* rowf_out,
                                  double* fpart, int nblk, unsigned int* ticket, double* est, cudaStream_t st) {
+    if (nblk < 1) return cudaErrorInvalidValue;
+    const long long rpt = (N + 256LL * nblk - 1) / (256LL * nblk);       // rows per thread
     dim3 grid(nblk, reff);
     k_rows_finalize<T><<<grid, 256, 0, st>>>(rowpart, rowmax, cg_count, N, F, tau, c, K, coef_scale, rowsave,
-                                             rowf_out, fpart, nblk, ticket, est);
+                                             rowf_out, fpart, nblk, (int)rpt, ticket, est);
     return cudaGetLastError();
 }
 template cudaError_t launch_rows_finalize<float>(const float*, const float*, int, long long, int, int, double, double,
