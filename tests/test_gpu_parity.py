@@ -4,7 +4,8 @@ seeded cases that span several tiles and ragged tails.
 Tolerances: points bit-exact; FP64 tier 1e-12 (norm-wise relative);
 FP32 tier: products within the elementwise dot-product bound
 (s+16) 2^-24 sum_j |x_j a_j|, estimates and gradients within 2e-5 relative
-(the FP32 arithmetic of s + tau accumulated terms; derivation in the design doc)."""
+(the FP32 arithmetic of s + tau accumulated terms: about (s + tau) 2^-24 relative
+for sums of like-signed terms, with room for the row sums' cancellation)."""
 import json
 import os
 
