@@ -177,7 +177,7 @@ qmc_status qmc_gen_points(const qmc_rule* rule, uint32_t shift_idx, int layout, 
  *  with the shift and transform of the rule applied to X (Sec. 2.3).
  *  d_A   DEVICE s x tau row-major (double for QMC_FP64, float otherwise).
  *  d_P   DEVICE R_eff x N x tau row-major, same element type: d_P[(r*N + k)*tau + t] = (x_k^T A)_t
- *        for shift r.
+ *        for shift r.  16-byte aligned (QMC_ERR_INVALID_ARG otherwise, before any CUDA call).
  */
 qmc_status qmc_reduced_matmul(const qmc_rule* rule, const void* d_A, uint32_t tau, int precision,
                               void* d_P, void* d_ws, size_t ws_bytes, void* stream);

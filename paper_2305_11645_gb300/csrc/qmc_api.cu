@@ -771,6 +771,8 @@ qmc_status qmc_reduced_matmul(const qmc_rule* rule, const void* d_A, uint32_t ta
     qmc_status st = make_plan(QMC_OP_REDUCED_MATMUL, rule, tau, nullptr, precision, d_A, P);
     if (st != QMC_OK) return st;
     if (!d_A || !d_P) return fail(QMC_ERR_INVALID_ARG, "d_A or d_P is NULL");
+    // (the product kernels write whole 8- and 16-byte groups of a row)
+    if (((uintptr_t)d_P) % 16) return fail(QMC_ERR_INVALID_ARG, "d_P must be 16-byte aligned");
     if (!d_ws || ws_bytes < P.total) return fail(QMC_ERR_NO_MEMORY, "workspace of %zu bytes, %zu needed", ws_bytes, P.total);
     if (((uintptr_t)d_ws) % 256) return fail(QMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
     cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);

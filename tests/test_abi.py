@@ -138,6 +138,17 @@ def test_workspace_size_and_its_errors(lib):
     assert st == L.QMC_ERR_INVALID_ARG
 
 
+def test_unaligned_product_rejected_before_any_cuda_call(lib):
+    p = I.random_problem(3)
+    r = Rule.from_problem(p)
+    fake = ctypes.c_void_p(0x1000)
+    unaligned = ctypes.c_void_p(0x1004)     # never dereferenced: the alignment check fails first
+    for prec in (L.QMC_FP64, L.QMC_FP32):
+        st = lib.qmc_reduced_matmul(ctypes.byref(r.struct()), fake, p.tau, prec, unaligned, fake, 1 << 30, None)
+        assert st == L.QMC_ERR_INVALID_ARG
+        assert b"16-byte aligned" in lib.qmc_last_error()
+
+
 def test_too_small_workspace_rejected_before_any_cuda_call(lib):
     p = I.random_problem(2, f_kind=I.F_MEAN_COS)
     r = Rule.from_problem(p)
