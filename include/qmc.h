@@ -49,6 +49,8 @@ typedef int qmc_status;
 /* point-set kinds */
 #define QMC_LATTICE      0        /* reduced rank-1 lattice, Sec. 1.3 */
 #define QMC_DIGITAL_NET  1        /* reduced digital net, Sec. 4, eq. reduced_genmat_net2 */
+#define QMC_REDUCED_MC   2        /* reduced Monte Carlo, Sec. 5, eq. randpts: coordinate j of point n is
+                                     the i.i.d. sample y_{j, n mod N_j}, N_j = 2^(m-min(w_j,m)) */
 
 /* coordinate transforms phi_j applied to the (shifted) points, Sec. 2.3 */
 #define QMC_T_IDENTITY   0        /* x */
@@ -92,7 +94,7 @@ typedef int qmc_status;
 
 /*
  * A reduced QMC rule (the point set).
- *  kind       QMC_LATTICE or QMC_DIGITAL_NET.
+ *  kind       QMC_LATTICE, QMC_DIGITAL_NET or QMC_REDUCED_MC.
  *  b          base; the GPU path supports b = 2 only (others: QMC_ERR_UNSUPPORTED).
  *  m          N = b^m points, 1 <= m <= 30.
  *  s          dimension (rows of A), 1 <= s <= 65536.
@@ -108,12 +110,18 @@ typedef int qmc_status;
  *             (the periodic reduced net; otherwise QMC_ERR_UNSUPPORTED: the paper's non-periodic
  *             Algorithm 4 is not built) and the leading (m-w_j) x (m-w_j) block must be nonsingular over
  *             GF(2) (so each value repeats exactly 2^{w_j} times; otherwise QMC_ERR_INVALID_ARG).
+ *  z          HOST uint32[R_eff * T] (reduced MC): the samples y_{j,i} as X32 = y 2^32, drawn by the
+ *             caller (i.i.d. uniform words give i.i.d. U[0,1) samples on the 2^-32 grid).  Replica r
+ *             holds, for j = 0..s-1 in order, the N_j = 2^(m-min(w_j,m)) samples y_{j,0..N_j-1} of
+ *             column j (the QMC_LAYOUT_DISTINCT layout); T = sum_j N_j.  C and shift must be NULL.
  *  R          number of random shifts (0 = unshifted rule); results are produced for R_eff = max(R,1).
+ *             Reduced MC: the number of independent replicas (each its own samples in z).
  *  shift      HOST uint32[R*s]: shift r of column j is shift[r*s + j] (units of 2^-32).
- *  transform  QMC_T_*; QMC_T_INV_NORMAL requires R >= 1 (the unshifted point 0 maps to -inf).
- *  d_gen      DEVICE copy of z (s words) or C (s*m words), or NULL: then the host array is copied
- *             into the workspace on every call (a pageable copy, which also prevents CUDA graph
- *             capture).  It must hold exactly the host values.
+ *  transform  QMC_T_*; QMC_T_INV_NORMAL requires R >= 1 for lattices and nets (the unshifted point 0
+ *             maps to -inf), and no zero sample word for reduced MC (checked on the host).
+ *  d_gen      DEVICE copy of z (s words; reduced MC: R_eff * T words) or C (s*m words), or NULL: then
+ *             the host array is copied into the workspace on every call (a pageable copy, which also
+ *             prevents CUDA graph capture).  It must hold exactly the host values.
  *  d_shift    DEVICE copy of shift (R*s words) or NULL (uploaded per call like d_gen).
  */
 typedef struct {
@@ -162,7 +170,7 @@ qmc_status qmc_workspace_size(int op, const qmc_rule* rules, const uint32_t* tau
 
 /*
  * qmc_gen_points: the point set (Sec. 1.3 lattice / Algorithm 3 net, Sec. 2.3 shift), bit-exact.
- *  shift_idx  which shift to apply (ignored when R = 0).
+ *  shift_idx  which shift to apply (ignored when R = 0); reduced MC: which replica.
  *  layout     QMC_LAYOUT_FULL: d_out is N*s uint32, d_out[k*s + j] = X32 of x_{k,j}.
  *             QMC_LAYOUT_DISTINCT: d_out holds, for j = 0..s-1 in order, the 2^(m-min(w_j,m)) values
  *             x_{k,j}, k < 2^(m-min(w_j,m)) (one period of the column).

@@ -30,6 +30,11 @@ reordering beyond what the definitions state:
   O7  the gradient of the shift-averaged estimate with respect to A:
       (1/(R N)) sum_r X_r^T grad f(Y_r).
   O8  central finite differences of the estimate in single entries of A.
+  O9  reduced Monte Carlo points (Sec. 5, eq. randpts): with N_j = 2^(m-w_j),
+      N_{s+1} = 1 and M_j = N_j / N_{j+1}, write n in the mixed radix
+      n = m_s N_{s+1} + m_{s-1} N_s + ... + m_1 N_2 (0 <= m_j < M_j) and take
+      x_{j,n} = y_{j, m_s N_{s+1} + ... + m_j N_{j+1}}, the samples y given as
+      32-bit words (the caller's draws).
 
 Parity pins for every function live in tests/test_oracle_pins.py.  Nothing in
 this file is "parity unpinned".
@@ -42,7 +47,7 @@ from typing import Iterable, Optional, Sequence
 import numpy as np
 from scipy import special as _sp
 
-LATTICE, DIGITAL_NET = 0, 1
+LATTICE, DIGITAL_NET, REDUCED_MC = 0, 1, 2
 T_IDENTITY, T_CENTER, T_INV_NORMAL, T_TENT = 0, 1, 2, 3
 F_NONE, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP = range(7)
 
@@ -117,9 +122,41 @@ def net_x32(m: int, w, C: np.ndarray, shift: Optional[np.ndarray] = None, ks=Non
     return x32
 
 
+# ----------------------------------------------------------------------------- O9 reduced Monte Carlo
+
+def mc_sample_index(m: int, w, ks=None) -> np.ndarray:
+    """Index of the sample that point n uses in coordinate j (eq. randpts), by the mixed-radix
+    digits of n.  The paper starts from w_1 = 0; a first column with w_1 > 0 is handled by a
+    leading virtual coordinate of weight 0, so that n < N is always representable."""
+    N = 1 << m
+    ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
+    wl = [0] + [min(int(wj), m) for wj in w] + [m]          # virtual w_0 = 0, ..., w_{s+1} = m
+    Nl = [1 << (m - wj) for wj in wl]                       # N_0 = N, N_1, ..., N_{s+1} = 1
+    Ml = [Nl[i] // Nl[i + 1] for i in range(len(Nl) - 1)]  # M_i = N_i / N_{i+1}
+    digits = [(ks // Nl[i + 1]) % Ml[i] for i in range(len(Ml))]     # m_i, place value N_{i+1}
+    out = np.empty((len(ks), len(w)), dtype=np.int64)
+    for j in range(len(w)):
+        jj = j + 1                                           # index in the extended sequence
+        idx = np.zeros(len(ks), dtype=np.int64)
+        for i in range(jj, len(Ml)):                         # m_{jj} N_{jj+1} + ... + m_s N_{s+1}
+            idx += digits[i] * Nl[i + 1]
+        out[:, j] = idx
+    return out
+
+
+def mc_x32(m: int, w, y: np.ndarray, ks=None) -> np.ndarray:
+    """X32 of the reduced MC points of one replica: x_{j,n} = y_{j, index}, where replica row y
+    holds column j's samples at offset sum_{j' < j} N_{j'}."""
+    idx = mc_sample_index(m, w, ks)
+    off = np.cumsum([0] + [1 << (m - min(int(wj), m)) for wj in w])[:-1]
+    return np.asarray(y, dtype=np.uint32)[idx + off[None, :]]
+
+
 # ----------------------------------------------------------------------------- O3/O4 shifts and transforms
 
 def x32_points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
+    if problem.kind == REDUCED_MC:
+        return mc_x32(problem.m, problem.w, problem.y[shift_idx], ks)
     shift = None if problem.shifts is None else problem.shifts[shift_idx]
     if problem.kind == LATTICE:
         return lattice_x32(problem.m, problem.w, problem.z, shift, ks)

@@ -19,7 +19,7 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .inputs import (DIGITAL_NET, LATTICE, T_CENTER, T_IDENTITY, T_INV_NORMAL, T_TENT,  # noqa: F401
+from .inputs import (DIGITAL_NET, LATTICE, REDUCED_MC, T_CENTER, T_IDENTITY, T_INV_NORMAL, T_TENT,  # noqa: F401
                      F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_LINEAR_MEAN, F_LOGSUMEXP, F_MEAN_COS, F_NONE,
                      F_PDE_INV_SQ)
 
@@ -41,9 +41,11 @@ def _u32(a) -> Optional[np.ndarray]:
 
 
 class Rule:
-    """A reduced QMC rule: lattice (z) or periodic reduced digital net (C), optional shifts."""
+    """A reduced QMC rule: lattice (z) or periodic reduced digital net (C) with optional shifts, or
+    reduced Monte Carlo (y: the replicas' samples, uint32 [R, sum_j N_j] in the distinct layout)."""
 
-    def __init__(self, kind: int, m: int, w, z=None, C=None, shifts=None, transform: int = T_IDENTITY, b: int = 2):
+    def __init__(self, kind: int, m: int, w, z=None, C=None, shifts=None, transform: int = T_IDENTITY, b: int = 2,
+                 y=None):
         self.kind, self.m, self.b, self.transform = int(kind), int(m), int(b), int(transform)
         self.w = _u32(w)
         self.s = int(self.w.shape[0])
@@ -51,11 +53,19 @@ class Rule:
         self.C = None if C is None else _u32(np.asarray(C).reshape(-1))
         self.shifts = None if shifts is None else _u32(np.asarray(shifts).reshape(-1, self.s))
         self.R = 0 if self.shifts is None else int(self.shifts.shape[0])
+        self.y = None
+        if self.kind == REDUCED_MC:
+            if y is None:
+                raise ValueError("a reduced MC rule needs its samples y")
+            T = sum(1 << (self.m - min(int(wj), self.m)) for wj in self.w)
+            self.y = _u32(np.asarray(y).reshape(-1, T))
+            self.R = int(self.y.shape[0])        # independent replicas
         self._dev = {}
 
     @classmethod
     def from_problem(cls, p) -> "Rule":
-        return cls(p.kind, p.m, p.w, z=p.z, C=p.C, shifts=p.shifts, transform=p.transform, b=p.b)
+        return cls(p.kind, p.m, p.w, z=p.z, C=p.C, shifts=p.shifts, transform=p.transform, b=p.b,
+                   y=getattr(p, "y", None))
 
     @property
     def N(self) -> int:
@@ -68,7 +78,8 @@ class Rule:
     def _device_arrays(self, device: torch.device):
         key = str(device)
         if key not in self._dev:
-            gen = self.z if self.kind == LATTICE else self.C
+            gen = {LATTICE: self.z, DIGITAL_NET: self.C, REDUCED_MC: None if self.y is None else self.y.reshape(-1)}[
+                self.kind]
             d_gen = None if gen is None else torch.from_numpy(gen.view(np.int32).copy()).to(device)
             d_shift = None if self.shifts is None else torch.from_numpy(
                 self.shifts.reshape(-1).view(np.int32).copy()).to(device)
@@ -80,7 +91,7 @@ class Rule:
             return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
         r = L.QmcRule()
         r.kind, r.b, r.m, r.s = self.kind, self.b, self.m, self.s
-        r.w, r.z, r.C = ptr(self.w), ptr(self.z), ptr(self.C)
+        r.w, r.z, r.C = ptr(self.w), ptr(self.y.reshape(-1) if self.kind == REDUCED_MC else self.z), ptr(self.C)
         r.R = self.R
         r.shift = ptr(None if self.shifts is None else self.shifts.reshape(-1))
         r.transform = self.transform

@@ -117,8 +117,8 @@ int gf2_rank(std::vector<uint32_t> v) {
 
 qmc_status validate(const qmc_rule* r) {
     if (!r) return fail(QMC_ERR_INVALID_ARG, "rule is NULL");
-    if (r->kind != QMC_LATTICE && r->kind != QMC_DIGITAL_NET)
-        return fail(QMC_ERR_INVALID_ARG, "kind %d is neither QMC_LATTICE nor QMC_DIGITAL_NET", r->kind);
+    if (r->kind != QMC_LATTICE && r->kind != QMC_DIGITAL_NET && r->kind != QMC_REDUCED_MC)
+        return fail(QMC_ERR_INVALID_ARG, "kind %d is not QMC_LATTICE, QMC_DIGITAL_NET or QMC_REDUCED_MC", r->kind);
     if (r->b < 2) return fail(QMC_ERR_INVALID_ARG, "base b=%u must be a prime >= 2", r->b);
     if (r->b != 2) return fail(QMC_ERR_UNSUPPORTED, "base b=%u: only b=2 is built", r->b);
     if (r->m < 1) return fail(QMC_ERR_INVALID_ARG, "m=%u: N = b^m needs m >= 1", r->m);
@@ -132,10 +132,26 @@ qmc_status validate(const qmc_rule* r) {
     if (r->transform < QMC_T_IDENTITY || r->transform > QMC_T_TENT)
         return fail(QMC_ERR_INVALID_ARG, "transform %d unknown", r->transform);
     if (r->R > 65535) return fail(QMC_ERR_INVALID_ARG, "R=%u shifts: at most 65535", r->R);
+    const uint32_t m = r->m;
+    if (r->kind == QMC_REDUCED_MC) {
+        // Sec. 5: the caller's i.i.d. samples, N_j = 2^(m - min(w_j, m)) per column and replica
+        if (!r->z) return fail(QMC_ERR_INVALID_ARG, "reduced MC needs its samples in z");
+        if (r->C || r->shift || r->d_shift)
+            return fail(QMC_ERR_INVALID_ARG, "reduced MC takes no C and no shift (R counts independent replicas)");
+        if (r->transform == QMC_T_INV_NORMAL) {
+            unsigned long long T = 0;
+            for (uint32_t j = 0; j < r->s; ++j) T += 1ull << (m - std::min(r->w[j], m));
+            const unsigned long long words = T * std::max<uint32_t>(r->R, 1);
+            for (unsigned long long i = 0; i < words; ++i)
+                if (r->z[i] == 0)
+                    return fail(QMC_ERR_INVALID_ARG, "sample word %llu is 0: the inverse-normal transform maps it to -inf",
+                                i);
+        }
+        return QMC_OK;
+    }
     if (r->R > 0 && !r->shift) return fail(QMC_ERR_INVALID_ARG, "R=%u but shift is NULL", r->R);
     if (r->transform == QMC_T_INV_NORMAL && r->R == 0)
         return fail(QMC_ERR_INVALID_ARG, "the inverse-normal transform needs a random shift (x=0 maps to -inf)");
-    const uint32_t m = r->m;
     if (r->kind == QMC_LATTICE) {
         if (!r->z) return fail(QMC_ERR_INVALID_ARG, "lattice rule needs z");
         for (uint32_t j = 0; j < r->s; ++j) {
@@ -195,10 +211,19 @@ struct Plan {
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
     bool fine_mat = false;         // materialised S4 band of the float tiers (column-pair lanes)
     bool need_gen = false, need_shift = false, need_pad = false;
+    bool has_shift = false;        // lattice / net with R shifts (reduced MC: R replicas, no shift)
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
            total = 0;
 };
+
+// words of the rule's generator: z (lattice), the column masks C (net), or the samples of every
+// replica (reduced MC: R_eff x sum_j N_j, the distinct-row table's layout)
+size_t gen_words(const Plan& P) {
+    if (P.kind == QMC_DIGITAL_NET) return (size_t)P.s * P.m;
+    if (P.kind == QMC_REDUCED_MC) return (size_t)P.reff * (size_t)P.T_tot;
+    return (size_t)P.s;
+}
 
 qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integrand* f, int precision,
                      const void* d_A, Plan& P) {
@@ -226,11 +251,12 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.T_tot = P.lev_tab[P.m + 1];
     P.tab_stride = (P.T_tot + 3) / 4 * 4;
     P.need_gen = (r->d_gen == nullptr);
-    P.need_shift = (P.R > 0 && r->d_shift == nullptr);
+    P.has_shift = P.kind != QMC_REDUCED_MC && P.R > 0;
+    P.need_shift = (P.has_shift && r->d_shift == nullptr);
 
     size_t off = 0;
     P.off_gen = off;
-    if (P.need_gen) off = align256(off + sizeof(uint32_t) * (size_t)P.s * (P.kind == QMC_DIGITAL_NET ? P.m : 1));
+    if (P.need_gen) off = align256(off + sizeof(uint32_t) * gen_words(P));
     P.off_shift = off;
     if (P.need_shift) off = align256(off + sizeof(uint32_t) * (size_t)P.R * P.s);
     if (op == QMC_OP_GEN_POINTS) { P.total = off; return QMC_OK; }
@@ -520,7 +546,8 @@ DevRule dev_rule(const Plan& P, const qmc_rule* r, char* ws) {
     DevRule R{};
     R.kind = P.kind; R.m = P.m; R.s = P.s; R.transform = P.transform; R.R = P.R;
     R.gen = P.need_gen ? reinterpret_cast<const uint32_t*>(ws + P.off_gen) : r->d_gen;
-    R.shift = P.R == 0 ? nullptr : (P.need_shift ? reinterpret_cast<const uint32_t*>(ws + P.off_shift) : r->d_shift);
+    R.shift = !P.has_shift ? nullptr : (P.need_shift ? reinterpret_cast<const uint32_t*>(ws + P.off_shift) : r->d_shift);
+    R.T_tot = P.T_tot;
     R.nlev = P.m + 1;
     for (int I = 0; I <= P.m; ++I) { R.lev_tau[I] = P.lev_tau[I]; R.lev_col0[I] = P.lev_col0[I]; }
     for (int I = 0; I <= P.m + 1; ++I) R.lev_tab[I] = P.lev_tab[I];
@@ -529,8 +556,7 @@ DevRule dev_rule(const Plan& P, const qmc_rule* r, char* ws) {
 
 qmc_status upload_rule(const Plan& P, const qmc_rule* r, char* ws, cudaStream_t st) {
     if (P.need_gen) {
-        const size_t words = (size_t)P.s * (P.kind == QMC_DIGITAL_NET ? P.m : 1);
-        QMC_CUDA(cudaMemcpyAsync(ws + P.off_gen, P.kind == QMC_DIGITAL_NET ? r->C : r->z, words * 4,
+        QMC_CUDA(cudaMemcpyAsync(ws + P.off_gen, P.kind == QMC_DIGITAL_NET ? r->C : r->z, gen_words(P) * 4,
                                  cudaMemcpyHostToDevice, st));
     }
     if (P.need_shift)
@@ -749,7 +775,7 @@ qmc_status qmc_gen_points(const qmc_rule* rule, uint32_t shift_idx, int layout, 
     if (!d_out) return fail(QMC_ERR_INVALID_ARG, "d_out is NULL");
     if (layout != QMC_LAYOUT_FULL && layout != QMC_LAYOUT_DISTINCT)
         return fail(QMC_ERR_INVALID_ARG, "layout %d unknown", layout);
-    if (P.R > 0 && shift_idx >= (uint32_t)P.R)
+    if (P.kind == QMC_REDUCED_MC ? shift_idx >= (uint32_t)P.reff : (P.R > 0 && shift_idx >= (uint32_t)P.R))
         return fail(QMC_ERR_INVALID_ARG, "shift_idx=%u but R=%d", shift_idx, P.R);
     const size_t need = layout == QMC_LAYOUT_FULL ? (size_t)P.N * P.s : (size_t)P.T_tot;
     if (out_words < need) return fail(QMC_ERR_INVALID_ARG, "d_out holds %zu words, %zu needed", out_words, need);

@@ -12,7 +12,7 @@ constexpr int kMaxLevels = 32;     // levels I = 0..m (level m holds the constan
 constexpr int kMaxChain = 48;      // coarse entries (levels, cut into column ranges); Chain stays ~4 KB
 
 // Kinds, transforms and integrands mirror include/qmc.h.
-enum { KIND_LATTICE = 0, KIND_NET = 1 };
+enum { KIND_LATTICE = 0, KIND_NET = 1, KIND_MC = 2 };
 enum { T_IDENTITY = 0, T_CENTER = 1, T_INV_NORMAL = 2, T_TENT = 3 };
 enum { F_NONE = 0, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP };
 enum { SHAPE_S0 = 0, SHAPE_S1 = 1, SHAPE_S4 = 4 };
@@ -24,8 +24,10 @@ enum { MODE_FUSED = 0, MODE_MATERIALIZE = 1 };
 struct DevRule {
     int kind, m, s, transform;
     int R;                          // shifts present in `shift` (0 = unshifted)
-    const uint32_t* gen;            // lattice: z[s]; net: C[s*m] column masks
+    const uint32_t* gen;            // lattice: z[s]; net: C[s*m] column masks; reduced MC: the samples
+                                    // of every replica, [r][T_tot] in the distinct-row table's layout
     const uint32_t* shift;          // R*s or nullptr
+    long long T_tot;                // distinct-row table entries per shift / replica
     int nlev;                       // m + 1
     int lev_tau[kMaxLevels];
     int lev_col0[kMaxLevels];

@@ -35,6 +35,11 @@ __global__ void k_table(const __grid_constant__ DevRule R, T* __restrict__ tab, 
     if (ticket && blockIdx.x == 0 && threadIdx.x == 0) *ticket = 0u;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < T_tot;
          g += (long long)gridDim.x * blockDim.x) {
+        if (R.kind == KIND_MC) {        // reduced MC (Sec. 5): replica r's samples are in the table's layout
+            for (int r = 0; r < reff; ++r)
+                tab[(long long)r * stride + g] = Tr<T>::apply(__ldg(R.gen + (long long)r * T_tot + g), R.transform);
+            continue;
+        }
         const int I = level_of(R, g);
         const int q = R.m - I;                              // 2^q rows per column at this level
         const long long idx = g - R.lev_tab[I];
@@ -67,8 +72,13 @@ __global__ void k_points_full(DevRule R, uint32_t* __restrict__ out, int shift_i
          e += (long long)gridDim.x * blockDim.x) {
         const long long k = e / R.s;
         const int j = (int)(e - k * R.s);
-        const int q = R.m - level_of_col(R, j);
+        const int I = level_of_col(R, j);
+        const int q = R.m - I;
         const uint32_t row = (uint32_t)(k & ((1LL << q) - 1));
+        if (R.kind == KIND_MC) {        // eq. randpts: x_{j,k} = y_{j, k mod N_j}
+            out[e] = R.gen[(long long)shift_idx * R.T_tot + R.lev_tab[I] + ((long long)(j - R.lev_col0[I]) << q) + row];
+            continue;
+        }
         uint32_t x = unshifted_x32(R, j, row, q);
         if (R.shift) x = apply_shift(R.kind, x, R.shift[(size_t)shift_idx * R.s + j]);
         out[e] = x;
@@ -86,6 +96,10 @@ cudaError_t launch_points_full(const DevRule& R, uint32_t* out, int shift_idx, c
 __global__ void k_points_distinct(DevRule R, uint32_t* __restrict__ out, long long T_tot, int shift_idx) {
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < T_tot;
          g += (long long)gridDim.x * blockDim.x) {
+        if (R.kind == KIND_MC) {        // the samples already are one period of every column
+            out[g] = R.gen[(long long)shift_idx * T_tot + g];
+            continue;
+        }
         const int I = level_of(R, g);
         const int q = R.m - I;
         const long long idx = g - R.lev_tab[I];

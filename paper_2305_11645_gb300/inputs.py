@@ -45,7 +45,7 @@ SEED_ROOT = 230511645
 # purpose identifiers of the seed sequence
 P_Z, P_C, P_A, P_SHIFT, P_FD, P_MISC = 0, 1, 2, 3, 4, 5
 
-LATTICE, DIGITAL_NET = 0, 1
+LATTICE, DIGITAL_NET, REDUCED_MC = 0, 1, 2
 T_IDENTITY, T_CENTER, T_INV_NORMAL, T_TENT = 0, 1, 2, 3
 
 F_NONE, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP = range(7)
@@ -61,13 +61,15 @@ def rng(config_id: int, purpose: int, extra: int = 0) -> np.random.Generator:
 @dataclasses.dataclass
 class Problem:
     """One reduced-QMC instance: the rule (points), the matrix A and the integrand."""
-    kind: int                 # LATTICE or DIGITAL_NET
+    kind: int                 # LATTICE, DIGITAL_NET or REDUCED_MC
     m: int                    # N = 2^m points
     w: np.ndarray             # uint32[s], nondecreasing reduction indices
     A: np.ndarray             # s x tau, float64 or float32
     z: Optional[np.ndarray] = None      # uint32[s], lattice generating vector (reduced z_j)
     C: Optional[np.ndarray] = None      # uint32[s, m], net column masks (column q, bit m-1-p = row p)
     shifts: Optional[np.ndarray] = None  # uint32[R, s], 32-bit shifts (add mod 2^32 / XOR)
+    y: Optional[np.ndarray] = None       # uint32[R, T], reduced MC samples per replica (X32 words; column j's
+                                         # N_j = 2^(m-min(w_j,m)) samples, columns in order, T = sum_j N_j)
     transform: int = T_IDENTITY
     f_kind: int = F_NONE
     f_params: tuple = (0.0, 0.0, 0.0, 0.0)
@@ -88,6 +90,8 @@ class Problem:
 
     @property
     def R(self) -> int:
+        if self.kind == REDUCED_MC:
+            return int(self.y.shape[0])          # independent replicas
         return 0 if self.shifts is None else int(self.shifts.shape[0])
 
     @property
@@ -142,6 +146,17 @@ def random_shifts(g: np.random.Generator, R: int, s: int, force_odd: bool = Fals
     if force_odd:
         D |= np.uint32(1)
     return D
+
+
+def mc_samples(g: np.random.Generator, m: int, w: np.ndarray, R: int, force_odd: bool = False) -> np.ndarray:
+    """Reduced MC draws (Sec. 5): per replica, N_j = 2^(m-min(w_j,m)) i.i.d. uniform 32-bit words for
+    every column j, columns in order.  Odd words (force_odd) keep x = X32 2^-32 away from 0 for the
+    inverse-normal transform."""
+    T = sum(1 << (m - min(int(wj), m)) for wj in w)
+    y = g.integers(0, 1 << 32, size=(max(R, 1), T), dtype=np.uint64).astype(np.uint32)
+    if force_odd:
+        y |= np.uint32(1)
+    return y
 
 
 def log2_weights(s: int, cap: int) -> np.ndarray:
@@ -240,6 +255,9 @@ def random_problem(seed: int, kind: int = LATTICE, m: Optional[int] = None, s: O
     if a_scale is None:
         a_scale = 1.0 / math.sqrt(max(s, 1))
     A = (g.standard_normal((s, tau)) * a_scale).astype(dtype)
+    if kind == REDUCED_MC:
+        return Problem(REDUCED_MC, m, w, A, y=mc_samples(g, m, w, R, force_odd=(transform == T_INV_NORMAL)),
+                       transform=transform, f_kind=f_kind, f_params=tuple(f_params), name=f"rand{seed}")
     shifts = random_shifts(g, R, s, force_odd=(transform == T_INV_NORMAL)) if R > 0 else None
     if kind == LATTICE:
         return Problem(LATTICE, m, w, A, z=odd_z(g, m, w), shifts=shifts, transform=transform,

@@ -165,3 +165,41 @@ def test_too_small_workspace_rejected_before_any_cuda_call(lib):
                                     ctypes.byref(ctypes.c_uint32(p.tau)), 1, ctypes.byref(f.struct()), L.QMC_FP64,
                                     fake, ctypes.byref(fake), 7, fake, 1 << 30, None)
     assert st == L.QMC_ERR_INVALID_ARG      # unknown flags
+
+
+def test_reduced_mc_rules(lib):
+    """Reduced MC (Sec. 5): valid rules pass; C, a shift, a missing sample array or, with the
+    inverse-normal transform, a zero sample word are rejected on the host."""
+    for seed in range(4):
+        p = I.random_problem(seed, kind=I.REDUCED_MC, transform=I.T_INV_NORMAL if seed % 2 else I.T_IDENTITY)
+        assert status(lib, Rule.from_problem(p)) == L.QMC_OK, lib.qmc_last_error()
+    p = I.random_problem(5, kind=I.REDUCED_MC, m=4, s=3, R=2)
+    r = Rule.from_problem(p)
+    st = r.struct()
+    keep = (ctypes.c_uint32 * 4)(1, 2, 3, 4)
+    st.C = ctypes.cast(keep, ctypes.POINTER(ctypes.c_uint32))
+    assert lib.qmc_validate_rule(ctypes.byref(st)) == L.QMC_ERR_INVALID_ARG
+    st = r.struct()
+    st.shift = ctypes.cast(keep, ctypes.POINTER(ctypes.c_uint32))
+    assert lib.qmc_validate_rule(ctypes.byref(st)) == L.QMC_ERR_INVALID_ARG
+    st = r.struct()
+    st.z = None
+    assert lib.qmc_validate_rule(ctypes.byref(st)) == L.QMC_ERR_INVALID_ARG
+    y = p.y.copy()
+    y[1, 5] = 0
+    r0 = Rule(I.REDUCED_MC, p.m, p.w, y=y, transform=I.T_INV_NORMAL)
+    assert status(lib, r0) == L.QMC_ERR_INVALID_ARG
+    assert "sample word" in lib.qmc_last_error().decode()
+    r0 = Rule(I.REDUCED_MC, p.m, p.w, y=y, transform=I.T_IDENTITY)      # a zero word is a valid sample
+    assert status(lib, r0) == L.QMC_OK
+
+
+def test_reduced_mc_workspace_holds_every_replica(lib):
+    """Without a device copy the samples of all replicas are uploaded into the workspace."""
+    p = I.random_problem(6, kind=I.REDUCED_MC, m=9, s=20, R=3)
+    r = Rule.from_problem(p)
+    T = sum(1 << (p.m - min(int(wj), p.m)) for wj in p.w)
+    nbytes = ctypes.c_size_t(0)
+    assert lib.qmc_workspace_size(L.QMC_OP_GEN_POINTS, ctypes.byref(r.struct()), None, 1, None, L.QMC_FP32,
+                                  ctypes.byref(nbytes)) == L.QMC_OK
+    assert nbytes.value >= 3 * T * 4

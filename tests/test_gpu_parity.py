@@ -43,6 +43,18 @@ def test_points_bit_exact(kind, seed):
         assert np.array_equal(dist, want)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_mc_points_bit_exact(seed):
+    """Reduced MC (Sec. 5): point n of column j is the sample y_{j, n mod N_j} of its replica."""
+    transform = [I.T_IDENTITY, I.T_INV_NORMAL, I.T_CENTER][seed % 3]
+    p = I.random_problem(40 + seed, kind=I.REDUCED_MC, transform=transform, R=seed % 4)
+    rule = api.Rule.from_problem(p)
+    for r in range(p.R_eff):
+        got = u32(api.gen_points(rule, "full", shift_idx=r, device=DEV))
+        assert np.array_equal(got, O.x32_points(p, r))
+        assert np.array_equal(u32(api.gen_points(rule, "distinct", shift_idx=r, device=DEV)), p.y[r])
+
+
 def test_points_worked_examples():
     with open(os.path.join(GOLD, "p3_shifts_b2_m3.json")) as fh:
         g = json.load(fh)
@@ -106,6 +118,9 @@ def shaped_problem(sh, kind, seed, transform=I.T_IDENTITY, R=2, dtype=np.float64
     w = np.asarray(sh["w"], dtype=np.uint32)
     s = len(w)
     A = (g.standard_normal((s, sh["tau"])) / np.sqrt(s)).astype(dtype)
+    if kind == I.REDUCED_MC:        # R independent replicas of the caller's samples
+        y = I.mc_samples(g, sh["m"], w, R, force_odd=transform == I.T_INV_NORMAL)
+        return I.Problem(kind, sh["m"], w, A, y=y, transform=transform, f_kind=f_kind, f_params=f_params)
     D = I.random_shifts(g, R, s, force_odd=transform == I.T_INV_NORMAL) if R else None
     if kind == I.LATTICE:
         return I.Problem(kind, sh["m"], w, A, z=I.odd_z(g, sh["m"], w), shifts=D, transform=transform,
@@ -188,6 +203,39 @@ def test_integrate_and_backward(fk, shape, dtype):
     api.integrate(rule, A, f, ws=ws)
     G2 = api.integrate_backward(rule, A, f, up, ws=ws, reuse_forward=True)[0].cpu().numpy()
     assert np.array_equal(G, G2)          # deterministic, and reuse gives the identical result
+
+
+@pytest.mark.parametrize("fk", range(len(FKINDS)))
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_mc_integrate_and_backward(fk, shape, dtype):
+    """Reduced MC replicas through the whole path: per-replica estimates, their mean, the rows'
+    integrand values, the product (FP64) and the gradient of the mean, against the oracle."""
+    f_kind, f_params = FKINDS[fk]
+    transform = I.T_CENTER if f_kind == I.F_PDE_INV_SQ else (I.T_INV_NORMAL if fk % 2 else I.T_IDENTITY)
+    if f_kind == I.F_CALL_MEAN_EXP:
+        f_params = (0.2, 0.9, 0, 0)
+    p = shaped_problem(SHAPES[shape], I.REDUCED_MC, 500 + 7 * fk + shape, transform=transform, R=3, dtype=dtype,
+                       f_kind=f_kind, f_params=f_params)
+    rule = api.Rule.from_problem(p)
+    A = torch.from_numpy(p.A).to(DEV)
+    f = integrand(p)
+    est, rowf = api.integrate(rule, A, f, rowf=True)
+    est = est.cpu().numpy()
+    Q, mean = O.estimate(p)
+    tol = 1e-12 if dtype == np.float64 else 2e-5
+    for r in range(p.R_eff):
+        assert rel(est[r], Q[r]) <= tol, (r, est[r], Q[r])
+        want_rows = O.integrand(p.f_kind, p.f_params, O.reduced_matmul(p, r))
+        assert norm_rel(rowf[0][r].cpu().numpy(), want_rows) <= tol
+    assert rel(est[-1], mean) <= tol
+    if dtype == np.float64 and fk == 0:
+        P = api.reduced_matmul(rule, A).cpu().numpy()
+        for r in range(p.R_eff):
+            assert norm_rel(P[r], O.reduced_matmul(p, r)) <= 1e-12
+    up = torch.tensor([0.6], dtype=torch.float64, device=DEV)
+    G = api.integrate_backward(rule, A, f, up)[0].cpu().numpy()
+    assert norm_rel(G, 0.6 * O.grad(p)) <= (1e-11 if dtype == np.float64 else 2e-5)
 
 
 def test_autograd_function_matches_oracle():

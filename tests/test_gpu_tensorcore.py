@@ -122,6 +122,38 @@ def test_integrate_and_backward(precision, fk, shape):
 
 
 @pytest.mark.parametrize("precision", ["split", "bf16"])
+@pytest.mark.parametrize("shape", [0, FOLD_SHAPE])
+def test_mc_tiers(precision, shape):
+    """Reduced MC replicas in the tensor-core tiers: the materialised product within the tier's
+    elementwise bound, the mean estimate and its gradient against the oracle."""
+    p = shaped_problem(TC_SHAPES[shape], I.REDUCED_MC, 600 + shape, transform=I.T_INV_NORMAL, R=2,
+                       dtype=np.float32, f_kind=I.F_CALL_MEAN_EXP, f_params=(0.2, 0.9, 0, 0))
+    rule = api.Rule.from_problem(p)
+    A = torch.from_numpy(p.A).to(DEV)
+    P = api.reduced_matmul(rule, A, precision=precision).cpu().numpy()
+    for r in range(p.R_eff):
+        X = O.points(p, r)
+        assert np.all(np.abs(P[r] - O.product(X, p.A)) <= product_bound(X, p.A, precision))
+    f = integrand(p)
+    est = api.integrate(rule, A, f, precision=precision).cpu().numpy()
+    Q, mean = O.estimate(p)
+    if precision == "split":
+        assert rel(est[-1], mean) <= 2e-5
+    else:       # the first-order bound of the bf16 products' error (as for the lattices and nets)
+        bounds = []
+        for r in range(p.R_eff):
+            X = O.points(p, r)
+            Y = O.product(X, p.A)
+            dY = product_bound(X, p.A, "bf16")
+            bounds.append(np.mean(np.sum(np.abs(O.integrand_grad(p.f_kind, p.f_params, Y)) * dY, axis=1)))
+            assert abs(est[r] - Q[r]) <= bounds[-1]
+        assert abs(est[-1] - mean) <= np.mean(bounds)
+    up = torch.ones(1, dtype=torch.float64, device=DEV)
+    G = api.integrate_backward(rule, A, f, up, precision=precision)[0].cpu().numpy()
+    assert norm_rel(G, O.grad(p)) <= (2e-5 if precision == "split" else 2e-2)
+
+
+@pytest.mark.parametrize("precision", ["split", "bf16"])
 def test_graph_integrator_and_autograd(precision):
     p = shaped_problem(TC_SHAPES[4], I.DIGITAL_NET, 9, transform=I.T_INV_NORMAL, R=3, dtype=np.float32,
                        f_kind=I.F_LOGSUMEXP)

@@ -327,3 +327,59 @@ def test_p7_gaussian_expectation_closed_form():
     S = p.A.T @ p.A
     exact = np.exp(0.02 * np.diag(S)).mean()
     assert abs(Q[0] - exact) < 2e-3 * exact
+
+
+# ----------------------------------------------------------------------------- O9 reduced Monte Carlo (Sec. 5)
+
+def mc_problem(m, w, A, R, seed, transform=I.T_IDENTITY, f_kind=I.F_NONE, f_params=(0, 0, 0, 0)):
+    w = np.array(w, dtype=np.uint32)
+    y = I.mc_samples(np.random.default_rng(seed), m, w, R, force_odd=transform == I.T_INV_NORMAL)
+    return I.Problem(I.REDUCED_MC, m, w, np.array(A, dtype=np.float64), y=y, transform=transform,
+                     f_kind=f_kind, f_params=f_params)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mc_mixed_radix_index_is_n_mod_Nj(seed):
+    """eq. randpts keeps the digits m_s..m_j of n's mixed-radix form, which is n mod N_j: checked
+    for every n by brute force (w_1 = 0 as in the paper, and with w_1 > 0 and w_j >= m)."""
+    g = np.random.default_rng(300 + seed)
+    m = int(g.integers(1, 11))
+    w = np.sort(g.integers(0, m + 3, size=int(g.integers(1, 12))))
+    if seed % 2 == 0:
+        w[0] = 0
+    idx = O.mc_sample_index(m, w)
+    n = np.arange(1 << m)
+    for j, wj in enumerate(w):
+        assert np.array_equal(idx[:, j], n % (1 << (m - min(int(wj), m))))
+
+
+def test_mc_one_period_is_the_given_samples():
+    """Points n < N_j of column j are the column's samples in order (the distinct layout)."""
+    m, w = 5, [0, 1, 1, 3, 5, 9]
+    p = mc_problem(m, w, np.ones((len(w), 2)), R=3, seed=7)
+    off = np.cumsum([0] + [1 << (m - min(wj, m)) for wj in w])
+    for r in range(3):
+        X = O.x32_points(p, r)
+        for j in range(len(w)):
+            Nj = off[j + 1] - off[j]
+            assert np.array_equal(X[:Nj, j], p.y[r, off[j]:off[j + 1]])
+
+
+def test_mc_linear_estimate_unbiased_with_closed_form_variance():
+    """Sec. 5: the reduced MC estimator is unbiased, and for an additive integrand its variance
+    (the theorem's sum with the cross terms zero) is sum_j c_j^2 Var(x) / N_j, c_j = tau^-1 sum_t A_jt.
+    Over 3000 replicas: the sample mean within 5 standard errors, the sample variance within 15 %
+    (5.8 standard errors).  Positive c_j make a wrong sharing of samples between columns visible."""
+    m, w = 6, [0, 1, 1, 2, 3, 4, 7]
+    A = np.linspace(0.5, 2.0, 3 * len(w)).reshape(len(w), 3)
+    R = 3000
+    p = mc_problem(m, w, A, R=R, seed=11, f_kind=I.F_LINEAR_MEAN)
+    Q, _ = O.estimate(p)
+    c = A.sum(axis=1) / A.shape[1]
+    Nj = np.array([1 << (m - min(wj, m)) for wj in w], dtype=np.float64)
+    mean_x = 0.5 - 2.0 ** -33                      # X32 uniform on {0, ..., 2^32 - 1}
+    var_x = (1.0 - 2.0 ** -64) / 12.0
+    EQ = c.sum() * mean_x
+    VQ = float((c ** 2 * var_x / Nj).sum())
+    assert abs(Q.mean() - EQ) <= 5 * math.sqrt(VQ / R)
+    assert 0.85 <= Q.var(ddof=1) / VQ <= 1.15
