@@ -51,6 +51,8 @@ typedef int qmc_status;
 #define QMC_DIGITAL_NET  1        /* reduced digital net, Sec. 4, eq. reduced_genmat_net2 */
 #define QMC_REDUCED_MC   2        /* reduced Monte Carlo, Sec. 5, eq. randpts: coordinate j of point n is
                                      the i.i.d. sample y_{j, n mod N_j}, N_j = 2^(m-min(w_j,m)) */
+#define QMC_POLY_LATTICE 3        /* reduced polynomial lattice, Sec. 1.3: x_{k,j} = nu(k(x) g_j(x) / x^m) with
+                                     g_j = x^{w_j} gt_j over F_2 (a digital net; digital shifts) */
 
 /* coordinate transforms phi_j applied to the (shifted) points, Sec. 2.3 */
 #define QMC_T_IDENTITY   0        /* x */
@@ -94,7 +96,7 @@ typedef int qmc_status;
 
 /*
  * A reduced QMC rule (the point set).
- *  kind       QMC_LATTICE, QMC_DIGITAL_NET or QMC_REDUCED_MC.
+ *  kind       QMC_LATTICE, QMC_DIGITAL_NET, QMC_REDUCED_MC or QMC_POLY_LATTICE.
  *  b          base; the GPU path supports b = 2 only (others: QMC_ERR_UNSUPPORTED).
  *  m          N = b^m points, 1 <= m <= 30.
  *  s          dimension (rows of A), 1 <= s <= 65536.
@@ -103,6 +105,10 @@ typedef int qmc_status;
  *  z          HOST uint32[s] (lattice): reduced generating vector, z_j in U_{b^(m-w_j)}, i.e. odd and
  *             < 2^(m-w_j) if w_j < m, else exactly 1 (Sec. 1.3).  The lattice's generating vector is
  *             (2^{w_1} z_1, ..., 2^{w_s} z_s).
+ *  z          HOST uint32[s] (polynomial lattice): the reduced generating polynomials gt_j, coefficient
+ *             of x^i at bit i, with gt_j(0) = 1 and deg gt_j < m - w_j (odd and < 2^(m-w_j)), or exactly 1
+ *             if w_j >= m: the analogue of z_j (then y = (k(x) gt_j(x) mod x^(m-w_j)) read with the
+ *             coefficient of x^i as the digit of 2^(i-(m-w_j))).
  *  C          HOST uint32[s*m] (net): generating matrices as column masks.  Word C[j*m + q] is column q+1
  *             of C^(j); row p (1-based, the digit of 2^-p) is bit m-p of the word (Sec. 4, eq.
  *             def:digital, digits of n least significant first).  The library zeroes the last

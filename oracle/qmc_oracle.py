@@ -30,6 +30,10 @@ reordering beyond what the definitions state:
   O7  the gradient of the shift-averaged estimate with respect to A:
       (1/(R N)) sum_r X_r^T grad f(Y_r).
   O8  central finite differences of the estimate in single entries of A.
+  O10 reduced polynomial lattice points (Sec. 1.3): x_{k,j} = nu(k(x) g_j(x) / x^m)
+      over F_2 with g_j = x^{w_j} gt_j, the product of the coefficient arrays
+      written out mod 2 and mod x^m, the coefficient of x^i the digit of 2^(i-m);
+      digital shifts as for nets.
   O9  reduced Monte Carlo points (Sec. 5, eq. randpts): with N_j = 2^(m-w_j),
       N_{s+1} = 1 and M_j = N_j / N_{j+1}, write n in the mixed radix
       n = m_s N_{s+1} + m_{s-1} N_s + ... + m_1 N_2 (0 <= m_j < M_j) and take
@@ -47,7 +51,7 @@ from typing import Iterable, Optional, Sequence
 import numpy as np
 from scipy import special as _sp
 
-LATTICE, DIGITAL_NET, REDUCED_MC = 0, 1, 2
+LATTICE, DIGITAL_NET, REDUCED_MC, POLY_LATTICE = 0, 1, 2, 3
 T_IDENTITY, T_CENTER, T_INV_NORMAL, T_TENT = 0, 1, 2, 3
 F_NONE, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP = range(7)
 
@@ -122,6 +126,32 @@ def net_x32(m: int, w, C: np.ndarray, shift: Optional[np.ndarray] = None, ks=Non
     return x32
 
 
+# ----------------------------------------------------------------------------- O10 polynomial lattices
+
+def poly_lattice_x32(m: int, w, gt, shift: Optional[np.ndarray] = None, ks=None) -> np.ndarray:
+    """b = 2 reduced polynomial lattice points as X32 = x * 2^32: k(x) has the binary digits of k as
+    coefficients, g_j(x) = x^{min(w_j,m)} gt_j(x) (gt_j's coefficient of x^i at bit i), the product
+    k(x) g_j(x) is taken mod 2 and mod x^m, and nu reads coefficient a_i as the digit of 2^(i-m)."""
+    N = 1 << m
+    ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
+    kd = digits_lsb_first(ks, m)                                  # coefficients of k(x), degree < m
+    out = np.empty((len(ks), len(w)), dtype=np.uint64)
+    for j, (wj, gj) in enumerate(zip(w, gt)):
+        wcl = min(int(wj), m)
+        g = [0] * wcl + [(int(gj) >> i) & 1 for i in range(m)]     # coefficients of x^w gt(x)
+        c = np.zeros((len(ks), m), dtype=np.int64)
+        for i in range(m):                                        # c_i = sum_{l <= i} k_l g_{i-l} mod 2
+            for l in range(i + 1):
+                if g[i - l]:
+                    c[:, i] ^= kd[:, l]
+        y_int = (c.astype(np.uint64) * (np.uint64(1) << np.arange(m, dtype=np.uint64))[None, :]).sum(axis=1)
+        out[:, j] = y_int << np.uint64(32 - m)                    # nu: y 2^m = sum_i a_i 2^i
+    x32 = out.astype(np.uint32)
+    if shift is not None:
+        x32 = x32 ^ np.asarray(shift, dtype=np.uint32)[None, :]
+    return x32
+
+
 # ----------------------------------------------------------------------------- O9 reduced Monte Carlo
 
 def mc_sample_index(m: int, w, ks=None) -> np.ndarray:
@@ -158,6 +188,8 @@ def x32_points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
     if problem.kind == REDUCED_MC:
         return mc_x32(problem.m, problem.w, problem.y[shift_idx], ks)
     shift = None if problem.shifts is None else problem.shifts[shift_idx]
+    if problem.kind == POLY_LATTICE:
+        return poly_lattice_x32(problem.m, problem.w, problem.z, shift, ks)
     if problem.kind == LATTICE:
         return lattice_x32(problem.m, problem.w, problem.z, shift, ks)
     return net_x32(problem.m, problem.w, problem.C, shift, ks)

@@ -19,7 +19,8 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from .inputs import (DIGITAL_NET, LATTICE, REDUCED_MC, T_CENTER, T_IDENTITY, T_INV_NORMAL, T_TENT,  # noqa: F401
+from .inputs import (DIGITAL_NET, LATTICE, POLY_LATTICE, REDUCED_MC, T_CENTER, T_IDENTITY, T_INV_NORMAL,  # noqa: F401
+                     T_TENT,
                      F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_LINEAR_MEAN, F_LOGSUMEXP, F_MEAN_COS, F_NONE,
                      F_PDE_INV_SQ)
 
@@ -41,8 +42,9 @@ def _u32(a) -> Optional[np.ndarray]:
 
 
 class Rule:
-    """A reduced QMC rule: lattice (z) or periodic reduced digital net (C) with optional shifts, or
-    reduced Monte Carlo (y: the replicas' samples, uint32 [R, sum_j N_j] in the distinct layout)."""
+    """A reduced QMC rule: lattice (z), polynomial lattice (z: the reduced generating polynomials) or
+    periodic reduced digital net (C) with optional shifts, or reduced Monte Carlo (y: the replicas'
+    samples, uint32 [R, sum_j N_j] in the distinct layout)."""
 
     def __init__(self, kind: int, m: int, w, z=None, C=None, shifts=None, transform: int = T_IDENTITY, b: int = 2,
                  y=None):
@@ -78,8 +80,8 @@ class Rule:
     def _device_arrays(self, device: torch.device):
         key = str(device)
         if key not in self._dev:
-            gen = {LATTICE: self.z, DIGITAL_NET: self.C, REDUCED_MC: None if self.y is None else self.y.reshape(-1)}[
-                self.kind]
+            gen = {LATTICE: self.z, POLY_LATTICE: self.z, DIGITAL_NET: self.C,
+                   REDUCED_MC: None if self.y is None else self.y.reshape(-1)}[self.kind]
             d_gen = None if gen is None else torch.from_numpy(gen.view(np.int32).copy()).to(device)
             d_shift = None if self.shifts is None else torch.from_numpy(
                 self.shifts.reshape(-1).view(np.int32).copy()).to(device)

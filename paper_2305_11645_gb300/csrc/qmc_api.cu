@@ -117,8 +117,10 @@ int gf2_rank(std::vector<uint32_t> v) {
 
 qmc_status validate(const qmc_rule* r) {
     if (!r) return fail(QMC_ERR_INVALID_ARG, "rule is NULL");
-    if (r->kind != QMC_LATTICE && r->kind != QMC_DIGITAL_NET && r->kind != QMC_REDUCED_MC)
-        return fail(QMC_ERR_INVALID_ARG, "kind %d is not QMC_LATTICE, QMC_DIGITAL_NET or QMC_REDUCED_MC", r->kind);
+    if (r->kind != QMC_LATTICE && r->kind != QMC_DIGITAL_NET && r->kind != QMC_REDUCED_MC &&
+        r->kind != QMC_POLY_LATTICE)
+        return fail(QMC_ERR_INVALID_ARG, "kind %d is not QMC_LATTICE, QMC_DIGITAL_NET, QMC_REDUCED_MC or "
+                    "QMC_POLY_LATTICE", r->kind);
     if (r->b < 2) return fail(QMC_ERR_INVALID_ARG, "base b=%u must be a prime >= 2", r->b);
     if (r->b != 2) return fail(QMC_ERR_UNSUPPORTED, "base b=%u: only b=2 is built", r->b);
     if (r->m < 1) return fail(QMC_ERR_INVALID_ARG, "m=%u: N = b^m needs m >= 1", r->m);
@@ -152,8 +154,10 @@ qmc_status validate(const qmc_rule* r) {
     if (r->R > 0 && !r->shift) return fail(QMC_ERR_INVALID_ARG, "R=%u but shift is NULL", r->R);
     if (r->transform == QMC_T_INV_NORMAL && r->R == 0)
         return fail(QMC_ERR_INVALID_ARG, "the inverse-normal transform needs a random shift (x=0 maps to -inf)");
-    if (r->kind == QMC_LATTICE) {
-        if (!r->z) return fail(QMC_ERR_INVALID_ARG, "lattice rule needs z");
+    if (r->kind == QMC_LATTICE || r->kind == QMC_POLY_LATTICE) {
+        // z_j in U_{2^q}; for polynomials: gt_j(0) = 1 and deg gt_j < q (gcd(gt_j, x^q) = 1)
+        const char* what = r->kind == QMC_LATTICE ? "lattice rule needs z" : "polynomial lattice rule needs z";
+        if (!r->z) return fail(QMC_ERR_INVALID_ARG, "%s", what);
         for (uint32_t j = 0; j < r->s; ++j) {
             const uint32_t q = m - std::min(r->w[j], m);
             const uint32_t z = r->z[j];

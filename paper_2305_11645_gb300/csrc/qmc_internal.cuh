@@ -12,7 +12,7 @@ constexpr int kMaxLevels = 32;     // levels I = 0..m (level m holds the constan
 constexpr int kMaxChain = 48;      // coarse entries (levels, cut into column ranges); Chain stays ~4 KB
 
 // Kinds, transforms and integrands mirror include/qmc.h.
-enum { KIND_LATTICE = 0, KIND_NET = 1, KIND_MC = 2 };
+enum { KIND_LATTICE = 0, KIND_NET = 1, KIND_MC = 2, KIND_POLY = 3 };
 enum { T_IDENTITY = 0, T_CENTER = 1, T_INV_NORMAL = 2, T_TENT = 3 };
 enum { F_NONE = 0, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP };
 enum { SHAPE_S0 = 0, SHAPE_S1 = 1, SHAPE_S4 = 4 };
@@ -49,6 +49,19 @@ __device__ __forceinline__ uint32_t unshifted_x32(const DevRule& R, int j, uint3
         const uint32_t u = (row * R.gen[j]) & mask;     // mod 2^q needs only the low 32 bits
         return (q >= 32) ? u : (u << (32 - q));
     }
+    if (R.kind == KIND_POLY) {
+        // k(x) x^w gt(x) mod x^m over F_2: the coefficients of x^w .. x^(m-1) are those of
+        // k(x) gt(x) mod x^q, q = m - w, and the coefficient of x^(w+i) is the digit of 2^(i-q)
+        // (nu of Sec. 1.3).  So u = (row carry-less-times gt) mod 2^q, x = u 2^-q.
+        if (q == 0) return 0u;
+        const uint32_t g = R.gen[j];
+        uint32_t u = 0;
+        for (int b = 0; b < q; ++b)
+            if ((row >> b) & 1u) u ^= g << b;
+        const uint32_t mask = (q >= 32) ? 0xFFFFFFFFu : ((1u << q) - 1u);
+        u &= mask;
+        return (q >= 32) ? u : (u << (32 - q));
+    }
     const uint32_t* Cj = R.gen + (size_t)j * (size_t)R.m;
     uint32_t y = 0;
     for (int b = 0; b < q; ++b)
@@ -59,7 +72,8 @@ __device__ __forceinline__ uint32_t unshifted_x32(const DevRule& R, int j, uint3
 }
 
 __device__ __forceinline__ uint32_t apply_shift(int kind, uint32_t x, uint32_t d) {
-    return kind == KIND_LATTICE ? (x + d) : (x ^ d);   // {x + Delta} mod 1, or the digital shift
+    return kind == KIND_LATTICE ? (x + d) : (x ^ d);   // {x + Delta} mod 1, or the digital shift (nets,
+                                                        // polynomial lattices)
 }
 
 // ---------------------------------------------------------------------------------------------

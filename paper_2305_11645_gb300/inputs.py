@@ -45,7 +45,7 @@ SEED_ROOT = 230511645
 # purpose identifiers of the seed sequence
 P_Z, P_C, P_A, P_SHIFT, P_FD, P_MISC = 0, 1, 2, 3, 4, 5
 
-LATTICE, DIGITAL_NET, REDUCED_MC = 0, 1, 2
+LATTICE, DIGITAL_NET, REDUCED_MC, POLY_LATTICE = 0, 1, 2, 3
 T_IDENTITY, T_CENTER, T_INV_NORMAL, T_TENT = 0, 1, 2, 3
 
 F_NONE, F_LINEAR_MEAN, F_MEAN_COS, F_CALL_MEAN_EXP, F_GAUSS_NORM2, F_PDE_INV_SQ, F_LOGSUMEXP = range(7)
@@ -61,11 +61,12 @@ def rng(config_id: int, purpose: int, extra: int = 0) -> np.random.Generator:
 @dataclasses.dataclass
 class Problem:
     """One reduced-QMC instance: the rule (points), the matrix A and the integrand."""
-    kind: int                 # LATTICE, DIGITAL_NET or REDUCED_MC
+    kind: int                 # LATTICE, DIGITAL_NET, REDUCED_MC or POLY_LATTICE
     m: int                    # N = 2^m points
     w: np.ndarray             # uint32[s], nondecreasing reduction indices
     A: np.ndarray             # s x tau, float64 or float32
-    z: Optional[np.ndarray] = None      # uint32[s], lattice generating vector (reduced z_j)
+    z: Optional[np.ndarray] = None      # uint32[s], lattice generating vector (reduced z_j), or the reduced
+                                        # generating polynomials gt_j (coefficient of x^i at bit i)
     C: Optional[np.ndarray] = None      # uint32[s, m], net column masks (column q, bit m-1-p = row p)
     shifts: Optional[np.ndarray] = None  # uint32[R, s], 32-bit shifts (add mod 2^32 / XOR)
     y: Optional[np.ndarray] = None       # uint32[R, T], reduced MC samples per replica (X32 words; column j's
@@ -259,8 +260,8 @@ def random_problem(seed: int, kind: int = LATTICE, m: Optional[int] = None, s: O
         return Problem(REDUCED_MC, m, w, A, y=mc_samples(g, m, w, R, force_odd=(transform == T_INV_NORMAL)),
                        transform=transform, f_kind=f_kind, f_params=tuple(f_params), name=f"rand{seed}")
     shifts = random_shifts(g, R, s, force_odd=(transform == T_INV_NORMAL)) if R > 0 else None
-    if kind == LATTICE:
-        return Problem(LATTICE, m, w, A, z=odd_z(g, m, w), shifts=shifts, transform=transform,
+    if kind in (LATTICE, POLY_LATTICE):     # odd z_j < 2^(m-w_j): also gt_j(0) = 1, deg gt_j < m - w_j
+        return Problem(kind, m, w, A, z=odd_z(g, m, w), shifts=shifts, transform=transform,
                        f_kind=f_kind, f_params=tuple(f_params), name=f"rand{seed}")
     return Problem(DIGITAL_NET, m, w, A, C=periodic_net_masks(g, m, w), shifts=shifts, transform=transform,
                    f_kind=f_kind, f_params=tuple(f_params), name=f"rand{seed}")

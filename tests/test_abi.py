@@ -203,3 +203,14 @@ def test_reduced_mc_workspace_holds_every_replica(lib):
     assert lib.qmc_workspace_size(L.QMC_OP_GEN_POINTS, ctypes.byref(r.struct()), None, 1, None, L.QMC_FP32,
                                   ctypes.byref(nbytes)) == L.QMC_OK
     assert nbytes.value >= 3 * T * 4
+
+
+def test_poly_lattice_rules(lib):
+    """Reduced polynomial lattices: gt_j(0) = 1 and deg gt_j < m - w_j (as z_j for lattices)."""
+    for seed in range(4):
+        p = I.random_problem(seed, kind=I.POLY_LATTICE)
+        assert status(lib, Rule.from_problem(p)) == L.QMC_OK, lib.qmc_last_error()
+    assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 1], z=[0b1010, 1])) == L.QMC_ERR_INVALID_ARG   # gt(0) = 0
+    assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 1], z=[0b10011, 1])) == L.QMC_ERR_INVALID_ARG  # degree 4
+    assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 9], z=[0b1011, 3])) == L.QMC_ERR_INVALID_ARG   # w >= m: 1
+    assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 9], z=[0b1011, 1])) == L.QMC_OK

@@ -44,6 +44,21 @@ def test_points_bit_exact(kind, seed):
 
 
 @pytest.mark.parametrize("seed", range(6))
+def test_poly_lattice_points_bit_exact(seed):
+    """Reduced polynomial lattices (carry-less products on the GPU) against the oracle's polynomial
+    arithmetic, every shift and both layouts."""
+    transform = [I.T_IDENTITY, I.T_INV_NORMAL, I.T_CENTER][seed % 3]
+    p = I.random_problem(60 + seed, kind=I.POLY_LATTICE, transform=transform,
+                         R=max(1, seed % 4) if transform == I.T_INV_NORMAL else seed % 4)
+    rule = api.Rule.from_problem(p)
+    for r in range(p.R_eff):
+        X = O.x32_points(p, r)
+        assert np.array_equal(u32(api.gen_points(rule, "full", shift_idx=r, device=DEV)), X)
+        dist = u32(api.gen_points(rule, "distinct", shift_idx=r, device=DEV))
+        assert np.array_equal(dist, np.concatenate([X[: 2 ** (p.m - min(int(w), p.m)), j] for j, w in enumerate(p.w)]))
+
+
+@pytest.mark.parametrize("seed", range(6))
 def test_mc_points_bit_exact(seed):
     """Reduced MC (Sec. 5): point n of column j is the sample y_{j, n mod N_j} of its replica."""
     transform = [I.T_IDENTITY, I.T_INV_NORMAL, I.T_CENTER][seed % 3]
@@ -122,7 +137,7 @@ def shaped_problem(sh, kind, seed, transform=I.T_IDENTITY, R=2, dtype=np.float64
         y = I.mc_samples(g, sh["m"], w, R, force_odd=transform == I.T_INV_NORMAL)
         return I.Problem(kind, sh["m"], w, A, y=y, transform=transform, f_kind=f_kind, f_params=f_params)
     D = I.random_shifts(g, R, s, force_odd=transform == I.T_INV_NORMAL) if R else None
-    if kind == I.LATTICE:
+    if kind in (I.LATTICE, I.POLY_LATTICE):
         return I.Problem(kind, sh["m"], w, A, z=I.odd_z(g, sh["m"], w), shifts=D, transform=transform,
                          f_kind=f_kind, f_params=f_params)
     return I.Problem(kind, sh["m"], w, A, C=I.periodic_net_masks(g, sh["m"], w), shifts=D, transform=transform,
@@ -236,6 +251,29 @@ def test_mc_integrate_and_backward(fk, shape, dtype):
     up = torch.tensor([0.6], dtype=torch.float64, device=DEV)
     G = api.integrate_backward(rule, A, f, up)[0].cpu().numpy()
     assert norm_rel(G, 0.6 * O.grad(p)) <= (1e-11 if dtype == np.float64 else 2e-5)
+
+
+@pytest.mark.parametrize("fk", [0, 2, 5])
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_poly_lattice_integrate_and_backward(fk, shape, dtype):
+    """Reduced polynomial lattices with digital shifts through the estimate and the adjoint."""
+    f_kind, f_params = FKINDS[fk]
+    if f_kind == I.F_CALL_MEAN_EXP:
+        f_params = (0.2, 0.9, 0, 0)
+    p = shaped_problem(SHAPES[shape], I.POLY_LATTICE, 700 + 7 * fk + shape, transform=I.T_INV_NORMAL, R=2,
+                       dtype=dtype, f_kind=f_kind, f_params=f_params)
+    rule = api.Rule.from_problem(p)
+    A = torch.from_numpy(p.A).to(DEV)
+    f = integrand(p)
+    est = api.integrate(rule, A, f).cpu().numpy()
+    Q, mean = O.estimate(p)
+    tol = 1e-12 if dtype == np.float64 else 2e-5
+    for r in range(p.R_eff):
+        assert rel(est[r], Q[r]) <= tol, (r, est[r], Q[r])
+    assert rel(est[-1], mean) <= tol
+    G = api.integrate_backward(rule, A, f, torch.ones(1, dtype=torch.float64, device=DEV))[0].cpu().numpy()
+    assert norm_rel(G, O.grad(p)) <= (1e-11 if dtype == np.float64 else 2e-5)
 
 
 def test_autograd_function_matches_oracle():

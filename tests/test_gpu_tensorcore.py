@@ -123,10 +123,12 @@ def test_integrate_and_backward(precision, fk, shape):
 
 @pytest.mark.parametrize("precision", ["split", "bf16"])
 @pytest.mark.parametrize("shape", [0, FOLD_SHAPE])
-def test_mc_tiers(precision, shape):
-    """Reduced MC replicas in the tensor-core tiers: the materialised product within the tier's
-    elementwise bound, the mean estimate and its gradient against the oracle."""
-    p = shaped_problem(TC_SHAPES[shape], I.REDUCED_MC, 600 + shape, transform=I.T_INV_NORMAL, R=2,
+@pytest.mark.parametrize("kind", [I.REDUCED_MC, I.POLY_LATTICE])
+def test_mc_and_poly_lattice_tiers(precision, shape, kind):
+    """Reduced MC replicas and shifted polynomial lattices in the tensor-core tiers: the
+    materialised product within the tier's elementwise bound, the mean estimate and its gradient
+    against the oracle."""
+    p = shaped_problem(TC_SHAPES[shape], kind, 600 + shape, transform=I.T_INV_NORMAL, R=2,
                        dtype=np.float32, f_kind=I.F_CALL_MEAN_EXP, f_params=(0.2, 0.9, 0, 0))
     rule = api.Rule.from_problem(p)
     A = torch.from_numpy(p.A).to(DEV)

@@ -383,3 +383,64 @@ def test_mc_linear_estimate_unbiased_with_closed_form_variance():
     VQ = float((c ** 2 * var_x / Nj).sum())
     assert abs(Q.mean() - EQ) <= 5 * math.sqrt(VQ / R)
     assert 0.85 <= Q.var(ddof=1) / VQ <= 1.15
+
+
+# ----------------------------------------------------------------------------- O10 polynomial lattices (Sec. 1.3)
+
+def test_poly_lattice_worked_example():
+    """b=2, m=3, w=(0,1,2), gt=(1+x, 1, 1), worked by hand from the definition.  Column 1:
+    k(x)(1+x) mod x^3 has coefficients (k0, k0+k1, k1+k2), read as k0/8 + (k0+k1)/4 + (k1+k2)/2.
+    Column 2: k(x) x mod x^3 = k0 x + k1 x^2, i.e. k0/4 + k1/2.  Column 3: k(x) x^2 mod x^3 = k0 x^2."""
+    X = O.poly_lattice_x32(3, [0, 1, 2], [0b11, 1, 1]).astype(np.float64) / 2.0 ** 32
+    want = np.array([[0, 0, 0], [3, 2, 4], [6, 4, 0], [5, 6, 4], [4, 0, 0], [7, 2, 4], [2, 4, 0], [1, 6, 4]]) / 8.0
+    assert np.array_equal(X, want)
+
+
+def hankel_masks(m, wj, gt):
+    """Generating matrix of x -> nu(k(x) g(x)/x^m) as a digital net: digit p (1-based, of 2^-p) is the
+    coefficient of x^(m-p) of k(x) g(x), i.e. C[p][q] = g_(m-p-(q-1)) for digit q-1 of k.  Returned
+    as column masks (word q-1 holds row p at bit m-p)."""
+    wcl = min(wj, m)
+    g = [0] * wcl + [(gt >> i) & 1 for i in range(m)] + [0] * m
+    masks = []
+    for q in range(1, m + 1):
+        word = 0
+        for p in range(1, m + 1):
+            r = m - p - (q - 1)
+            if r >= 0 and g[r]:
+                word |= 1 << (m - p)
+        masks.append(word)
+    return masks
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_poly_lattice_is_a_digital_net(seed):
+    """A polynomial lattice point set is the digital net of its (Hankel) generating matrices: the
+    polynomial-product oracle (O10) and the matrix-vector oracle (O2, pinned by P2) agree, shifts
+    included.  The reduced g_j = x^w gt_j also makes the rows beyond m-w_j zero, as eq.
+    reduced_genmat_net2 does for nets."""
+    g = np.random.default_rng(900 + seed)
+    m = int(g.integers(1, 11))
+    w = np.sort(g.integers(0, m + 2, size=int(g.integers(1, 9)))).astype(np.uint32)
+    gt = I.odd_z(g, m, w)
+    D = I.random_shifts(g, 1, len(w))[0]
+    C = np.array([hankel_masks(m, int(wj), int(t)) for wj, t in zip(w, gt)], dtype=np.uint32)
+    assert np.array_equal(O.poly_lattice_x32(m, w, gt), O.net_x32(m, w, C))
+    assert np.array_equal(O.poly_lattice_x32(m, w, gt, D), O.net_x32(m, w, C, D))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_poly_lattice_periodic_permutation(seed):
+    """With gt_j(0) = 1, column j depends only on k mod 2^(m-w_j) and one period is a permutation
+    of the grid {0, ..., 2^(m-w_j) - 1} / 2^(m-w_j) (brute force)."""
+    g = np.random.default_rng(950 + seed)
+    m = int(g.integers(2, 11))
+    w = np.sort(g.integers(0, m + 1, size=6)).astype(np.uint32)
+    X = O.poly_lattice_x32(m, w, I.odd_z(g, m, w)).astype(np.uint64)
+    k = np.arange(1 << m)
+    for j, wj in enumerate(w):
+        q = m - min(int(wj), m)
+        per = X[:, j][k % (1 << q)]
+        assert np.array_equal(X[:, j], per)
+        grid = np.sort(X[: 1 << q, j] >> np.uint64(32 - q)) if q else X[:1, j]
+        assert np.array_equal(grid, np.arange(1 << q, dtype=np.uint64)) if q else grid[0] == 0
