@@ -162,9 +162,18 @@ qmc_status qmc_validate_rule(const qmc_rule* rule);
  * qmc_device_status: synchronises the current device and reads its sticky device error word.
  *  Returns QMC_ERR_TIMEOUT if a tensor-core kernel (QMC_SPLIT / QMC_BF16) gave up a bounded
  *  wait on its MMA completion since the word was last cleared (its outputs were then written
- *  as NaN), QMC_OK otherwise.  clear != 0 resets the word.  Not callable during stream capture.
+ *  as NaN), or qmc_selftest_wait_timeout ran, QMC_OK otherwise.  clear != 0 resets the word.
+ *  Not callable during stream capture.
  */
 qmc_status qmc_device_status(int clear);
+
+/*
+ * qmc_selftest_wait_timeout: exercises the failure path of the bounded device-side waits without a
+ *  fault.  Enqueues one CTA whose single thread polls, at most `polls` times (1 <= polls <= 2^20),
+ *  an mbarrier that nothing arrives at, then sets bit 31 of the sticky error word and returns; a
+ *  following qmc_device_status reports QMC_ERR_TIMEOUT, and the context stays usable.
+ */
+qmc_status qmc_selftest_wait_timeout(uint32_t polls, void* stream);
 
 /*
  * qmc_workspace_size: bytes of device workspace `op` needs for these arguments (written to *bytes).

@@ -748,7 +748,16 @@ qmc_status qmc_device_status(int clear) {
     unsigned int word = 0;
     QMC_CUDA(cudaDeviceSynchronize());
     QMC_CUDA(tc_error_word(&word, clear != 0));
-    if (word) return fail(QMC_ERR_TIMEOUT, "a tensor-core kernel's bounded wait ran out (error word 0x%x)", word);
+    if (word)
+        return fail(QMC_ERR_TIMEOUT, "a bounded device-side wait ran out (error word 0x%x: bit 0 a tensor-core "
+                    "kernel, bit 31 the self-test)", word);
+    return QMC_OK;
+}
+
+qmc_status qmc_selftest_wait_timeout(uint32_t polls, void* stream) {
+    if (polls < 1 || polls > (1u << 20)) return fail(QMC_ERR_INVALID_ARG, "polls=%u outside [1, 2^20]", polls);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    QMC_LAUNCH(st, "k_selftest_wait", launch_selftest_wait(polls, st));
     return QMC_OK;
 }
 

@@ -303,6 +303,8 @@ cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const 
                                   const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
                                   float* part, int reff, int ntiles, int pieces, cudaStream_t st);
 cudaError_t tc_error_word(unsigned int* value, bool clear);
+// one CTA whose bounded wait on an mbarrier that nothing completes runs out after `polls` polls
+cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t st);
 // the S4 fine band in FP32 on the CUDA cores: forward CTAs of fine_s4_fwd_roots() roots (grid:
 // root blocks x column groups of a.cr <= 512 columns x shifts), adjoint CTAs of fine_s4_bwd_cols()
 // columns (grid: root groups of a.roots_per_cta roots, a multiple of fine_s4_bwd_batch() x

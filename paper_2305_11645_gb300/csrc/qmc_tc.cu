@@ -529,6 +529,25 @@ cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const 
     return cudaGetLastError();
 }
 
+// Self-test of the bounded waits: one thread polls, at most `polls` times, an mbarrier that nothing
+// arrives at, then raises bit 31 of the error word as a tensor-core kernel whose wait ran out raises
+// bit 0.  The kernel returns either way; the host reads the word through qmc_device_status.
+__global__ void k_selftest_wait(uint32_t polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    const uint32_t a = tc::smem_u32(&bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(a) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bool done = false;
+    for (uint32_t it = 0; it < polls && !done; ++it) done = tc::mbar_try(a, 0);
+    if (!done) atomicOr(&g_tc_error, 0x80000000u);
+}
+
+cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t st) {
+    k_selftest_wait<<<1, 32, 0, st>>>(polls);
+    return cudaGetLastError();
+}
+
 cudaError_t tc_error_word(unsigned int* value, bool clear) {
     cudaError_t e = cudaMemcpyFromSymbol(value, g_tc_error, sizeof(unsigned int));
     if (e != cudaSuccess || !clear) return e;

@@ -166,6 +166,16 @@ __device__ __forceinline__ void issue_kstep(uint32_t tmem, uint64_t adesc, uint6
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
+// one poll of phase `parity` of an mbarrier (true once that phase has completed)
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    return done != 0;
+}
+
 __device__ __forceinline__ unsigned char* align_1k(unsigned char* p) {
     return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
 }

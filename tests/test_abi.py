@@ -214,3 +214,9 @@ def test_poly_lattice_rules(lib):
     assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 1], z=[0b10011, 1])) == L.QMC_ERR_INVALID_ARG  # degree 4
     assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 9], z=[0b1011, 3])) == L.QMC_ERR_INVALID_ARG   # w >= m: 1
     assert status(lib, Rule(I.POLY_LATTICE, 4, [0, 9], z=[0b1011, 1])) == L.QMC_OK
+
+
+def test_selftest_wait_arguments_checked_on_the_host(lib):
+    """The wait self-test's poll count is checked before anything is enqueued."""
+    assert lib.qmc_selftest_wait_timeout(0, None) == L.QMC_ERR_INVALID_ARG
+    assert lib.qmc_selftest_wait_timeout((1 << 20) + 1, None) == L.QMC_ERR_INVALID_ARG
