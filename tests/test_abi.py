@@ -220,3 +220,29 @@ def test_selftest_wait_arguments_checked_on_the_host(lib):
     """The wait self-test's poll count is checked before anything is enqueued."""
     assert lib.qmc_selftest_wait_timeout(0, None) == L.QMC_ERR_INVALID_ARG
     assert lib.qmc_selftest_wait_timeout((1 << 20) + 1, None) == L.QMC_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_planner_never_fails_uncleanly(lib, seed):
+    """The host planner (workspace query: validation, block schedule, grids, workspace layout) on
+    random rules of every kind, operation and tier: a status and a size, no abort, and a workspace
+    that at least holds the point table of every shift."""
+    g = np.random.default_rng(4000 + seed)
+    kind = [I.LATTICE, I.DIGITAL_NET, I.REDUCED_MC, I.POLY_LATTICE][seed % 4]
+    m = int(g.integers(1, 21))
+    s = int(g.integers(1, 300))
+    p = I.random_problem(seed, kind=kind, m=m, s=s, tau=int(g.integers(1, 600)), R=int(g.integers(0, 4)))
+    r = Rule.from_problem(p)
+    f = Integrand([I.F_LINEAR_MEAN, I.F_MEAN_COS, I.F_CALL_MEAN_EXP, I.F_GAUSS_NORM2, I.F_PDE_INV_SQ,
+                   I.F_LOGSUMEXP][seed % 6], (0.2, 0.9, 0, 0))
+    T = sum(1 << (m - min(int(wj), m)) for wj in p.w)
+    for op in (L.QMC_OP_GEN_POINTS, L.QMC_OP_REDUCED_MATMUL, L.QMC_OP_INTEGRATE, L.QMC_OP_INTEGRATE_BWD):
+        for prec in (L.QMC_FP64, L.QMC_FP32, L.QMC_SPLIT, L.QMC_BF16):
+            nbytes = ctypes.c_size_t(0)
+            st = lib.qmc_workspace_size(op, ctypes.byref(r.struct()), ctypes.byref(ctypes.c_uint32(p.tau)), 1,
+                                        ctypes.byref(f.struct()) if op >= L.QMC_OP_INTEGRATE else None, prec,
+                                        ctypes.byref(nbytes))
+            assert st == L.QMC_OK, (op, prec, lib.qmc_last_error())
+            if op != L.QMC_OP_GEN_POINTS:
+                elt = 8 if prec == L.QMC_FP64 else 4
+                assert nbytes.value >= elt * T * p.R_eff
