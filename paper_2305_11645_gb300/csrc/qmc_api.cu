@@ -99,18 +99,22 @@ struct TraceScope {
         QMC_CUDA(call);                   \
     } while (0)
 
-// GF(2) rank of q vectors of q bits
-int gf2_rank(std::vector<uint32_t> v) {
+// GF(2) rank of n vectors of at most 32 bits: each vector is reduced against an XOR basis indexed
+// by leading bit and joins it if something is left (no allocation: the check runs on every call)
+int gf2_rank(const uint32_t* v, int n) {
+    uint32_t basis[32] = {0};
     int rank = 0;
-    for (int bit = 31; bit >= 0; --bit) {
-        int piv = -1;
-        for (size_t i = rank; i < v.size(); ++i)
-            if ((v[i] >> bit) & 1u) { piv = (int)i; break; }
-        if (piv < 0) continue;
-        std::swap(v[rank], v[piv]);
-        for (size_t i = 0; i < v.size(); ++i)
-            if ((int)i != rank && ((v[i] >> bit) & 1u)) v[i] ^= v[rank];
-        ++rank;
+    for (int i = 0; i < n; ++i) {
+        uint32_t x = v[i];
+        while (x) {
+            const int b = 31 - __builtin_clz(x);
+            if (!basis[b]) {
+                basis[b] = x;
+                ++rank;
+                break;
+            }
+            x ^= basis[b];
+        }
     }
     return rank;
 }
@@ -172,7 +176,8 @@ qmc_status validate(const qmc_rule* r) {
         for (uint32_t j = 0; j < r->s; ++j) {
             const uint32_t wcl = std::min(r->w[j], m), q = m - wcl;
             const uint32_t rowmask = (wcl >= 32) ? 0u : ~((1u << wcl) - 1u);
-            std::vector<uint32_t> lead;
+            uint32_t lead[32];
+            int nlead = 0;
             for (uint32_t c = 0; c < m; ++c) {
                 const uint32_t word = r->C[(size_t)j * m + c];
                 if (m < 32 && (word >> m) != 0)
@@ -183,9 +188,9 @@ qmc_status validate(const qmc_rule* r) {
                                 "column %u of the reduced C^(%u) is nonzero: the net is not periodic with period "
                                 "2^(m-w_j) (non-periodic reduced nets, Algorithm 4, are not built)",
                                 c + 1, j);
-                if (c < q) lead.push_back(red >> wcl);
+                if (c < q) lead[nlead++] = red >> wcl;
             }
-            if (gf2_rank(lead) != (int)q)
+            if (gf2_rank(lead, nlead) != (int)q)
                 return fail(QMC_ERR_INVALID_ARG, "leading %ux%u block of C^(%u) is singular over GF(2)", q, q, j);
         }
     }

@@ -246,3 +246,41 @@ def test_planner_never_fails_uncleanly(lib, seed):
             if op != L.QMC_OP_GEN_POINTS:
                 elt = 8 if prec == L.QMC_FP64 else 4
                 assert nbytes.value >= elt * T * p.R_eff
+
+
+def gf2_rank_reference(rows):
+    """Row echelon form over GF(2) with numpy (an independent restatement for the test)."""
+    M = np.array(rows, dtype=np.uint8) % 2
+    rank = 0
+    for col in range(M.shape[1]):
+        piv = next((i for i in range(rank, M.shape[0]) if M[i, col]), None)
+        if piv is None:
+            continue
+        M[[rank, piv]] = M[[piv, rank]]
+        for i in range(M.shape[0]):
+            if i != rank and M[i, col]:
+                M[i] ^= M[rank]
+        rank += 1
+    return rank
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_net_leading_block_rank_check(lib, seed):
+    """The library accepts a periodic reduced net exactly when every leading (m-w_j) x (m-w_j)
+    block is nonsingular over GF(2): random blocks, about half of them singular."""
+    g = np.random.default_rng(7000 + seed)
+    m = int(g.integers(2, 13))
+    w = np.sort(g.integers(0, m, size=int(g.integers(1, 6)))).astype(np.uint32)
+    C = np.zeros((len(w), m), dtype=np.uint32)
+    expect_ok = True
+    bad = int(g.integers(0, len(w))) if seed % 2 else -1     # one singular block in odd seeds
+    for j, wj in enumerate(w):
+        q = m - int(wj)
+        B = I.gf2_nonsingular(g, q).astype(np.int64)
+        if j == bad:                                       # make a column depend on the others
+            B[:, -1] = B[:, 0] ^ (B[:, 1] if q > 2 else 0) if q > 1 else 0
+        expect_ok &= gf2_rank_reference(B) == q
+        for col in range(q):
+            C[j, col] = sum(int(B[p, col]) << (m - 1 - p) for p in range(q))
+    st = status(lib, Rule(I.DIGITAL_NET, m, w, C=C))
+    assert st == (L.QMC_OK if expect_ok else L.QMC_ERR_INVALID_ARG), lib.qmc_last_error()
