@@ -4,11 +4,12 @@
  *
  * The library evaluates QMC rules Q_N(f) = N^-1 sum_{k<N} f(x_k^T A)
  * (eq. (2) of Dick, Ebert, Herrmann, Kritzer, Longo, "The fast reduced QMC
- * matrix-vector product") over N = 2^m points of a reduced rank-1 lattice
- * (Sec. 1.3) or of a reduced digital net (Sec. 4), exploiting that coordinate
- * j of x_k depends only on k mod 2^(m-w_j) (Sec. 3): every weight block of A's
- * rows is multiplied only against its distinct point rows (Algorithm 2) and
- * the partial products are summed back periodically over the N outputs.
+ * matrix-vector product") over N = 2^m points of a reduced rank-1 lattice or a
+ * reduced polynomial lattice (Sec. 1.3), of a reduced digital net (Sec. 4) or
+ * of a reduced Monte Carlo point set (Sec. 5), exploiting that coordinate j of
+ * x_k depends only on k mod 2^(m-w_j) (Sec. 3): every weight block of A's rows
+ * is multiplied only against its distinct point rows (Algorithm 2) and the
+ * partial products are summed back periodically over the N outputs.
  *
  * Conventions shared by every entry point
  *  - Columns are 0-based: j = 0..s-1 is the paper's j+1.
