@@ -15,7 +15,8 @@
  *  - Columns are 0-based: j = 0..s-1 is the paper's j+1.
  *  - Points are held as 32-bit fixed point X32 = x * 2^32 (x in [0,1)).
  *    A random shift Delta_j is D_j * 2^-32 with D_j a uint32: lattices add it
- *    mod 2^32 ({x + Delta}, Sec. 2.3), nets XOR it (digital shift).
+ *    mod 2^32 ({x + Delta}, Sec. 2.3), nets and polynomial lattices XOR it
+ *    (digital shift).  Reduced Monte Carlo takes no shift.
  *  - A is s x tau row-major (row j is a_j, Sec. 3.1).  Its element type is
  *    fixed by the precision: QMC_FP64 -> double; QMC_FP32, QMC_SPLIT and
  *    QMC_BF16 -> float.
@@ -120,7 +121,7 @@ typedef int qmc_status;
  *  z          HOST uint32[R_eff * T] (reduced MC): the samples y_{j,i} as X32 = y 2^32, drawn by the
  *             caller (i.i.d. uniform words give i.i.d. U[0,1) samples on the 2^-32 grid).  Replica r
  *             holds, for j = 0..s-1 in order, the N_j = 2^(m-min(w_j,m)) samples y_{j,0..N_j-1} of
- *             column j (the QMC_LAYOUT_DISTINCT layout); T = sum_j N_j.  C and shift must be NULL.
+ *             column j (the QMC_LAYOUT_DISTINCT layout); T = sum_j N_j.  C, shift and d_shift must be NULL.
  *  R          number of random shifts (0 = unshifted rule); results are produced for R_eff = max(R,1).
  *             Reduced MC: the number of independent replicas (each its own samples in z).
  *  shift      HOST uint32[R*s]: shift r of column j is shift[r*s + j] (units of 2^-32).
