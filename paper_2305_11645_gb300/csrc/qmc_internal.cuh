@@ -182,24 +182,6 @@ template <int F, class T> struct Fn {
     }
 };
 
-// g(u) and g'(u) in double (tau, params as given)
-__device__ __forceinline__ double g_of(int F, double u, double tau, double c, double K) {
-    switch (F) {
-        case F_LINEAR_MEAN: case F_MEAN_COS: case F_PDE_INV_SQ: return u / tau;
-        case F_CALL_MEAN_EXP: return fmax(u / tau - K, 0.0);
-        case F_GAUSS_NORM2: return exp(-u / (2.0 * tau));
-        default: return u;   // LOGSUMEXP: u already is log sum exp
-    }
-}
-__device__ __forceinline__ double gprime_of(int F, double u, double tau, double c, double K) {
-    switch (F) {
-        case F_LINEAR_MEAN: case F_MEAN_COS: case F_PDE_INV_SQ: return 1.0 / tau;
-        case F_CALL_MEAN_EXP: return (u / tau - K > 0.0) ? 1.0 / tau : 0.0;
-        case F_GAUSS_NORM2: return -exp(-u / (2.0 * tau)) / (2.0 * tau);
-        default: return 1.0;
-    }
-}
-
 // ---------------------------------------------------------------------------------------------
 // Kernel argument blocks
 // ---------------------------------------------------------------------------------------------
