@@ -30,6 +30,10 @@ reordering beyond what the definitions state:
   O7  the gradient of the shift-averaged estimate with respect to A:
       (1/(R N)) sum_r X_r^T grad f(Y_r).
   O8  central finite differences of the estimate in single entries of A.
+  O11 Algorithm 4 (fast reduced product for digital nets, unshifted): for
+      j = s*, ..., 1 the row vectors c_k = k / b^(m-w_j) a_j, k < b^(m-w_j), and
+      P_j = P_{j+1} + (c_{floor(y_{n,j} b^(m-w_j))})_n; it returns P_1 = X A for
+      any reduced net, periodic or not (exact rationals on request).
   O10 reduced polynomial lattice points (Sec. 1.3): x_{k,j} = nu(k(x) g_j(x) / x^m)
       over F_2 with g_j = x^{w_j} gt_j, the product of the coefficient arrays
       written out mod 2 and mod x^m, the coefficient of x^i the digit of 2^(i-m);
@@ -150,6 +154,36 @@ def poly_lattice_x32(m: int, w, gt, shift: Optional[np.ndarray] = None, ks=None)
     if shift is not None:
         x32 = x32 ^ np.asarray(shift, dtype=np.uint32)[None, :]
     return x32
+
+
+# ----------------------------------------------------------------------------- O11 Algorithm 4
+
+def alg4_product(m: int, w, C: np.ndarray, A, exact: bool = False):
+    """Algorithm 4 on the unshifted reduced net with column masks C (b = 2): P = X A built column
+    by column from the gathered multiples c_k of a_j.  With exact=True, A's entries and the result
+    are Fractions (an N x tau list of lists)."""
+    from fractions import Fraction
+    N = 1 << m
+    s = len(w)
+    X32 = net_x32(m, w, C)                                      # y_{n,j} 2^32, O2
+    s_star = max([j + 1 for j in range(s) if int(w[j]) < m] + [0])
+    tau = len(A[0])
+    zero = Fraction(0) if exact else 0.0
+    P = [[zero] * tau for _ in range(N)] if exact else np.zeros((N, tau))
+    for j in range(s_star - 1, -1, -1):                         # j = s*, ..., 1 (0-based)
+        q = m - int(w[j])
+        a = [Fraction(v) for v in A[j]] if exact else np.asarray(A[j], dtype=np.float64)
+        if exact:
+            c = [[Fraction(k, 1 << q) * v for v in a] for k in range(1 << q)]
+        else:
+            c = (np.arange(1 << q, dtype=np.float64) / (1 << q))[:, None] * a[None, :]
+        idx = (X32[:, j].astype(np.uint64) >> np.uint64(32 - q)).astype(np.int64)   # floor(y b^(m-w_j))
+        if exact:
+            for n in range(N):
+                P[n] = [P[n][t] + c[idx[n]][t] for t in range(tau)]
+        else:
+            P = P + c[idx]
+    return P
 
 
 # ----------------------------------------------------------------------------- O9 reduced Monte Carlo

@@ -444,3 +444,66 @@ def test_poly_lattice_periodic_permutation(seed):
         assert np.array_equal(X[:, j], per)
         grid = np.sort(X[: 1 << q, j] >> np.uint64(32 - q)) if q else X[:1, j]
         assert np.array_equal(grid, np.arange(1 << q, dtype=np.uint64)) if q else grid[0] == 0
+
+
+# ----------------------------------------------------------------------------- O11 Algorithm 4 (Sec. 4)
+
+def nonperiodic_reduced_masks(g, m, w):
+    """Random generating matrices whose reduced form (last w_j rows zeroed) keeps full row rank
+    m - w_j but, in general, nonzero columns beyond m - w_j: reduced nets that are not periodic."""
+    C = np.zeros((len(w), m), dtype=np.uint32)
+    for j, wj in enumerate(w):
+        q = m - min(int(wj), m)
+        while True:
+            B = g.integers(0, 2, size=(m, m))
+            B[q:, :] = 0
+            if q == 0 or np.linalg.matrix_rank(B[:q].astype(float)) == q:
+                # (a real-valued rank >= the GF(2) rank; full GF(2) rank is checked below)
+                rows = [int(sum(int(B[p, c]) << c for c in range(m))) for p in range(q)]
+                basis, ok = [0] * 32, True
+                for x in rows:
+                    while x:
+                        b = x.bit_length() - 1
+                        if not basis[b]:
+                            basis[b] = x
+                            break
+                        x ^= basis[b]
+                    else:
+                        ok = False
+                if ok:
+                    break
+        for col in range(m):
+            C[j, col] = sum(int(B[p, col]) << (m - 1 - p) for p in range(m))
+    return C
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_alg4_returns_XA_exactly(seed):
+    """Algorithm 4 in exact rationals equals the dense definition X A (Sec. 4: 'Return: P = X A'),
+    on reduced nets that are not periodic, with a constant column (w_j >= m) skipped."""
+    g = np.random.default_rng(1200 + seed)
+    m = int(g.integers(2, 6))
+    w = np.sort(np.append(g.integers(0, m, size=3), m + 1)).astype(np.uint32)
+    C = nonperiodic_reduced_masks(g, m, w)
+    A = [[Fraction(int(v), 7) for v in g.integers(-9, 10, size=3)] for _ in range(len(w))]
+    P = O.alg4_product(m, w, C, A, exact=True)
+    X = [[Fraction(int(v), 1 << 32) for v in row] for row in O.net_x32(m, w, C)]
+    for n in range(1 << m):
+        for t in range(3):
+            assert P[n][t] == sum(X[n][j] * A[j][t] for j in range(len(w)))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_reduced_net_values_repeat_exactly_2_to_the_w(seed):
+    """Sec. 4: in a reduced net whose reduced matrix keeps rank m - w_j, column j takes the values
+    k / 2^(m-w_j) only, each exactly 2^(w_j) times, also when it is not periodic."""
+    g = np.random.default_rng(1300 + seed)
+    m = int(g.integers(2, 9))
+    w = np.sort(g.integers(0, m + 1, size=5)).astype(np.uint32)
+    C = nonperiodic_reduced_masks(g, m, w)
+    X = O.net_x32(m, w, C).astype(np.uint64)
+    for j, wj in enumerate(w):
+        q = m - min(int(wj), m)
+        v = X[:, j] >> np.uint64(32 - q) if q else np.zeros(1 << m, dtype=np.uint64)
+        assert np.array_equal(v << np.uint64(32 - q) if q else X[:, j], X[:, j])      # on the 2^-q grid
+        assert np.array_equal(np.bincount(v.astype(np.int64), minlength=1 << q), np.full(1 << q, 1 << min(int(wj), m)))
