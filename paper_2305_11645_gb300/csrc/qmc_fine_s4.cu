@@ -634,13 +634,11 @@ cudaError_t launch_fine_mat_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t
 template <int F>
 static cudaError_t fwd_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {
     const size_t smem = (size_t)a.cr * kAQuads * sizeof(float4);
-    static bool opted_in = false;                  // dynamic + static shared memory may exceed 48 KB
-    if (!opted_in) {
-        const cudaError_t e = cudaFuncSetAttribute(k_fine_fwd_s4<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(kMaxCRS4 * kAQuads * sizeof(float4)));
-        if (e != cudaSuccess) return e;
-        opted_in = true;
-    }
+    // dynamic + static shared memory may exceed 48 KB; the attribute belongs to the current device,
+    // so it is set on every launch (as for the tensor-core kernels), not once per process
+    const cudaError_t e = cudaFuncSetAttribute(k_fine_fwd_s4<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(kMaxCRS4 * kAQuads * sizeof(float4)));
+    if (e != cudaSuccess) return e;
     k_fine_fwd_s4<F><<<grid, kFwdThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
