@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--precision", choices=list(TIERS), default="split")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense X*A comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--workload", choices=["c2", "c3", "c5", "basket"], default="c2",
+                    help="c2: the contract line (default); c3, c5, basket: a timing line for a larger "
+                         "workload (graph-replayed step, per-kernel trace), not the contract line")
     return ap.parse_args()
 
 
@@ -510,8 +513,77 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": "outputs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_workload(args):
+    """A timing line for one of the larger workloads (the c2 contract line is run_ours):
+    the graph-replayed step with L2 flushed before each step (median over the steps), and the
+    library's per-kernel trace of eager steps."""
+    import torch
+    from paper_2305_11645_gb300 import _lib as L
+    from paper_2305_11645_gb300 import api
+    from paper_2305_11645_gb300 import inputs as I
+    prec = args.precision
+    if args.workload == "c3":
+        p, backward, desc = I.c3(), False, ("c3 reduced periodic digital net b=2 m=20 (N=1048576), s=tau=1024, "
+                                            "w_j=min(floor(log2(j+1)),12), 16 XOR shifts, f=exp(-|y|^2/(2 tau)), estimate")
+    elif args.workload == "c5":
+        p, backward, desc = I.c5(), True, ("c5 reduced rank-1 lattice b=2 m=20 (N=1048576), s=tau=1024, "
+                                           "w_j=min(floor(log2(j+1)),12), 8 shifts, f=log sum exp(y), estimate + adjoint")
+    else:
+        m, s = 25, 10
+        sig, rho, S0, K = 0.4, 0.2, 100.0, 110.0
+        Sig = np.diag([sig] * s) + np.diag([rho] * (s - 1), 1) + np.diag([rho] * (s - 1), -1)
+        A = np.linalg.cholesky(Sig).T.astype(np.float32)
+        w = np.array([min(int(math.floor(math.log2(j))), m) for j in range(1, s + 1)], dtype=np.uint32)
+        y = I.mc_samples(I.rng(6, I.P_MISC), m, w, 1, force_odd=True)
+        p = I.Problem(I.REDUCED_MC, m, w, A, y=y, transform=I.T_INV_NORMAL, f_kind=I.F_CALL_MEAN_EXP,
+                      f_params=(1.0, K / S0 * math.exp(sig / 2), 0, 0))
+        backward, desc = False, ("basket option by reduced Monte Carlo: m=25 (N=33554432), s=tau=10, "
+                                 "w_j=floor(log2 j) (1-based), tridiagonal Sigma (0.4, 0.2), K=110, one replica")
+    dev = torch.device("cuda", 0)
+    rule = api.Rule.from_problem(p)
+    A = torch.from_numpy(p.A).to(dev)
+    f = api.Integrand(p.f_kind, p.f_params)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    it = api.Integrator(rule, A, f, backward=backward, graph=True, precision=prec)
+    for _ in range(args.warmup):
+        it.run()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        it.run()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    eager = api.Integrator(rule, A, f, backward=backward, graph=False, precision=prec)
+    eager.run()
+    torch.cuda.synchronize()
+    L.trace_enable(True)
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda._sleep(3_000_000)        # the host queues the whole step before the GPU reaches it
+        eager.run()
+    torch.cuda.synchronize()
+    kern = L.trace_collect()
+    L.trace_enable(False)
+    L.device_status()
+    ms = float(np.median(ts))
+    outputs = p.N * p.tau * p.R_eff
+    return {"workload": args.workload, "description": desc, "metric": METRIC, "value": outputs / (ms / 1e3),
+            "unit": "outputs/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "precision": prec,
+            "backward": backward, "estimate": float(it.est[-1].item()), "data": "synthetic",
+            "l2": "flushed before every timed step (512 MiB write, untimed)",
+            "kernels": {k: {"launches": c // args.steps, "ms_per_step": t / args.steps}
+                        for k, (c, t) in sorted(kern.items())}}
+
+
 def main():
     args = parse()
+    if args.workload != "c2" and args.impl == "ours":
+        print(json.dumps(run_workload(args)))
+        return
     dist, rank, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)
