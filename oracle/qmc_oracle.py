@@ -17,7 +17,8 @@ reordering beyond what the definitions state:
   O2  digital-net points (Sec. 4, eq. def:digital with the reduced generating
       matrices of eq. reduced_genmat_net2): digits of n least significant
       first, the last min(w_j, m) rows of C^(j) set to zero, y digits as the
-      matrix-vector product over GF(2), y = sum_p y_p b^-p.
+      matrix-vector product over GF(2), y = sum_p y_p b^-p; net_points_base
+      does the same over F_b for any prime b.
   O3  random shifts as 32-bit fixed point D_j * 2^-32 (Sec. 2.3):
       lattice {x + Delta} = (X32 + D) mod 2^32, nets (digital shift)
       X32 XOR D, with X32 = x * 2^32.
@@ -214,6 +215,24 @@ def mc_x32(m: int, w, y: np.ndarray, ks=None) -> np.ndarray:
     idx = mc_sample_index(m, w, ks)
     off = np.cumsum([0] + [1 << (m - min(int(wj), m)) for wj in w])[:-1]
     return np.asarray(y, dtype=np.uint32)[idx + off[None, :]]
+
+
+def net_points_base(b: int, m: int, w, C: np.ndarray, ks=None) -> np.ndarray:
+    """Digital net in a prime base b (Sec. 4, eq. def:digital) with the reduced matrices of eq.
+    reduced_genmat_net2, as float64 points: C[j] is the m x m matrix over F_b (entries 0..b-1,
+    row p-1 the digit of b^-p, column q-1 digit q-1 of n, least significant first), the last
+    min(w_j, m) rows are zeroed, y digits = C n mod b, y = sum_p y_p b^-p.  (b = 2 agrees with O2.)"""
+    N = b ** m
+    ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
+    dig = np.stack([(ks // b ** q) % b for q in range(m)], axis=1)          # len(ks) x m, n's digits
+    out = np.empty((len(ks), len(w)), dtype=np.float64)
+    place = np.array([b ** (m - 1 - p) for p in range(m)], dtype=np.int64)     # y_p b^-p, scaled by b^m
+    for j, wj in enumerate(w):
+        Chat = np.array(C[j], dtype=np.int64) % b
+        Chat[m - min(int(wj), m):, :] = 0
+        ydig = (dig @ Chat.T) % b
+        out[:, j] = (ydig @ place) / float(N)       # one rounding: the integer y b^m over b^m
+    return out
 
 
 # ----------------------------------------------------------------------------- O3/O4 shifts and transforms

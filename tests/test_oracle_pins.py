@@ -507,3 +507,43 @@ def test_reduced_net_values_repeat_exactly_2_to_the_w(seed):
         v = X[:, j] >> np.uint64(32 - q) if q else np.zeros(1 << m, dtype=np.uint64)
         assert np.array_equal(v << np.uint64(32 - q) if q else X[:, j], X[:, j])      # on the 2^-q grid
         assert np.array_equal(np.bincount(v.astype(np.int64), minlength=1 << q), np.full(1 << q, 1 << min(int(wj), m)))
+
+
+# ----------------------------------------------------------------------------- O2 in a prime base b
+
+@pytest.mark.parametrize("b,m", [(3, 4), (5, 3), (7, 2)])
+def test_base_b_identity_net_is_the_radical_inverse(b, m):
+    """C = identity over F_b gives the van der Corput sequence in base b: the digits of n mirrored
+    about the radix point (a textbook closed form)."""
+    X = O.net_points_base(b, m, [0], [np.eye(m, dtype=np.int64)])
+    for n in range(b ** m):
+        d, v, scale = n, Fraction(0), Fraction(1, b)
+        while d:
+            v += (d % b) * scale
+            d //= b
+            scale /= b
+        assert X[n, 0] == float(v)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_base_b_net_reduces_like_base_2(seed):
+    """For b = 2 the general-base net equals O2 on random reduced nets; for b = 3 a reduced column
+    takes each of its b^(m-w_j) grid values exactly b^(w_j) times when the leading block is invertible."""
+    g = np.random.default_rng(1400 + seed)
+    m = int(g.integers(2, 8))
+    w = np.sort(g.integers(0, m + 1, size=4)).astype(np.uint32)
+    C2 = I.periodic_net_masks(g, m, w)
+    mats = [[[(int(C2[j, q]) >> (m - 1 - p)) & 1 for q in range(m)] for p in range(m)] for j in range(len(w))]
+    assert np.array_equal(O.net_points_base(2, m, w, mats), O.net_x32(m, w, C2).astype(np.float64) / 2.0 ** 32)
+    b, m3 = 3, 4
+    for wj in range(m3 + 1):
+        q = m3 - wj
+        while True:
+            B = g.integers(0, b, size=(q, q))
+            if q == 0 or round(abs(np.linalg.det(B))) % b != 0:
+                break
+        Cm = np.zeros((m3, m3), dtype=np.int64)
+        Cm[:q, :q] = B
+        x = O.net_points_base(b, m3, [wj], [Cm])[:, 0]
+        vals, counts = np.unique(np.round(x * b ** q).astype(np.int64), return_counts=True)
+        assert np.array_equal(vals, np.arange(b ** q)) and np.all(counts == b ** wj)
