@@ -126,7 +126,10 @@ typedef int qmc_status;
  *             Reduced MC: the number of independent replicas (each its own samples in z).
  *  shift      HOST uint32[R*s]: shift r of column j is shift[r*s + j] (units of 2^-32).
  *  transform  QMC_T_*; QMC_T_INV_NORMAL requires R >= 1 for lattices and nets (the unshifted point 0
- *             maps to -inf), and no zero sample word for reduced MC (checked on the host).
+ *             maps to -inf) and every shift word D_j with a nonzero bit among its low 32 - q_j bits,
+ *             q_j = m - min(w_j, m) (otherwise some shifted point of column j is exactly 0, because
+ *             the column takes every value u 2^(32-q_j), u < 2^q_j, over a period); reduced MC
+ *             requires no zero sample word.  All of this is checked on the host.
  *  d_gen      DEVICE copy of z (s words; reduced MC: R_eff * T words) or C (s*m words), or NULL: then
  *             the host array is copied into the workspace on every call (a pageable copy, which also
  *             prevents CUDA graph capture).  It must hold exactly the host values.

@@ -31,10 +31,11 @@ reordering beyond what the definitions state:
   O7  the gradient of the shift-averaged estimate with respect to A:
       (1/(R N)) sum_r X_r^T grad f(Y_r).
   O8  central finite differences of the estimate in single entries of A.
-  O11 Algorithm 4 (fast reduced product for digital nets, unshifted): for
-      j = s*, ..., 1 the row vectors c_k = k / b^(m-w_j) a_j, k < b^(m-w_j), and
-      P_j = P_{j+1} + (c_{floor(y_{n,j} b^(m-w_j))})_n; it returns P_1 = X A for
-      any reduced net, periodic or not (exact rationals on request).
+  O11 the product of Sec. 4 (Algorithm 4) for reduced nets, unshifted: coordinate
+      j takes only the grid values v / 2^(m-w_j), so x_{n,j} a_j is a row of the
+      table of multiples (v / 2^(m-w_j)) a_j selected by v = floor(x_{n,j}
+      2^(m-w_j)); X A is the sum of the selected rows over j (exact rationals
+      on request).  It holds for any reduced net, periodic or not.
   O10 reduced polynomial lattice points (Sec. 1.3): x_{k,j} = nu(k(x) g_j(x) / x^m)
       over F_2 with g_j = x^{w_j} gt_j, the product of the coefficient arrays
       written out mod 2 and mod x^m, the coefficient of x^i the digit of 2^(i-m);
@@ -160,30 +161,31 @@ def poly_lattice_x32(m: int, w, gt, shift: Optional[np.ndarray] = None, ks=None)
 # ----------------------------------------------------------------------------- O11 Algorithm 4
 
 def alg4_product(m: int, w, C: np.ndarray, A, exact: bool = False):
-    """Algorithm 4 on the unshifted reduced net with column masks C (b = 2): P = X A built column
-    by column from the gathered multiples c_k of a_j.  With exact=True, A's entries and the result
-    are Fractions (an N x tau list of lists)."""
+    """X A for the unshifted reduced net with column masks C (b = 2), as Sec. 4 obtains it without
+    multiplying every entry: coordinate j of every point lies on the grid {v / 2^(m - w_j)}, v <
+    2^(m - w_j), so the products x_{n,j} a_j are drawn from a table of the 2^(m - w_j) multiples
+    (v / 2^(m - w_j)) a_j, indexed by v = floor(x_{n,j} 2^(m - w_j)), and X A is the sum over the
+    coordinates j with w_j < m of the table rows each point selects (coordinates with w_j >= m are
+    zero).  Columns are taken in ascending j.  It holds for any reduced net, periodic or not.  With
+    exact=True, A's entries and the result are Fractions (an N x tau list of lists)."""
     from fractions import Fraction
     N = 1 << m
-    s = len(w)
     X32 = net_x32(m, w, C)                                      # y_{n,j} 2^32, O2
-    s_star = max([j + 1 for j in range(s) if int(w[j]) < m] + [0])
     tau = len(A[0])
-    zero = Fraction(0) if exact else 0.0
-    P = [[zero] * tau for _ in range(N)] if exact else np.zeros((N, tau))
-    for j in range(s_star - 1, -1, -1):                         # j = s*, ..., 1 (0-based)
-        q = m - int(w[j])
-        a = [Fraction(v) for v in A[j]] if exact else np.asarray(A[j], dtype=np.float64)
+    P = [[Fraction(0)] * tau for _ in range(N)] if exact else np.zeros((N, tau))
+    for j in range(len(w)):
+        q = m - min(int(w[j]), m)                               # grid of 2^q values
+        if q == 0:
+            continue                                            # the coordinate is 0
+        v = (X32[:, j].astype(np.uint64) >> np.uint64(32 - q)).astype(np.int64)   # x 2^q, exact
         if exact:
-            c = [[Fraction(k, 1 << q) * v for v in a] for k in range(1 << q)]
-        else:
-            c = (np.arange(1 << q, dtype=np.float64) / (1 << q))[:, None] * a[None, :]
-        idx = (X32[:, j].astype(np.uint64) >> np.uint64(32 - q)).astype(np.int64)   # floor(y b^(m-w_j))
-        if exact:
+            a = [Fraction(x) for x in A[j]]
+            table = [[Fraction(k, 1 << q) * x for x in a] for k in range(1 << q)]
             for n in range(N):
-                P[n] = [P[n][t] + c[idx[n]][t] for t in range(tau)]
+                P[n] = [p + c for p, c in zip(P[n], table[v[n]])]
         else:
-            P = P + c[idx]
+            table = (np.arange(1 << q, dtype=np.float64) / (1 << q))[:, None] * np.asarray(A[j], dtype=np.float64)
+            P = P + table[v]
     return P
 
 

@@ -167,6 +167,22 @@ qmc_status validate(const qmc_rule* r) {
     if (r->R > 0 && !r->shift) return fail(QMC_ERR_INVALID_ARG, "R=%u but shift is NULL", r->R);
     if (r->transform == QMC_T_INV_NORMAL && r->R == 0)
         return fail(QMC_ERR_INVALID_ARG, "the inverse-normal transform needs a random shift (x=0 maps to -inf)");
+    if (r->transform == QMC_T_INV_NORMAL) {
+        // Column j takes, over one period, every value u 2^(32-q) with u < 2^q (q = m - min(w_j, m)):
+        // the lattice's u = k z_j mod 2^q with z_j odd, the polynomial lattice's carry-less product with
+        // gt_j(0) = 1 and the net's nonsingular leading block are all bijections.  So the shifted column
+        // reaches X32 = 0, which the inverse normal maps to -inf, exactly when the low 32 - q bits of
+        // D_j vanish ((u 2^(32-q) + D_j) mod 2^32 = 0 and (u 2^(32-q)) XOR D_j = 0 each have a solution u).
+        for (uint32_t i = 0; i < r->R; ++i)
+            for (uint32_t j = 0; j < r->s; ++j) {
+                const uint32_t q = m - std::min(r->w[j], m), low = 32 - q;
+                const uint32_t mask = low >= 32 ? 0xFFFFFFFFu : ((1u << low) - 1u);
+                if ((r->shift[(size_t)i * r->s + j] & mask) == 0)
+                    return fail(QMC_ERR_INVALID_ARG,
+                                "shift %u of column %u (0x%x) has its low %u bits zero: a shifted point is 0, which "
+                                "the inverse-normal transform maps to -inf", i, j, r->shift[(size_t)i * r->s + j], low);
+            }
+    }
     if (r->kind == QMC_LATTICE || r->kind == QMC_POLY_LATTICE) {
         // z_j in U_{2^q}; for polynomials: gt_j(0) = 1 and deg gt_j < q (gcd(gt_j, x^q) = 1)
         const char* what = r->kind == QMC_LATTICE ? "lattice rule needs z" : "polynomial lattice rule needs z";
@@ -958,14 +974,19 @@ extern "C" {
 qmc_status qmc_integrate_noalloc(const qmc_rule* rule, const void* d_A, uint32_t tau, const qmc_integrand* f,
                                  int precision, double* d_est, void* stream) {
     if (!d_A || !d_est || !f) return fail(QMC_ERR_INVALID_ARG, "d_A, d_est and f must be non-NULL");
-    Plan P;
+    Plan P, Pq;
     qmc_status st = make_plan(QMC_OP_INTEGRATE, rule, tau, f, precision, d_A, P);
     if (st != QMC_OK) return st;
-    if (P.total > kNoAllocScratchBytes)
+    // The limit is checked against qmc_workspace_size's plan (made without d_A, so it always holds
+    // the padded copy of A): a problem is accepted exactly when that query fits the array, whatever
+    // A's alignment.  The plan for the given d_A is never larger.
+    st = make_plan(QMC_OP_INTEGRATE, rule, tau, f, precision, nullptr, Pq);
+    if (st != QMC_OK) return st;
+    if (Pq.total > kNoAllocScratchBytes)
         return fail(QMC_ERR_NO_MEMORY,
                     "qmc_integrate_noalloc: this problem needs %zu bytes of scratch, the static array holds %zu "
                     "(use qmc_integrate with a caller workspace)",
-                    P.total, kNoAllocScratchBytes);
+                    Pq.total, kNoAllocScratchBytes);
     void* scratch = nullptr;
     st = noalloc_scratch(&scratch);
     if (st != QMC_OK) return st;

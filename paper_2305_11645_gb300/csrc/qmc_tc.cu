@@ -67,6 +67,14 @@ __device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols) {
     }
 }
 
+// After a wait ran out: one more bounded wait (by one thread, before the teardown's barrier) on
+// the barrier of the last committed chunk.  A commit arrives once every MMA issued before it has
+// completed, so when this wait succeeds no MMA still reads the stages or writes the tensor memory
+// that the teardown releases.  If it runs out too, the CTA returns regardless (bounded).
+__device__ __forceinline__ void drain_committed(uint64_t* bar, int committed) {
+    if (committed >= 0) mbar_wait(smem_u32(&bar[committed & 1]), (committed >> 1) & 1);
+}
+
 // Publish the stage to the tensor core; returns false (in every thread) if any thread's
 // wait ran out.
 __device__ __forceinline__ bool publish_stage(bool ok) {
@@ -134,6 +142,7 @@ __global__ void __launch_bounds__(256) k_coarse_fwd_tc(const float* __restrict__
     const long long kstride = lower ? n_e : (long long)ldA;
     float vv[KC];
     bool ok = true, first = true;
+    int committed = -1;                                // last chunk whose MMAs were committed
     // Iteration it loads chunk it and converts chunk it - 1 (one load site keeps the code small).
     for (int it = 0; it <= nchunks; ++it) {
         float vc[KC];
@@ -168,11 +177,15 @@ __global__ void __launch_bounds__(256) k_coarse_fwd_tc(const float* __restrict__
                                            smem_desc_sw64(smem_u32(As) + 32 * ks), idesc, first);
             mma_commit(smem_u32(&bar[s]));
         }
+        committed = c;
     }
     if (ok) ok = mbar_wait(smem_u32(&bar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
     fence_after_sync();
     ok = __syncthreads_and(ok);
-    if (!ok && tid == 0) atomicOr(&g_tc_error, 1u);
+    if (!ok && tid == 0) {
+        atomicOr(&g_tc_error, 1u);
+        drain_committed(bar, committed);
+    }
 
     float* Be = B + (long long)r * B_stride + ch.boff[e];
     const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);
@@ -274,6 +287,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
     const float* Fcol = Fsrc + (col_ok ? t : 0);
     const bool whole = n_e >= KC;                      // a chunk never crosses a shift boundary
     bool ok = true;
+    int committed = -1;                                // last chunk whose MMAs were committed
     if (whole && fold == 1) {
         // ------------------------------------------------------------ main path
         const int lane = tid & 31;
@@ -342,6 +356,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
                                                  smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, fresh);
                 mma_commit(smem_u32(&bar[s]));
             }
+            committed = c;
         }
         cp_async_wait<0>();
     } else {
@@ -433,12 +448,16 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
                                              smem_desc_sw64(smem_u32(Xs) + 32 * ks), idesc, fresh);
             mma_commit(smem_u32(&bar[s]));
         }
+        committed = c;
     }
     }
     if (ok && nchunks > 0) ok = mbar_wait(smem_u32(&bar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
     fence_after_sync();
     ok = __syncthreads_and(ok);
-    if (!ok && tid == 0) atomicOr(&g_tc_error, 1u);
+    if (!ok && tid == 0) {
+        atomicOr(&g_tc_error, 1u);
+        drain_committed(bar, committed);
+    }
 
     // D[t][j]: TMEM lane = t - t0, column = j - j0; warps w and w + 4 share lanes 32 (w % 4) ..,
     // the lower ones store columns 0..31, the upper ones 32..63

@@ -111,6 +111,35 @@ def test_null_pointers_and_shift_rules(lib):
     assert "shift" in lib.qmc_last_error().decode()
 
 
+@pytest.mark.parametrize("kind", [I.LATTICE, I.DIGITAL_NET, I.POLY_LATTICE])
+def test_inverse_normal_rejects_shifts_that_reach_zero(lib, kind):
+    """Under the inverse normal a shift word whose low 32 - q_j bits vanish puts a point at x = 0
+    (the column takes every value u 2^(32-q_j) over its period), which maps to -inf: rejected.
+    One set bit among those low bits keeps every point away from 0."""
+    from oracle import qmc_oracle as O
+    m, w = 6, np.array([0, 1, 2, 6], dtype=np.uint32)
+    g = np.random.default_rng(7)
+    z = I.odd_z(I.rng(9, I.P_Z), m, w)
+    C = I.periodic_net_masks(I.rng(9, I.P_C), m, w)
+    base = np.array([1 << 31, 3 << 29, 5 << 28, 0x80000000], dtype=np.uint32)   # low bits of each zero
+    for j in range(len(w)):
+        q = m - min(int(w[j]), m)
+        D = (g.integers(0, 1 << 32, size=len(w), dtype=np.uint64) | 1).astype(np.uint32)
+        D[j] = base[j] & np.uint32(~((1 << (32 - q)) - 1) & 0xFFFFFFFF)
+        r = Rule(kind, m, w, z=z if kind != I.DIGITAL_NET else None, C=C if kind == I.DIGITAL_NET else None,
+                 shifts=D[None, :], transform=I.T_INV_NORMAL)
+        assert status(lib, r) == L.QMC_ERR_INVALID_ARG, (j, lib.qmc_last_error())
+        assert "low" in lib.qmc_last_error().decode()
+        # the oracle's points of that column indeed reach 0 over one period
+        p = I.Problem(kind, m, w, np.zeros((len(w), 1)), z=z if kind != I.DIGITAL_NET else None,
+                      C=C if kind == I.DIGITAL_NET else None, shifts=D[None, :], transform=I.T_IDENTITY)
+        assert np.any(O.x32_points(p, 0)[:, j] == 0)
+        D[j] |= np.uint32(1 << (32 - q - 1))               # one low bit set: accepted
+        r = Rule(kind, m, w, z=z if kind != I.DIGITAL_NET else None, C=C if kind == I.DIGITAL_NET else None,
+                 shifts=D[None, :], transform=I.T_INV_NORMAL)
+        assert status(lib, r) == L.QMC_OK, lib.qmc_last_error()
+
+
 def ws_size(lib, op, rule, tau, f, prec):
     out = ctypes.c_size_t(0)
     fa = None if f is None else ctypes.byref(f.struct())

@@ -44,6 +44,21 @@ def test_p1_lattice_worked_example():
     assert np.array_equal(X.sum(axis=0), np.array(g["column_sums"], dtype=float))
 
 
+def test_p1_algorithm_1_intermediates():
+    """The hand-worked intermediates of Algorithm 1 (Sec. 3.1) on the P1 example: P_3 has the two
+    distinct rows of column 3, P_2 the four of columns 2-3, and P_1 is X A."""
+    g = load("p1_lattice_b2_m3.json")
+    p = lattice_problem(g["m"], g["w"], g["z"], g["A"])
+    Afr = [[Fraction(v) for v in row] for row in g["A"]]
+    trace = {}
+    P = alg1(p, Afr, trace)
+    as_fr = lambda rows: [[Fraction(v) for v in row] for row in rows]
+    assert trace[3] == as_fr(g["alg1_P3"])
+    assert trace[2] == as_fr(g["alg1_P2"])
+    assert P == [[Fraction(v, 8) for v in row] for row in g["XA_times_8"]]
+    assert trace[1] == P
+
+
 def test_p2_net_worked_example():
     g = load("p2_net_b2_m3.json")
     p = net_problem(g["m"], g["w"], g["C"], g["A"])
@@ -93,8 +108,9 @@ def test_p4_reduced_form_equals_unreduced_definition(b, mmax):
                     assert Fraction(int(num[k]), N) == red
 
 
-def alg1(p, Afr):
-    """Algorithm 1 (Sec. 3.1) in exact rationals, lattice, b = 2."""
+def alg1(p, Afr, trace=None):
+    """Algorithm 1 (Sec. 3.1) in exact rationals, lattice, b = 2.  With a dict `trace`, the
+    intermediate P_j of every step is recorded under the paper's 1-based j."""
     m, w, z = p.m, [int(v) for v in p.w], [int(v) for v in p.z]
     s, tau = len(w), len(Afr[0])
     sstar = max([j + 1 for j in range(s) if w[j] < m], default=0)
@@ -106,6 +122,8 @@ def alg1(p, Afr):
         assert reps * len(P) == n
         Xj = [Fraction((k * z[j]) % n, n) for k in range(n)]
         P = [[P[k % len(P)][t] + Xj[k] * Afr[j][t] for t in range(tau)] for k in range(n)]
+        if trace is not None:
+            trace[j + 1] = P
     N = 2 ** m
     return [[P[k % len(P)][t] for t in range(tau)] for k in range(N)]
 
