@@ -30,7 +30,9 @@ reordering beyond what the definitions state:
       the mean over the R shifts.
   O7  the gradient of the shift-averaged estimate with respect to A:
       (1/(R N)) sum_r X_r^T grad f(Y_r).
-  O8  central finite differences of the estimate in single entries of A.
+  O8  central finite differences of the estimate in single entries of A: by
+      re-evaluating the estimate (fd_grad), or in one pass over the rows
+      (fd_grad_rows), since only entry t of every y_k moves with A_jt.
   O11 the product of Sec. 4 (Algorithm 4) for reduced nets, unshifted: coordinate
       j takes only the grid values v / 2^(m-w_j), so x_{n,j} a_j is a row of the
       table of multiples (v / 2^(m-w_j)) a_j selected by v = floor(x_{n,j}
@@ -85,10 +87,8 @@ def lattice_x32(m: int, w, z, shift: Optional[np.ndarray] = None, ks=None) -> np
     """b = 2 lattice points as 32-bit fixed point X32 = x * 2^32 (x exact, m <= 32),
     optionally shifted: (X32 + D_j) mod 2^32."""
     num = lattice_numerators(2, m, w, z, ks).astype(np.uint64)      # < 2^m
-    x32 = num * np.uint64(1 << (32 - m))                           # x * 2^32, < 2^32
-    if shift is not None:
-        x32 = (x32 + np.asarray(shift, dtype=np.uint64)[None, :]) % np.uint64(TWO32)
-    return x32.astype(np.uint32)
+    x32 = (num * np.uint64(1 << (32 - m))).astype(np.uint32)       # x * 2^32, < 2^32
+    return x32 if shift is None else apply_shift(LATTICE, x32, shift)
 
 
 # ----------------------------------------------------------------------------- O2 digital nets
@@ -118,18 +118,18 @@ def net_x32(m: int, w, C: np.ndarray, shift: Optional[np.ndarray] = None, ks=Non
     """b = 2 reduced digital net (Algorithm 3) as X32 = y * 2^32, optionally XOR-shifted."""
     N = 1 << m
     ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
-    dig = digits_lsb_first(ks, m)                         # len(ks) x m
+    # (the integer sums below are at most m ones, or y 2^m < 2^m: exact in float64, so the
+    # products run through the float BLAS)
+    dig = digits_lsb_first(ks, m).astype(np.float64)      # len(ks) x m
     out = np.empty((len(ks), len(w)), dtype=np.uint64)
-    place = np.array([1 << (m - 1 - p) for p in range(m)], dtype=np.uint64)   # y_p b^-p, scaled by 2^m
+    place = np.array([1 << (m - 1 - p) for p in range(m)], dtype=np.float64)   # y_p b^-p, scaled by 2^m
     for j, wj in enumerate(w):
-        Chat = reduced_net_matrix(C[j], m, int(wj))
-        ydig = (dig @ Chat.T) % 2                          # y digits = Chat n over GF(2)
-        y_int = (ydig.astype(np.uint64) * place[None, :]).sum(axis=1)   # y * 2^m
+        Chat = reduced_net_matrix(C[j], m, int(wj)).astype(np.float64)
+        ydig = np.mod(dig @ Chat.T, 2.0)                   # y digits = Chat n over GF(2)
+        y_int = (ydig @ place).astype(np.uint64)           # y * 2^m
         out[:, j] = y_int << np.uint64(32 - m)
     x32 = out.astype(np.uint32)
-    if shift is not None:
-        x32 = x32 ^ np.asarray(shift, dtype=np.uint32)[None, :]
-    return x32
+    return x32 if shift is None else apply_shift(DIGITAL_NET, x32, shift)
 
 
 # ----------------------------------------------------------------------------- O10 polynomial lattices
@@ -153,9 +153,7 @@ def poly_lattice_x32(m: int, w, gt, shift: Optional[np.ndarray] = None, ks=None)
         y_int = (c.astype(np.uint64) * (np.uint64(1) << np.arange(m, dtype=np.uint64))[None, :]).sum(axis=1)
         out[:, j] = y_int << np.uint64(32 - m)                    # nu: y 2^m = sum_i a_i 2^i
     x32 = out.astype(np.uint32)
-    if shift is not None:
-        x32 = x32 ^ np.asarray(shift, dtype=np.uint32)[None, :]
-    return x32
+    return x32 if shift is None else apply_shift(POLY_LATTICE, x32, shift)
 
 
 # ----------------------------------------------------------------------------- O11 Algorithm 4
@@ -238,6 +236,38 @@ def net_points_base(b: int, m: int, w, C: np.ndarray, ks=None) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- O3/O4 shifts and transforms
+
+def apply_shift(kind: int, x32: np.ndarray, shift) -> np.ndarray:
+    """O3 on 32-bit fixed-point rows: a lattice adds D mod 2^32 ({x + Delta}); nets and
+    polynomial lattices XOR it (the digital shift)."""
+    D = np.asarray(shift, dtype=np.uint64)[None, :]
+    if kind == LATTICE:
+        return ((np.asarray(x32, dtype=np.uint64) + D) % np.uint64(TWO32)).astype(np.uint32)
+    return (np.asarray(x32, dtype=np.uint64) ^ D).astype(np.uint32)
+
+
+def unshifted_x32(problem, ks=None) -> np.ndarray:
+    """The rule's points before any shift (O1, O2 or O10)."""
+    if problem.kind == POLY_LATTICE:
+        return poly_lattice_x32(problem.m, problem.w, problem.z, None, ks)
+    if problem.kind == LATTICE:
+        return lattice_x32(problem.m, problem.w, problem.z, None, ks)
+    return net_x32(problem.m, problem.w, problem.C, None, ks)
+
+
+def shifted_rows(problem, ks):
+    """(r, X) for every shift r (reduced MC: every replica) of the rows ks, X the transformed
+    points (O4): the unshifted points of the rows are formed once and each shift is applied to
+    them (O3)."""
+    if problem.kind == REDUCED_MC:
+        for r in range(problem.R_eff):
+            yield r, transform(mc_x32(problem.m, problem.w, problem.y[r], ks), problem.transform)
+        return
+    base = unshifted_x32(problem, ks)
+    for r in range(problem.R_eff):
+        x32 = base if problem.shifts is None else apply_shift(problem.kind, base, problem.shifts[r])
+        yield r, transform(x32, problem.transform)
+
 
 def x32_points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
     if problem.kind == REDUCED_MC:
@@ -338,31 +368,30 @@ def integrand_grad(f_kind: int, params, Y: np.ndarray) -> np.ndarray:
 # ----------------------------------------------------------------------------- O6/O7 estimate and gradient
 
 def estimate(problem, chunk: int = 1 << 16):
-    """Per-shift Q_N(f) (eq. (2)) and their mean; R = 0 counts as one unshifted rule."""
+    """Per-shift Q_N(f) (eq. (2)) and their mean; R = 0 counts as one unshifted rule.  Each shift's
+    sum over the rows is taken chunk by chunk in increasing row order."""
     Q = np.zeros(problem.R_eff)
-    for r in range(problem.R_eff):
-        acc = 0.0
-        for ks in row_chunks(problem.N, chunk):
-            acc += integrand(problem.f_kind, problem.f_params, reduced_matmul(problem, r, ks)).sum()
-        Q[r] = acc / problem.N
+    for ks in row_chunks(problem.N, chunk):
+        for r, X in shifted_rows(problem, ks):
+            Q[r] += integrand(problem.f_kind, problem.f_params, product(X, problem.A)).sum()
+    Q /= problem.N
     return Q, Q.mean()
 
 
 def grad(problem, chunk: int = 1 << 16) -> np.ndarray:
     """d(mean_r Q_r)/dA = (1/(R N)) sum_r X_r^T grad f(X_r A)."""
     G = np.zeros((problem.s, problem.tau))
-    for r in range(problem.R_eff):
-        for ks in row_chunks(problem.N, chunk):
-            X = points(problem, r, ks)
+    for ks in row_chunks(problem.N, chunk):
+        for r, X in shifted_rows(problem, ks):
             G += X.T @ integrand_grad(problem.f_kind, problem.f_params, product(X, problem.A))
     return G / (problem.R_eff * problem.N)
 
 
 def estimate_with_A(problem, A: np.ndarray, chunk: int = 1 << 16) -> float:
     Q = 0.0
-    for r in range(problem.R_eff):
-        for ks in row_chunks(problem.N, chunk):
-            Q += integrand(problem.f_kind, problem.f_params, product(points(problem, r, ks), A)).sum()
+    for ks in row_chunks(problem.N, chunk):
+        for r, X in shifted_rows(problem, ks):
+            Q += integrand(problem.f_kind, problem.f_params, product(X, A)).sum()
     return Q / (problem.R_eff * problem.N)
 
 
@@ -376,3 +405,45 @@ def fd_grad(problem, pairs: np.ndarray, h: float) -> np.ndarray:
         Am = A.copy(); Am[j, t] -= h
         out[i] = (estimate_with_A(problem, Ap) - estimate_with_A(problem, Am)) / (2.0 * h)
     return out
+
+
+# ----------------------------------------------------------------------------- O8 in one pass over the rows
+
+def separable(f_kind: int, params, tau: int):
+    """The integrands as f(y) = g(u), u = sum_t h(y_t) (row-separable).  Returns (h, g), where h
+    and g also take the row's shift M (used by log-sum-exp only: h = exp(y - M), g = M + log u,
+    the same value for any M)."""
+    c, K = params[0], params[1]
+    if f_kind == F_LINEAR_MEAN:
+        return (lambda y, M: y), (lambda u, M: u / tau)
+    if f_kind == F_MEAN_COS:
+        return (lambda y, M: np.cos(y)), (lambda u, M: u / tau)
+    if f_kind == F_CALL_MEAN_EXP:
+        return (lambda y, M: np.exp(c * y)), (lambda u, M: np.maximum(u / tau - K, 0.0))
+    if f_kind == F_GAUSS_NORM2:
+        return (lambda y, M: y * y), (lambda u, M: np.exp(-u / (2.0 * tau)))
+    if f_kind == F_PDE_INV_SQ:
+        return (lambda y, M: 1.0 / (1.0 + c * y) ** 2), (lambda u, M: u / tau)
+    if f_kind == F_LOGSUMEXP:
+        return (lambda y, M: np.exp(y - M)), (lambda u, M: M + np.log(u))
+    raise ValueError(f_kind)
+
+
+def fd_grad_rows(problem, pairs: np.ndarray, h: float, chunk: int = 1 << 16) -> np.ndarray:
+    """O8 without re-evaluating the estimate: moving A_jt by +-h moves only entry t of every
+    y_k = x_k^T A, by +-h x_kj, so with f = g(u), u_k = sum_t h(y_kt), the perturbed row values are
+    g(u_k - h(y_kt) + h(y_kt +- h x_kj)).  Returns (1/(2 h R N)) sum_r sum_k (f_k^+ - f_k^-) for
+    every (j, t) in pairs: the same central differences as fd_grad, in one pass over the rows."""
+    A = np.asarray(problem.A, dtype=np.float64)
+    hf, gf = separable(problem.f_kind, problem.f_params, problem.tau)
+    acc = np.zeros(len(pairs))
+    for ks in row_chunks(problem.N, chunk):
+        for r, X in shifted_rows(problem, ks):
+            Y = product(X, A)
+            M = Y.max(axis=1) if problem.f_kind == F_LOGSUMEXP else np.zeros(len(ks))
+            u = hf(Y, M[:, None]).sum(axis=1)
+            for i, (j, t) in enumerate(pairs):
+                y, d = Y[:, t], h * X[:, j]
+                rest = u - hf(y, M)
+                acc[i] += (gf(rest + hf(y + d, M), M) - gf(rest + hf(y - d, M), M)).sum()
+    return acc / (2.0 * h * problem.R_eff * problem.N)

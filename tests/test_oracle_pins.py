@@ -335,6 +335,34 @@ def test_p6_oracle_gradient_matches_central_differences(f_kind, params):
     assert np.allclose(fd, want, rtol=2e-7, atol=1e-10)
 
 
+@pytest.mark.parametrize("f_kind,params", FKINDS)
+def test_separable_form_is_the_integrand(f_kind, params):
+    """f(y) = g(sum_t h(y_t)) for every integrand (log-sum-exp for any row shift M)."""
+    g = np.random.default_rng(13)
+    Y = g.standard_normal((6, 9)) * 0.8
+    hf, gf = O.separable(f_kind, params, Y.shape[1])
+    for M in (np.zeros(6), Y.max(axis=1), np.full(6, -2.5)):
+        got = gf(hf(Y, M[:, None]).sum(axis=1), M)
+        assert np.allclose(got, O.integrand(f_kind, params, Y), rtol=1e-13, atol=1e-15)
+
+
+@pytest.mark.parametrize("f_kind,params", FKINDS[1:])
+@pytest.mark.parametrize("kind", [I.LATTICE, I.DIGITAL_NET, I.REDUCED_MC])
+def test_o8_one_pass_differences_match_reevaluation(kind, f_kind, params):
+    """O8 in one pass over the rows (only entry t of every y_k moves with A_jt) gives the central
+    differences of the full re-evaluation, and both match the analytic gradient to O(h^2)."""
+    p = I.random_problem(6, kind=kind, m=6, s=9, tau=5, R=3, transform=I.T_CENTER if kind != I.REDUCED_MC
+                         else I.T_IDENTITY, f_kind=f_kind, f_params=params, a_scale=0.4)
+    pairs = np.array([(j, t) for j in range(9) for t in range(5)])
+    h = 1e-5 * np.abs(p.A).max()
+    rows = O.fd_grad_rows(p, pairs, h)
+    full = O.fd_grad(p, pairs, h)
+    scale = np.abs(full).max()
+    assert np.all(np.abs(rows - full) <= 1e-8 * scale)
+    G = O.grad(p)
+    assert np.allclose(rows, [G[j, t] for j, t in pairs], rtol=2e-7, atol=1e-9 * scale)
+
+
 def test_p7_gaussian_expectation_closed_form():
     """Sec. 1: E[mean_t exp(0.2 y_t)] with y = L x, x ~ N(0, I) equals
     mean_t exp(0.02 Sigma_tt); the shifted, inverse-normal reduced lattice must
