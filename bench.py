@@ -1,16 +1,20 @@
 """Benchmark of the reduced QMC matrix-vector product on one GB300 (or N replicas).
 
-A step is one pass of the whole hot path over the Gaussian-expectation workload
-(reduced rank-1 lattice, b=2, m=16 -> N=65536, s=tau=512, w_j=min(floor(log2(j+1)),10),
-one random shift, inverse-normal transform, A=L^T of the exp(-|t_i-t_j|/0.1) covariance,
-f=max(mean_t exp(0.2 y_t)-1,0)): point generation, transform, coarse block products, the
-fused periodic broadcast-accumulate with f and the mean, and the folded adjoint dQ/dA.
+A step is one pass of the whole hot path over the reduced digital-net workload (b=2, m=20 ->
+N=1048576 points, s=tau=1024, w_j=min(floor(log2(j+1)),12), C_j=[[B_j,0],[0,0]] with B_j a
+random nonsingular GF(2) block, A ~ N(0,1/s) in FP32, 16 random 32-bit digital shifts,
+f(y)=exp(-|y|^2/(2 tau))): point generation and shifts, the coarse block products on the
+distinct rows, the periodic broadcast-accumulate fused with f and the mean, and the folded
+adjoint dQ/dA, for all 16 shifts in one call each.
 Metric: x_k^T A outputs per second, N*tau*R / step time.  The headline tier is the split
-tier (bf16x6 tensor-core coarse block products, FP32 elsewhere); the FP32 and plain-bf16
-tiers are timed beside it.
+tier (bf16x6 tensor-core block products, FP32 elsewhere); the FP32 and plain-bf16 tiers are
+timed beside it, with the dense X*A on the same GPU (FP32, BF16 and the three-product split
+BF16 GEMMs of torch) and the oracle on the host cores.  The Gaussian-expectation lattice
+(m=16, s=tau=512) and the adjoint lattice (m=20, s=tau=1024, R=8, log-sum-exp) are timed as
+extra keys.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--precision split|fp32|bf16]
+                    [--precision split|fp32|bf16] [--workload net20|gauss16|adjoint20|basket]
 """
 from __future__ import annotations
 
@@ -33,12 +37,12 @@ sys.path.insert(0, ROOT)
 METRIC = "x_k^T A products/sec (N*tau/s) vs dense X*A on same GB300, at stated rel. error"
 L2_FLUSH_BYTES = 512 << 20        # > 129 MB L2
 SM_COUNT = 152
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of a kernel on this workload, from the
-# ncu captures summarised under profiles/ (cold cache); a kernel missing here has changed since
-# its counters were taken and reports traffic null
-TRAFFIC_BYTES = {"k_fine_bwd_s4": 10012928, "k_fine_fwd_s4": 9484544, "k_coarse_grad_tc": 17909248,
-                 "k_coarse_fwd_tc": 2355712}
 TIERS = ("split", "fp32", "bf16")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled to the contract workload from
+# the ncu captures summarised under profiles/ (workload name, kernel name); a kernel missing
+# here has changed since its counters were taken and reports traffic null
+TRAFFIC_BYTES = {}
 
 
 def parse():
@@ -50,10 +54,54 @@ def parse():
     ap.add_argument("--precision", choices=list(TIERS), default="split")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense X*A comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--workload", choices=["c2", "c3", "c5", "basket"], default="c2",
-                    help="c2: the contract line (default); c3, c5, basket: a timing line for a larger "
-                         "workload (graph-replayed step, per-kernel trace), not the contract line")
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="net20",
+                    help="net20: the contract line (default); the others time one workload alone")
     return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- workloads
+
+def _basket():
+    from paper_2305_11645_gb300 import inputs as I
+    m, s = 25, 10
+    sig, rho, S0, K = 0.4, 0.2, 100.0, 110.0
+    Sig = np.diag([sig] * s) + np.diag([rho] * (s - 1), 1) + np.diag([rho] * (s - 1), -1)
+    A = np.linalg.cholesky(Sig).T.astype(np.float32)
+    w = np.array([min(int(math.floor(math.log2(j))), m) for j in range(1, s + 1)], dtype=np.uint32)
+    y = I.mc_samples(I.rng(6, I.P_MISC), m, w, 1, force_odd=True)
+    return I.Problem(I.REDUCED_MC, m, w, A, y=y, transform=I.T_INV_NORMAL, f_kind=I.F_CALL_MEAN_EXP,
+                     f_params=(1.0, K / S0 * math.exp(sig / 2), 0, 0), name="basket")
+
+
+def _make(name):
+    from paper_2305_11645_gb300 import inputs as I
+    return {"net20": I.c3, "gauss16": lambda: I.c2(dtype=np.float32), "adjoint20": I.c5, "basket": _basket}[name]()
+
+
+# name -> (step includes the adjoint, golden key, description)
+WORKLOADS = {
+    "net20": (True, "c3", "reduced periodic digital net b=2 m=20 (N=1048576), s=tau=1024, "
+                          "w_j=min(floor(log2(j+1)),12), C_j=[[B_j,0],[0,0]] (B_j random nonsingular over GF(2)), "
+                          "A~N(0,1/s) FP32, R=16 random 32-bit digital shifts, f=exp(-|y|^2/(2 tau)); "
+                          "estimate + adjoint dQ/dA"),
+    "gauss16": (True, None, "Gaussian expectation: reduced rank-1 lattice b=2 m=16 (N=65536), s=tau=512, "
+                            "w_j=min(floor(log2(j+1)),10), 1 odd 32-bit shift, inverse-normal transform, A=L^T "
+                            "(exp covariance), f=max(mean exp(0.2y)-1,0); estimate + adjoint"),
+    "adjoint20": (True, "c5", "reduced rank-1 lattice b=2 m=20 (N=1048576), s=tau=1024, "
+                              "w_j=min(floor(log2(j+1)),12), A~N(0,1/s) FP32, R=8 shifts, f=log sum exp(y); "
+                              "estimate + adjoint"),
+    "basket": (False, None, "basket option by reduced Monte Carlo: m=25 (N=33554432), s=tau=10, "
+                            "w_j=floor(log2 j) (1-based), tridiagonal Sigma (0.4, 0.2), K=110, one replica; estimate"),
+}
+
+
+def golden(key):
+    """The oracle's stored full-size values (written by tests/golden/make_full_size.py), or None."""
+    if key is None or not os.path.exists(GOLDEN):
+        return None
+    with open(GOLDEN) as fh:
+        return json.load(fh).get(key)
 
 
 # ----------------------------------------------------------------------------- distributed (replicas)
@@ -137,12 +185,7 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ----------------------------------------------------------------------------- workload
-
-def workload():
-    from paper_2305_11645_gb300 import inputs as I
-    return I.c2(dtype=np.float32)
-
+# ----------------------------------------------------------------------------- work models
 
 def band_of(p):
     """Fine band the library's planner picks for this rule (JF levels expanded per root)."""
@@ -158,33 +201,37 @@ def band_of(p):
     return jf, tau_I, chain
 
 
-H_OPS = {1: (0, 0), 2: (1, 1), 3: (1, 1), 4: (1, 0), 5: (3, 1), 6: (1, 1)}   # (fp32 ops, mufu ops) per h(y)
+# FP32-pipe operations (an FMA counts once) and MUFU operations of h(y) per output, with the
+# row accumulation: linear u += v; cos: MUFU cos, add; call: MUFU ex2, add; Gaussian norm:
+# u = fma(v, v, u); inverse square: fma(c, v, 1), MUFU rcp, fma(r, r, u); log-sum-exp: the
+# difference to the running maximum, MUFU ex2, the select/fma and the maximum
+H_OPS = {1: (1, 0), 2: (1, 1), 3: (1, 1), 4: (1, 0), 5: (2, 1), 6: (3, 1)}
 # MUFU (ex2, sin, cos, rcp) lanes per SM per clock: ncu's peak for the XU pipe is one warp
 # instruction per 4 cycles per SM sub-partition (measured: an ex2 loop reaches 27.6 per clock)
 MUFU_LANES = 32
 
 
 def fine_work(p, name):
-    """Algorithmic work of one launch of the fine-band (S4) kernel, counted per output of all
-    shifts: the tree's multiply-adds sum_{I<4} tau_I 2^-I (4 for a full band), h(y) and the row
+    """Algorithmic work of the fine-band (S4) kernels per step, counted per output of all shifts:
+    the tree's multiply-adds sum_{I<4} tau_I 2^-I (4 for a full band) and h(y) with the row
     accumulation (forward); the recomputed tree, G = coef h'(y) (h' and a multiply), the fold
-    (one add per output amortised) and the gradient multiply-adds (adjoint).  Returns (FP32
-    pipe operations, an FMA counted once, MUFU operations)."""
+    (one add per output amortised) and the gradient multiply-adds (adjoint: twice the tree).
+    Returns (FP32 pipe operations, MUFU operations)."""
     jf, tau_I, _ = band_of(p)
     outs = p.N * p.tau * p.R_eff
     fma = sum(tau_I[I] / 2.0 ** I for I in range(jf))
     fp_h, mufu_h = H_OPS[p.f_kind]
-    per = (fma + fp_h + 1) if "fwd" in name else (2 * fma + fp_h + 2)
+    per = (fma + fp_h) if "fwd" in name else (2 * fma + fp_h + 2)
     return outs * per, outs * mufu_h
 
 
 def coarse_mma_flops(p, pieces):
-    """MMA flops of a coarse block-product launch (forward X_I A_I or adjoint X_I^T F_I, the
-    same contraction sizes): 2 n_I tau tau_I per level I >= 4 (n_I = 2^(m-I) distinct rows),
-    times the piece products (6 in the split tier, 1 in the bf16 tier)."""
+    """MMA flops of the coarse block products of one step (forward X_I A_I or adjoint X_I^T F_I, the
+    same contraction sizes): 2 n_I tau tau_I per coarse level I (n_I = 2^(m-I) distinct rows), for
+    every shift, times the piece products (6 in the split tier, 1 in the bf16 tier)."""
     jf, tau_I, chain = band_of(p)
     np_ = 6 if pieces == 3 else 1
-    return sum(2.0 * 2 ** (p.m - I) * p.tau * tau_I[I] for I in chain if I < p.m + 1) * p.R_eff * np_
+    return sum(2.0 * 2 ** (p.m - I) * p.tau * tau_I[I] for I in chain) * p.R_eff * np_
 
 
 def tensor_roofline(flops, seconds, peak_tflops):
@@ -198,7 +245,8 @@ def peaks():
             mp = json.load(fh)
         return mp, "measured"
     except OSError:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
 
 
 def alu_roofline(fp32_ops, mufu_ops, seconds, clock_mhz):
@@ -215,6 +263,98 @@ def alu_roofline(fp32_ops, mufu_ops, seconds, clock_mhz):
             "unit": "Gop/s", "frac": t_fp32 / seconds}
 
 
+def roofline_of(p, prec, name, ms_per_step, launches_per_step, clk, mp, peak_src):
+    """Roofline of one kernel from its device time per step (the sum over its launches; its
+    algorithmic work per step is the sum over the same launches)."""
+    sec = ms_per_step / 1e3
+    if name.endswith("_tc"):
+        fl = coarse_mma_flops(p, 3 if prec == "split" else 1)
+        r = tensor_roofline(fl, sec, mp["bf16_tflops_sustained"])
+        r["peak_source"] = (f"{peak_src} dense bf16 sustained peak (MEASURED_PEAKS.json bf16_tflops_sustained: "
+                            f"the kernel runs inside a long step)")
+        r["work"] = {"mma_flops_per_step": fl}
+    else:
+        w32, wmu = fine_work(p, name)
+        r = alu_roofline(w32, wmu, sec, clk)
+        r["peak_source"] = (f"derived: {SM_COUNT} SMs x pipe lanes (FP32 128, MUFU {MUFU_LANES}) x median SM "
+                            f"clock {clk:.0f} MHz sampled during the timed region")
+        r["work"] = {"fp32_ops_per_step": w32, "mufu_ops_per_step": wmu}
+    r.update({"kernel": name, "ms_per_step": ms_per_step, "launches_per_step": launches_per_step,
+              "traffic": TRAFFIC_BYTES.get(name)})
+    return r
+
+
+# ----------------------------------------------------------------------------- timing helpers
+
+class Timer:
+    """CUDA-event timing of a step on the launching stream, with L2 flushed before every step."""
+
+    def __init__(self, dev, dist):
+        self.dev, self.dist = dev, dist
+        self.stream = torch.cuda.current_stream(dev)
+        self.flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def run(self, fn, steps, trace=False, prequeue=False):
+        from paper_2305_11645_gb300 import _lib as L
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(self.dist)
+        torch.cuda.synchronize()
+        if trace:
+            L.trace_enable(True)
+        for a, b in evs:
+            self.flush.zero_()
+            if prequeue:
+                torch.cuda._sleep(3_000_000)    # the host queues the whole step before the GPU reaches it
+            a.record(self.stream)
+            fn()
+            b.record(self.stream)
+        torch.cuda.synchronize()
+        barrier(self.dist)
+        kern = None
+        if trace:
+            L.trace_enable(False)
+            kern = L.trace_collect()
+        return [a.elapsed_time(b) for a, b in evs], kern
+
+
+def measure(p, prec, backward, timer, steps, warmup):
+    """The graph-replayed step of one workload: mean ms, and the per-kernel device times of the same
+    steps launched eagerly with the library's kernel trace."""
+    from paper_2305_11645_gb300 import api
+    dev = timer.dev
+    rule = api.Rule.from_problem(p)
+    A = torch.from_numpy(np.ascontiguousarray(p.A)).to(dev)
+    f = api.Integrand(p.f_kind, p.f_params)
+    integ = api.Integrator(rule, A, f, backward=backward, graph=True, precision=prec)
+    eager = api.Integrator(rule, A, f, backward=backward, graph=False, precision=prec)
+    for _ in range(warmup):
+        integ.run()
+        eager.run()
+    torch.cuda.synchronize()
+    times, _ = timer.run(integ.run, steps)
+    _, kern = timer.run(eager.run, steps, trace=True, prequeue=True)
+    del eager
+    kernels = {k: {"launches_per_step": c / steps, "ms_per_step": t / steps} for k, (c, t) in sorted(kern.items())}
+    return integ, statistics.mean(times), kernels, sum(c for c, _ in kern.values()) / steps
+
+
+def accuracy(key, p, est, grad, tier):
+    """Errors against the oracle's stored full-size values: the mean estimate (relative) and, where
+    stored, the gradient (max-norm relative)."""
+    g = golden(key)
+    if g is None:
+        return {"estimate": float(est[-1]), "oracle": None}
+    e = est.cpu().numpy()
+    out = {"estimate": float(e[-1]), "oracle_estimate": g["mean"],
+           "estimate_rel_err": abs(float(e[-1]) - g["mean"]) / abs(g["mean"]),
+           "per_shift_max_rel_err": float(np.max(np.abs(e[:-1] - np.array(g["Q"])) / np.abs(np.array(g["Q"]))))}
+    if grad is not None and g.get("grad_file"):
+        G = np.load(os.path.join(os.path.dirname(GOLDEN), g["grad_file"])).astype(np.float64)
+        out["grad_rel_err"] = float(np.max(np.abs(grad.double().cpu().numpy() - G)) / np.max(np.abs(G)))
+    out["tolerance"] = {"split": 1e-6, "fp32": 2e-5, "bf16": 2e-3}[tier]
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def run_ours(args, dist, rank, world):
@@ -225,256 +365,289 @@ def run_ours(args, dist, rank, world):
         B.build()
     barrier(dist)
     dev = torch.device("cuda", torch.cuda.current_device())
-    p = workload()
-    rule = api.Rule.from_problem(p)
-    f = api.Integrand(p.f_kind, p.f_params)
-    A = torch.from_numpy(p.A).to(dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-    # the step as a user runs it repeatedly: one CUDA graph of the forward and backward launches
+    timer = Timer(dev, dist)
+    name = args.workload
+    backward, gkey, desc = WORKLOADS[name]
+    p = _make(name)
     prec = args.precision
-    integ = api.Integrator(rule, A, f, backward=True, graph=True, precision=prec)
-    eager = api.Integrator(rule, A, f, backward=True, graph=False, precision=prec)
-    others = {t: api.Integrator(rule, A, f, backward=True, graph=True, precision=t) for t in TIERS if t != prec}
-    step = integ.run
+    outputs = p.N * p.tau * p.R_eff
 
-    for _ in range(args.warmup):
-        step()
-        eager.run()
-        for o in others.values():
-            o.run()
-    torch.cuda.synchronize()
-
-    def timed(fn, trace=False, prequeue=False):
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        barrier(dist)
-        torch.cuda.synchronize()
-        if trace:
-            L.trace_enable(True)
-        for a, b in evs:
-            flush.zero_()
-            if prequeue:
-                torch.cuda._sleep(3_000_000)    # the host queues the whole step before the GPU reaches it
-            a.record(stream)
-            fn()
-            b.record(stream)
-        torch.cuda.synchronize()
-        barrier(dist)
-        kern = None
-        if trace:
-            L.trace_enable(False)
-            kern = L.trace_collect()
-        return [a.elapsed_time(b) for a, b in evs], kern
-
+    # the contract step: one CUDA graph of the forward and backward launches (api.Integrator)
     clocks = ClockSampler(dev.index)
     clocks.start()
     time.sleep(0.3)
-    times, _ = timed(step)
+    integ, ms, kernels, launches = measure(p, prec, backward, timer, args.steps, args.warmup)
     clock_info = clocks.stop()
-    ms = statistics.mean(times)
     ms_max = max_over_ranks(dist, ms)
-    outputs = p.N * p.tau * p.R_eff
     value = world * outputs / (ms_max / 1e3)
-    eager_ms = statistics.mean(timed(eager.run)[0])
-    tier_ms = {prec: ms}
-    for t, o in others.items():
-        tier_ms[t] = statistics.mean(timed(o.run)[0])
+    est, grad = integ.run()
+    torch.cuda.synchronize()
 
-    # the same steps launched eagerly with the library's per-kernel events, the stream pre-queued
-    # so each pair of events brackets device time only (roofline of the dominant kernel)
-    ttimes, kern = timed(eager.run, trace=True, prequeue=True)
-    launches = sum(c for c, _ in kern.values())
-    top = max(kern.items(), key=lambda kv: kv[1][1])
     mp, peak_src = peaks()
     clk = clock_info["sm_mhz"] or mp.get("sm_max_mhz", 2070.0)
-    name, (cnt, tot) = top
-    per_launch = tot / cnt / 1e3
-    if name.endswith("_tc"):
-        fl = coarse_mma_flops(p, 3 if prec == "split" else 1)
-        roof = tensor_roofline(fl, per_launch, mp["bf16_tflops"])
-        roof["peak_source"] = f"{peak_src} dense bf16 burst peak (MEASURED_PEAKS.json bf16_tflops)"
-        roof["work"] = {"mma_flops": fl}
-    else:
-        w32, wmu = fine_work(p, name)
-        roof = alu_roofline(w32, wmu, per_launch, clk)
-        roof["peak_source"] = (f"derived: {SM_COUNT} SMs x pipe lanes (FP32 128, MUFU {MUFU_LANES}) x median SM "
-                               f"clock {clk:.0f} MHz sampled during the timed region")
-        roof["work"] = {"fp32_ops": w32, "mufu_ops": wmu}
-    roof.update({"kernel": name, "launch_ms": per_launch * 1e3, "traffic": TRAFFIC_BYTES.get(name)})
-    kernels = {k: {"launches": c, "ms_per_step": t / args.steps} for k, (c, t) in sorted(kern.items())}
-
-    # the materialised product P = X A of the same workload and tier (qmc_reduced_matmul): its
-    # band kernel is bound by the output writes, 4 bytes per output (the root values and the
-    # point table it reads are under 5 % of that)
-    mws = torch.empty(max(api.workspace_size(L.QMC_OP_REDUCED_MATMUL, [rule], [p.tau], None,
-                                             api._precision(A, prec)), 256), dtype=torch.uint8, device=dev)
-
-    def materialize():
-        api.reduced_matmul(rule, A, ws=mws, precision=prec)
-
-    for _ in range(3):
-        materialize()
-    mat_ms = statistics.mean(timed(materialize)[0])
-    _, mkern = timed(materialize, trace=True, prequeue=True)
-    out_bytes = outputs * 4
-    materialized = {"op": "qmc_reduced_matmul (P = X A, R x N x tau float32)", "ms_per_call": mat_ms,
-                    "value": outputs / (mat_ms / 1e3), "unit": "outputs/s",
-                    "kernels": {k: {"launches": c, "ms_per_call": t / args.steps} for k, (c, t) in sorted(mkern.items())}}
-    band = "k_fine_mat_s4" if "k_fine_mat_s4" in mkern else "k_fine_fwd_materialize"
-    if band in mkern:
-        cnt, tot = mkern[band]
-        sec = tot / cnt / 1e3
-        materialized["roofline"] = {"bound": "hbm", "kernel": band, "achieved": out_bytes / sec / 1e9,
-                                    "peak": mp["hbm_gbs"], "unit": "GB/s", "frac": out_bytes / sec / 1e9 / mp["hbm_gbs"],
-                                    "bytes_per_launch": out_bytes, "launch_ms": sec * 1e3, "traffic": None,
-                                    "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
-    del mws
+    top = max(kernels.items(), key=lambda kv: kv[1]["ms_per_step"])
+    roof = roofline_of(p, prec, top[0], top[1]["ms_per_step"], top[1]["launches_per_step"], clk, mp, peak_src)
+    kernel_total = sum(k["ms_per_step"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = k["ms_per_step"] / kernel_total
+    # every kernel's roofline fraction, and the whole step's: the ALU, tensor and MUFU work of the
+    # step at full rate against the graph-replayed step time
+    per_kernel = {}
+    for k, v in kernels.items():
+        if k.startswith("k_fine_") and "mat" not in k:
+            per_kernel[k] = roofline_of(p, prec, k, v["ms_per_step"], v["launches_per_step"], clk, mp, peak_src)["frac"]
+        elif k.endswith("_tc"):
+            per_kernel[k] = roofline_of(p, prec, k, v["ms_per_step"], v["launches_per_step"], clk, mp, peak_src)["frac"]
+    roof["per_kernel_frac"] = per_kernel
 
     # end to end through the public API with host buffers: H2D of A, D2H of the estimates and dQ/dA
-    A_host = torch.from_numpy(p.A).pin_memory()
+    A_host = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()
     est_host = torch.empty(p.R_eff + 1, dtype=torch.float64).pin_memory()
     grad_host = torch.empty(p.A.shape, dtype=torch.float32).pin_memory()
 
     def e2e_step():
         integ.A.copy_(A_host, non_blocking=True)
-        est, grad = integ.run()
-        est_host.copy_(est, non_blocking=True)
-        grad_host.copy_(grad, non_blocking=True)
+        e, g = integ.run()
+        est_host.copy_(e, non_blocking=True)
+        if backward:
+            grad_host.copy_(g, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
 
     for _ in range(2):
         e2e_step()
-    etimes, _ = timed(e2e_step)
+    etimes, _ = timer.run(e2e_step, args.steps)
     e_ms = max_over_ranks(dist, statistics.mean(etimes))
     e2e = {"value": world * outputs / (e_ms / 1e3), "unit": "outputs/s", "ms_per_step": e_ms,
            "h2d_bytes_per_step": int(A_host.numel() * 4),
-           "d2h_bytes_per_step": int(est_host.numel() * 8 + grad_host.numel() * 4)}
+           "d2h_bytes_per_step": int(est_host.numel() * 8 + (grad_host.numel() * 4 if backward else 0))}
 
     result = {"metric": METRIC, "value": value, "unit": "outputs/s", "n_gpus": world, "steps": args.steps,
               "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
               "vs_baseline": None, "dtype": {"split": "bf16x6+f32", "fp32": "f32", "bf16": "bf16+f32"}[prec],
               "data": "synthetic",
-              "config": {"workload": "c2 Gaussian expectation: reduced rank-1 lattice b=2 m=16 (N=65536), "
-                                     "s=tau=512, w_j=min(floor(log2(j+1)),10), 1 odd 32-bit shift, inverse-normal "
-                                     "transform, A=L^T (exp covariance), f=max(mean exp(0.2y)-1,0)",
-                         "N": p.N, "s": p.s, "tau": p.tau, "R": p.R_eff, "precision": prec,
-                         "step": "qmc_integrate + qmc_integrate_backward (reuse forward workspace), "
-                                 "replayed as one CUDA graph (api.Integrator)",
+              "config": {"workload": desc, "name": name, "N": p.N, "s": p.s, "tau": p.tau, "R": p.R_eff,
+                         "outputs_per_step": outputs, "precision": prec,
+                         "step": ("qmc_integrate + qmc_integrate_backward (reusing the forward's workspace)"
+                                  if backward else "qmc_integrate") + ", replayed as one CUDA graph (api.Integrator)",
                          "l2": "flushed before every timed step (512 MiB write, untimed)",
                          "parallelism": "replicas" if world > 1 else "single"},
-              "eager_ms_per_step": eager_ms,
-              "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clock_info,
-              "kernels": kernels, "materialized": materialized, "peaks": peak_src}
+              "roofline": roof, "e2e": e2e, "gpu_launches": int(round(launches * args.steps)), "clocks": clock_info,
+              "kernels": kernels, "peaks": peak_src}
+    del integ
+    torch.cuda.empty_cache()
 
-    est, grad = step()
-    torch.cuda.synchronize()
     if rank == 0:
-        result["accuracy"] = accuracy(p, est, grad, args, prec)
-        tiers = {}
+        result["accuracy"] = accuracy(gkey, p, est, grad if backward else None, prec)
+        tiers = {prec: {"ms_per_step": ms, "value": outputs / (ms / 1e3), **result["accuracy"]}}
         for t in TIERS:
-            e_t, g_t = (est, grad) if t == prec else others[t].run()
+            if t == prec:
+                continue
+            it, t_ms, t_k, _ = measure(p, t, backward, timer, max(3, args.steps // 2), 2)
+            e_t, g_t = it.run()
             torch.cuda.synchronize()
-            tiers[t] = {"ms_per_step": tier_ms[t], "value": outputs / (tier_ms[t] / 1e3),
-                        **accuracy(p, e_t, g_t, args, t)}
+            tiers[t] = {"ms_per_step": t_ms, "value": outputs / (t_ms / 1e3),
+                        "kernels": {k: v["ms_per_step"] for k, v in t_k.items()},
+                        **accuracy(gkey, p, e_t, g_t if backward else None, t)}
+            del it
+            torch.cuda.empty_cache()
         result["tiers"] = tiers
+        result["materialized"] = materialized_product(p, prec, timer, args)
         if not args.no_dense:
-            result["dense_xa"] = dense_baseline(p, rule, A, args, flush, stream)
+            result["dense_xa"] = dense_baseline(p, gkey, backward, timer, args)
+        if not args.no_extra:
+            extra = {}
+            for nm in ("gauss16", "adjoint20"):
+                if nm == name:
+                    continue
+                q = _make(nm)
+                bw, gk, d = WORKLOADS[nm]
+                it, q_ms, q_k, _ = measure(q, prec, bw, timer, max(5, args.steps // 2), 3)
+                e_q, g_q = it.run()
+                torch.cuda.synchronize()
+                extra[nm] = {"workload": d, "ms_per_step": q_ms, "value": q.N * q.tau * q.R_eff / (q_ms / 1e3),
+                             "unit": "outputs/s", "kernels": {k: v["ms_per_step"] for k, v in q_k.items()},
+                             **accuracy(gk, q, e_q, g_q if bw else None, prec)}
+                del it
+                torch.cuda.empty_cache()
+            result["extra_workloads"] = extra
         if not args.no_cpu:
             result["cpu_baseline"] = cpu_baseline(p, budget_s=12.0)
     return result
 
 
-_ORACLE_CACHE = {}
-
-
-def oracle_full(p):
-    if "full" not in _ORACLE_CACHE:
-        from oracle import qmc_oracle as O
-        Q, mean = O.estimate(p)
-        _ORACLE_CACHE["full"] = (mean, O.grad(p))
-    return _ORACLE_CACHE["full"]
-
-
-# stated tolerances on the estimate (relative) and the gradient (max-norm relative) per tier
-TOLERANCE = {"split": (1e-6, 1e-6), "fp32": (2e-5, 2e-5), "bf16": (2e-3, 2e-2)}
-
-
-def accuracy(p, est, grad, args, tier):
-    mean, G = oracle_full(p)
-    e = est.cpu().numpy()[-1]
-    g = grad.double().cpu().numpy()
-    return {"estimate": float(e), "oracle_estimate": float(mean), "estimate_rel_err": float(abs(e - mean) / abs(mean)),
-            "grad_rel_err": float(np.max(np.abs(g - G)) / np.max(np.abs(G))),
-            "tolerance": {"estimate": TOLERANCE[tier][0], "grad": TOLERANCE[tier][1]}}
-
-
-def dense_baseline(p, rule, A, args, flush, stream):
-    """Dense X*A on the same GPU: X materialised once by gen_points (untimed), then per step
-    Y = X A (torch.matmul), f, the mean, and dQ/dA = X^T G -- FP32 (TF32 off) and BF16."""
+def materialized_product(p, prec, timer, args):
+    """The materialised product P = X A of the workload's shape (qmc_reduced_matmul) for its first two
+    shifts (2 x N x tau FP32 outputs): the band kernel is bound by its output writes, 4 bytes per
+    output (the root values and the point table it reads are under 5 % of that)."""
+    from paper_2305_11645_gb300 import _lib as L
     from paper_2305_11645_gb300 import api
-    x32 = api.gen_points(rule, "full", 0, device=A.device).to(torch.int64) & 0xFFFFFFFF
+    from paper_2305_11645_gb300 import inputs as I
+    import dataclasses
+    q = dataclasses.replace(p, shifts=None if p.shifts is None else p.shifts[:2])
+    rule = api.Rule.from_problem(q)
+    A = torch.from_numpy(np.ascontiguousarray(q.A)).to(timer.dev)
+    mws = torch.empty(max(api.workspace_size(L.QMC_OP_REDUCED_MATMUL, [rule], [q.tau], None,
+                                             api._precision(A, prec)), 256), dtype=torch.uint8, device=timer.dev)
+    P = torch.empty((q.R_eff, q.N, q.tau), dtype=torch.float32, device=timer.dev)
+
+    def call():
+        api.reduced_matmul(rule, A, ws=mws, precision=prec, out=P)
+
+    for _ in range(3):
+        call()
+    steps = max(3, args.steps // 2)
+    ms = statistics.mean(timer.run(call, steps)[0])
+    _, kern = timer.run(call, steps, trace=True, prequeue=True)
+    outputs = q.N * q.tau * q.R_eff
+    mp, peak_src = peaks()
+    res = {"op": f"qmc_reduced_matmul (P = X A, {q.R_eff} x N x tau float32, the workload's first shifts)",
+           "ms_per_call": ms, "value": outputs / (ms / 1e3), "unit": "outputs/s",
+           "kernels": {k: {"launches": c / steps, "ms_per_call": t / steps} for k, (c, t) in sorted(kern.items())}}
+    band = "k_fine_mat_s4" if "k_fine_mat_s4" in kern else "k_fine_fwd_materialize"
+    if band in kern:
+        cnt, tot = kern[band]
+        sec = tot / cnt / 1e3
+        res["roofline"] = {"bound": "hbm", "kernel": band, "achieved": outputs * 4 / sec / 1e9, "peak": mp["hbm_gbs"],
+                           "unit": "GB/s", "frac": outputs * 4 / sec / 1e9 / mp["hbm_gbs"],
+                           "bytes_per_launch": outputs * 4, "launch_ms": sec * 1e3, "traffic": None,
+                           "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    res["whole_call_hbm_frac"] = outputs * 4 / (ms / 1e3) / 1e9 / mp["hbm_gbs"]
+    del P, mws
+    torch.cuda.empty_cache()
+    return res
+
+
+def torch_integrand(kind, params, Y, tau):
+    """f per row and df/dy of the QMC_F_* integrands, in torch (the dense baseline's epilogue)."""
+    c, K = params[0], params[1]
+    Y = Y.float()
+    if kind == 4:                                             # Gaussian norm
+        fv = torch.exp(-(Y * Y).sum(dim=1) / (2.0 * tau))
+        return fv, -fv[:, None] * Y / tau
+    if kind == 3:                                             # call on the mean exponential
+        E = torch.exp(c * Y)
+        m_ = E.mean(dim=1)
+        return torch.clamp(m_ - K, min=0.0), (c * E / tau) * (m_ > K).float()[:, None]
+    if kind == 6:                                             # log-sum-exp
+        return torch.logsumexp(Y, dim=1), torch.softmax(Y, dim=1)
+    if kind == 5:
+        r = 1.0 / (1.0 + c * Y)
+        return (r * r).mean(dim=1), -2.0 * c * r ** 3 / tau
+    if kind == 2:
+        return torch.cos(Y).mean(dim=1), -torch.sin(Y) / tau
+    return Y.mean(dim=1), torch.full_like(Y, 1.0 / tau)
+
+
+def dense_baseline(p, gkey, backward, timer, args):
+    """Dense X*A on the same GPU for the first shift: X materialised once by gen_points (untimed),
+    then per step Y = X A (torch GEMM), f, the mean and dQ/dA = X^T G, in FP32 (TF32 off), BF16, and
+    the three-product split BF16 of the 1e-6 tier (hi/lo bf16 pieces of X, A and G, products
+    hi*hi + hi*lo + lo*hi accumulated in FP32 by torch.mm(..., out_dtype=float32)).  Outputs per
+    second count the N x tau outputs of one shift."""
+    from paper_2305_11645_gb300 import api
+    dev = timer.dev
+    rule = api.Rule.from_problem(p)
+    x32 = api.gen_points(rule, "full", 0, device=dev).to(torch.int64) & 0xFFFFFFFF
     X = x32.double().mul_(2.0 ** -32)
-    X = torch.special.ndtri(X).float()
-    c, K = p.f_params[0], p.f_params[1]
+    del x32
+    if p.transform == 2:
+        X = torch.special.ndtri(X)
+    elif p.transform == 1:
+        X = X - 0.5
+    X = X.float()
+    A = torch.from_numpy(np.ascontiguousarray(p.A)).to(dev).float()
+    g = golden(gkey)
     out = {}
-    mean, G_or = oracle_full(p)
     prev = torch.backends.cuda.matmul.allow_tf32
     torch.backends.cuda.matmul.allow_tf32 = False
-    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
-        Xd, Ad = X.to(dt), A.to(dt)
 
-        def step():
-            Y = Xd @ Ad
-            E = torch.exp(c * Y.float())
-            m_ = E.mean(dim=1)
-            fval = torch.clamp(m_ - K, min=0.0)
-            est = fval.double().mean()
-            Gm = (c * E / p.tau) * (m_ > K).float()[:, None] / p.N
-            grad = Xd.t() @ Gm.to(dt)
-            return est, grad
+    def split(T):
+        hi = T.to(torch.bfloat16)
+        return hi, (T - hi.float()).to(torch.bfloat16)
+
+    def mm3(a, b):
+        ah, al = a
+        bh, bl = b
+        return (torch.mm(ah, bh, out_dtype=torch.float32) + torch.mm(ah, bl, out_dtype=torch.float32)
+                + torch.mm(al, bh, out_dtype=torch.float32))
+
+    for name in ("fp32", "bf16", "split3_bf16"):
+        if name == "split3_bf16":
+            try:
+                torch.mm(X[:8, :8].to(torch.bfloat16), A[:8, :8].to(torch.bfloat16), out_dtype=torch.float32)
+            except (TypeError, RuntimeError) as e:
+                out[name] = {"unavailable": f"torch.mm(..., out_dtype=float32) on bf16: {type(e).__name__}"}
+                continue
+            Xs, As_ = split(X), split(A)
+            XsT = (Xs[0].t().contiguous(), Xs[1].t().contiguous())
+
+            def step():
+                Y = mm3(Xs, As_)
+                fv, G = torch_integrand(p.f_kind, p.f_params, Y, p.tau)
+                est = fv.double().mean()
+                grad = mm3(XsT, split(G / p.N)) if backward else None
+                return est, grad
+        else:
+            dt = torch.float32 if name == "fp32" else torch.bfloat16
+            Xd, Ad = X.to(dt), A.to(dt)
+            XdT = Xd.t().contiguous()
+
+            def step():
+                Y = Xd @ Ad
+                fv, G = torch_integrand(p.f_kind, p.f_params, Y, p.tau)
+                est = fv.double().mean()
+                grad = (XdT @ (G / p.N).to(dt)) if backward else None
+                return est, grad
 
         for _ in range(3):
             step()
         torch.cuda.synchronize()
         ts = []
-        for _ in range(max(5, args.steps // 2)):
-            flush.zero_()
+        for _ in range(max(5, args.steps // 4)):
+            timer.flush.zero_()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            a.record(timer.stream)
             est, grad = step()
-            b.record(stream)
+            b.record(timer.stream)
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
         ms = statistics.mean(ts)
-        g = grad.double().cpu().numpy()
-        out[name] = {"value": p.N * p.tau / (ms / 1e3), "unit": "outputs/s", "ms_per_step": ms,
-                     "estimate_rel_err": float(abs(est.item() - mean) / abs(mean)),
-                     "grad_rel_err": float(np.max(np.abs(g - G_or)) / np.max(np.abs(G_or)))}
+        res = {"value": p.N * p.tau / (ms / 1e3), "unit": "outputs/s", "ms_per_shift": ms,
+               "estimate_shift0": est.item()}
+        if g is not None:
+            res["estimate_rel_err"] = abs(est.item() - g["Q"][0]) / abs(g["Q"][0])
+        out[name] = res
+        torch.cuda.empty_cache()
     torch.backends.cuda.matmul.allow_tf32 = prev
     return out
 
 
-def cpu_baseline(p, budget_s: float = 12.0, rows: int = None):
-    """The oracle as it stands (numpy FP64: points from the unreduced definition, inverse normal,
-    dense X A, f, X^T grad f) on a bounded sample of the workload's rows."""
+def oracle_sample(p, ks):
+    """The oracle on the rows ks of every shift: points from the definitions, X A, f and X^T grad f."""
     from oracle import qmc_oracle as O
-    rows = rows or 4096
-    ks = np.arange(rows, dtype=np.int64)
-    t0 = time.perf_counter()
-    done = 0
-    while True:
-        X = O.points(p, 0, ks + done % p.N)
+    for r, X in O.shifted_rows(p, ks):
         Y = O.product(X, p.A)
         O.integrand(p.f_kind, p.f_params, Y).sum()
         X.T @ O.integrand_grad(p.f_kind, p.f_params, Y)
+
+
+def cpu_baseline(p, budget_s: float = 12.0, rows: int = 512):
+    """The oracle as it stands (numpy FP64) on a bounded sample of the workload: blocks of rows of
+    every shift, until the time budget is spent."""
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        ks = (np.arange(rows, dtype=np.int64) + done) % p.N
+        oracle_sample(p, ks)
         done += rows
         el = time.perf_counter() - t0
         if el >= budget_s or done >= p.N:
             break
     cores = len(os.sched_getaffinity(0))
-    return {"value": done * p.tau / el, "unit": "outputs/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {p.N} rows of the workload (shift 0), forward estimate terms and X^T grad f, "
-                      f"numpy FP64 (BLAS matmul may use up to {cores} threads, the rest one thread), {el:.1f} s"}
+    return {"value": done * p.tau * p.R_eff / el, "unit": "outputs/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {p.N} rows of the workload for all {p.R_eff} shifts: points from the definitions, "
+                      f"X A, f and X^T grad f in numpy FP64 (BLAS may use up to {cores} threads, the rest one "
+                      f"thread), {el:.1f} s"}
 
 
 # ----------------------------------------------------------------------------- reference arm (the oracle)
@@ -482,16 +655,13 @@ def cpu_baseline(p, budget_s: float = 12.0, rows: int = None):
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    p = workload()
-    rows = 2048
-    from oracle import qmc_oracle as O
+    name = getattr(args, "workload", "net20")
+    p = _make(name)
+    backward, _, desc = WORKLOADS[name]
+    rows = 256
 
     def step(i):
-        ks = (np.arange(rows, dtype=np.int64) + i * rows) % p.N
-        X = O.points(p, 0, ks)
-        Y = O.product(X, p.A)
-        O.integrand(p.f_kind, p.f_params, Y).sum()
-        X.T @ O.integrand_grad(p.f_kind, p.f_params, Y)
+        oracle_sample(p, (np.arange(rows, dtype=np.int64) + i * rows) % p.N)
 
     for i in range(args.warmup):
         step(i)
@@ -501,89 +671,21 @@ def run_reference(args, rank, world):
         step(args.warmup + i)
         ts.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(ts)
-    value = rows * p.tau / (ms / 1e3)
+    value = rows * p.tau * p.R_eff / (ms / 1e3)
     cores = len(os.sched_getaffinity(0))
-    sample = f"{rows} rows of the workload per step (shift 0), numpy FP64 oracle: forward terms and X^T grad f"
+    sample = (f"{rows} rows of the workload per step for all {p.R_eff} shifts, numpy FP64 oracle: points from "
+              f"the definitions, X A, f and X^T grad f")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "outputs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "c2 Gaussian expectation (see ours); bounded row sample per step",
-                       "N": p.N, "s": p.s, "tau": p.tau, "R": p.R_eff, "rows_per_step": rows},
+            "config": {"workload": desc + "; bounded row sample per step", "name": name, "N": p.N, "s": p.s,
+                       "tau": p.tau, "R": p.R_eff, "rows_per_step": rows},
             "cpu_baseline": {"value": value, "unit": "outputs/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "outputs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_workload(args):
-    """A timing line for one of the larger workloads (the c2 contract line is run_ours):
-    the graph-replayed step with L2 flushed before each step (median over the steps), and the
-    library's per-kernel trace of eager steps."""
-    import torch
-    from paper_2305_11645_gb300 import _lib as L
-    from paper_2305_11645_gb300 import api
-    from paper_2305_11645_gb300 import inputs as I
-    prec = args.precision
-    if args.workload == "c3":
-        p, backward, desc = I.c3(), False, ("c3 reduced periodic digital net b=2 m=20 (N=1048576), s=tau=1024, "
-                                            "w_j=min(floor(log2(j+1)),12), 16 XOR shifts, f=exp(-|y|^2/(2 tau)), estimate")
-    elif args.workload == "c5":
-        p, backward, desc = I.c5(), True, ("c5 reduced rank-1 lattice b=2 m=20 (N=1048576), s=tau=1024, "
-                                           "w_j=min(floor(log2(j+1)),12), 8 shifts, f=log sum exp(y), estimate + adjoint")
-    else:
-        m, s = 25, 10
-        sig, rho, S0, K = 0.4, 0.2, 100.0, 110.0
-        Sig = np.diag([sig] * s) + np.diag([rho] * (s - 1), 1) + np.diag([rho] * (s - 1), -1)
-        A = np.linalg.cholesky(Sig).T.astype(np.float32)
-        w = np.array([min(int(math.floor(math.log2(j))), m) for j in range(1, s + 1)], dtype=np.uint32)
-        y = I.mc_samples(I.rng(6, I.P_MISC), m, w, 1, force_odd=True)
-        p = I.Problem(I.REDUCED_MC, m, w, A, y=y, transform=I.T_INV_NORMAL, f_kind=I.F_CALL_MEAN_EXP,
-                      f_params=(1.0, K / S0 * math.exp(sig / 2), 0, 0))
-        backward, desc = False, ("basket option by reduced Monte Carlo: m=25 (N=33554432), s=tau=10, "
-                                 "w_j=floor(log2 j) (1-based), tridiagonal Sigma (0.4, 0.2), K=110, one replica")
-    dev = torch.device("cuda", 0)
-    rule = api.Rule.from_problem(p)
-    A = torch.from_numpy(p.A).to(dev)
-    f = api.Integrand(p.f_kind, p.f_params)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    it = api.Integrator(rule, A, f, backward=backward, graph=True, precision=prec)
-    for _ in range(args.warmup):
-        it.run()
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        it.run()
-        b.record()
-        torch.cuda.synchronize()
-        ts.append(a.elapsed_time(b))
-    eager = api.Integrator(rule, A, f, backward=backward, graph=False, precision=prec)
-    eager.run()
-    torch.cuda.synchronize()
-    L.trace_enable(True)
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda._sleep(3_000_000)        # the host queues the whole step before the GPU reaches it
-        eager.run()
-    torch.cuda.synchronize()
-    kern = L.trace_collect()
-    L.trace_enable(False)
-    L.device_status()
-    ms = float(np.median(ts))
-    outputs = p.N * p.tau * p.R_eff
-    return {"workload": args.workload, "description": desc, "metric": METRIC, "value": outputs / (ms / 1e3),
-            "unit": "outputs/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup, "precision": prec,
-            "backward": backward, "estimate": float(it.est[-1].item()), "data": "synthetic",
-            "l2": "flushed before every timed step (512 MiB write, untimed)",
-            "kernels": {k: {"launches": c // args.steps, "ms_per_step": t / args.steps}
-                        for k, (c, t) in sorted(kern.items())}}
-
-
 def main():
     args = parse()
-    if args.workload != "c2" and args.impl == "ours":
-        print(json.dumps(run_workload(args)))
-        return
     dist, rank, world = dist_setup(args)
     if args.impl == "reference":
         res = run_reference(args, rank, world)

@@ -164,15 +164,21 @@ def gen_points(rule: Rule, layout: str = "full", shift_idx: int = 0, device="cud
 
 
 def reduced_matmul(rule: Rule, A: torch.Tensor, ws: Optional[torch.Tensor] = None,
-                   precision: Optional[str] = None) -> torch.Tensor:
+                   precision: Optional[str] = None, out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """P = X A for every shift: (R_eff, N, tau), dtype of A (float64 -> FP64 tier, float32 -> FP32
-    tier unless `precision` names a tensor-core tier)."""
+    tier unless `precision` names a tensor-core tier), written into `out` when given."""
     A = A.contiguous()
     prec = _precision(A, precision)
     tau = A.shape[1]
     nbytes = workspace_size(L.QMC_OP_REDUCED_MATMUL, [rule], [tau], None, prec)
     ws = _workspace(nbytes, A.device, ws)
-    P = torch.empty((rule.R_eff, rule.N, tau), dtype=A.dtype, device=A.device)
+    shape = (rule.R_eff, rule.N, tau)
+    if out is not None:
+        if tuple(out.shape) != shape or out.dtype != A.dtype or not out.is_contiguous() or out.device != A.device:
+            raise ValueError(f"out must be a contiguous {A.dtype} tensor of shape {shape} on {A.device}")
+        P = out
+    else:
+        P = torch.empty(shape, dtype=A.dtype, device=A.device)
     r = rule.struct(A.device)
     L.check(L.load().qmc_reduced_matmul(ctypes.byref(r), A.data_ptr(), tau, prec, P.data_ptr(), ws.data_ptr(),
                                         ws.numel(), _stream(A.device)))

@@ -1,4 +1,7 @@
 """Shared helpers of the GPU parity tests (compare the CUDA path with the oracle)."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -42,3 +45,17 @@ def oracle_rows(p, r, ks):
 
 def integrand(p):
     return api.Integrand(p.f_kind, p.f_params)
+
+
+GOLDEN_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(key):
+    """The oracle's stored values for a full-size workload (written by tests/golden/make_full_size.py,
+    which calls only the oracle)."""
+    with open(os.path.join(GOLDEN_DIR, "full_size_oracle.json")) as fh:
+        return json.load(fh)[key]
+
+
+def golden_grad(key):
+    return np.load(os.path.join(GOLDEN_DIR, golden(key)["grad_file"])).astype(np.float64)
