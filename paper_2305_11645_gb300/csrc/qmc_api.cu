@@ -245,6 +245,8 @@ struct Plan {
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
     bool fine_mat = false;         // materialised S4 band of the float tiers (column-pair lanes)
     bool need_gen = false, need_shift = false, need_pad = false;
+    bool lv = false;               // tensor-core tiers: Algorithm 2 top down (k_level_tc passes)
+    LevelPlan lvp{};
     bool has_shift = false;        // lattice / net with R shifts (reduced MC: R replicas, no shift)
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
@@ -257,6 +259,80 @@ size_t gen_words(const Plan& P) {
     if (P.kind == QMC_DIGITAL_NET) return (size_t)P.s * P.m;
     if (P.kind == QMC_REDUCED_MC) return (size_t)P.reff * (size_t)P.T_tot;
     return (size_t)P.s;
+}
+
+// Algorithm 2 on the tensor cores (split and bf16 tiers): the coarse levels I >= JF with columns,
+// from the top down, as passes of k_level_tc.  Levels with fewer than 128 distinct rows go
+// together into the first passes (their rows are stored repeated up to a 128-row tile); every
+// other level is a pass of its own, except that the two lowest levels share the last pass
+// (which writes the root values S): that pass then multiplies the second level on twice its
+// distinct rows, but the level's partial sum (half the size of S) is never written or read.
+// Falls back to the block products and chain sum when a limit below is exceeded.
+void plan_levels(Plan& P) {
+    LevelPlan& L = P.lvp;
+    L = LevelPlan{};
+    L.pieces = P.tc_pieces;
+    const int t_tiles = (P.tau_pad + 255) / 256;
+    L.tA = t_tiles * 256;
+    int levs[kMaxLevels], nl = 0;
+    for (int I = P.m; I >= P.JF; --I)
+        if (P.lev_tau[I] > 0) levs[nl++] = I;
+    if (nl == 0) return;
+    // group: [tiny levels in groups of kMaxPassSeg] [one level each] ... [the two lowest]
+    int group[kMaxLevels], ng = 0, i = 0;
+    while (i < nl && P.m - levs[i] < 7) {
+        int k = 0;
+        while (i + k < nl && P.m - levs[i + k] < 7 && k < kMaxPassSeg) ++k;
+        group[ng++] = k;
+        i += k;
+    }
+    while (i < nl) {
+        const int rest = nl - i;
+        const int k = rest == 2 ? 2 : 1;
+        group[ng++] = k;
+        i += k;
+    }
+    if (ng > kMaxPasses) return;
+    long long xrow = 0, arow = 0;
+    const long long n_root = 1LL << (P.m - P.JF);
+    for (int g = 0, li = 0; g < ng; ++g) {
+        LevelPass& ps = L.pass[g];
+        ps = LevelPass{};
+        ps.nseg = group[g];
+        int lowest = 0;
+        for (int k = 0; k < ps.nseg; ++k, ++li) {
+            const int I = levs[li];
+            LevelSeg& sg = ps.seg[k];
+            sg.level = I;
+            sg.chunks = (P.lev_tau[I] + 31) / 32;
+            sg.last_ksteps = (P.lev_tau[I] - 32 * (sg.chunks - 1) + 15) / 16;
+            sg.logn = P.m - I;
+            sg.logn_rep = std::max(P.m - I, 7);
+            sg.col0 = P.lev_col0[I];
+            sg.tau = P.lev_tau[I];
+            sg.tab = P.lev_tab[I];
+            sg.xrow = xrow;
+            sg.arow = arow;
+            xrow += (long long)L.pieces * sg.chunks << sg.logn_rep;
+            arow += (long long)L.pieces * sg.chunks * L.tA;
+            lowest = std::max(lowest, sg.logn);
+        }
+        ps.logn_out = g + 1 == ng ? P.m - P.JF : lowest;
+        ps.logn_next = g == 0 ? -1 : L.pass[g - 1].logn_out;
+        const long long n_out = 1LL << ps.logn_out;
+        ps.rho_tiles = (int)std::max(1LL, n_out / 128);
+        ps.t_tiles = t_tiles;
+        ps.reps = 1;
+        if (ps.logn_next >= 7 && ps.logn_out > ps.logn_next) ps.reps = 1 << (ps.logn_out - ps.logn_next);
+        ps.ntiles = (long long)ps.rho_tiles * ps.t_tiles * P.reff;
+    }
+    (void)n_root;
+    // TMA coordinates are 32-bit
+    if (xrow >= (1LL << 31) || arow >= (1LL << 31)) return;
+    L.npass = ng;
+    L.x_rows_per_shift = xrow;
+    L.a_rows = arow;
+    P.lv = true;
 }
 
 qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integrand* f, int precision,
@@ -361,6 +437,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.chf.tile0[P.chf.count] = tiles;
     P.B_per_shift = boff;
     P.S_per_shift = P.chf.count ? n_root * P.tau_pad : 0;
+    if (P.tc_pieces && P.chf.count) plan_levels(P);
 
     // fine forward grid: 128 roots per CTA, column groups to fill the GPU
     P.root_blocks = (int)((n_root + 127) / 128);
@@ -551,7 +628,31 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     const size_t u0 = off;
     size_t uend = u0;
     P.off_B = u0;
-    uend = std::max(uend, align256(u0 + E * (size_t)P.reff * P.B_per_shift));
+    if (P.lv) {
+        // X pieces, A pieces, then the outputs of every pass but the last (which writes S)
+        LevelPlan& L = P.lvp;
+        size_t o = u0;
+        L.x_off = o;
+        o = align256(o + (size_t)P.reff * (size_t)L.x_rows_per_shift * 64);
+        L.a_off = o;
+        o = align256(o + (size_t)L.a_rows * 64);
+        for (int q = 0; q + 1 < L.npass; ++q) {
+            LevelPass& ps = L.pass[q];
+            ps.out_off = (long long)(o / 4);
+            ps.out_stride = (1LL << ps.logn_out) * P.tau_pad;
+            o = align256(o + 4 * (size_t)P.reff * (size_t)ps.out_stride);
+        }
+        LevelPass& last = L.pass[L.npass - 1];
+        last.out_off = (long long)(P.off_S / 4);
+        last.out_stride = P.S_per_shift;
+        for (int q = 1; q < L.npass; ++q) {
+            L.pass[q].next_off = L.pass[q - 1].out_off;
+            L.pass[q].next_stride = L.pass[q - 1].out_stride;
+        }
+        uend = std::max(uend, o);
+    } else {
+        uend = std::max(uend, align256(u0 + E * (size_t)P.reff * P.B_per_shift));
+    }
     if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
         size_t o = u0;
         P.off_rowpart = o;
@@ -655,7 +756,15 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     T* tab = reinterpret_cast<T*>(ws + P.off_tab);
     unsigned int* ticket = mode == MODE_FUSED ? reinterpret_cast<unsigned int*>(ws + P.off_ticket) : nullptr;
     QMC_LAUNCH(st, "k_table", launch_table<T>(R, tab, P.T_tot, P.tab_stride, P.reff, ticket, st));
-    if (P.chf.count) {
+    if (P.chf.count && P.lv) {
+        if constexpr (std::is_same<T, float>::value) {
+            unsigned char* wsb = reinterpret_cast<unsigned char*>(ws);
+            QMC_LAUNCH(st, "k_split_a", launch_split_a(A, ldA, P.tau, P.lvp, wsb, st));
+            QMC_LAUNCH(st, "k_split_x", launch_split_x(tab, P.tab_stride, P.lvp, P.reff, wsb, st));
+            for (int q = 0; q < P.lvp.npass; ++q)
+                QMC_LAUNCH(st, "k_level_tc", launch_level_pass(P.lvp, q, P.reff, P.tau_pad, wsb, st));
+        }
+    } else if (P.chf.count) {
         T* B = reinterpret_cast<T*>(ws + P.off_B);
         if (P.tc_pieces) {
             if constexpr (std::is_same<T, float>::value)
@@ -775,9 +884,11 @@ const char* qmc_last_error(void) { return g_err.c_str(); }
 qmc_status qmc_validate_rule(const qmc_rule* rule) { return validate(rule); }
 
 qmc_status qmc_device_status(int clear) {
-    unsigned int word = 0;
+    unsigned int word = 0, lword = 0;
     QMC_CUDA(cudaDeviceSynchronize());
     QMC_CUDA(tc_error_word(&word, clear != 0));
+    QMC_CUDA(level_error_word(&lword, clear != 0));
+    word |= lword;
     if (word)
         return fail(QMC_ERR_TIMEOUT, "a bounded device-side wait ran out (error word 0x%x: bit 0 a tensor-core "
                     "kernel, bit 31 the self-test)", word);

@@ -213,6 +213,61 @@ struct FoldLevels {
 
 constexpr int kMaxCR = 256;          // columns per CTA of the fine forward kernel
 
+// ---------------------------------------------------------------------------------------------
+// Algorithm 2 on the tensor cores, top down: a pass computes, for rho < n_out,
+//   Pt_out[rho] = sum over its levels I of X~_I[rho mod n_I] A~_I + Pt_next[rho mod n_next],
+// where Pt_next is the previous (coarser) pass's output (none for the first pass).  One level
+// per pass is Algorithm 2's step P~_I = tile(P~_{I+1}) + X~_I A~_I; the last pass writes the
+// root values S of the fine band.  The operands come as bf16 pieces in global memory, in
+// blocks of 32 columns (64-byte rows) that a TMA box of 32 x 128 (X) or 32 x 256 (A) copies:
+//   X pieces: per shift, per level I, per piece p, per chunk kc: n'_I = max(n_I, 128) rows of
+//             columns 32 kc .. 32 kc + 31 of the level (row rho holds X~_I[rho mod n_I]);
+//   A pieces: per level I, per piece p, per chunk kc: tA rows (columns t of A, tA a multiple
+//             of 256) of the same 32 columns j.
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxPassSeg = 4;       // levels summed by one pass
+constexpr int kMaxPasses = 40;
+
+struct LevelSeg {
+    int level;                       // I
+    int chunks;                      // K chunks of 32 columns
+    int last_ksteps;                 // 16-column K-steps of the last chunk (1 or 2)
+    int logn;                        // log2 n_I (n_I = 2^(m-I) distinct rows)
+    int logn_rep;                    // log2 n'_I, n'_I = max(n_I, 128)
+    int col0, tau;                   // the level's columns of A (first, count)
+    long long tab;                   // the level's offset in the FP32 point table
+    long long xrow;                  // X-pieces row of (piece 0, chunk 0, row 0) within a shift
+    long long arow;                  // A-pieces row of (piece 0, chunk 0, t 0)
+};
+
+struct LevelPass {
+    int nseg;
+    LevelSeg seg[kMaxPassSeg];
+    int logn_out;                    // rows written: n_out = 2^logn_out
+    long long out_off, out_stride;   // float offsets of the output area and of one shift's part
+    int logn_next;                   // log2 n_next, or -1 (no coarser pass)
+    long long next_off, next_stride;
+    int rho_tiles, t_tiles, reps;    // 128-row tiles, 256-column tiles, row tiles per next-pass tile
+    long long ntiles;                // rho_tiles * t_tiles * shifts
+};
+
+struct LevelPlan {
+    int npass;
+    LevelPass pass[kMaxPasses];
+    int pieces;                      // 3 (split tier) or 1 (bf16 tier)
+    long long x_rows_per_shift;      // rows of 32 bf16 of one shift's X pieces
+    long long a_rows;                // rows of 32 bf16 of the A pieces
+    int tA;                          // A-piece rows per chunk block (columns t, a multiple of 256)
+    size_t x_off, a_off;             // byte offsets of the piece areas in the workspace
+};
+
+cudaError_t launch_split_a(const float* A, int ldA, int tau, const LevelPlan& lp, unsigned char* ws,
+                           cudaStream_t st);
+cudaError_t launch_split_x(const float* tab, long long tab_stride, const LevelPlan& lp, int reff, unsigned char* ws,
+                           cudaStream_t st);
+cudaError_t launch_level_pass(const LevelPlan& lp, int p, int reff, int tau_pad, unsigned char* ws, cudaStream_t st);
+cudaError_t level_error_word(unsigned int* value, bool clear);
+
 template <class T> struct FineArgs {
     const T* tab; long long tab_stride;       // distinct-row table, per shift
     const T* A; int ldA;                      // A (or its padded copy), row stride ldA
