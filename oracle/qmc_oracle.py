@@ -95,11 +95,9 @@ def lattice_x32(m: int, w, z, shift: Optional[np.ndarray] = None, ks=None) -> np
 
 def net_matrix(masks: Sequence[int], m: int) -> np.ndarray:
     """Column masks -> m x m 0/1 matrix C[p, q] (0-based p, q), row p at bit m-1-p."""
-    C = np.zeros((m, m), dtype=np.int64)
-    for q in range(m):
-        for p in range(m):
-            C[p, q] = (int(masks[q]) >> (m - 1 - p)) & 1
-    return C
+    col = np.array([int(v) for v in masks[:m]], dtype=np.int64)[None, :]
+    row_bit = np.array([m - 1 - p for p in range(m)], dtype=np.int64)[:, None]
+    return (col >> row_bit) & 1
 
 
 def reduced_net_matrix(masks: Sequence[int], m: int, wj: int) -> np.ndarray:
@@ -119,15 +117,18 @@ def net_x32(m: int, w, C: np.ndarray, shift: Optional[np.ndarray] = None, ks=Non
     N = 1 << m
     ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
     # (the integer sums below are at most m ones, or y 2^m < 2^m: exact in float64, so the
-    # products run through the float BLAS)
+    # products run through the float BLAS, a block of columns per call)
     dig = digits_lsb_first(ks, m).astype(np.float64)      # len(ks) x m
     out = np.empty((len(ks), len(w)), dtype=np.uint64)
     place = np.array([1 << (m - 1 - p) for p in range(m)], dtype=np.float64)   # y_p b^-p, scaled by 2^m
-    for j, wj in enumerate(w):
-        Chat = reduced_net_matrix(C[j], m, int(wj)).astype(np.float64)
-        ydig = np.mod(dig @ Chat.T, 2.0)                   # y digits = Chat n over GF(2)
-        y_int = (ydig @ place).astype(np.uint64)           # y * 2^m
-        out[:, j] = y_int << np.uint64(32 - m)
+    blk = 64
+    for j0 in range(0, len(w), blk):
+        cols = range(j0, min(len(w), j0 + blk))
+        Chats = np.concatenate([reduced_net_matrix(C[j], m, int(w[j])).astype(np.float64).T for j in cols], axis=1)
+        ydig = ((dig @ Chats).astype(np.int64) & 1).astype(np.float64)   # y digits = Chat n over GF(2)
+        ydig = ydig.reshape(len(ks), len(cols), m)
+        y_int = (ydig @ place).astype(np.uint64)                        # y * 2^m, per column
+        out[:, j0:j0 + len(cols)] = y_int << np.uint64(32 - m)
     x32 = out.astype(np.uint32)
     return x32 if shift is None else apply_shift(DIGITAL_NET, x32, shift)
 
@@ -240,10 +241,11 @@ def net_points_base(b: int, m: int, w, C: np.ndarray, ks=None) -> np.ndarray:
 def apply_shift(kind: int, x32: np.ndarray, shift) -> np.ndarray:
     """O3 on 32-bit fixed-point rows: a lattice adds D mod 2^32 ({x + Delta}); nets and
     polynomial lattices XOR it (the digital shift)."""
-    D = np.asarray(shift, dtype=np.uint64)[None, :]
+    # (uint32 array addition wraps modulo 2^32)
+    D = np.asarray(shift, dtype=np.uint32)[None, :]
     if kind == LATTICE:
-        return ((np.asarray(x32, dtype=np.uint64) + D) % np.uint64(TWO32)).astype(np.uint32)
-    return (np.asarray(x32, dtype=np.uint64) ^ D).astype(np.uint32)
+        return np.asarray(x32, dtype=np.uint32) + D
+    return np.asarray(x32, dtype=np.uint32) ^ D
 
 
 def unshifted_x32(problem, ks=None) -> np.ndarray:
