@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-dense", action="store_true", help="skip the dense X*A comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-extra", action="store_true", help="skip the extra workloads")
+    ap.add_argument("--no-tiers", action="store_true", help="time only the requested precision tier")
+    ap.add_argument("--no-mat", action="store_true", help="skip the materialised product")
+    ap.add_argument("--shifts", type=int, default=0,
+                    help="keep only the first R shifts of the workload (smaller profiler captures; not the "
+                         "contract line)")
     ap.add_argument("--workload", choices=list(WORKLOADS), default="net20",
                     help="net20: the contract line (default); the others time one workload alone")
     return ap.parse_args()
@@ -76,6 +81,8 @@ def _basket():
 
 def _make(name):
     from paper_2305_11645_gb300 import inputs as I
+    if name == "pde8":
+        return [I.c4(i) for i in range(len(I.C4_INSTANCES))]
     return {"net20": I.c3, "gauss16": lambda: I.c2(dtype=np.float32), "adjoint20": I.c5, "basket": _basket}[name]()
 
 
@@ -91,6 +98,11 @@ WORKLOADS = {
     "adjoint20": (True, "c5", "reduced rank-1 lattice b=2 m=20 (N=1048576), s=tau=1024, "
                               "w_j=min(floor(log2(j+1)),12), A~N(0,1/s) FP32, R=8 shifts, f=log sum exp(y); "
                               "estimate + adjoint"),
+    "pde8": (False, "c4", "8 uneven PDE-like reduced lattice instances (m, s, tau) = (14,256,1024), (14,2048,4096), "
+                          "(16,1024,2048), (16,256,4096), (16,2048,1024), (18,1024,1024), (18,256,2048), "
+                          "(18,2048,4096), w_j=min(floor(log2(j+1)),12), centred points, 4 shifts each, "
+                          "A_ji=(j+1)^-2 sin((j+1) pi t_i), f=mean (1+0.5y)^-2; schedules autotuned per instance, "
+                          "all instances in one call replayed as one CUDA graph; estimate"),
     "basket": (False, None, "basket option by reduced Monte Carlo: m=25 (N=33554432), s=tau=10, "
                             "w_j=floor(log2 j) (1-based), tridiagonal Sigma (0.4, 0.2), K=110, one replica; estimate"),
 }
@@ -338,6 +350,41 @@ def measure(p, prec, backward, timer, steps, warmup):
     return integ, statistics.mean(times), kernels, sum(c for c, _ in kern.values()) / steps
 
 
+def measure_batch(ps, prec, timer, steps, warmup, tune=True):
+    """Several problems in one call (the library runs them on parallel internal streams), replayed as
+    one CUDA graph; each instance's fine schedules autotuned first.  Returns the integrator, mean ms
+    per step, the per-kernel device times (eager, traced) and the timed candidates."""
+    from paper_2305_11645_gb300 import api
+    dev = timer.dev
+    rules = [api.Rule.from_problem(p) for p in ps]
+    As = [torch.from_numpy(np.ascontiguousarray(p.A)).to(dev) for p in ps]
+    fs = [api.Integrand(p.f_kind, p.f_params) for p in ps]
+    timed = sum(api.autotune(r, a, f, precision=prec) for r, a, f in zip(rules, As, fs)) if tune else 0
+    integ = api.Integrator(rules, As, fs, backward=False, graph=True, precision=prec)
+    eager = api.Integrator(rules, As, fs, backward=False, graph=False, precision=prec)
+    for _ in range(warmup):
+        integ.run()
+        eager.run()
+    torch.cuda.synchronize()
+    times, _ = timer.run(integ.run, steps)
+    _, kern = timer.run(eager.run, steps, trace=True)
+    del eager
+    kernels = {k: {"launches_per_step": c / steps, "ms_per_step": t / steps} for k, (c, t) in sorted(kern.items())}
+    return integ, statistics.mean(times), kernels, timed
+
+
+def batch_accuracy(ps, est, tier):
+    g = golden("c4")
+    if g is None:
+        return {}
+    e = est.cpu().numpy()
+    off, worst = 0, 0.0
+    for i, p in enumerate(ps):
+        worst = max(worst, abs(float(e[off + p.R_eff]) - g[i]["mean"]) / abs(g[i]["mean"]))
+        off += p.R_eff + 1
+    return {"max_instance_estimate_rel_err": worst, "tolerance": {"split": 1e-6, "fp32": 2e-5, "bf16": 2e-3}[tier]}
+
+
 def accuracy(key, p, est, grad, tier):
     """Errors against the oracle's stored full-size values: the mean estimate (relative) and, where
     stored, the gradient (max-norm relative)."""
@@ -357,6 +404,30 @@ def accuracy(key, p, est, grad, tier):
 
 # ----------------------------------------------------------------------------- our arm
 
+def run_batch(args, dist, world, timer):
+    """The uneven batch (pde8) alone: one line with its step time, kernels and accuracy."""
+    ps = _make("pde8")
+    prec = args.precision
+    clocks = ClockSampler(timer.dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    integ, ms, kernels, ntimed = measure_batch(ps, prec, timer, args.steps, args.warmup)
+    clock_info = clocks.stop()
+    est = integ.run()[0]
+    torch.cuda.synchronize()
+    ms_max = max_over_ranks(dist, ms)
+    outputs = sum(q.N * q.tau * q.R_eff for q in ps)
+    return {"metric": METRIC, "value": world * outputs / (ms_max / 1e3), "unit": "outputs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"split": "bf16x6+f32", "fp32": "f32", "bf16": "bf16+f32"}[prec],
+            "data": "synthetic", "config": {"workload": WORKLOADS["pde8"][2], "name": "pde8",
+                                            "outputs_per_step": outputs, "precision": prec,
+                                            "l2": "flushed before every timed step (512 MiB write, untimed)"},
+            "autotune_candidates_timed": ntimed, "kernels": kernels, "clocks": clock_info,
+            "gpu_launches": int(round(sum(k["launches_per_step"] for k in kernels.values()) * args.steps)),
+            "accuracy": batch_accuracy(ps, est, prec)}
+
+
 def run_ours(args, dist, rank, world):
     from paper_2305_11645_gb300 import _lib as L
     from paper_2305_11645_gb300 import api
@@ -367,8 +438,15 @@ def run_ours(args, dist, rank, world):
     dev = torch.device("cuda", torch.cuda.current_device())
     timer = Timer(dev, dist)
     name = args.workload
+    if name == "pde8":
+        return run_batch(args, dist, world, timer)
     backward, gkey, desc = WORKLOADS[name]
     p = _make(name)
+    if args.shifts and p.shifts is not None:
+        import dataclasses
+        p = dataclasses.replace(p, shifts=p.shifts[:args.shifts])
+        gkey = None
+        desc += f" (first {p.R_eff} shifts only)"
     prec = args.precision
     outputs = p.N * p.tau * p.R_eff
 
@@ -440,7 +518,7 @@ def run_ours(args, dist, rank, world):
         result["accuracy"] = accuracy(gkey, p, est, grad if backward else None, prec)
         tiers = {prec: {"ms_per_step": ms, "value": outputs / (ms / 1e3), **result["accuracy"]}}
         for t in TIERS:
-            if t == prec:
+            if t == prec or args.no_tiers:
                 continue
             it, t_ms, t_k, _ = measure(p, t, backward, timer, max(3, args.steps // 2), 2)
             e_t, g_t = it.run()
@@ -451,11 +529,22 @@ def run_ours(args, dist, rank, world):
             del it
             torch.cuda.empty_cache()
         result["tiers"] = tiers
-        result["materialized"] = materialized_product(p, prec, timer, args)
+        if not args.no_mat:
+            result["materialized"] = materialized_product(p, prec, timer, args)
         if not args.no_dense:
             result["dense_xa"] = dense_baseline(p, gkey, backward, timer, args)
         if not args.no_extra:
             extra = {}
+            ps8 = _make("pde8")
+            it, b_ms, b_k, b_n = measure_batch(ps8, prec, timer, max(5, args.steps // 2), 3)
+            e_b = it.run()[0]
+            torch.cuda.synchronize()
+            outs8 = sum(q.N * q.tau * q.R_eff for q in ps8)
+            extra["pde8"] = {"workload": WORKLOADS["pde8"][2], "ms_per_step": b_ms, "value": outs8 / (b_ms / 1e3),
+                             "unit": "outputs/s", "autotune_candidates_timed": b_n,
+                             "kernels": {k: v["ms_per_step"] for k, v in b_k.items()}, **batch_accuracy(ps8, e_b, prec)}
+            del it
+            torch.cuda.empty_cache()
             for nm in ("gauss16", "adjoint20"):
                 if nm == name:
                     continue
@@ -656,12 +745,14 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     name = getattr(args, "workload", "net20")
-    p = _make(name)
+    ps = _make(name)
+    ps = ps if isinstance(ps, list) else [ps]
     backward, _, desc = WORKLOADS[name]
-    rows = 256
+    rows = 256 // len(ps)
 
     def step(i):
-        oracle_sample(p, (np.arange(rows, dtype=np.int64) + i * rows) % p.N)
+        for p in ps:
+            oracle_sample(p, (np.arange(rows, dtype=np.int64) + i * rows) % p.N)
 
     for i in range(args.warmup):
         step(i)
@@ -671,10 +762,11 @@ def run_reference(args, rank, world):
         step(args.warmup + i)
         ts.append(time.perf_counter() - t0)
     ms = 1e3 * statistics.mean(ts)
-    value = rows * p.tau * p.R_eff / (ms / 1e3)
+    value = sum(rows * p.tau * p.R_eff for p in ps) / (ms / 1e3)
     cores = len(os.sched_getaffinity(0))
-    sample = (f"{rows} rows of the workload per step for all {p.R_eff} shifts, numpy FP64 oracle: points from "
-              f"the definitions, X A, f and X^T grad f")
+    p = ps[0]
+    sample = (f"{rows} rows of {'each instance of ' if len(ps) > 1 else ''}the workload per step for all shifts, "
+              f"numpy FP64 oracle: points from the definitions, X A, f and X^T grad f")
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "outputs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -42,7 +42,7 @@ extern "C" {
 typedef int qmc_status;
 #define QMC_OK                0
 #define QMC_ERR_INVALID_ARG   1   /* argument violates the paper's definitions or the sizes */
-#define QMC_ERR_UNSUPPORTED   2   /* valid in the paper, not built here (b != 2, non-periodic net, ...) */
+#define QMC_ERR_UNSUPPORTED   2   /* valid in the paper, not built here (b != 2, ...) */
 #define QMC_ERR_NO_MEMORY     3   /* workspace smaller than qmc_workspace_size() */
 #define QMC_ERR_CUDA          4   /* a CUDA runtime call failed (message has the CUDA error string) */
 #define QMC_ERR_DEVICE        5   /* a kernel reported an inconsistent state through its error word */
@@ -114,10 +114,13 @@ typedef int qmc_status;
  *  C          HOST uint32[s*m] (net): generating matrices as column masks.  Word C[j*m + q] is column q+1
  *             of C^(j); row p (1-based, the digit of 2^-p) is bit m-p of the word (Sec. 4, eq.
  *             def:digital, digits of n least significant first).  The library zeroes the last
- *             min(w_j,m) rows (eq. reduced_genmat_net2).  After that the columns q >= m-w_j must be zero
- *             (the periodic reduced net; otherwise QMC_ERR_UNSUPPORTED: the paper's non-periodic
- *             Algorithm 4 is not built) and the leading (m-w_j) x (m-w_j) block must be nonsingular over
- *             GF(2) (so each value repeats exactly 2^{w_j} times; otherwise QMC_ERR_INVALID_ARG).
+ *             min(w_j,m) rows (eq. reduced_genmat_net2); the first m-w_j rows that remain must be
+ *             linearly independent over GF(2), so that each value repeats exactly 2^{w_j} times
+ *             (otherwise QMC_ERR_INVALID_ARG).  If every reduced C^(j) is zero beyond its column
+ *             m-w_j, the net is periodic (column j depends on n mod 2^(m-w_j)) and takes the reduced
+ *             product of Algorithm 2.  Otherwise it is a non-periodic reduced net (Sec. 4, Algorithm 4's
+ *             case): no column repeats periodically, every column has N distinct rows, the product is
+ *             formed densely over all N points, and the workspace grows with N*s.
  *  z          HOST uint32[R_eff * T] (reduced MC): the samples y_{j,i} as X32 = y 2^32, drawn by the
  *             caller (i.i.d. uniform words give i.i.d. U[0,1) samples on the 2^-32 grid).  Replica r
  *             holds, for j = 0..s-1 in order, the N_j = 2^(m-min(w_j,m)) samples y_{j,0..N_j-1} of
@@ -193,7 +196,8 @@ qmc_status qmc_workspace_size(int op, const qmc_rule* rules, const uint32_t* tau
  *  shift_idx  which shift to apply (ignored when R = 0); reduced MC: which replica.
  *  layout     QMC_LAYOUT_FULL: d_out is N*s uint32, d_out[k*s + j] = X32 of x_{k,j}.
  *             QMC_LAYOUT_DISTINCT: d_out holds, for j = 0..s-1 in order, the 2^(m-min(w_j,m)) values
- *             x_{k,j}, k < 2^(m-min(w_j,m)) (one period of the column).
+ *             x_{k,j}, k < 2^(m-min(w_j,m)) (one period of the column); for a non-periodic net, all N
+ *             values of every column.
  *  out_words  capacity of d_out in uint32 words (checked).
  *  d_ws       DEVICE workspace (may be NULL when d_gen and d_shift are given).
  */
@@ -235,6 +239,28 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
                                   uint32_t nprob, const qmc_integrand* f, int precision,
                                   const double* d_upstream, void* const* d_gradA, uint32_t flags,
                                   void* d_ws, size_t ws_bytes, void* stream);
+
+/*
+ * Schedule autotuning (the paper has no counterpart: it picks launch shapes of this library's
+ * kernels, never the arithmetic).  For a problem shape (m, the column counts per weight level,
+ * tau, shifts, precision, integrand) the planner uses a cached schedule of the fine band
+ * (forward: columns per CTA; adjoint: roots per CTA) when one exists, else its cost models.
+ *  qmc_autotune  times, with CUDA events on `stream`, the forward and the forward + backward of this
+ *                problem under the cost model's schedule and a ladder of others, and caches the
+ *                fastest.  d_est (R_eff + 1 doubles), d_gradA (s x tau) and d_ws are scratch: the
+ *                timed runs overwrite them.  Candidates whose workspace exceeds ws_bytes are skipped;
+ *                a tuned schedule can change qmc_workspace_size, so size workspaces after tuning.
+ *                Synchronises the stream (not callable during stream capture).  *n_timed (may be
+ *                NULL) receives the number of candidates timed.
+ *  qmc_tune_save / qmc_tune_load   write / merge the cache as a text file, one line per shape
+ *                ("key|columns per CTA / 4|roots per CTA"; 0 keeps the cost model's choice).
+ *  qmc_tune_clear  empties the cache.
+ */
+qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, const qmc_integrand* f, int precision,
+                        double* d_est, void* d_gradA, void* d_ws, size_t ws_bytes, void* stream, uint32_t* n_timed);
+qmc_status qmc_tune_save(const char* path);
+qmc_status qmc_tune_load(const char* path, uint32_t* n_entries);
+qmc_status qmc_tune_clear(void);
 
 /*
  * qmc_integrate_noalloc: qmc_integrate for one problem without a caller workspace and without

@@ -25,7 +25,8 @@ reordering beyond what the definitions state:
   O4  coordinate transforms applied elementwise (Sec. 2.3): identity,
       centring x - 1/2, inverse normal CDF (scipy.special.ndtri), tent
       1 - |1 - 2x| (Sec. 1.2).
-  O5  the dense product Y = X A (eq. Eq_XA_product), numpy matmul.
+  O5  the dense product Y = X A (eq. Eq_XA_product), numpy matmul; and Sec. 1's
+      PDE assembly D_k = sum_j x_{j,k} C_j summed matrix by matrix (assemble).
   O6  the QMC rule Q_N(f) = N^-1 sum_k f(x_k^T A) (eq. (2)) per shift, and
       the mean over the R shifts.
   O7  the gradient of the shift-averaged estimate with respect to A:
@@ -315,6 +316,17 @@ def row_chunks(N: int, chunk: int) -> Iterable[np.ndarray]:
 def reduced_matmul(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
     """Rows of P = X A for the given shift (all N rows by default)."""
     return product(points(problem, shift_idx, ks), problem.A)
+
+
+def assemble(problem, C: np.ndarray, shift_idx: int = 0, ks=None) -> np.ndarray:
+    """Sec. 1's PDE assembly, D_k = sum_j x_{j,k} C_j (C: s x M x M), for the rows ks of the given
+    shift, summed over j directly (not through X A)."""
+    X = points(problem, shift_idx, ks)
+    C = np.asarray(C, dtype=np.float64)
+    D = np.zeros((X.shape[0],) + C.shape[1:])
+    for j in range(C.shape[0]):
+        D += X[:, j][:, None, None] * C[j][None, :, :]
+    return D
 
 
 # ----------------------------------------------------------------------------- O6 integrands

@@ -73,6 +73,26 @@ class Rule:
     def N(self) -> int:
         return self.b ** self.m
 
+    def nonperiodic(self) -> bool:
+        """A net whose reduced generating matrices (last min(w_j, m) rows zeroed) have a nonzero
+        column beyond m - w_j: its columns do not repeat periodically (Sec. 4, Algorithm 4's case)."""
+        if self.kind != DIGITAL_NET:
+            return False
+        C = self.C.reshape(self.s, self.m)
+        for j in range(self.s):
+            wcl = min(int(self.w[j]), self.m)
+            rowmask = (0xFFFFFFFF << wcl) & 0xFFFFFFFF
+            if any(int(C[j, c]) & rowmask for c in range(self.m - wcl, self.m)):
+                return True
+        return False
+
+    def distinct_rows(self) -> int:
+        """Entries of the distinct layout: one period of every column, or all N rows of every column
+        of a non-periodic net."""
+        if self.nonperiodic():
+            return self.s * self.N
+        return int(sum(2 ** (self.m - min(int(w), self.m)) for w in self.w))
+
     @property
     def R_eff(self) -> int:
         return max(self.R, 1)
@@ -155,8 +175,7 @@ def gen_points(rule: Rule, layout: str = "full", shift_idx: int = 0, device="cud
     if lay == L.QMC_LAYOUT_FULL:
         out = torch.empty((rule.N, rule.s), dtype=torch.int32, device=device)
     else:
-        n = int(sum(2 ** (rule.m - min(int(w), rule.m)) for w in rule.w))
-        out = torch.empty(n, dtype=torch.int32, device=device)
+        out = torch.empty(rule.distinct_rows(), dtype=torch.int32, device=device)
     r = rule.struct(device)
     L.check(L.load().qmc_gen_points(ctypes.byref(r), shift_idx, lay, out.data_ptr(), out.numel(), None, 0,
                                     _stream(device)))
@@ -183,6 +202,17 @@ def reduced_matmul(rule: Rule, A: torch.Tensor, ws: Optional[torch.Tensor] = Non
     L.check(L.load().qmc_reduced_matmul(ctypes.byref(r), A.data_ptr(), tau, prec, P.data_ptr(), ws.data_ptr(),
                                         ws.numel(), _stream(A.device)))
     return P
+
+
+def assemble(rule: Rule, C: torch.Tensor, ws: Optional[torch.Tensor] = None,
+             precision: Optional[str] = None) -> torch.Tensor:
+    """The matrices D_k = sum_j x_{k,j} C_j for every point k and shift (Sec. 1's PDE assembly), as the
+    reduced product X A with A's row j the flattened C_j (tau = M^2): (R_eff, N, M, M)."""
+    if C.dim() != 3 or C.shape[1] != C.shape[2] or C.shape[0] != rule.s:
+        raise ValueError(f"C must be (s, M, M) with s = {rule.s} (got {tuple(C.shape)})")
+    M = C.shape[1]
+    P = reduced_matmul(rule, C.reshape(rule.s, M * M), ws=ws, precision=precision)
+    return P.view(rule.R_eff, rule.N, M, M)
 
 
 def integrate(rules: Union[Rule, Sequence[Rule]], As, fs, rowf: bool = False,
@@ -237,6 +267,38 @@ def integrate_backward(rules, As, fs, upstream: torch.Tensor, ws: Optional[torch
     return grads
 
 
+def autotune(rule: Rule, A: torch.Tensor, f: Integrand, precision: Optional[str] = None) -> int:
+    """Time the fine band's schedules for this problem shape on the GPU and cache the fastest (the
+    library's planner then uses it for every call of this shape).  Returns the candidates timed.
+    Synchronises the current stream; call it before sizing workspaces and before graph capture."""
+    A = A.contiguous()
+    prec = _precision(A, precision)
+    nbytes = workspace_size(L.QMC_OP_INTEGRATE_BWD, [rule], [A.shape[1]], [f], prec)
+    ws = torch.empty(max(2 * nbytes, 256), dtype=torch.uint8, device=A.device)
+    est = torch.empty(rule.R_eff + 1, dtype=torch.float64, device=A.device)
+    grad = torch.empty_like(A)
+    n = ctypes.c_uint32(0)
+    r = rule.struct(A.device)
+    L.check(L.load().qmc_autotune(ctypes.byref(r), A.data_ptr(), A.shape[1], ctypes.byref(f.struct()), prec,
+                                  est.data_ptr(), grad.data_ptr(), ws.data_ptr(), ws.numel(), _stream(A.device),
+                                  ctypes.byref(n)))
+    return int(n.value)
+
+
+def tune_save(path: str) -> None:
+    L.check(L.load().qmc_tune_save(str(path).encode()))
+
+
+def tune_load(path: str) -> int:
+    n = ctypes.c_uint32(0)
+    L.check(L.load().qmc_tune_load(str(path).encode(), ctypes.byref(n)))
+    return int(n.value)
+
+
+def tune_clear() -> None:
+    L.check(L.load().qmc_tune_clear())
+
+
 class QMCEstimate(torch.autograd.Function):
     """Randomised QMC estimate (mean over shifts) of N^-1 sum_k f(x_k^T A), differentiable in A.
     The backward reuses the forward's workspace (no recomputation of the forward pass)."""
@@ -265,33 +327,42 @@ def qmc_estimate(A: torch.Tensor, rule: Rule, f: Integrand, precision: Optional[
 
 
 class Integrator:
-    """A fixed problem (rule, A's shape and dtype, f) evaluated repeatedly: the estimate and,
-    with ``backward=True``, dQ/dA, through one CUDA graph of the library's launches.
+    """Fixed problems (rules, A's shapes and dtype, integrands) evaluated repeatedly: the estimates
+    and, with ``backward=True``, dQ/dA, through one CUDA graph of the library's launches.
 
-    The C structures, the workspace and the input/output buffers are built once; ``A`` is a
-    static device tensor the caller overwrites (``integrator.A.copy_(...)``) before each
-    ``run()``, which replays the graph on the current stream and returns the static outputs
-    ``(est, grad)`` -- est holds the R_eff per-shift estimates and their mean.
+    Pass one problem (rule, A, f) or lists of them: several problems go to the library in one call,
+    which runs them on parallel internal streams joined back to the caller's stream, so the graph
+    holds every instance's launches as concurrent branches and one replay runs them all.
+    The C structures, the workspace and the input/output buffers are built once; ``A`` (a tensor,
+    or ``As``, a list) are static device tensors the caller overwrites before each ``run()``, which
+    replays the graph on the current stream and returns the static outputs ``(est, grad)``: est holds,
+    per problem, the R_eff per-shift estimates and their mean; grad is dQ/dA (a list for several
+    problems).
     """
 
-    def __init__(self, rule: Rule, A: torch.Tensor, f: Integrand, backward: bool = True, graph: bool = True,
+    def __init__(self, rule, A, f, backward: bool = True, graph: bool = True,
                  precision: Optional[str] = None):
-        self.rule, self.f, self.backward = rule, f, backward
-        self.device = A.device
-        self.A = A.detach().contiguous().clone()
-        self.prec = _precision(self.A, precision)
+        self.single = not isinstance(rule, (list, tuple))
+        rules, As, fs = _as_list(rule), _as_list(A), _as_list(f)
+        if not (len(rules) == len(As) == len(fs)):
+            raise ValueError("rules, As and fs must have the same length")
+        self.rules, self.fs, self.backward = rules, fs, backward
+        self.device = As[0].device
+        self.As = [a.detach().contiguous().clone() for a in As]
+        self.prec = _precision(self.As[0], precision)
+        n = len(rules)
         op = L.QMC_OP_INTEGRATE_BWD if backward else L.QMC_OP_INTEGRATE
-        self.ws = torch.empty(max(workspace_size(op, [rule], [self.A.shape[1]], [f], self.prec), 256),
+        self.ws = torch.empty(max(workspace_size(op, rules, [a.shape[1] for a in self.As], fs, self.prec), 256),
                               dtype=torch.uint8, device=self.device)
-        self.est = torch.empty(rule.R_eff + 1, dtype=torch.float64, device=self.device)
-        self.grad = torch.empty_like(self.A)
-        self.upstream = torch.ones(1, dtype=torch.float64, device=self.device)
-        self._rs = L.QmcRule * 1
-        self._r = self._rs(rule.struct(self.device))
-        self._ap = (ctypes.c_void_p * 1)(self.A.data_ptr())
-        self._ts = (ctypes.c_uint32 * 1)(self.A.shape[1])
-        self._fa = (L.QmcIntegrand * 1)(f.struct())
-        self._gp = (ctypes.c_void_p * 1)(self.grad.data_ptr())
+        self.est = torch.empty(sum(r.R_eff + 1 for r in rules), dtype=torch.float64, device=self.device)
+        self.grads = [torch.empty_like(a) for a in self.As]
+        self.upstream = torch.ones(n, dtype=torch.float64, device=self.device)
+        self._r = (L.QmcRule * n)(*[r.struct(self.device) for r in rules])
+        self._ap = (ctypes.c_void_p * n)(*[a.data_ptr() for a in self.As])
+        self._ts = (ctypes.c_uint32 * n)(*[a.shape[1] for a in self.As])
+        self._fa = (L.QmcIntegrand * n)(*[x.struct() for x in fs])
+        self._gp = (ctypes.c_void_p * n)(*[g.data_ptr() for g in self.grads])
+        self._n = n
         self._lib = L.load()
         self.graph = None
         if graph:
@@ -306,12 +377,20 @@ class Integrator:
             torch.cuda.current_stream(self.device).wait_stream(s)
             self.graph = g
 
+    @property
+    def A(self) -> torch.Tensor:
+        return self.As[0]
+
+    @property
+    def grad(self) -> torch.Tensor:
+        return self.grads[0]
+
     def _eager(self, stream) -> None:
         st = ctypes.c_void_p(stream.cuda_stream)
-        L.check(self._lib.qmc_integrate(self._r, self._ap, self._ts, 1, self._fa, self.prec, self.est.data_ptr(),
+        L.check(self._lib.qmc_integrate(self._r, self._ap, self._ts, self._n, self._fa, self.prec, self.est.data_ptr(),
                                         None, self.ws.data_ptr(), self.ws.numel(), st))
         if self.backward:
-            L.check(self._lib.qmc_integrate_backward(self._r, self._ap, self._ts, 1, self._fa, self.prec,
+            L.check(self._lib.qmc_integrate_backward(self._r, self._ap, self._ts, self._n, self._fa, self.prec,
                                                      self.upstream.data_ptr(), self._gp, L.QMC_BWD_REUSE_FORWARD,
                                                      self.ws.data_ptr(), self.ws.numel(), st))
 
@@ -320,4 +399,4 @@ class Integrator:
             self.graph.replay()
         else:
             self._eager(torch.cuda.current_stream(self.device))
-        return self.est, self.grad
+        return self.est, (self.grad if self.single else self.grads)

@@ -201,26 +201,57 @@ qmc_status validate(const qmc_rule* r) {
         for (uint32_t j = 0; j < r->s; ++j) {
             const uint32_t wcl = std::min(r->w[j], m), q = m - wcl;
             const uint32_t rowmask = (wcl >= 32) ? 0u : ~((1u << wcl) - 1u);
-            uint32_t lead[32];
-            int nlead = 0;
+            uint32_t rows[32];
             for (uint32_t c = 0; c < m; ++c) {
                 const uint32_t word = r->C[(size_t)j * m + c];
                 if (m < 32 && (word >> m) != 0)
                     return fail(QMC_ERR_INVALID_ARG, "C[%u][%u]=0x%x has bits above row 1 (bit m-1)", j, c, word);
-                const uint32_t red = word & rowmask;      // eq. reduced_genmat_net2
-                if (c >= q && red != 0)
-                    return fail(QMC_ERR_UNSUPPORTED,
-                                "column %u of the reduced C^(%u) is nonzero: the net is not periodic with period "
-                                "2^(m-w_j) (non-periodic reduced nets, Algorithm 4, are not built)",
-                                c + 1, j);
-                if (c < q) lead[nlead++] = red >> wcl;
+                rows[c] = (word & rowmask) >> wcl;     // eq. reduced_genmat_net2: the first q rows remain
             }
-            if (gf2_rank(lead, nlead) != (int)q)
-                return fail(QMC_ERR_INVALID_ARG, "leading %ux%u block of C^(%u) is singular over GF(2)", q, q, j);
+            // The first q rows of the reduced C^(j) must be linearly independent over GF(2), so that
+            // column j takes every value v 2^-q, v < 2^q, exactly 2^{w_j} times (Sec. 4).  For a periodic
+            // net (columns q+1.. zero) this is the nonsingular leading block.
+            if (gf2_rank(rows, (int)m) != (int)q)
+                return fail(QMC_ERR_INVALID_ARG, "the first %u rows of the reduced C^(%u) have GF(2) rank below %u", q, j,
+                            q);
         }
     }
     return QMC_OK;
 }
+
+// A net whose reduced matrices have a nonzero column beyond m - w_j (Sec. 4: reduced by rows, not
+// periodic in the point index): Algorithm 4's case.
+bool net_nonperiodic(const qmc_rule* r) {
+    if (r->kind != QMC_DIGITAL_NET) return false;
+    const uint32_t m = r->m;
+    for (uint32_t j = 0; j < r->s; ++j) {
+        const uint32_t wcl = std::min(r->w[j], m), q = m - wcl;
+        const uint32_t rowmask = (wcl >= 32) ? 0u : ~((1u << wcl) - 1u);
+        for (uint32_t c = q; c < m; ++c)
+            if (r->C[(size_t)j * m + c] & rowmask) return true;
+    }
+    return false;
+}
+
+// ------------------------------------------------------------------------------------------
+// schedule autotuning: per problem shape, the fine band's forward column groups (columns per
+// CTA = 4 qpg) and adjoint roots per CTA, measured by qmc_autotune; 0 keeps the cost model's
+// choice.  The planner consults the cache on every call; qmc_autotune passes its candidates
+// through a thread-local hint.
+// ------------------------------------------------------------------------------------------
+struct TuneVal {
+    int fwd_qpg = 0;
+    int bwd_rpc = 0;
+};
+struct TuneCache {
+    std::mutex mu;
+    std::map<std::string, TuneVal> m;
+};
+TuneCache& tune_cache() {
+    static TuneCache c;
+    return c;
+}
+thread_local const TuneVal* t_hint = nullptr;
 
 // ------------------------------------------------------------------------------------------
 // the plan: block schedule and workspace layout of one problem
@@ -245,9 +276,17 @@ struct Plan {
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
     bool fine_mat = false;         // materialised S4 band of the float tiers (column-pair lanes)
     bool need_gen = false, need_shift = false, need_pad = false;
+    std::string tune_key;          // the problem shape the schedule cache is keyed by
+    TuneVal tuned{};               // the cached (or hinted) schedule applied to this plan
     bool lv = false;               // tensor-core tiers: Algorithm 2 top down (k_level_tc passes)
     LevelPlan lvp{};
     bool has_shift = false;        // lattice / net with R shifts (reduced MC: R replicas, no shift)
+    bool nonper = false;           // non-periodic reduced net: every column on level 0 with N rows
+    // tensor-core tiers with points in [0, 1) (identity, tent): the block products take x - 1/2, so
+    // that their terms take both signs (the tensor core's FP32 accumulation rounds toward zero, which
+    // biases long sums of terms of one sign), and the constant 1/2 returns as one exact term
+    float xc = 0.0f;
+    size_t off_gsum = 0;           // backward: column sums of the folded gradient (65 x tau_pad doubles)
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
            total = 0;
@@ -343,9 +382,11 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.kind = r->kind; P.m = (int)r->m; P.s = (int)r->s; P.transform = r->transform;
     P.R = (int)r->R; P.reff = std::max(P.R, 1);
     P.N = 1LL << P.m;
+    P.nonper = net_nonperiodic(r);
     for (int I = 0; I <= P.m; ++I) { P.lev_tau[I] = 0; P.lev_col0[I] = -1; }
     for (int j = 0; j < P.s; ++j) {
-        const int I = (int)std::min<uint32_t>(r->w[j], r->m);
+        // (a non-periodic net has no distinct-row reuse: every column is on level 0)
+        const int I = P.nonper ? 0 : (int)std::min<uint32_t>(r->w[j], r->m);
         if (P.lev_col0[I] < 0) P.lev_col0[I] = j;
         P.lev_tau[I]++;
     }
@@ -356,6 +397,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             else next = P.lev_col0[I];
         }
     }
+    P.xc = 0.0f;
     P.lev_tab[0] = 0;
     for (int I = 0; I <= P.m; ++I) P.lev_tab[I + 1] = P.lev_tab[I] + (long long)P.lev_tau[I] * (1LL << (P.m - I));
     P.T_tot = P.lev_tab[P.m + 1];
@@ -375,6 +417,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         return fail(QMC_ERR_INVALID_ARG, "precision %d unknown", precision);
     // the tensor-core tiers keep FP32 data and FP32 arithmetic outside the coarse block products
     P.tc_pieces = precision == QMC_SPLIT ? 3 : precision == QMC_BF16 ? 1 : 0;
+    if (P.tc_pieces && (P.transform == QMC_T_IDENTITY || P.transform == QMC_T_TENT)) P.xc = 0.5f;
     if (tau < 1 || tau > 65536) return fail(QMC_ERR_INVALID_ARG, "tau=%u outside [1, 65536]", tau);
     P.precision = precision;
     P.elt = precision == QMC_FP64 ? 8 : 4;
@@ -457,6 +500,20 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     // table entries, 2 * 2^m row-save floats) below 2^30.
     P.fine_s4 = (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) && P.shape == SHAPE_S4 &&
                 precision != QMC_FP64 && P.m <= 27;
+    {   // the schedule cache's key: everything the fine schedules depend on
+        std::string k = "m" + std::to_string(P.m) + " p" + std::to_string(precision) + " f" + std::to_string(P.fkind) +
+                        " t" + std::to_string(P.tau_pad) + " r" + std::to_string(P.reff) + " L";
+        for (int I = 0; I <= P.m; ++I) k += (I ? "," : "") + std::to_string(P.lev_tau[I]);
+        P.tune_key = k;
+        if (t_hint) {
+            P.tuned = *t_hint;
+        } else {
+            TuneCache& tc = tune_cache();
+            std::lock_guard<std::mutex> g(tc.mu);
+            auto it = tc.m.find(k);
+            if (it != tc.m.end()) P.tuned = it->second;
+        }
+    }
     if (P.fine_s4) {
         const int rows = fine_s4_fwd_roots();
         P.root_blocks = (int)((n_root + rows - 1) / rows);
@@ -471,6 +528,8 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             const long long cost = std::max(per_sm, resident) * (qpg + 2);
             if (best < 0 || cost < best) { best = cost; P.cr = 4 * qpg; P.cg_count = (quads + qpg - 1) / qpg; }
         }
+        const int qpg = P.tuned.fwd_qpg;
+        if (qpg > 0 && qpg <= qmax && qpg <= quads) { P.cr = 4 * qpg; P.cg_count = (quads + qpg - 1) / qpg; }
     }
     // the materialised product of the float tiers with the S4 band: CTAs of 256 columns over a
     // range of roots, as many as fill 5 CTAs per SM once (the band is bound by its output writes;
@@ -508,6 +567,11 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             const long long per_sm = ((long long)P.passes * g * P.reff + 151) / 152;
             const long long cost = std::max(per_sm, 2LL) * (rpc + rb);
             if (best < 0 || cost < best) { best = cost; P.roots_per_cta = (int)rpc; P.groups = (int)g; }
+        }
+        const long long rpc = P.tuned.bwd_rpc;
+        if (rpc >= 2 && rpc % 2 == 0 && rpc <= n_root + 1) {
+            P.roots_per_cta = (int)rpc;
+            P.groups = (int)((n_root + rpc - 1) / rpc);
         }
     }
     if (op == QMC_OP_INTEGRATE_BWD) {
@@ -585,6 +649,9 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             const double we = (double)jt * ttiles * K * (fma_w + fold_w * fold);
             long long split = (long long)(we / std::max(wtot, 1.0) * target / ((double)jt * ttiles) + 0.5);
             split = std::max(1LL, std::min(split, std::max(1LL, K / kmin)));
+            // tensor-core splits of at most 4096 rows: an FP32 accumulator in tensor memory then sums
+            // at most 1024 rows (four per CTA), and the splits are summed in double
+            if (tc) split = std::max(split, (K + 4095) / 4096);
             split = std::min(split, 4096LL);
             long long kper = (K + split - 1) / split;
             if (tc) {                       // whole chunks of 32 rows per split
@@ -636,6 +703,11 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         o = align256(o + (size_t)P.reff * (size_t)L.x_rows_per_shift * 64);
         L.a_off = o;
         o = align256(o + (size_t)L.a_rows * 64);
+        L.c_off = o;
+        o = align256(o + 4 * (size_t)P.tau_pad);
+        L.xc = P.xc;
+        for (int q = 0; q < L.npass; ++q) L.pass[q].const_off = -1;
+        if (P.xc != 0.0f) L.pass[0].const_off = (long long)(L.c_off / 4);
         for (int q = 0; q + 1 < L.npass; ++q) {
             LevelPass& ps = L.pass[q];
             ps.out_off = (long long)(o / 4);
@@ -671,6 +743,8 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         o = align256(o + E * (size_t)P.reff * P.groups * std::max(P.kf_width, 1) * P.tau_pad);
         P.off_partc = o;
         o = align256(o + E * (size_t)std::max(P.partc_elems, 1LL));
+        P.off_gsum = o;
+        if (P.xc != 0.0f) o = align256(o + sizeof(double) * 65 * (size_t)P.tau_pad);
         uend = std::max(uend, o);
     }
     P.total = uend;
@@ -686,6 +760,15 @@ DevRule dev_rule(const Plan& P, const qmc_rule* r, char* ws) {
     R.nlev = P.m + 1;
     for (int I = 0; I <= P.m; ++I) { R.lev_tau[I] = P.lev_tau[I]; R.lev_col0[I] = P.lev_col0[I]; }
     for (int I = 0; I <= P.m + 1; ++I) R.lev_tab[I] = P.lev_tab[I];
+    R.nonper = P.nonper ? 1 : 0;
+    R.nw = 0;
+    if (P.nonper) {
+        for (int j = 0; j < P.s; ++j) {
+            const int v = (int)std::min<uint32_t>(r->w[j], r->m);
+            if (R.nw == 0 || R.wval[R.nw - 1] != v) { R.wcol0[R.nw] = j; R.wval[R.nw] = v; ++R.nw; }
+        }
+        R.wcol0[R.nw] = P.s;
+    }
     return R;
 }
 
@@ -759,6 +842,8 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     if (P.chf.count && P.lv) {
         if constexpr (std::is_same<T, float>::value) {
             unsigned char* wsb = reinterpret_cast<unsigned char*>(ws);
+            if (P.xc != 0.0f)
+                QMC_LAUNCH(st, "k_const_row", launch_const_row(A, ldA, P.tau, P.tau_pad, P.lvp, wsb, st));
             QMC_LAUNCH(st, "k_split_a", launch_split_a(A, ldA, P.tau, P.lvp, wsb, st));
             QMC_LAUNCH(st, "k_split_x", launch_split_x(tab, P.tab_stride, P.lvp, P.reff, wsb, st));
             for (int q = 0; q < P.lvp.npass; ++q)
@@ -847,10 +932,21 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
             QMC_LAUNCH(st, "k_fold_tree", launch_fold_tree<T>(Froot, root_stride, Fchain, P.Fchain_per_shift, P.fold,
                                                               P.tau_pad, P.reff, st));
         if (P.tc_pieces) {
-            if constexpr (std::is_same<T, float>::value)
+            if constexpr (std::is_same<T, float>::value) {
                 QMC_LAUNCH(st, "k_coarse_grad_tc",
                            launch_coarse_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
-                                                 P.tau_pad, P.chb, partc, P.reff, P.bwd_tiles, P.tc_pieces, st));
+                                                 P.tau_pad, P.chb, partc, P.reff, P.bwd_tiles, P.tc_pieces, P.xc, st));
+                if (P.xc != 0.0f) {
+                    // 1^T G over every shift: the column sums of the top folded level (or of the roots)
+                    const bool top = P.fold.depth > 0;
+                    const float* Ft = top ? Fchain + P.fold.off[P.fold.depth] : Froot;
+                    const long long rows = top ? (1LL << P.fold.logn_top) : n_root;
+                    double* part = reinterpret_cast<double*>(ws + P.off_gsum);
+                    QMC_LAUNCH(st, "k_col_sums",
+                               launch_col_sums(Ft, top ? P.Fchain_per_shift : root_stride, rows, P.reff, P.tau_pad,
+                                               part, part + 64LL * P.tau_pad, st));
+                }
+            }
         } else {
             QMC_LAUNCH(st, "k_coarse_grad",
                        launch_coarse_grad<T>(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
@@ -865,9 +961,11 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
         taul[I] = P.lev_tau[I];
         o += P.shape == SHAPE_S4 ? kmax_s4[I] : 16;
     }
+    const double* gsum = P.xc != 0.0f && P.chb.count
+                             ? reinterpret_cast<const double*>(ws + P.off_gsum) + 64LL * P.tau_pad : nullptr;
     QMC_LAUNCH(st, "k_grad_reduce",
                launch_grad_reduce<T>(a.gradpart, nfine_part, std::max(P.kf_width, 1), koff, col0, taul, P.JF,
-                                     partc, P.chb, P.tau, P.tau_pad, P.s, grad, st));
+                                     partc, P.chb, P.tau, P.tau_pad, P.s, grad, gsum, (double)P.xc, st));
     return QMC_OK;
 }
 
@@ -967,6 +1065,24 @@ qmc_status qmc_reduced_matmul(const qmc_rule* rule, const void* d_A, uint32_t ta
                               nullptr, st_, &A, &ld);
 }
 
+// Several problems in one call run on internal streams: the caller's stream forks into them
+// through an event and joins back through one event per stream, so the call stays ordered on the
+// caller's stream and can be captured into a CUDA graph (the forked streams join the capture).
+// Problems are dealt to the streams largest first (work ~ N tau R), each to the stream with the
+// least work so far.
+struct Forker {
+    static constexpr int K = 4;
+    static constexpr int kDevices = 64;
+    std::mutex mu;
+    bool ready[kDevices] = {};
+    cudaStream_t s[kDevices][K];
+    cudaEvent_t fork[kDevices], join[kDevices][K];
+};
+Forker& forker() {
+    static Forker f;
+    return f;
+}
+
 static qmc_status integrate_common(int op, const qmc_rule* rules, const void* const* d_A, const uint32_t* tau,
                                    uint32_t nprob, const qmc_integrand* f, int precision, double* d_est,
                                    void* const* d_rowf, const double* d_upstream, void* const* d_gradA,
@@ -988,11 +1104,55 @@ static qmc_status integrate_common(int op, const qmc_rule* rules, const void* co
     }
     if (!d_ws || ws_bytes < total) return fail(QMC_ERR_NO_MEMORY, "workspace of %zu bytes, %zu needed", ws_bytes, total);
     if (((uintptr_t)d_ws) % 256) return fail(QMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
-    cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
-    char* ws = reinterpret_cast<char*>(d_ws);
-    size_t est_off = 0;
+    cudaStream_t caller = reinterpret_cast<cudaStream_t>(stream);
+    char* ws0 = reinterpret_cast<char*>(d_ws);
+    // per problem: its workspace and estimate offsets, and its stream
+    std::vector<size_t> ws_off(nprob), est_offs(nprob);
+    std::vector<int> lane(nprob, -1);
+    {
+        size_t wo = 0, eo = 0;
+        for (uint32_t p = 0; p < nprob; ++p) {
+            ws_off[p] = wo; est_offs[p] = eo;
+            wo += align256(plans[p].total);
+            eo += (size_t)plans[p].reff + 1;
+        }
+    }
+    Forker& fk = forker();
+    std::unique_lock<std::mutex> lock(fk.mu, std::defer_lock);
+    int dev = 0, used = 0;
+    if (nprob > 1) {
+        QMC_CUDA(cudaGetDevice(&dev));
+        if (dev < 0 || dev >= Forker::kDevices) return fail(QMC_ERR_CUDA, "device ordinal %d out of range", dev);
+        lock.lock();
+        if (!fk.ready[dev]) {
+            for (int k = 0; k < Forker::K; ++k) {
+                QMC_CUDA(cudaStreamCreateWithFlags(&fk.s[dev][k], cudaStreamNonBlocking));
+                QMC_CUDA(cudaEventCreateWithFlags(&fk.join[dev][k], cudaEventDisableTiming));
+            }
+            QMC_CUDA(cudaEventCreateWithFlags(&fk.fork[dev], cudaEventDisableTiming));
+            fk.ready[dev] = true;
+        }
+        std::vector<uint32_t> order(nprob);
+        for (uint32_t p = 0; p < nprob; ++p) order[p] = p;
+        auto work = [&](uint32_t p) { return (double)plans[p].N * plans[p].tau * plans[p].reff; };
+        std::sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return work(a) > work(b); });
+        double load[Forker::K] = {};
+        for (uint32_t p : order) {
+            int best = 0;
+            for (int k = 1; k < Forker::K; ++k)
+                if (load[k] < load[best]) best = k;
+            lane[p] = best;
+            load[best] += work(p);
+        }
+        used = std::min<int>(Forker::K, (int)nprob);
+        QMC_CUDA(cudaEventRecord(fk.fork[dev], caller));
+        for (int k = 0; k < used; ++k) QMC_CUDA(cudaStreamWaitEvent(fk.s[dev][k], fk.fork[dev], 0));
+    }
     for (uint32_t p = 0; p < nprob; ++p) {
         const Plan& P = plans[p];
+        cudaStream_t st_ = lane[p] < 0 ? caller : fk.s[dev][lane[p]];
+        char* ws = ws0 + ws_off[p];
+        const size_t est_off = est_offs[p];
         qmc_status st;
         if (op == QMC_OP_INTEGRATE) {
             void* rowf = d_rowf ? d_rowf[p] : nullptr;
@@ -1014,9 +1174,18 @@ static qmc_status integrate_common(int op, const qmc_rule* rules, const void* co
                 st = run_backward<float>(P, &rules[p], (const float*)d_A[p], ws, &f[p], d_upstream + p,
                                          (float*)d_gradA[p], reuse, st_);
         }
-        if (st != QMC_OK) return st;
-        est_off += (size_t)P.reff + 1;
-        ws += align256(P.total);
+        if (st != QMC_OK) {
+            // join what was forked, so that the caller's stream (or its capture) stays consistent
+            for (int k = 0; k < used; ++k) {
+                cudaEventRecord(fk.join[dev][k], fk.s[dev][k]);
+                cudaStreamWaitEvent(caller, fk.join[dev][k], 0);
+            }
+            return st;
+        }
+    }
+    for (int k = 0; k < used; ++k) {
+        QMC_CUDA(cudaEventRecord(fk.join[dev][k], fk.s[dev][k]));
+        QMC_CUDA(cudaStreamWaitEvent(caller, fk.join[dev][k], 0));
     }
     return QMC_OK;
 }
@@ -1033,6 +1202,146 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
                                   void* const* d_gradA, uint32_t flags, void* d_ws, size_t ws_bytes, void* stream) {
     return integrate_common(QMC_OP_INTEGRATE_BWD, rules, d_A, tau, nprob, f, precision, nullptr, nullptr, d_upstream,
                             d_gradA, flags, d_ws, ws_bytes, stream);
+}
+
+qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, const qmc_integrand* f, int precision,
+                        double* d_est, void* d_gradA, void* d_ws, size_t ws_bytes, void* stream, uint32_t* n_timed) {
+    if (!rule || !d_A || !f || !d_est || !d_gradA || !d_ws)
+        return fail(QMC_ERR_INVALID_ARG, "rule, d_A, f, d_est, d_gradA and d_ws must be non-NULL");
+    if (((uintptr_t)d_ws) % 256) return fail(QMC_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    Plan base;
+    t_hint = nullptr;
+    qmc_status st = make_plan(QMC_OP_INTEGRATE_BWD, rule, tau, f, precision, d_A, base);
+    if (st != QMC_OK) return st;
+    cudaStream_t st_ = reinterpret_cast<cudaStream_t>(stream);
+    char* ws = reinterpret_cast<char*>(d_ws);
+    uint32_t timed = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    QMC_CUDA(cudaEventCreate(&e0));
+    QMC_CUDA(cudaEventCreate(&e1));
+    // the timed backward reads its upstream factor dL/dQ from the mean estimate's slot (any value
+    // does: the gradients written while timing are scratch)
+    const double* d_up = d_est + base.reff;
+    // time one candidate: the forward, or the forward and the backward that reuses it
+    auto time_it = [&](const TuneVal& tv, bool bwd, float* ms) -> qmc_status {
+        Plan P;
+        t_hint = &tv;
+        qmc_status s2 = make_plan(QMC_OP_INTEGRATE_BWD, rule, tau, f, precision, d_A, P);
+        t_hint = nullptr;
+        if (s2 != QMC_OK) return s2;
+        if (P.total > ws_bytes) { *ms = -1.0f; return QMC_OK; }     // does not fit the caller's workspace
+        float best = -1.0f;
+        for (int rep = 0; rep < 4; ++rep) {
+            QMC_CUDA(cudaEventRecord(e0, st_));
+            if (precision == QMC_FP64) {
+                const double* A; int ld;
+                s2 = run_forward<double>(P, rule, (const double*)d_A, ws, f, MODE_FUSED, nullptr, nullptr, d_est, st_, &A, &ld);
+                if (s2 == QMC_OK && bwd)
+                    s2 = run_backward<double>(P, rule, (const double*)d_A, ws, f, d_up, (double*)d_gradA, true, st_);
+            } else {
+                const float* A; int ld;
+                s2 = run_forward<float>(P, rule, (const float*)d_A, ws, f, MODE_FUSED, nullptr, nullptr, d_est, st_, &A, &ld);
+                if (s2 == QMC_OK && bwd)
+                    s2 = run_backward<float>(P, rule, (const float*)d_A, ws, f, d_up, (float*)d_gradA, true, st_);
+            }
+            if (s2 != QMC_OK) return s2;
+            QMC_CUDA(cudaEventRecord(e1, st_));
+            QMC_CUDA(cudaEventSynchronize(e1));
+            float t = 0.0f;
+            QMC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0 && (best < 0.0f || t < best)) best = t;     // (the first run warms up)
+        }
+        ++timed;
+        *ms = best;
+        return QMC_OK;
+    };
+    TuneVal bestv{};
+    if (base.fine_s4) {
+        // forward: the cost model's column groups and a ladder of others (columns per CTA = 4 qpg)
+        const int quads = base.tau_pad / 4;
+        const int ladder[] = {base.cr / 4, 8, 16, 24, 32, 48, 64, 96, 128};
+        float bt = -1.0f;
+        for (int qpg : ladder) {
+            if (qpg < 1 || qpg > quads || qpg > 128) continue;
+            TuneVal tv{qpg, 0};
+            float ms = 0.0f;
+            st = time_it(tv, false, &ms);
+            if (st != QMC_OK) break;
+            if (ms > 0.0f && (bt < 0.0f || ms < bt)) { bt = ms; bestv.fwd_qpg = qpg; }
+        }
+        // adjoint: roots per CTA around the cost model's choice, with the forward just chosen
+        const long long n_root = 1LL << (base.m - base.JF);
+        const double fac[] = {1.0, 0.5, 0.75, 1.5, 2.0, 3.0};
+        float bb = -1.0f;
+        for (double fc : fac) {
+            if (st != QMC_OK) break;
+            long long rpc = (long long)(base.roots_per_cta * fc + 0.5);
+            rpc = std::max(2LL, (rpc + 1) / 2 * 2);
+            if (rpc > n_root + 1) continue;
+            TuneVal tv{bestv.fwd_qpg, (int)rpc};
+            float ms = 0.0f;
+            st = time_it(tv, true, &ms);
+            if (st != QMC_OK) break;
+            if (ms > 0.0f && (bb < 0.0f || ms < bb)) { bb = ms; bestv.bwd_rpc = (int)rpc; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != QMC_OK) return st;
+    {
+        TuneCache& tc = tune_cache();
+        std::lock_guard<std::mutex> g(tc.mu);
+        tc.m[base.tune_key] = bestv;
+    }
+    if (n_timed) *n_timed = timed;
+    return QMC_OK;
+}
+
+qmc_status qmc_tune_clear(void) {
+    TuneCache& tc = tune_cache();
+    std::lock_guard<std::mutex> g(tc.mu);
+    tc.m.clear();
+    return QMC_OK;
+}
+
+qmc_status qmc_tune_save(const char* path) {
+    if (!path) return fail(QMC_ERR_INVALID_ARG, "path is NULL");
+    TuneCache& tc = tune_cache();
+    std::lock_guard<std::mutex> g(tc.mu);
+    FILE* fh = fopen(path, "w");
+    if (!fh) return fail(QMC_ERR_INVALID_ARG, "cannot write %s", path);
+    fprintf(fh, "# qmc_gb300 schedule cache: shape key | forward column quads per CTA | adjoint roots per CTA\n");
+    for (auto& kv : tc.m) fprintf(fh, "%s|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc);
+    fclose(fh);
+    return QMC_OK;
+}
+
+qmc_status qmc_tune_load(const char* path, uint32_t* n_entries) {
+    if (!path) return fail(QMC_ERR_INVALID_ARG, "path is NULL");
+    FILE* fh = fopen(path, "r");
+    if (!fh) return fail(QMC_ERR_INVALID_ARG, "cannot read %s", path);
+    TuneCache& tc = tune_cache();
+    std::lock_guard<std::mutex> g(tc.mu);
+    char line[4096];
+    uint32_t n = 0;
+    int lineno = 0;
+    qmc_status st = QMC_OK;
+    while (fgets(line, sizeof(line), fh)) {
+        ++lineno;
+        if (line[0] == '#' || line[0] == '\n') continue;
+        char* a = strchr(line, '|');
+        char* b = a ? strchr(a + 1, '|') : nullptr;
+        int q = 0, r = 0;
+        if (!a || !b || sscanf(a + 1, "%d", &q) != 1 || sscanf(b + 1, "%d", &r) != 1 || q < 0 || r < 0 || q > 128) {
+            st = fail(QMC_ERR_INVALID_ARG, "%s:%d: not a schedule entry", path, lineno);
+            break;
+        }
+        tc.m[std::string(line, a - line)] = TuneVal{q, r};
+        ++n;
+    }
+    fclose(fh);
+    if (st == QMC_OK && n_entries) *n_entries = n;
+    return st;
 }
 
 }  // extern "C"

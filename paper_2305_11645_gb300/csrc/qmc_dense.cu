@@ -524,14 +524,16 @@ constexpr int kGradCols = 256;
 template <class T>
 __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradpart_f, const FineCols fc,
                                                      const T* __restrict__ part_c, const __grid_constant__ Chain ch,
-                                                     int tau, int tau_pad, int s, T* __restrict__ grad) {
-    __shared__ T red[8][kGradCols];
+                                                     int tau, int tau_pad, int s, T* __restrict__ grad,
+                                                     const double* __restrict__ gsum, double xc) {
+    __shared__ double red[8][kGradCols];        // (partials summed in double whatever T is)
     const int j = blockIdx.x, t0 = blockIdx.y * kGradCols;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // where column j's partials are: base + p * stride, p < count
     const T* base = nullptr;
     long long stride = 0;
     int count = 0;
+    bool coarse = false;
     for (int I = 0; I < fc.jf; ++I)
         if (fc.tau[I] > 0 && j >= fc.col0[I] && j < fc.col0[I] + fc.tau[I]) {
             base = gradpart_f + (long long)(fc.koff[I] + (j - fc.col0[I])) * tau_pad;
@@ -543,11 +545,12 @@ __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradp
             base = part_c + ch.poff[q] + (long long)(j - ch.col0[q]) * tau_pad;
             stride = (long long)ch.tau[q] * tau_pad;
             count = ch.split[q];
+            coarse = true;
         }
     constexpr int C = kGradCols / 32;
-    T v[C];
+    double v[C];
 #pragma unroll
-    for (int c = 0; c < C; ++c) v[c] = T(0);
+    for (int c = 0; c < C; ++c) v[c] = 0.0;
     int p = warp;
     for (; p + 24 < count; p += 32) {
         T w[4][C];
@@ -558,23 +561,26 @@ __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradp
             for (int c = 0; c < C; ++c) w[h][c] = t0 + 32 * c + lane < tau ? __ldg(bp + 32 * c) : T(0);
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c) v[c] += (w[0][c] + w[1][c]) + (w[2][c] + w[3][c]);
+        for (int c = 0; c < C; ++c)
+            v[c] += ((double)w[0][c] + (double)w[1][c]) + ((double)w[2][c] + (double)w[3][c]);
     }
     for (; p < count; p += 8) {
         const T* bp = base + (long long)p * stride + t0 + lane;
 #pragma unroll
         for (int c = 0; c < C; ++c)
-            if (t0 + 32 * c + lane < tau) v[c] += __ldg(bp + 32 * c);
+            if (t0 + 32 * c + lane < tau) v[c] += (double)__ldg(bp + 32 * c);
     }
 #pragma unroll
     for (int c = 0; c < C; ++c) red[warp][32 * c + lane] = v[c];
     __syncthreads();
     for (int i = threadIdx.x; i < kGradCols; i += 256) {
         if (t0 + i < tau) {
-            T acc = T(0);
+            double acc = 0.0;
 #pragma unroll
             for (int w = 0; w < 8; ++w) acc += red[w][i];
-            grad[(long long)j * tau + t0 + i] = acc;
+            // centred block products: X^T G = (X - xc)^T G + xc 1 (1^T G), 1^T G summed in double
+            if (coarse && gsum) acc += xc * gsum[t0 + i];
+            grad[(long long)j * tau + t0 + i] = (T)acc;
         }
     }
 }
@@ -582,7 +588,7 @@ __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradp
 template <class T>
 cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width, const int* koff_lev,
                                const int* col0_lev, const int* tau_lev, int jf, const T* part_c, const Chain& ch,
-                               int tau, int tau_pad, int s, T* grad, cudaStream_t st) {
+                               int tau, int tau_pad, int s, T* grad, const double* gsum, double xc, cudaStream_t st) {
     FineCols fc;
     fc.jf = jf;
     fc.kf_width = kf_width;
@@ -593,12 +599,14 @@ cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width
         fc.tau[i] = i < jf ? tau_lev[i] : 0;
     }
     const dim3 grid((unsigned)s, (unsigned)((tau + kGradCols - 1) / kGradCols));
-    k_grad_reduce<T><<<grid, 256, 0, st>>>(gradpart_f, fc, part_c, ch, tau, tau_pad, s, grad);
+    k_grad_reduce<T><<<grid, 256, 0, st>>>(gradpart_f, fc, part_c, ch, tau, tau_pad, s, grad, gsum, xc);
     return cudaGetLastError();
 }
 template cudaError_t launch_grad_reduce<float>(const float*, int, int, const int*, const int*, const int*, int,
-                                               const float*, const Chain&, int, int, int, float*, cudaStream_t);
+                                               const float*, const Chain&, int, int, int, float*, const double*, double,
+                                               cudaStream_t);
 template cudaError_t launch_grad_reduce<double>(const double*, int, int, const int*, const int*, const int*, int,
-                                                const double*, const Chain&, int, int, int, double*, cudaStream_t);
+                                                const double*, const Chain&, int, int, int, double*, const double*,
+                                                double, cudaStream_t);
 
 }  // namespace qmc

@@ -32,7 +32,21 @@ struct DevRule {
     int lev_tau[kMaxLevels];
     int lev_col0[kMaxLevels];
     long long lev_tab[kMaxLevels + 1];   // offset of level I in the distinct-row table (prefix sums)
+    // A non-periodic reduced net (Sec. 4, Algorithm 4's case): every column is on level 0 with all
+    // N rows, its points use every digit of the row index, and column j's last min(w_j, m) rows of
+    // C^(j) are zeroed by its own w: the columns wcol0[g] .. wcol0[g+1]-1 have min(w, m) = wval[g].
+    int nonper;
+    int nw;
+    int wcol0[kMaxLevels + 1], wval[kMaxLevels];
 };
+
+// min(w_j, m) of column j of a non-periodic net
+__device__ __forceinline__ int wcl_of(const DevRule& R, int j) {
+    int v = 0;
+    for (int g = 0; g < R.nw; ++g)
+        if (j >= R.wcol0[g]) v = R.wval[g];
+    return v;
+}
 
 // ---------------------------------------------------------------------------------------------
 // Point generator (bit-exact integer arithmetic).
@@ -40,7 +54,8 @@ struct DevRule {
 //   net (Sec. 4, Algorithm 3): y = XOR of the column masks selected by the digits of row
 //        (least significant first), with the last min(w_j,m) rows zeroed
 //        (eq. reduced_genmat_net2), X32 = y * 2^(32-m)
-//   q = m - min(w_j, m); row < 2^q is the row index within one period.
+//   q = m - min(w_j, m); row < 2^q is the row index within one period.  A non-periodic net
+//   passes q = m (every digit of the point index) and zeroes column j's own last rows.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t unshifted_x32(const DevRule& R, int j, uint32_t row, int q) {
     if (R.kind == KIND_LATTICE) {
@@ -66,7 +81,7 @@ __device__ __forceinline__ uint32_t unshifted_x32(const DevRule& R, int j, uint3
     uint32_t y = 0;
     for (int b = 0; b < q; ++b)
         if ((row >> b) & 1u) y ^= Cj[b];
-    const int wcl = R.m - q;
+    const int wcl = R.nonper ? wcl_of(R, j) : R.m - q;
     y &= (wcl >= 32) ? 0u : ~((1u << wcl) - 1u);
     return y << (32 - R.m);
 }
@@ -249,6 +264,8 @@ struct LevelPass {
     long long next_off, next_stride;
     int rho_tiles, t_tiles, reps;    // 128-row tiles, 256-column tiles, row tiles per next-pass tile
     long long ntiles;                // rho_tiles * t_tiles * shifts
+    long long const_off;             // first pass of centred points: float offset of the constant row
+                                     // xc sum_j a_j (added in place of a coarser pass), else -1
 };
 
 struct LevelPlan {
@@ -259,6 +276,8 @@ struct LevelPlan {
     long long a_rows;                // rows of 32 bf16 of the A pieces
     int tA;                          // A-piece rows per chunk block (columns t, a multiple of 256)
     size_t x_off, a_off;             // byte offsets of the piece areas in the workspace
+    size_t c_off;                    // byte offset of the constant row (tau_pad floats)
+    float xc;                        // centring of the points (x - xc is split; 0 or 1/2)
 };
 
 cudaError_t launch_split_a(const float* A, int ldA, int tau, const LevelPlan& lp, unsigned char* ws,
@@ -267,6 +286,12 @@ cudaError_t launch_split_x(const float* tab, long long tab_stride, const LevelPl
                            cudaStream_t st);
 cudaError_t launch_level_pass(const LevelPlan& lp, int p, int reff, int tau_pad, unsigned char* ws, cudaStream_t st);
 cudaError_t level_error_word(unsigned int* value, bool clear);
+// the constant row xc sum_{coarse j} A[j][t] of centred points, summed in double
+cudaError_t launch_const_row(const float* A, int ldA, int tau, int tau_pad, const LevelPlan& lp, unsigned char* ws,
+                             cudaStream_t st);
+// column sums of the top folded gradient level over every shift and row, in double: gsum[t]
+cudaError_t launch_col_sums(const float* F, long long shift_stride, long long rows, int reff, int tau_pad,
+                            double* part, double* gsum, cudaStream_t st);
 
 template <class T> struct FineArgs {
     const T* tab; long long tab_stride;       // distinct-row table, per shift
@@ -328,7 +353,8 @@ cudaError_t launch_coarse_grad(const T* tab, long long tab_stride, const T* Froo
 template <class T>
 cudaError_t launch_grad_reduce(const T* gradpart_f, int nfine_part, int kf_width, const int* koff_lev,
                                const int* col0_lev, const int* tau_lev, int jf, const T* part_c,
-                               const Chain& ch, int tau, int tau_pad, int s, T* grad, cudaStream_t st);
+                               const Chain& ch, int tau, int tau_pad, int s, T* grad, const double* gsum,
+                               double xc, cudaStream_t st);
 
 // tensor-core block products (split tier: pieces = 3, bf16 tier: pieces = 1); FP32 data
 int tc_fwd_rows();        // rows of a forward tile (the chain's tile0 counts tiles of this many rows)
@@ -338,7 +364,7 @@ cudaError_t launch_coarse_fwd_tc(const float* tab, long long tab_stride, const f
                                  cudaStream_t st);
 cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
                                   const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
-                                  float* part, int reff, int ntiles, int pieces, cudaStream_t st);
+                                  float* part, int reff, int ntiles, int pieces, float xc, cudaStream_t st);
 cudaError_t tc_error_word(unsigned int* value, bool clear);
 // one CTA whose bounded wait on an mbarrier that nothing completes runs out after `polls` polls
 cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t st);

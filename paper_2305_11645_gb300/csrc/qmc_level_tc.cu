@@ -109,7 +109,7 @@ struct SplitXArgs {
 template <int P>
 __global__ void __launch_bounds__(256) k_split_x(const float* __restrict__ tab, long long tab_stride,
                                                  const __grid_constant__ SplitXArgs sa, long long rows_per_shift,
-                                                 uint4* __restrict__ xp) {
+                                                 uint4* __restrict__ xp, float xc) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int r = blockIdx.y;
     if (i >= sa.blk0[sa.nlev]) return;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) k_split_x(const float* __restrict__ tab, 
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int jj = kc * 32 + g * 8 + q;
-        v[q] = jj < sg.tau ? __ldg(src + ((long long)jj << sg.logn)) : 0.0f;
+        v[q] = jj < sg.tau ? __ldg(src + ((long long)jj << sg.logn)) - xc : 0.0f;
     }
     uint32_t w[P][4];
 #pragma unroll
@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
             float* out = wsf + ps.out_off + (long long)ti.r * ps.out_stride + rho * 4;
             const float* nx = has_next ? wsf + ps.next_off + (long long)ti.r * ps.next_stride + (rho & nmask) * 4
                                        : nullptr;
+            const float* cr = ps.const_off >= 0 ? wsf + ps.const_off : nullptr;
             const uint32_t lane_addr = tmem + (uint32_t)(a * LT_N + half * 128) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
             for (int cg = 0; cg < 4; ++cg) {
@@ -331,7 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
                     const int t = tb + 4 * q;
                     pv[q] = (has_next && row_ok && t < tau_pad)
                                 ? __ldg(reinterpret_cast<const float4*>(nx + ((long long)(t >> 2) << ps.logn_next) * 4))
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
+                                : (cr && t < tau_pad) ? __ldg(reinterpret_cast<const float4*>(cr + t))
+                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 uint32_t d[32];
                 tmem_ld32(lane_addr + cg * 32, d);
@@ -413,6 +415,58 @@ SplitXArgs split_args(const LevelPlan& lp, bool a_side, int tA) {
 
 }  // namespace
 
+// c[t] = xc sum over the coarse columns j of A[j][t], accumulated in double (one thread per column t)
+__global__ void __launch_bounds__(128) k_const_row(const float* __restrict__ A, int ldA, int tau, int tau_pad,
+                                                   const __grid_constant__ SplitXArgs sa, float xc, float* __restrict__ c) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= tau_pad) return;
+    double acc = 0.0;
+    if (t < tau)
+        for (int l = 0; l < sa.nlev; ++l)
+            for (int jj = 0; jj < sa.seg[l].tau; ++jj) acc += (double)__ldg(A + (long long)(sa.seg[l].col0 + jj) * ldA + t);
+    c[t] = (float)((double)xc * acc);
+}
+
+cudaError_t launch_const_row(const float* A, int ldA, int tau, int tau_pad, const LevelPlan& lp, unsigned char* ws,
+                             cudaStream_t st) {
+    const SplitXArgs sa = split_args(lp, true, lp.tA);
+    k_const_row<<<(tau_pad + 127) / 128, 128, 0, st>>>(A, ldA, tau, tau_pad, sa, lp.xc,
+                                                       reinterpret_cast<float*>(ws + lp.c_off));
+    return cudaGetLastError();
+}
+
+// Column sums of F (rows x tau_pad per shift) over every shift and row, in double and a fixed order:
+// CTA (t block, chunk c) sums rows c, c + 64, ... of every shift into part[c][t]; the last kernel sums
+// the 64 chunks in order.
+constexpr int kColChunks = 64;
+__global__ void __launch_bounds__(128) k_col_sums(const float* __restrict__ F, long long shift_stride, long long rows,
+                                                  int reff, int tau_pad, double* __restrict__ part) {
+    const int t = blockIdx.x * 128 + threadIdx.x;
+    const int c = blockIdx.y;
+    if (t >= tau_pad) return;
+    double acc = 0.0;
+    for (int r = 0; r < reff; ++r)
+        for (long long k = c; k < rows; k += kColChunks) acc += (double)__ldg(F + r * shift_stride + k * tau_pad + t);
+    part[(long long)c * tau_pad + t] = acc;
+}
+__global__ void __launch_bounds__(128) k_col_sums_final(const double* __restrict__ part, int tau_pad,
+                                                        double* __restrict__ gsum) {
+    const int t = blockIdx.x * 128 + threadIdx.x;
+    if (t >= tau_pad) return;
+    double acc = 0.0;
+    for (int c = 0; c < kColChunks; ++c) acc += part[(long long)c * tau_pad + t];
+    gsum[t] = acc;
+}
+
+cudaError_t launch_col_sums(const float* F, long long shift_stride, long long rows, int reff, int tau_pad,
+                            double* part, double* gsum, cudaStream_t st) {
+    k_col_sums<<<dim3((tau_pad + 127) / 128, kColChunks), 128, 0, st>>>(F, shift_stride, rows, reff, tau_pad, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_col_sums_final<<<(tau_pad + 127) / 128, 128, 0, st>>>(part, tau_pad, gsum);
+    return cudaGetLastError();
+}
+
 cudaError_t level_error_word(unsigned int* value, bool clear) {
     cudaError_t e = cudaMemcpyFromSymbol(value, g_level_error, sizeof(unsigned int));
     if (e != cudaSuccess || !clear) return e;
@@ -429,8 +483,8 @@ cudaError_t launch_split_x(const float* tab, long long tab_stride, const LevelPl
     if (n == 0) return cudaSuccess;
     dim3 grid((unsigned)((n + 255) / 256), (unsigned)reff);
     uint4* xp = reinterpret_cast<uint4*>(ws + lp.x_off);
-    if (lp.pieces == 3) k_split_x<3><<<grid, 256, 0, st>>>(tab, tab_stride, sa, lp.x_rows_per_shift, xp);
-    else k_split_x<1><<<grid, 256, 0, st>>>(tab, tab_stride, sa, lp.x_rows_per_shift, xp);
+    if (lp.pieces == 3) k_split_x<3><<<grid, 256, 0, st>>>(tab, tab_stride, sa, lp.x_rows_per_shift, xp, lp.xc);
+    else k_split_x<1><<<grid, 256, 0, st>>>(tab, tab_stride, sa, lp.x_rows_per_shift, xp, lp.xc);
     return cudaGetLastError();
 }
 

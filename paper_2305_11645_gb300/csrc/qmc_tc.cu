@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
                                                            const float* __restrict__ Froot, long long root_stride,
                                                            const float* __restrict__ Fchain, long long chain_stride,
                                                            int tau_pad, const __grid_constant__ Chain ch,
-                                                           float* __restrict__ part, int reff) {
+                                                           float* __restrict__ part, int reff, float xcen) {
     constexpr uint32_t TILEA = TM * ROWB, TILEB = NJ * ROWB;
     constexpr uint32_t OPA = P * TILEA, OPB = P * TILEB;
     constexpr uint32_t STAGE = OPA + OPB;
@@ -341,8 +341,9 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
                 if (xj < (int)nmma) {
                     const float4* xr = reinterpret_cast<const float4*>(rs + RAW_F + xj * RAW_XROW) + 2 * xq;
                     const float4 a = xr[0], b = xr[1];
-                    const float xc[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-                    store_group<P>(Xs, TILEB, xj, xq, xc);
+                    const float d = xj < nj ? xcen : 0.0f;          // (padding rows stay zero)
+                    const float xv[8] = {a.x - d, a.y - d, a.z - d, a.w - d, b.x - d, b.y - d, b.z - d, b.w - d};
+                    store_group<P>(Xs, TILEB, xj, xq, xv);
                 }
             }
             ok = publish_stage(ok);
@@ -433,6 +434,10 @@ __global__ void __launch_bounds__(256, 1) k_coarse_grad_tc(const float* __restri
             for (int g = 0; g < 4; ++g)
                 if (g < 2 * ksteps) store_group<P>(Fs, TILEA, tq, g, fc + 8 * g);
             if (khalf < ksteps) {
+                // (centred rows; rows beyond the split's end meet F = 0, padding columns are not stored)
+                const float d = jrow_ok ? xcen : 0.0f;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) xc[i] -= d;
                 store_group<P>(Xs, TILEB, jrow, 2 * khalf, xc);
                 store_group<P>(Xs, TILEB, jrow, 2 * khalf + 1, xc + 8);
             }
@@ -528,7 +533,7 @@ cudaError_t launch_coarse_fwd_tc(const float* tab, long long tab_stride, const f
 
 cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
                                   const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch,
-                                  float* part, int reff, int ntiles, int pieces, cudaStream_t st) {
+                                  float* part, int reff, int ntiles, int pieces, float xc, cudaStream_t st) {
     if (ch.count == 0 || ntiles == 0) return cudaSuccess;
     if (pieces != 1 && pieces != 3) return cudaErrorInvalidValue;
     dim3 grid(ntiles, (tau_pad + TM - 1) / TM);
@@ -537,13 +542,13 @@ cudaError_t launch_coarse_grad_tc(const float* tab, long long tab_stride, const 
                                              (int)bwd_smem<3>());
         if (e != cudaSuccess) return e;
         k_coarse_grad_tc<3><<<grid, 256, bwd_smem<3>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
-                                                              chain_stride, tau_pad, ch, part, reff);
+                                                              chain_stride, tau_pad, ch, part, reff, xc);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_coarse_grad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)bwd_smem<1>());
         if (e != cudaSuccess) return e;
         k_coarse_grad_tc<1><<<grid, 256, bwd_smem<1>(), st>>>(tab, tab_stride, Froot, root_stride, Fchain,
-                                                              chain_stride, tau_pad, ch, part, reff);
+                                                              chain_stride, tau_pad, ch, part, reff, xc);
     }
     return cudaGetLastError();
 }

@@ -142,6 +142,19 @@ def periodic_net_masks(g: np.random.Generator, m: int, w: np.ndarray) -> np.ndar
     return C
 
 
+def nonsingular_net_masks(g: np.random.Generator, m: int, s: int) -> np.ndarray:
+    """Column masks of s random nonsingular m x m GF(2) generating matrices: the nets of Sec. 4
+    before the row reduction, which the library applies (the last min(w_j, m) rows zeroed).  The
+    reduced matrices then generally have nonzero columns beyond m - w_j: a non-periodic reduced
+    net (Algorithm 4's case), whose first m - w_j rows stay linearly independent."""
+    C = np.zeros((s, m), dtype=np.uint32)
+    for j in range(s):
+        B = gf2_nonsingular(g, m)
+        for col in range(m):
+            C[j, col] = sum(1 << (m - 1 - p) for p in range(m) if B[p, col])
+    return C
+
+
 def random_shifts(g: np.random.Generator, R: int, s: int, force_odd: bool = False) -> np.ndarray:
     D = g.integers(0, 1 << 32, size=(R, s), dtype=np.uint64).astype(np.uint32)
     if force_odd:
@@ -225,6 +238,44 @@ def c5(m: int = 20, s: int = 1024, R: int = 8) -> Problem:
     D = random_shifts(rng(5, P_SHIFT), R, s)
     return Problem(LATTICE, m, w, A, z=z, shifts=D, transform=T_IDENTITY,
                    f_kind=F_LOGSUMEXP, name="c5")
+
+
+def stiffness_terms(s: int, M: int) -> np.ndarray:
+    """Matrices C_j (s x M x M) of a PDE with an affine random coefficient (Sec. 1's assembly
+    example): the 1-D P1 finite-element stiffness matrix on M interior nodes of a uniform mesh of
+    (0, 1), h = 1/(M+1), for the coefficient term psi_j(t) = (j+1)^-2 sin((j+1) pi t) taken at each
+    element's midpoint.  Element e (nodes e-1, e in 0-based interior numbering) adds
+    psi_j(t_e)/h [[1, -1], [-1, 1]]; the boundary elements touch one interior node."""
+    h = 1.0 / (M + 1)
+    mid = (np.arange(M + 1) + 0.5) * h                     # element midpoints, elements 0..M
+    C = np.zeros((s, M, M))
+    for j in range(s):
+        k = psi_coeff(j) * np.sin((j + 1) * math.pi * mid) / h
+        for e in range(M + 1):
+            a, b = e - 1, e                                # the element's interior nodes (-1, M: none)
+            if a >= 0:
+                C[j, a, a] += k[e]
+            if b < M:
+                C[j, b, b] += k[e]
+            if a >= 0 and b < M:
+                C[j, a, b] -= k[e]
+                C[j, b, a] -= k[e]
+    return C
+
+
+def psi_coeff(j: int) -> float:
+    return (j + 1.0) ** -2
+
+
+def pde_assembly(m: int = 16, s: int = 256, M: int = 32, R: int = 1) -> Problem:
+    """The PDE matrix-assembly workload: a reduced lattice (w_j = min(floor(log2(j+1)), 12), random odd
+    z, R random shifts) and A whose row j is C_j flattened, so that row k of X A is D_k flattened
+    (tau = M^2)."""
+    w = log2_weights(s, 12)
+    z = odd_z(rng(7, P_Z), m, w)
+    D = random_shifts(rng(7, P_SHIFT), R, s) if R else None
+    A = stiffness_terms(s, M).reshape(s, M * M).astype(np.float32)
+    return Problem(LATTICE, m, w, A, z=z, shifts=D, transform=T_IDENTITY, f_kind=F_NONE, name="pde_assembly")
 
 
 def fd_pairs(config_id: int, s: int, tau: int, count: int = 64) -> np.ndarray:

@@ -79,13 +79,17 @@ def test_z_outside_units(lib, z):
 
 def test_singular_and_nonperiodic_nets(lib):
     m = 3
-    # singular leading block (two equal columns)
+    # singular (two equal columns, the third row alone cannot make rank 3)
     C = np.array([[4, 4, 1]], dtype=np.uint32)
     assert status(lib, Rule(I.DIGITAL_NET, m, [0], C=C)) == L.QMC_ERR_INVALID_ARG
-    assert "singular" in lib.qmc_last_error().decode()
-    # w=1 but column 3 (beyond m-w) nonzero after row reduction: not periodic
+    assert "rank" in lib.qmc_last_error().decode()
+    # w=1 and column 3 (beyond m-w) nonzero after the row reduction: a non-periodic reduced net
+    # (Algorithm 4's case), accepted; its first two rows [[1,0,1],[0,1,0]] have rank 2
     C = np.array([[4, 2, 4]], dtype=np.uint32)
-    assert status(lib, Rule(I.DIGITAL_NET, m, [1], C=C)) == L.QMC_ERR_UNSUPPORTED
+    assert status(lib, Rule(I.DIGITAL_NET, m, [1], C=C)) == L.QMC_OK
+    # w=1 with the first two reduced rows dependent ([[1,0,1],[1,0,1]]): rejected
+    C = np.array([[6, 0, 6]], dtype=np.uint32)
+    assert status(lib, Rule(I.DIGITAL_NET, m, [1], C=C)) == L.QMC_ERR_INVALID_ARG
     # bits above row 1
     C = np.array([[8, 2, 1]], dtype=np.uint32)
     assert status(lib, Rule(I.DIGITAL_NET, m, [0], C=C)) == L.QMC_ERR_INVALID_ARG
@@ -313,3 +317,39 @@ def test_net_leading_block_rank_check(lib, seed):
             C[j, col] = sum(int(B[p, col]) << (m - 1 - p) for p in range(q))
     st = status(lib, Rule(I.DIGITAL_NET, m, w, C=C))
     assert st == (L.QMC_OK if expect_ok else L.QMC_ERR_INVALID_ARG), lib.qmc_last_error()
+
+
+def tune_key(p, precision, f_kind, tau):
+    """The schedule cache's shape key: m, precision, integrand, tau padded to 4, shifts, and the
+    column count of every level min(w_j, m) = 0..m."""
+    lev = [int(np.sum(np.minimum(p.w, p.m) == I)) for I in range(p.m + 1)]
+    return (f"m{p.m} p{precision} f{f_kind} t{(tau + 3) // 4 * 4} r{max(p.R, 1)} L" + ",".join(map(str, lev)))
+
+
+def test_schedule_cache_file_and_planner(lib, tmp_path):
+    """A loaded schedule changes the plan (in the FP32 tier the forward's column groups size the row
+    partials, the largest area of this workspace, so the workspace changes with them); save writes
+    what was loaded; a malformed file is rejected."""
+    p = I.c2(m=10, s=64, dtype=np.float32)
+    r = Rule.from_problem(p)
+    f = Integrand(I.F_CALL_MEAN_EXP, (0.2, 1.0))
+    assert lib.qmc_tune_clear() == L.QMC_OK
+    st, base = ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)
+    assert st == L.QMC_OK
+    key = tune_key(p, L.QMC_FP32, I.F_CALL_MEAN_EXP, 64)
+    path = tmp_path / "sched.txt"
+    path.write_text(f"# comment\n{key}|16|6\n")              # 64 columns per CTA: one column group
+    n = ctypes.c_uint32(0)
+    assert lib.qmc_tune_load(str(path).encode(), ctypes.byref(n)) == L.QMC_OK and n.value == 1
+    st, tuned = ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)
+    assert st == L.QMC_OK and tuned != base                  # (the cost model takes 16 groups of 4 columns)
+    out = tmp_path / "saved.txt"
+    assert lib.qmc_tune_save(str(out).encode()) == L.QMC_OK
+    assert f"{key}|16|6" in out.read_text().splitlines()
+    assert lib.qmc_tune_clear() == L.QMC_OK
+    assert ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)[1] == base
+    bad = tmp_path / "bad.txt"
+    bad.write_text("no separators here\n")
+    assert lib.qmc_tune_load(str(bad).encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
+    assert lib.qmc_tune_load(str(tmp_path / "missing.txt").encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
+    assert lib.qmc_tune_clear() == L.QMC_OK

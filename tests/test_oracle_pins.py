@@ -593,3 +593,22 @@ def test_base_b_net_reduces_like_base_2(seed):
         x = O.net_points_base(b, m3, [wj], [Cm])[:, 0]
         vals, counts = np.unique(np.round(x * b ** q).astype(np.int64), return_counts=True)
         assert np.array_equal(vals, np.arange(b ** q)) and np.all(counts == b ** wj)
+
+
+def test_pde_assembly_pins():
+    """Sec. 1's D_k = sum_j x_{j,k} C_j: with C_j = delta_{j,j0} I every D_k is x_{k,j0} I, and over
+    the whole point set sum_k D_k = sum_j c_j C_j with the exact column sums c_j (P5)."""
+    p = I.pde_assembly(m=7, s=12, M=5, R=1)
+    C = I.stiffness_terms(12, 5)
+    for j0 in (0, 5, 11):
+        E = np.zeros_like(C)
+        E[j0] = np.eye(5)
+        D = O.assemble(p, E)
+        X = O.points(p)
+        assert np.array_equal(D, X[:, j0][:, None, None] * np.eye(5)[None])
+    D = O.assemble(p, C)
+    c = np.array([float(v) for v in closed_form_column_sums(p, 0)])
+    assert np.allclose(D.sum(axis=0), np.einsum("j,juv->uv", c, C), rtol=1e-13, atol=1e-12)
+    # the stiffness terms are symmetric and their rows sum to zero away from the boundary
+    assert np.allclose(C, C.transpose(0, 2, 1))
+    assert np.allclose(C[:, 1:-1, :].sum(axis=2), 0.0, atol=1e-9)
