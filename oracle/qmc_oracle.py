@@ -21,7 +21,9 @@ reordering beyond what the definitions state:
       does the same over F_b for any prime b.
   O3  random shifts as 32-bit fixed point D_j * 2^-32 (Sec. 2.3):
       lattice {x + Delta} = (X32 + D) mod 2^32, nets (digital shift)
-      X32 XOR D, with X32 = x * 2^32.
+      X32 XOR D, with X32 = x * 2^32.  Lattices in a prime base b > 2 have points
+      u / b^q that 32 bits cannot hold: they are float64, x = num / b^m, and
+      {x + Delta} is the rounded sum, less 1 if it reaches 1 (lattice_points_base).
   O4  coordinate transforms applied elementwise (Sec. 2.3): identity,
       centring x - 1/2, inverse normal CDF (scipy.special.ndtri), tent
       1 - |1 - 2x| (Sec. 1.2).
@@ -191,14 +193,14 @@ def alg4_product(m: int, w, C: np.ndarray, A, exact: bool = False):
 
 # ----------------------------------------------------------------------------- O9 reduced Monte Carlo
 
-def mc_sample_index(m: int, w, ks=None) -> np.ndarray:
+def mc_sample_index(m: int, w, ks=None, b: int = 2) -> np.ndarray:
     """Index of the sample that point n uses in coordinate j (eq. randpts), by the mixed-radix
-    digits of n.  The paper starts from w_1 = 0; a first column with w_1 > 0 is handled by a
-    leading virtual coordinate of weight 0, so that n < N is always representable."""
-    N = 1 << m
+    digits of n (N_j = b^(m-w_j)).  The paper starts from w_1 = 0; a first column with w_1 > 0 is
+    handled by a leading virtual coordinate of weight 0, so that n < N is always representable."""
+    N = b ** m
     ks = np.arange(N, dtype=np.int64) if ks is None else np.asarray(ks, dtype=np.int64)
     wl = [0] + [min(int(wj), m) for wj in w] + [m]          # virtual w_0 = 0, ..., w_{s+1} = m
-    Nl = [1 << (m - wj) for wj in wl]                       # N_0 = N, N_1, ..., N_{s+1} = 1
+    Nl = [b ** (m - wj) for wj in wl]                       # N_0 = N, N_1, ..., N_{s+1} = 1
     Ml = [Nl[i] // Nl[i + 1] for i in range(len(Nl) - 1)]  # M_i = N_i / N_{i+1}
     digits = [(ks // Nl[i + 1]) % Ml[i] for i in range(len(Ml))]     # m_i, place value N_{i+1}
     out = np.empty((len(ks), len(w)), dtype=np.int64)
@@ -211,11 +213,11 @@ def mc_sample_index(m: int, w, ks=None) -> np.ndarray:
     return out
 
 
-def mc_x32(m: int, w, y: np.ndarray, ks=None) -> np.ndarray:
+def mc_x32(m: int, w, y: np.ndarray, ks=None, b: int = 2) -> np.ndarray:
     """X32 of the reduced MC points of one replica: x_{j,n} = y_{j, index}, where replica row y
     holds column j's samples at offset sum_{j' < j} N_{j'}."""
-    idx = mc_sample_index(m, w, ks)
-    off = np.cumsum([0] + [1 << (m - min(int(wj), m)) for wj in w])[:-1]
+    idx = mc_sample_index(m, w, ks, b)
+    off = np.cumsum([0] + [b ** (m - min(int(wj), m)) for wj in w])[:-1]
     return np.asarray(y, dtype=np.uint32)[idx + off[None, :]]
 
 
@@ -258,13 +260,33 @@ def unshifted_x32(problem, ks=None) -> np.ndarray:
     return net_x32(problem.m, problem.w, problem.C, None, ks)
 
 
+def lattice_points_base(b: int, m: int, w, z, shift=None, ks=None) -> np.ndarray:
+    """Rank-1 lattice points in base b as float64 (O1 with the 32-bit shift of O3): x = num / b^m
+    with num = (k b^{min(w_j,m)} z_j) mod b^m from the unreduced generating vector, one rounded
+    division; shifted, {x + D_j 2^-32} = x + D_j 2^-32, less 1 if it reaches 1 (one rounded
+    addition, the subtraction exact)."""
+    x = lattice_numerators(b, m, w, z, ks).astype(np.float64) / float(b ** m)
+    if shift is not None:
+        x = x + np.asarray(shift, dtype=np.float64)[None, :] * (1.0 / TWO32)
+        x = np.where(x >= 1.0, x - 1.0, x)
+    return x
+
+
 def shifted_rows(problem, ks):
     """(r, X) for every shift r (reduced MC: every replica) of the rows ks, X the transformed
     points (O4): the unshifted points of the rows are formed once and each shift is applied to
     them (O3)."""
     if problem.kind == REDUCED_MC:
         for r in range(problem.R_eff):
-            yield r, transform(mc_x32(problem.m, problem.w, problem.y[r], ks), problem.transform)
+            yield r, transform(mc_x32(problem.m, problem.w, problem.y[r], ks, problem.b), problem.transform)
+        return
+    if problem.b != 2:
+        if problem.kind != LATTICE:
+            raise ValueError("base b > 2: lattices and reduced MC only")
+        for r in range(problem.R_eff):
+            shift = None if problem.shifts is None else problem.shifts[r]
+            yield r, transform_x(lattice_points_base(problem.b, problem.m, problem.w, problem.z, shift, ks),
+                                 problem.transform)
         return
     base = unshifted_x32(problem, ks)
     for r in range(problem.R_eff):
@@ -284,7 +306,12 @@ def x32_points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
 
 
 def transform(x32: np.ndarray, kind: int) -> np.ndarray:
-    x = np.asarray(x32, dtype=np.float64) * (1.0 / TWO32)     # exact: 32 bits < 53
+    return transform_x(np.asarray(x32, dtype=np.float64) * (1.0 / TWO32), kind)   # exact: 32 bits < 53
+
+
+def transform_x(x: np.ndarray, kind: int) -> np.ndarray:
+    """O4 on points given as float64."""
+    x = np.asarray(x, dtype=np.float64)
     if kind == T_IDENTITY:
         return x
     if kind == T_CENTER:
@@ -299,6 +326,14 @@ def transform(x32: np.ndarray, kind: int) -> np.ndarray:
 
 def points(problem, shift_idx: int = 0, ks=None) -> np.ndarray:
     """Rows x_k^T (after shift and transform) as float64, for k in ks (default all)."""
+    if problem.b != 2 and problem.kind != REDUCED_MC:
+        if problem.kind != LATTICE:
+            raise ValueError("base b > 2: lattices and reduced MC only")
+        shift = None if problem.shifts is None else problem.shifts[shift_idx]
+        return transform_x(lattice_points_base(problem.b, problem.m, problem.w, problem.z, shift, ks),
+                           problem.transform)
+    if problem.kind == REDUCED_MC:
+        return transform(mc_x32(problem.m, problem.w, problem.y[shift_idx], ks, problem.b), problem.transform)
     return transform(x32_points(problem, shift_idx, ks), problem.transform)
 
 

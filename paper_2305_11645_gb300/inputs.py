@@ -318,6 +318,40 @@ def random_problem(seed: int, kind: int = LATTICE, m: Optional[int] = None, s: O
                    f_kind=f_kind, f_params=tuple(f_params), name=f"rand{seed}")
 
 
+def units_z(g: np.random.Generator, b: int, m: int, w: np.ndarray) -> np.ndarray:
+    """z_j uniform in U_{b^q} (prime b: not divisible by b, 1 <= z_j < b^q), z_j = 1 where w_j >= m."""
+    z = np.ones(len(w), dtype=np.uint32)
+    for j, wj in enumerate(w):
+        q = m - min(int(wj), m)
+        if q >= 1:
+            while True:
+                v = int(g.integers(1, b ** q))
+                if v % b:
+                    z[j] = v
+                    break
+    return z
+
+
+def base_b_problem(seed: int, b: int, m: int, s: int, tau: int, R: int = 0, kind: int = LATTICE,
+                   transform: int = T_IDENTITY, f_kind: int = F_NONE, f_params=(0.0, 0.0, 0.0, 0.0),
+                   dtype=np.float64, w=None) -> Problem:
+    """A reduced lattice (Sec. 1.3, N = b^m) or reduced MC point set (Sec. 5, N_j = b^(m-w_j)) in a
+    prime base b, with A ~ N(0, 1/s)."""
+    g = rng(101, P_MISC, seed)
+    w = random_weights(g, m, s) if w is None else np.asarray(w, dtype=np.uint32)
+    A = (g.standard_normal((s, tau)) / math.sqrt(s)).astype(dtype)
+    if kind == REDUCED_MC:
+        T = sum(b ** (m - min(int(wj), m)) for wj in w)
+        y = g.integers(0, 1 << 32, size=(max(R, 1), T), dtype=np.uint64).astype(np.uint32)
+        if transform == T_INV_NORMAL:
+            y |= np.uint32(1)
+        return Problem(REDUCED_MC, m, w, A, y=y, transform=transform, f_kind=f_kind, f_params=tuple(f_params), b=b,
+                       name=f"b{b}mc{seed}")
+    D = random_shifts(g, R, s, force_odd=transform == T_INV_NORMAL) if R else None
+    return Problem(LATTICE, m, w, A, z=units_z(g, b, m, w), shifts=D, transform=transform, f_kind=f_kind,
+                   f_params=tuple(f_params), b=b, name=f"b{b}lat{seed}")
+
+
 def named(name: str) -> List[Problem]:
     if name == "c1":
         return [c1()]

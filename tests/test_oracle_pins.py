@@ -612,3 +612,55 @@ def test_pde_assembly_pins():
     # the stiffness terms are symmetric and their rows sum to zero away from the boundary
     assert np.allclose(C, C.transpose(0, 2, 1))
     assert np.allclose(C[:, 1:-1, :].sum(axis=2), 0.0, atol=1e-9)
+
+
+# ----------------------------------------------------------------------------- prime bases b > 2
+
+@pytest.mark.parametrize("b,m", [(3, 4), (5, 3), (7, 2)])
+def test_base_b_lattice_points_exact(b, m):
+    """Base-b lattice points (Sec. 1.3) against exact rationals: x = {k b^w z / b^m} from the
+    unreduced definition equals the reduced (k z mod b^q)/b^q, the shifted {x + D 2^-32} is within
+    two roundings of the exact value, and every column over one period is a permutation of the grid."""
+    w = np.array([0, 0, 1, min(2, m), m, m + 1], dtype=np.uint32)
+    p = I.base_b_problem(b * 10 + m, b, m, len(w), 2, R=2, w=w)
+    X0 = O.lattice_points_base(b, m, p.w, p.z)
+    N = b ** m
+    for j, wj in enumerate(p.w):
+        q = m - min(int(wj), m)
+        for k in range(N):
+            red = Fraction((k * int(p.z[j])) % (b ** q), b ** q) if q else Fraction(0)
+            assert abs(Fraction(float(X0[k, j])) - red) <= Fraction(1, 2 ** 53)      # one rounding
+        per = sorted(Fraction(int(round(float(X0[k, j]) * b ** q)), b ** q) for k in range(b ** q))
+        assert per == [Fraction(u, b ** q) for u in range(b ** q)]
+    for r in range(2):
+        Xs = O.points(p, r)
+        for j in range(len(w)):
+            for k in range(N):
+                q = m - min(int(p.w[j]), m)
+                red = Fraction((k * int(p.z[j])) % (b ** q), b ** q) if q else Fraction(0)
+                exact = red + Fraction(int(p.shifts[r, j]), 2 ** 32)
+                exact -= math.floor(exact)
+                assert abs(Fraction(float(Xs[k, j])) - exact) <= Fraction(2, 2 ** 53)
+
+
+@pytest.mark.parametrize("b", [3, 5])
+def test_base_b_mc_index_is_n_mod_Nj(b):
+    m = 4 if b == 3 else 3
+    w = np.array([0, 1, 1, 2, m], dtype=np.uint32)
+    idx = O.mc_sample_index(m, w, b=b)
+    for j, wj in enumerate(w):
+        Nj = b ** (m - min(int(wj), m))
+        assert np.array_equal(idx[:, j], np.arange(b ** m) % Nj)
+
+
+@pytest.mark.parametrize("b", [3, 5])
+def test_base_b_linear_closed_form(b):
+    """Unshifted: column j sums to b^w (b^q - 1)/2 over the N points, so the linear integrand's
+    estimate is sum_j c_j sum_t a_jt / (N tau) exactly (up to float rounding)."""
+    m = 5 if b == 3 else 3
+    p = I.base_b_problem(7 + b, b, m, 9, 4, R=0, f_kind=I.F_LINEAR_MEAN)
+    c = np.array([b ** min(int(wj), m) * (b ** (m - min(int(wj), m)) - 1) / 2 for wj in p.w])
+    want = c @ np.asarray(p.A, dtype=np.float64).sum(axis=1) / (p.N * p.tau)
+    Q, _ = O.estimate(p)
+    assert abs(Q[0] - want) <= 1e-14 * max(1.0, abs(want))
+    assert np.allclose(O.points(p).sum(axis=0), c, rtol=1e-14, atol=1e-12)
