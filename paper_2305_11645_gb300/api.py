@@ -59,7 +59,7 @@ class Rule:
         if self.kind == REDUCED_MC:
             if y is None:
                 raise ValueError("a reduced MC rule needs its samples y")
-            T = sum(1 << (self.m - min(int(wj), self.m)) for wj in self.w)
+            T = sum(self.b ** (self.m - min(int(wj), self.m)) for wj in self.w)
             self.y = _u32(np.asarray(y).reshape(-1, T))
             self.R = int(self.y.shape[0])        # independent replicas
         self._dev = {}
@@ -91,7 +91,7 @@ class Rule:
         of a non-periodic net."""
         if self.nonperiodic():
             return self.s * self.N
-        return int(sum(2 ** (self.m - min(int(w), self.m)) for w in self.w))
+        return int(sum(self.b ** (self.m - min(int(w), self.m)) for w in self.w))
 
     @property
     def R_eff(self) -> int:

@@ -126,9 +126,21 @@ qmc_status validate(const qmc_rule* r) {
         return fail(QMC_ERR_INVALID_ARG, "kind %d is not QMC_LATTICE, QMC_DIGITAL_NET, QMC_REDUCED_MC or "
                     "QMC_POLY_LATTICE", r->kind);
     if (r->b < 2) return fail(QMC_ERR_INVALID_ARG, "base b=%u must be a prime >= 2", r->b);
-    if (r->b != 2) return fail(QMC_ERR_UNSUPPORTED, "base b=%u: only b=2 is built", r->b);
+    for (uint32_t d = 2; d * d <= r->b; ++d)
+        if (r->b % d == 0) return fail(QMC_ERR_INVALID_ARG, "base b=%u is not prime", r->b);
     if (r->m < 1) return fail(QMC_ERR_INVALID_ARG, "m=%u: N = b^m needs m >= 1", r->m);
-    if (r->m > 30) return fail(QMC_ERR_UNSUPPORTED, "m=%u: N = 2^m is limited to m <= 30", r->m);
+    if (r->b == 2 && r->m > 30) return fail(QMC_ERR_UNSUPPORTED, "m=%u: N = 2^m is limited to m <= 30", r->m);
+    if (r->b > 2) {
+        // Sec. 1.3 lattices and Sec. 5 reduced MC in base b; nets and polynomial lattices over F_b are
+        // not built
+        if (r->kind != QMC_LATTICE && r->kind != QMC_REDUCED_MC)
+            return fail(QMC_ERR_UNSUPPORTED, "base b=%u: only lattices and reduced Monte Carlo are built", r->b);
+        unsigned long long N = 1;
+        for (uint32_t i = 0; i < r->m; ++i) {
+            N *= r->b;
+            if (N > (1ull << 31)) return fail(QMC_ERR_UNSUPPORTED, "N = %u^%u exceeds 2^31 points", r->b, r->m);
+        }
+    }
     if (r->s < 1 || r->s > 65536) return fail(QMC_ERR_INVALID_ARG, "s=%u outside [1, 65536]", r->s);
     if (!r->w) return fail(QMC_ERR_INVALID_ARG, "w is NULL");
     for (uint32_t j = 1; j < r->s; ++j)
@@ -139,14 +151,20 @@ qmc_status validate(const qmc_rule* r) {
         return fail(QMC_ERR_INVALID_ARG, "transform %d unknown", r->transform);
     if (r->R > 65535) return fail(QMC_ERR_INVALID_ARG, "R=%u shifts: at most 65535", r->R);
     const uint32_t m = r->m;
+    // b^e for the base's exponents (b^m <= 2^31 for b > 2 was checked above)
+    auto bpow = [&](uint32_t e) -> unsigned long long {
+        unsigned long long v = 1;
+        for (uint32_t i = 0; i < e; ++i) v *= r->b;
+        return v;
+    };
     if (r->kind == QMC_REDUCED_MC) {
-        // Sec. 5: the caller's i.i.d. samples, N_j = 2^(m - min(w_j, m)) per column and replica
+        // Sec. 5: the caller's i.i.d. samples, N_j = b^(m - min(w_j, m)) per column and replica
         if (!r->z) return fail(QMC_ERR_INVALID_ARG, "reduced MC needs its samples in z");
         if (r->C || r->shift || r->d_shift)
             return fail(QMC_ERR_INVALID_ARG, "reduced MC takes no C and no shift (R counts independent replicas)");
         if (r->transform == QMC_T_INV_NORMAL) {
             unsigned long long T = 0;
-            for (uint32_t j = 0; j < r->s; ++j) T += 1ull << (m - std::min(r->w[j], m));
+            for (uint32_t j = 0; j < r->s; ++j) T += bpow(m - std::min(r->w[j], m));
             // (blocks reduced by a branch-free minimum, which the compiler vectorises; a block
             // holding a zero is then searched for its index)
             const unsigned long long words = T * std::max<uint32_t>(r->R, 1);
@@ -167,6 +185,41 @@ qmc_status validate(const qmc_rule* r) {
     if (r->R > 0 && !r->shift) return fail(QMC_ERR_INVALID_ARG, "R=%u but shift is NULL", r->R);
     if (r->transform == QMC_T_INV_NORMAL && r->R == 0)
         return fail(QMC_ERR_INVALID_ARG, "the inverse-normal transform needs a random shift (x=0 maps to -inf)");
+    if (r->b > 2) {
+        // z_j in U_{b^q}: 1 <= z_j < b^q and not divisible by the prime b (z_j = 1 when q = 0)
+        if (!r->z) return fail(QMC_ERR_INVALID_ARG, "lattice rule needs z");
+        for (uint32_t j = 0; j < r->s; ++j) {
+            const uint32_t q = m - std::min(r->w[j], m);
+            const unsigned long long n = bpow(q);
+            const uint32_t z = r->z[j];
+            if (q == 0 ? z != 1 : (z < 1 || z % r->b == 0 || z >= n))
+                return fail(QMC_ERR_INVALID_ARG, "z[%u]=%u not in U_{%u^%u}", j, z, r->b, q);
+        }
+        if (r->transform == QMC_T_INV_NORMAL) {
+            // the shifted point {u / b^q + D 2^-32} is formed in double: reject a shift that puts a point
+            // within 2^-50 of 1 (the rounded sum could reach 1, so the point 0 and -inf), or D = 0 (the
+            // point u = 0 stays 0).  The nearest u / b^q to 1 - D 2^-32 is found in exact integers.
+            for (uint32_t i = 0; i < r->R; ++i)
+                for (uint32_t j = 0; j < r->s; ++j) {
+                    const unsigned long long D = r->shift[(size_t)i * r->s + j];
+                    const uint32_t q = m - std::min(r->w[j], m);
+                    const long long n = (long long)bpow(q);
+                    const long long e = (long long)((1ull << 32) - D);          // 2^32 (1 - D 2^-32)
+                    bool near = D == 0;
+                    const long long u0 = (long long)(((unsigned long long)e * (unsigned long long)n) >> 32);
+                    for (long long u = u0 - 1; u <= u0 + 1 && !near; ++u) {
+                        if (u < 0 || u >= n) continue;
+                        const long long diff = u * (1LL << 32) - e * n;          // 2^32 n (u/n - (1 - D 2^-32))
+                        const unsigned long long ad = (unsigned long long)(diff < 0 ? -diff : diff);
+                        if (ad < (unsigned long long)n && (ad << 18) < (unsigned long long)n) near = true;
+                    }
+                    if (near)
+                        return fail(QMC_ERR_INVALID_ARG, "shift %u of column %u (0x%llx) puts a point at or within "
+                                    "2^-50 of 0 under the inverse-normal transform", i, j, D);
+                }
+        }
+        return QMC_OK;
+    }
     if (r->transform == QMC_T_INV_NORMAL) {
         // Column j takes, over one period, every value u 2^(32-q) with u < 2^q (q = m - min(w_j, m)):
         // the lattice's u = k z_j mod 2^q with z_j odd, the polynomial lattice's carry-less product with
@@ -287,6 +340,14 @@ struct Plan {
     // biases long sums of terms of one sign), and the constant 1/2 returns as one exact term
     float xc = 0.0f;
     size_t off_gsum = 0;           // backward: column sums of the folded gradient (65 x tau_pad doubles)
+    // base b > 2: the levels with columns from the coarsest down, each written at bl_rows rows
+    bool base_b = false;
+    int b = 2;
+    long long lev_n[kMaxLevels] = {};
+    int bl_n = 0, bl_lev[kMaxLevels] = {};
+    long long bl_rows[kMaxLevels] = {}, bl_kper[kMaxLevels] = {};
+    int bl_split[kMaxLevels] = {};
+    size_t bl_out[kMaxLevels] = {}, bl_F[kMaxLevels] = {}, bl_part[kMaxLevels] = {}, off_G = 0;
     size_t off_gen = 0, off_shift = 0, off_A = 0, off_tab = 0, off_B = 0, off_S = 0, off_rowpart = 0, off_rowmax = 0,
            off_rowsave = 0, off_fpart = 0, off_ticket = 0, off_F = 0, off_Fchain = 0, off_gradpart = 0, off_partc = 0,
            total = 0;
@@ -374,10 +435,156 @@ void plan_levels(Plan& P) {
     P.lv = true;
 }
 
+// The plan of a rule in a prime base b > 2: the generic top-down levels on the CUDA cores (every
+// tier; the tensor-core tiers compute in FP32), no binary fine band (the last level is written at
+// all N rows), the integrand row by row, and the adjoint's folds and block gradients per level.
+qmc_status make_plan_b(int op, const qmc_rule* r, uint32_t tau, const qmc_integrand* f, int precision,
+                       const void* d_A, Plan& P) {
+    P.op = op;
+    P.base_b = true;
+    P.b = (int)r->b;
+    P.kind = r->kind; P.m = (int)r->m; P.s = (int)r->s; P.transform = r->transform;
+    P.R = (int)r->R; P.reff = std::max(P.R, 1);
+    for (int I = 0; I <= P.m; ++I) {
+        long long n = 1;
+        for (int i = 0; i < P.m - I; ++i) n *= P.b;
+        P.lev_n[I] = n;
+        P.lev_tau[I] = 0;
+        P.lev_col0[I] = -1;
+    }
+    P.N = P.lev_n[0];
+    for (int j = 0; j < P.s; ++j) {
+        const int I = (int)std::min<uint32_t>(r->w[j], r->m);
+        if (P.lev_col0[I] < 0) P.lev_col0[I] = j;
+        P.lev_tau[I]++;
+    }
+    {
+        int next = P.s;
+        for (int I = P.m; I >= 0; --I) {
+            if (P.lev_col0[I] < 0) P.lev_col0[I] = next;
+            else next = P.lev_col0[I];
+        }
+    }
+    P.lev_tab[0] = 0;
+    for (int I = 0; I <= P.m; ++I) P.lev_tab[I + 1] = P.lev_tab[I] + (long long)P.lev_tau[I] * P.lev_n[I];
+    P.T_tot = P.lev_tab[P.m + 1];
+    P.tab_stride = (P.T_tot + 3) / 4 * 4;
+    P.need_gen = (r->d_gen == nullptr);
+    P.has_shift = P.kind != QMC_REDUCED_MC && P.R > 0;
+    P.need_shift = (P.has_shift && r->d_shift == nullptr);
+    size_t off = 0;
+    P.off_gen = off;
+    if (P.need_gen) off = align256(off + sizeof(uint32_t) * gen_words(P));
+    P.off_shift = off;
+    if (P.need_shift) off = align256(off + sizeof(uint32_t) * (size_t)P.R * P.s);
+    if (op == QMC_OP_GEN_POINTS) { P.total = off; return QMC_OK; }
+    if (precision != QMC_FP64 && precision != QMC_FP32 && precision != QMC_SPLIT && precision != QMC_BF16)
+        return fail(QMC_ERR_INVALID_ARG, "precision %d unknown", precision);
+    if (tau < 1 || tau > 65536) return fail(QMC_ERR_INVALID_ARG, "tau=%u outside [1, 65536]", tau);
+    P.precision = precision;
+    P.tc_pieces = 0;
+    P.elt = precision == QMC_FP64 ? 8 : 4;
+    P.tau = (int)tau;
+    P.tau_pad = (int)((tau + 3) / 4 * 4);
+    if (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) {
+        if (!f) return fail(QMC_ERR_INVALID_ARG, "integrand is NULL");
+        if (f->kind < QMC_F_LINEAR_MEAN || f->kind > QMC_F_LOGSUMEXP)
+            return fail(QMC_ERR_INVALID_ARG, "integrand kind %d unknown (QMC_F_NONE is only for the product)", f->kind);
+        P.fkind = f->kind;
+    }
+    P.JF = 0;
+    P.cg_count = 1;
+    P.bl_n = 0;
+    for (int I = P.m; I >= 0; --I)
+        if (P.lev_tau[I] > 0) P.bl_lev[P.bl_n++] = I;
+    for (int q = 0; q < P.bl_n; ++q) P.bl_rows[q] = q + 1 == P.bl_n ? P.N : P.lev_n[P.bl_lev[q]];
+    {
+        const long long rpt = std::max(1LL, std::min(16LL, P.N * P.reff / (152LL * 8 * 256 * 4)));
+        P.nblk = (int)((P.N + 256 * rpt - 1) / (256 * rpt));
+    }
+    const size_t E = (size_t)P.elt;
+    P.need_pad = !((tau % 4) == 0 && d_A != nullptr && (((uintptr_t)d_A) % 16) == 0);
+    P.off_A = off;
+    if (P.need_pad) off = align256(off + E * (size_t)P.s * P.tau_pad);
+    P.off_tab = off;
+    off = align256(off + E * (size_t)P.reff * P.tab_stride);
+    const bool fused = op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD;
+    P.S_per_shift = P.N * P.tau_pad;
+    P.off_S = off;
+    if (fused && P.bl_n) off = align256(off + E * (size_t)P.reff * P.S_per_shift);
+    if (fused) {
+        P.off_rowsave = off;
+        off = align256(off + 2 * E * (size_t)P.reff * P.N);
+        P.off_fpart = off;
+        off = align256(off + sizeof(double) * (size_t)P.reff * P.nblk);
+        P.off_ticket = off;
+        off = align256(off + sizeof(unsigned int));
+    }
+    // shared region: the levels' partial sums (dead after the last level), the row partials, then
+    // the backward's gradients
+    const size_t u0 = off;
+    size_t uend = u0, o = u0;
+    for (int q = 0; q + 1 < P.bl_n; ++q) {
+        P.bl_out[q] = o;
+        o = align256(o + E * (size_t)P.reff * (size_t)P.bl_rows[q] * P.tau_pad);
+    }
+    if (P.bl_n) P.bl_out[P.bl_n - 1] = P.off_S;
+    uend = std::max(uend, o);
+    if (fused) {
+        o = u0;
+        P.off_rowpart = o;
+        o = align256(o + E * (size_t)P.reff * P.N);
+        P.off_rowmax = o;
+        if (P.fkind == QMC_F_LOGSUMEXP) o = align256(o + E * (size_t)P.reff * P.N);
+        uend = std::max(uend, o);
+    }
+    if (op == QMC_OP_INTEGRATE_BWD) {
+        o = u0;
+        P.off_G = o;
+        o = align256(o + E * (size_t)P.reff * (size_t)P.N * P.tau_pad);
+        // F of every level, from the lowest up (the lowest level's F is G itself when it has N rows)
+        P.chb = Chain{};
+        long long poff = 0;
+        for (int q = P.bl_n - 1; q >= 0; --q) {
+            const int I = P.bl_lev[q];
+            const long long n = P.lev_n[I];
+            if (n == P.N) P.bl_F[q] = P.off_G;
+            else {
+                P.bl_F[q] = o;
+                o = align256(o + E * (size_t)P.reff * (size_t)n * P.tau_pad);
+            }
+            const long long K = (long long)P.reff * n;
+            long long split = std::min(4096LL, (K + 8191) / 8192);
+            P.bl_kper[q] = (K + split - 1) / split;
+            P.bl_split[q] = (int)split;
+            const int e = P.chb.count++;
+            P.chb.col0[e] = P.lev_col0[I];
+            P.chb.tau[e] = P.lev_tau[I];
+            P.chb.split[e] = (int)split;
+            P.chb.poff[e] = poff;
+            poff += split * P.lev_tau[I] * P.tau_pad;
+        }
+        for (int q = 0; q < P.bl_n; ++q) P.bl_part[q] = 0;
+        const size_t part0 = o;
+        o = align256(o + E * (size_t)std::max(poff, 1LL));
+        P.off_partc = part0;
+        P.partc_elems = poff;
+        P.groups = 1;
+        P.kf_width = 1;
+        P.off_gradpart = o;                  // (no fine band: one zero-sized partial)
+        o = align256(o + E * (size_t)P.tau_pad);
+        uend = std::max(uend, o);
+    }
+    P.total = uend;
+    if (P.chb.count > kMaxChain) return fail(QMC_ERR_UNSUPPORTED, "too many weight levels");
+    return QMC_OK;
+}
+
 qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integrand* f, int precision,
                      const void* d_A, Plan& P) {
     qmc_status st = validate(r);
     if (st != QMC_OK) return st;
+    if (r->b > 2) return make_plan_b(op, r, tau, f, precision, d_A, P);
     P.op = op;
     P.kind = r->kind; P.m = (int)r->m; P.s = (int)r->s; P.transform = r->transform;
     P.R = (int)r->R; P.reff = std::max(P.R, 1);
@@ -705,6 +912,8 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         o = align256(o + (size_t)L.a_rows * 64);
         L.c_off = o;
         o = align256(o + 4 * (size_t)P.tau_pad);
+        L.cpart_off = o;
+        if (P.xc != 0.0f) o = align256(o + sizeof(double) * 64 * (size_t)P.tau_pad);
         L.xc = P.xc;
         for (int q = 0; q < L.npass; ++q) L.pass[q].const_off = -1;
         if (P.xc != 0.0f) L.pass[0].const_off = (long long)(L.c_off / 4);
@@ -760,6 +969,8 @@ DevRule dev_rule(const Plan& P, const qmc_rule* r, char* ws) {
     R.nlev = P.m + 1;
     for (int I = 0; I <= P.m; ++I) { R.lev_tau[I] = P.lev_tau[I]; R.lev_col0[I] = P.lev_col0[I]; }
     for (int I = 0; I <= P.m + 1; ++I) R.lev_tab[I] = P.lev_tab[I];
+    R.b = P.b;
+    for (int I = 0; I <= P.m; ++I) R.lev_n[I] = P.base_b ? P.lev_n[I] : (1LL << (P.m - I));
     R.nonper = P.nonper ? 1 : 0;
     R.nw = 0;
     if (P.nonper) {
@@ -819,10 +1030,102 @@ FineArgs<T> fine_args(const Plan& P, char* ws, const T* A, int ldA, const qmc_in
     return a;
 }
 
+// base b > 2: the table, the levels top down (the last at all N rows: the root values, or the
+// product itself when materialised), then the integrand's row sums and the finalisation
+template <class T>
+qmc_status run_forward_b(const Plan& P, const qmc_rule* r, const T* dA, char* ws, const qmc_integrand* f, int mode,
+                         T* dP, T* rowf, double* est, cudaStream_t st, const T** Aused, int* ldA_used) {
+    qmc_status s0 = upload_rule(P, r, ws, st);
+    if (s0 != QMC_OK) return s0;
+    const DevRule R = dev_rule(P, r, ws);
+    const T* A = dA;
+    int ldA = P.tau;
+    if (P.need_pad) {
+        T* Ap = reinterpret_cast<T*>(ws + P.off_A);
+        QMC_LAUNCH(st, "k_pad_A", launch_pad_A<T>(dA, Ap, P.s, P.tau, P.tau_pad, st));
+        A = Ap;
+        ldA = P.tau_pad;
+    }
+    *Aused = A;
+    *ldA_used = ldA;
+    T* tab = reinterpret_cast<T*>(ws + P.off_tab);
+    unsigned int* ticket = mode == MODE_FUSED ? reinterpret_cast<unsigned int*>(ws + P.off_ticket) : nullptr;
+    QMC_LAUNCH(st, "k_table_b", launch_table_b<T>(R, tab, P.T_tot, P.tab_stride, P.reff, ticket, st));
+    const bool mat = mode == MODE_MATERIALIZE;
+    for (int q = 0; q < P.bl_n; ++q) {
+        const int I = P.bl_lev[q];
+        LevelB lv{I, P.lev_tau[I], P.lev_col0[I], P.lev_n[I], P.lev_tab[I], P.bl_rows[q], q ? P.bl_rows[q - 1] : 1};
+        const bool last = q + 1 == P.bl_n;
+        T* out = last && mat ? dP : reinterpret_cast<T*>(ws + P.bl_out[q]);
+        const long long out_stride = last && mat ? P.N * P.tau : P.bl_rows[q] * P.tau_pad;
+        const T* next = q ? reinterpret_cast<const T*>(ws + P.bl_out[q - 1]) : nullptr;
+        QMC_LAUNCH(st, "k_level_b", launch_level_b<T>(tab, P.tab_stride, A, ldA, P.tau_pad, lv, out, out_stride, next,
+                                                     q ? P.bl_rows[q - 1] * P.tau_pad : 0, last && mat, P.tau,
+                                                     P.reff, st));
+    }
+    if (mat && P.bl_n == 0)                  // no columns with points: P = 0
+        QMC_CUDA(cudaMemsetAsync(dP, 0, sizeof(T) * (size_t)P.reff * P.N * P.tau, st));
+    if (mode == MODE_FUSED) {
+        if (P.bl_n == 0) QMC_CUDA(cudaMemsetAsync(ws + P.off_S, 0, sizeof(T) * (size_t)P.reff * P.S_per_shift, st));
+        T* rowpart = reinterpret_cast<T*>(ws + P.off_rowpart);
+        T* rowmax = reinterpret_cast<T*>(ws + P.off_rowmax);
+        const double c0 = f->params[0];
+        QMC_LAUNCH(st, "k_rows_b", launch_rows_b<T>(reinterpret_cast<const T*>(ws + P.off_S), P.S_per_shift, P.N, P.tau,
+                                                   P.fkind, kappa_of(P.fkind, c0), c0, rowpart, rowmax, P.reff, st));
+        T* rowsave = reinterpret_cast<T*>(ws + P.off_rowsave);
+        double* fpart = reinterpret_cast<double*>(ws + P.off_fpart);
+        const double coef_scale = gfac_of(P.fkind, c0) / ((double)P.reff * (double)P.N);
+        QMC_LAUNCH(st, "k_rows_finalize",
+                   launch_rows_finalize<T>(rowpart, rowmax, 1, P.N, P.reff, P.fkind, (double)P.tau, c0, f->params[1],
+                                           coef_scale, rowsave, rowf, fpart, P.nblk, ticket, est, st));
+    }
+    return QMC_OK;
+}
+
+// base b > 2 adjoint: G = f'(Y)/(R N) row by row, folded level by level from the lowest up, each
+// level's block gradient X~_I^T F_I in row splits, and the fixed-order sum of the splits
+template <class T>
+qmc_status run_backward_b(const Plan& P, const qmc_rule* r, const T* dA, char* ws, const qmc_integrand* f,
+                          const double* upstream, T* grad, bool reuse, cudaStream_t st) {
+    const T* A;
+    int ldA;
+    if (!reuse) {
+        qmc_status s0 = run_forward_b<T>(P, r, dA, ws, f, MODE_FUSED, nullptr, nullptr, nullptr, st, &A, &ldA);
+        if (s0 != QMC_OK) return s0;
+    }
+    const double c0 = f->params[0];
+    T* G = reinterpret_cast<T*>(ws + P.off_G);
+    QMC_LAUNCH(st, "k_grad_rows_b",
+               launch_grad_rows_b<T>(reinterpret_cast<const T*>(ws + P.off_S), P.S_per_shift, P.N, P.tau, P.tau_pad,
+                                     P.fkind, kappa_of(P.fkind, c0), c0, reinterpret_cast<const T*>(ws + P.off_rowsave),
+                                     upstream, G, P.reff, st));
+    const T* tab = reinterpret_cast<const T*>(ws + P.off_tab);
+    T* partc = reinterpret_cast<T*>(ws + P.off_partc);
+    const T* prev = G;
+    long long n_prev = P.N;
+    for (int q = P.bl_n - 1, e = 0; q >= 0; --q, ++e) {
+        const int I = P.bl_lev[q];
+        const long long n = P.lev_n[I];
+        T* F = reinterpret_cast<T*>(ws + P.bl_F[q]);
+        if (n < n_prev) QMC_LAUNCH(st, "k_fold_b", launch_fold_b<T>(prev, n_prev, F, n, P.tau_pad, P.reff, st));
+        LevelB lv{I, P.lev_tau[I], P.lev_col0[I], n, P.lev_tab[I], n, 1};
+        QMC_LAUNCH(st, "k_grad_b", launch_grad_b<T>(tab, P.tab_stride, F, lv, P.bl_kper[q], P.bl_split[q], P.reff,
+                                                   P.tau_pad, partc + P.chb.poff[e], st));
+        prev = F;
+        n_prev = n;
+    }
+    int koff[4] = {0, 0, 0, 0}, col0[4] = {0, 0, 0, 0}, taul[4] = {0, 0, 0, 0};
+    QMC_LAUNCH(st, "k_grad_reduce",
+               launch_grad_reduce<T>(reinterpret_cast<const T*>(ws + P.off_gradpart), 0, 1, koff, col0, taul, 0, partc,
+                                     P.chb, P.tau, P.tau_pad, P.s, grad, nullptr, 0.0, st));
+    return QMC_OK;
+}
+
 // forward through the fine kernel (fused or materialised); returns the A pointer/ld used
 template <class T>
 qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, const qmc_integrand* f, int mode,
                        T* dP, T* rowf, double* est, cudaStream_t st, const T** Aused, int* ldA_used) {
+    if (P.base_b) return run_forward_b<T>(P, r, dA, ws, f, mode, dP, rowf, est, st, Aused, ldA_used);
     qmc_status s0 = upload_rule(P, r, ws, st);
     if (s0 != QMC_OK) return s0;
     const DevRule R = dev_rule(P, r, ws);
@@ -894,6 +1197,7 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
 template <class T>
 qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, const qmc_integrand* f,
                         const double* upstream, T* grad, bool reuse, cudaStream_t st) {
+    if (P.base_b) return run_backward_b<T>(P, r, dA, ws, f, upstream, grad, reuse, st);
     const T* A;
     int ldA;
     if (!reuse) {
@@ -1038,6 +1342,11 @@ qmc_status qmc_gen_points(const qmc_rule* rule, uint32_t shift_idx, int layout, 
     st = upload_rule(P, rule, ws, st_);
     if (st != QMC_OK) return st;
     const DevRule R = dev_rule(P, rule, ws);
+    if (P.base_b) {
+        QMC_LAUNCH(st_, "k_points_b", launch_points_b(R, d_out, (long long)need, layout == QMC_LAYOUT_FULL,
+                                                      (int)shift_idx, st_));
+        return QMC_OK;
+    }
     if (layout == QMC_LAYOUT_FULL) QMC_LAUNCH(st_, "k_points_full", launch_points_full(R, d_out, (int)shift_idx, st_));
     else QMC_LAUNCH(st_, "k_points_distinct", launch_points_distinct(R, d_out, P.T_tot, (int)shift_idx, st_));
     return QMC_OK;

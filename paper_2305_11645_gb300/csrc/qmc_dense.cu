@@ -548,9 +548,9 @@ __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradp
             coarse = true;
         }
     constexpr int C = kGradCols / 32;
-    double v[C];
+    T v[C];                                      // (a warp's partials in T, the 8 warp sums in double)
 #pragma unroll
-    for (int c = 0; c < C; ++c) v[c] = 0.0;
+    for (int c = 0; c < C; ++c) v[c] = T(0);
     int p = warp;
     for (; p + 24 < count; p += 32) {
         T w[4][C];
@@ -561,17 +561,16 @@ __global__ void __launch_bounds__(256) k_grad_reduce(const T* __restrict__ gradp
             for (int c = 0; c < C; ++c) w[h][c] = t0 + 32 * c + lane < tau ? __ldg(bp + 32 * c) : T(0);
         }
 #pragma unroll
-        for (int c = 0; c < C; ++c)
-            v[c] += ((double)w[0][c] + (double)w[1][c]) + ((double)w[2][c] + (double)w[3][c]);
+        for (int c = 0; c < C; ++c) v[c] += (w[0][c] + w[1][c]) + (w[2][c] + w[3][c]);
     }
     for (; p < count; p += 8) {
         const T* bp = base + (long long)p * stride + t0 + lane;
 #pragma unroll
         for (int c = 0; c < C; ++c)
-            if (t0 + 32 * c + lane < tau) v[c] += (double)__ldg(bp + 32 * c);
+            if (t0 + 32 * c + lane < tau) v[c] += __ldg(bp + 32 * c);
     }
 #pragma unroll
-    for (int c = 0; c < C; ++c) red[warp][32 * c + lane] = v[c];
+    for (int c = 0; c < C; ++c) red[warp][32 * c + lane] = (double)v[c];
     __syncthreads();
     for (int i = threadIdx.x; i < kGradCols; i += 256) {
         if (t0 + i < tau) {

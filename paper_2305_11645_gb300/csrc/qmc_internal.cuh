@@ -38,6 +38,9 @@ struct DevRule {
     int nonper;
     int nw;
     int wcol0[kMaxLevels + 1], wval[kMaxLevels];
+    // a prime base b > 2 (Sec. 1.3, Sec. 5): level I has n_I = b^(m-I) distinct rows
+    int b;
+    long long lev_n[kMaxLevels];
 };
 
 // min(w_j, m) of column j of a non-periodic net
@@ -229,6 +232,36 @@ struct FoldLevels {
 constexpr int kMaxCR = 256;          // columns per CTA of the fine forward kernel
 
 // ---------------------------------------------------------------------------------------------
+// Base b > 2: one weight level of the top-down sum (qmc_base_b.cu).  Level I's n = b^(m-I)
+// distinct rows of its tau columns (A's rows col0 ..), written at n_out rows (n, or N for the
+// last level) on top of the coarser level's n_next rows.
+// ---------------------------------------------------------------------------------------------
+struct LevelB {
+    int level, tau, col0;
+    long long n, tab, n_out, n_next;
+};
+template <class T>
+cudaError_t launch_table_b(const DevRule& R, T* tab, long long T_tot, long long stride, int reff, unsigned int* ticket,
+                           cudaStream_t st);
+cudaError_t launch_points_b(const DevRule& R, uint32_t* out, long long total, bool full, int shift_idx,
+                            cudaStream_t st);
+template <class T>
+cudaError_t launch_level_b(const T* tab, long long tab_stride, const T* A, int ldA, int tau_pad, const LevelB& lv,
+                           T* out, long long out_stride, const T* next, long long next_stride, bool rowmajor, int tau,
+                           int reff, cudaStream_t st);
+template <class T>
+cudaError_t launch_rows_b(const T* S, long long S_stride, long long N, int tau, int F, double kappa, double c0,
+                          T* rowpart, T* rowmax, int reff, cudaStream_t st);
+template <class T>
+cudaError_t launch_grad_rows_b(const T* S, long long S_stride, long long N, int tau, int tau_pad, int F, double kappa,
+                               double c0, const T* rowsave, const double* upstream, T* G, int reff, cudaStream_t st);
+template <class T>
+cudaError_t launch_fold_b(const T* src, long long n_src, T* dst, long long n_dst, int tau_pad, int reff, cudaStream_t st);
+template <class T>
+cudaError_t launch_grad_b(const T* tab, long long tab_stride, const T* F, const LevelB& lv, long long kper, int splits,
+                          int reff, int tau_pad, T* part, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------------
 // Algorithm 2 on the tensor cores, top down: a pass computes, for rho < n_out,
 //   Pt_out[rho] = sum over its levels I of X~_I[rho mod n_I] A~_I + Pt_next[rho mod n_next],
 // where Pt_next is the previous (coarser) pass's output (none for the first pass).  One level
@@ -277,6 +310,7 @@ struct LevelPlan {
     int tA;                          // A-piece rows per chunk block (columns t, a multiple of 256)
     size_t x_off, a_off;             // byte offsets of the piece areas in the workspace
     size_t c_off;                    // byte offset of the constant row (tau_pad floats)
+    size_t cpart_off;                // byte offset of its 64 x tau_pad double partial sums
     float xc;                        // centring of the points (x - xc is split; 0 or 1/2)
 };
 

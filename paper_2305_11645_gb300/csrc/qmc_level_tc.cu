@@ -311,6 +311,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
         const bool has_next = ps.logn_next >= 0;
         const long long nmask = has_next ? (1LL << ps.logn_next) - 1 : 0;
         long long n = 0;
+        const float* cr = ps.const_off >= 0 ? wsf + ps.const_off : nullptr;
+        // the coarser pass's rows (or the constant row) of one 32-column group of a tile
+        auto load_group = [&](const TileIdx& ti, int cg, float4 (&pv)[8]) {
+            const long long rho = ti.rho0 + quarter * 32 + lane;
+            const bool row_ok = rho < n_out;
+            const float* nx = has_next ? wsf + ps.next_off + (long long)ti.r * ps.next_stride + (rho & nmask) * 4
+                                       : nullptr;
+            const int tb = ti.t0 + half * 128 + cg * 32;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int t = tb + 4 * q;
+                pv[q] = (has_next && row_ok && t < tau_pad)
+                            ? __ldg(reinterpret_cast<const float4*>(nx + ((long long)(t >> 2) << ps.logn_next) * 4))
+                            : (cr && t < tau_pad) ? __ldg(reinterpret_cast<const float4*>(cr + t))
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        float4 pn[8];                 // the next group's values, loaded one group ahead
+        if (blockIdx.x < ps.ntiles) load_group(tile_of(ps, blockIdx.x), 0, pn);
         for (long long tile = blockIdx.x; tile < ps.ntiles; tile += gridDim.x, ++n) {
             const int a = (int)(n & 1);
             if (!bar_wait(smem_u32(&tfull[a]), (uint32_t)((n >> 1) & 1))) { ok = false; break; }
@@ -319,22 +338,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
             const long long rho = ti.rho0 + quarter * 32 + lane;
             const bool row_ok = rho < n_out;
             float* out = wsf + ps.out_off + (long long)ti.r * ps.out_stride + rho * 4;
-            const float* nx = has_next ? wsf + ps.next_off + (long long)ti.r * ps.next_stride + (rho & nmask) * 4
-                                       : nullptr;
-            const float* cr = ps.const_off >= 0 ? wsf + ps.const_off : nullptr;
             const uint32_t lane_addr = tmem + (uint32_t)(a * LT_N + half * 128) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
             for (int cg = 0; cg < 4; ++cg) {
                 const int tb = ti.t0 + half * 128 + cg * 32;        // first column of the group
                 float4 pv[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int t = tb + 4 * q;
-                    pv[q] = (has_next && row_ok && t < tau_pad)
-                                ? __ldg(reinterpret_cast<const float4*>(nx + ((long long)(t >> 2) << ps.logn_next) * 4))
-                                : (cr && t < tau_pad) ? __ldg(reinterpret_cast<const float4*>(cr + t))
-                                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
+                for (int q = 0; q < 8; ++q) pv[q] = pn[q];
+                if (cg < 3) load_group(ti, cg + 1, pn);
+                else if (tile + gridDim.x < ps.ntiles) load_group(tile_of(ps, tile + gridDim.x), 0, pn);
                 uint32_t d[32];
                 tmem_ld32(lane_addr + cg * 32, d);
                 tmem_wait_ld();
@@ -415,26 +427,6 @@ SplitXArgs split_args(const LevelPlan& lp, bool a_side, int tA) {
 
 }  // namespace
 
-// c[t] = xc sum over the coarse columns j of A[j][t], accumulated in double (one thread per column t)
-__global__ void __launch_bounds__(128) k_const_row(const float* __restrict__ A, int ldA, int tau, int tau_pad,
-                                                   const __grid_constant__ SplitXArgs sa, float xc, float* __restrict__ c) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= tau_pad) return;
-    double acc = 0.0;
-    if (t < tau)
-        for (int l = 0; l < sa.nlev; ++l)
-            for (int jj = 0; jj < sa.seg[l].tau; ++jj) acc += (double)__ldg(A + (long long)(sa.seg[l].col0 + jj) * ldA + t);
-    c[t] = (float)((double)xc * acc);
-}
-
-cudaError_t launch_const_row(const float* A, int ldA, int tau, int tau_pad, const LevelPlan& lp, unsigned char* ws,
-                             cudaStream_t st) {
-    const SplitXArgs sa = split_args(lp, true, lp.tA);
-    k_const_row<<<(tau_pad + 127) / 128, 128, 0, st>>>(A, ldA, tau, tau_pad, sa, lp.xc,
-                                                       reinterpret_cast<float*>(ws + lp.c_off));
-    return cudaGetLastError();
-}
-
 // Column sums of F (rows x tau_pad per shift) over every shift and row, in double and a fixed order:
 // CTA (t block, chunk c) sums rows c, c + 64, ... of every shift into part[c][t]; the last kernel sums
 // the 64 chunks in order.
@@ -464,6 +456,37 @@ cudaError_t launch_col_sums(const float* F, long long shift_stride, long long ro
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_col_sums_final<<<(tau_pad + 127) / 128, 128, 0, st>>>(part, tau_pad, gsum);
+    return cudaGetLastError();
+}
+
+// c[t] = xc * (sum of 64 chunk partials of the coarse rows of A), in double
+__global__ void __launch_bounds__(128) k_const_final(const double* __restrict__ part, int tau, int tau_pad, float xc,
+                                                     float* __restrict__ c) {
+    const int t = blockIdx.x * 128 + threadIdx.x;
+    if (t >= tau_pad) return;
+    double acc = 0.0;
+    for (int k = 0; k < 64; ++k) acc += part[(long long)k * tau_pad + t];
+    c[t] = t < tau ? (float)((double)xc * acc) : 0.0f;
+}
+
+cudaError_t launch_const_row(const float* A, int ldA, int tau, int tau_pad, const LevelPlan& lp, unsigned char* ws,
+                             cudaStream_t st) {
+    // the coarse columns are the contiguous rows col0 .. s-1 of A (w is nondecreasing): their column
+    // sums in 64 row chunks, then the chunks in order
+    const SplitXArgs sa = split_args(lp, true, lp.tA);
+    int j0 = 1 << 30, j1 = 0;
+    for (int l = 0; l < sa.nlev; ++l) {
+        j0 = std::min(j0, sa.seg[l].col0);
+        j1 = std::max(j1, sa.seg[l].col0 + sa.seg[l].tau);
+    }
+    if (j1 <= j0) return cudaSuccess;
+    double* part = reinterpret_cast<double*>(ws + lp.cpart_off);
+    if (ldA != tau_pad) return cudaErrorInvalidValue;
+    k_col_sums<<<dim3((tau_pad + 127) / 128, 64), 128, 0, st>>>(A + (long long)j0 * ldA, 0, j1 - j0, 1, tau_pad, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // (A's row stride is tau_pad: A is read in place only when tau is a multiple of 4)
+    k_const_final<<<(tau_pad + 127) / 128, 128, 0, st>>>(part, tau, tau_pad, lp.xc, reinterpret_cast<float*>(ws + lp.c_off));
     return cudaGetLastError();
 }
 

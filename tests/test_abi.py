@@ -51,10 +51,11 @@ def test_valid_rules_pass(lib):
 
 
 def test_invalid_base_and_sizes(lib):
-    p = I.random_problem(1)
+    p = I.random_problem(1, kind=I.DIGITAL_NET)
     r = Rule.from_problem(p)
-    r.b = 3
+    r.b = 3                                   # nets over F_b, b > 2, are not built
     assert status(lib, r) == L.QMC_ERR_UNSUPPORTED
+    p = I.random_problem(1)
     r.b = 1
     assert status(lib, r) == L.QMC_ERR_INVALID_ARG
     r = Rule.from_problem(p)
@@ -353,3 +354,23 @@ def test_schedule_cache_file_and_planner(lib, tmp_path):
     assert lib.qmc_tune_load(str(bad).encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
     assert lib.qmc_tune_load(str(tmp_path / "missing.txt").encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
     assert lib.qmc_tune_clear() == L.QMC_OK
+
+
+def test_base_b_rules_checked_on_the_host(lib):
+    """Base b > 2 (lattices, reduced MC): a zero shift under the inverse normal (the point u = 0
+    stays 0), z_j divisible by b, a composite base and a net over F_b are rejected; valid rules pass."""
+    for b, m in ((3, 7), (5, 5), (7, 4)):
+        for kind in (I.LATTICE, I.REDUCED_MC):
+            p = I.base_b_problem(1 + b, b, m, 29, 3, R=2, kind=kind)
+            assert status(lib, Rule.from_problem(p)) == L.QMC_OK, lib.qmc_last_error()
+    assert status(lib, Rule(I.LATTICE, 4, [0, 1], z=[1, 1], b=9)) == L.QMC_ERR_INVALID_ARG      # 9 = 3^2
+    assert status(lib, Rule(I.LATTICE, 30, [0], z=[1], b=3)) == L.QMC_ERR_UNSUPPORTED         # 3^30 > 2^31
+    p = I.base_b_problem(3, 3, 5, 8, 4, R=1, transform=I.T_INV_NORMAL)
+    r = Rule.from_problem(p)
+    r.shifts = r.shifts.copy()
+    r.shifts[0, 0] = 0                         # x = u/b^q + 0 reaches 0 at k = 0
+    assert status(lib, r) == L.QMC_ERR_INVALID_ARG
+    r = Rule(I.LATTICE, 4, [0, 1], z=[3, 1], b=3)    # z_0 = 3 is divisible by b
+    assert status(lib, r) == L.QMC_ERR_INVALID_ARG
+    r = Rule(I.DIGITAL_NET, 3, [0], C=[[1, 0, 0]], b=3)
+    assert status(lib, r) == L.QMC_ERR_UNSUPPORTED
