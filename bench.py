@@ -83,6 +83,8 @@ def _make(name):
     from paper_2305_11645_gb300 import inputs as I
     if name == "pde8":
         return [I.c4(i) for i in range(len(I.C4_INSTANCES))]
+    if name == "pde_asm":
+        return I.pde_assembly(m=18, s=256, M=32, R=1)
     return {"net20": I.c3, "gauss16": lambda: I.c2(dtype=np.float32), "adjoint20": I.c5, "basket": _basket}[name]()
 
 
@@ -103,6 +105,10 @@ WORKLOADS = {
                           "(18,2048,4096), w_j=min(floor(log2(j+1)),12), centred points, 4 shifts each, "
                           "A_ji=(j+1)^-2 sin((j+1) pi t_i), f=mean (1+0.5y)^-2; schedules autotuned per instance, "
                           "all instances in one call replayed as one CUDA graph; estimate"),
+    "pde_asm": (False, None, "PDE matrix assembly D_k = sum_j x_{j,k} C_j (Sec. 1) as the materialised reduced "
+                             "product: reduced lattice b=2 m=18 (N=262144), s=256 stiffness terms of M=32 interior "
+                             "nodes (tau=M^2=1024), w_j=min(floor(log2(j+1)),12), one shift; D written as N x M x M "
+                             "FP32"),
     "basket": (False, None, "basket option by reduced Monte Carlo: m=25 (N=33554432), s=tau=10, "
                             "w_j=floor(log2 j) (1-based), tridiagonal Sigma (0.4, 0.2), K=110, one replica; estimate"),
 }
@@ -428,6 +434,60 @@ def run_batch(args, dist, world, timer):
             "accuracy": batch_accuracy(ps, est, prec)}
 
 
+def run_assembly(args, dist, world, timer):
+    """Sec. 1's PDE assembly alone: D = X A written to HBM (api.assemble), its band kernel's share of
+    the measured copy bandwidth, and the oracle's matrices on sampled points."""
+    from paper_2305_11645_gb300 import api
+    from paper_2305_11645_gb300 import inputs as I
+    from paper_2305_11645_gb300 import _lib as L
+    p = _make("pde_asm")
+    M = 32
+    prec = args.precision
+    rule = api.Rule.from_problem(p)
+    C = torch.from_numpy(I.stiffness_terms(p.s, M).astype(np.float32)).to(timer.dev)
+    ws = torch.empty(max(api.workspace_size(L.QMC_OP_REDUCED_MATMUL, [rule], [M * M], None,
+                                            api._precision(C.reshape(p.s, -1), prec)), 256),
+                     dtype=torch.uint8, device=timer.dev)
+    for _ in range(args.warmup):
+        D = api.assemble(rule, C, ws=ws, precision=prec)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(timer.dev.index)
+    clocks.start()
+    time.sleep(0.3)
+    times, _ = timer.run(lambda: api.assemble(rule, C, ws=ws, precision=prec), args.steps)
+    clock_info = clocks.stop()
+    _, kern = timer.run(lambda: api.assemble(rule, C, ws=ws, precision=prec), args.steps, trace=True)
+    ms = max_over_ranks(dist, statistics.mean(times))
+    outputs = p.N * M * M * p.R_eff
+    D = api.assemble(rule, C, ws=ws, precision=prec)
+    torch.cuda.synchronize()
+    ks = np.array([0, 1, 12345, p.N - 1])
+    want = O_assemble(p, I.stiffness_terms(p.s, M).astype(np.float32).astype(np.float64), ks)
+    got = D[0][torch.from_numpy(ks).to(timer.dev)].double().cpu().numpy()
+    mp, peak_src = peaks()
+    band = "k_fine_mat_s4"
+    roof = None
+    if band in kern:
+        cnt, tot = kern[band]
+        sec = tot / cnt / 1e3
+        roof = {"bound": "hbm", "kernel": band, "achieved": outputs * 4 / sec / 1e9, "peak": mp["hbm_gbs"],
+                "unit": "GB/s", "frac": outputs * 4 / sec / 1e9 / mp["hbm_gbs"], "bytes_per_launch": outputs * 4,
+                "traffic": None, "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}
+    return {"metric": METRIC, "value": world * outputs / (ms / 1e3), "unit": "outputs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": {"split": "bf16x6+f32", "fp32": "f32", "bf16": "bf16+f32"}[prec],
+            "data": "synthetic", "config": {"workload": WORKLOADS["pde_asm"][2], "name": "pde_asm",
+                                            "outputs_per_step": outputs, "precision": prec},
+            "roofline": roof, "clocks": clock_info,
+            "kernels": {k: {"launches": c / args.steps, "ms_per_step": t / args.steps} for k, (c, t) in sorted(kern.items())},
+            "accuracy": {"sampled_rows_max_rel_err": float(np.max(np.abs(got - want)) / np.max(np.abs(want)))}}
+
+
+def O_assemble(p, C, ks):
+    from oracle import qmc_oracle as O
+    return O.assemble(p, C, 0, ks)
+
+
 def run_ours(args, dist, rank, world):
     from paper_2305_11645_gb300 import _lib as L
     from paper_2305_11645_gb300 import api
@@ -440,6 +500,8 @@ def run_ours(args, dist, rank, world):
     name = args.workload
     if name == "pde8":
         return run_batch(args, dist, world, timer)
+    if name == "pde_asm":
+        return run_assembly(args, dist, world, timer)
     backward, gkey, desc = WORKLOADS[name]
     p = _make(name)
     if args.shifts and p.shifts is not None:
@@ -716,6 +778,8 @@ def oracle_sample(p, ks):
     from oracle import qmc_oracle as O
     for r, X in O.shifted_rows(p, ks):
         Y = O.product(X, p.A)
+        if p.f_kind == 0:                          # the product alone (the assembly workload)
+            continue
         O.integrand(p.f_kind, p.f_params, Y).sum()
         X.T @ O.integrand_grad(p.f_kind, p.f_params, Y)
 

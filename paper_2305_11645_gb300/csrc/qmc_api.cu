@@ -295,6 +295,7 @@ bool net_nonperiodic(const qmc_rule* r) {
 struct TuneVal {
     int fwd_qpg = 0;
     int bwd_rpc = 0;
+    int coarse = 0;                // tensor-core tiers: 1 level passes, 2 block products + chain sum
 };
 struct TuneCache {
     std::mutex mu;
@@ -637,6 +638,20 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.fkind = f->kind;
     }
 
+    {   // the schedule cache's key: everything the fine schedules depend on
+        std::string k = "m" + std::to_string(P.m) + " p" + std::to_string(precision) + " f" + std::to_string(P.fkind) +
+                        " t" + std::to_string(P.tau_pad) + " r" + std::to_string(P.reff) + " L";
+        for (int I = 0; I <= P.m; ++I) k += (I ? "," : "") + std::to_string(P.lev_tau[I]);
+        P.tune_key = k;
+        if (t_hint) {
+            P.tuned = *t_hint;
+        } else {
+            TuneCache& tc = tune_cache();
+            std::lock_guard<std::mutex> g(tc.mu);
+            auto it = tc.m.find(k);
+            if (it != tc.m.end()) P.tuned = it->second;
+        }
+    }
     // fine band shape
     auto fits = [&](int jf, const int* kmax) {
         if (P.m < jf) return false;
@@ -687,7 +702,18 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.chf.tile0[P.chf.count] = tiles;
     P.B_per_shift = boff;
     P.S_per_shift = P.chf.count ? n_root * P.tau_pad : 0;
-    if (P.tc_pieces && P.chf.count) plan_levels(P);
+    if (P.tc_pieces && P.chf.count) {
+        // Level passes (Algorithm 2 top down) once the coarse partial sums are large enough for their
+        // memory traffic to matter (each pass is one persistent launch with a fixed cost); below that
+        // the block products and the chain sum.  A tuned schedule decides either way.
+        long long partial = 0;
+        for (int I = P.JF; I <= P.m; ++I)
+            if (P.lev_tau[I] > 0) partial += (1LL << (P.m - I)) * P.tau_pad * P.reff;
+        bool use = partial >= (1LL << 24);
+        if (P.tuned.coarse == 1) use = true;
+        if (P.tuned.coarse == 2) use = false;
+        if (use) plan_levels(P);
+    }
 
     // fine forward grid: 128 roots per CTA, column groups to fill the GPU
     P.root_blocks = (int)((n_root + 127) / 128);
@@ -707,20 +733,6 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     // table entries, 2 * 2^m row-save floats) below 2^30.
     P.fine_s4 = (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) && P.shape == SHAPE_S4 &&
                 precision != QMC_FP64 && P.m <= 27;
-    {   // the schedule cache's key: everything the fine schedules depend on
-        std::string k = "m" + std::to_string(P.m) + " p" + std::to_string(precision) + " f" + std::to_string(P.fkind) +
-                        " t" + std::to_string(P.tau_pad) + " r" + std::to_string(P.reff) + " L";
-        for (int I = 0; I <= P.m; ++I) k += (I ? "," : "") + std::to_string(P.lev_tau[I]);
-        P.tune_key = k;
-        if (t_hint) {
-            P.tuned = *t_hint;
-        } else {
-            TuneCache& tc = tune_cache();
-            std::lock_guard<std::mutex> g(tc.mu);
-            auto it = tc.m.find(k);
-            if (it != tc.m.end()) P.tuned = it->second;
-        }
-    }
     if (P.fine_s4) {
         const int rows = fine_s4_fwd_roots();
         P.root_blocks = (int)((n_root + rows - 1) / rows);
@@ -1572,11 +1584,20 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
         float bt = -1.0f;
         for (int qpg : ladder) {
             if (qpg < 1 || qpg > quads || qpg > 128) continue;
-            TuneVal tv{qpg, 0};
+            TuneVal tv{qpg, 0, 0};
             float ms = 0.0f;
             st = time_it(tv, false, &ms);
             if (st != QMC_OK) break;
             if (ms > 0.0f && (bt < 0.0f || ms < bt)) { bt = ms; bestv.fwd_qpg = qpg; }
+        }
+        // tensor-core tiers: the coarse path (level passes or block products), with the forward
+        // schedule just chosen
+        if (base.tc_pieces && base.chf.count && st == QMC_OK) {
+            float b1 = -1.0f, b2 = -1.0f;
+            TuneVal t1{bestv.fwd_qpg, 0, 1}, t2{bestv.fwd_qpg, 0, 2};
+            st = time_it(t1, false, &b1);
+            if (st == QMC_OK) st = time_it(t2, false, &b2);
+            if (st == QMC_OK && b1 > 0.0f && b2 > 0.0f) bestv.coarse = b1 <= b2 ? 1 : 2;
         }
         // adjoint: roots per CTA around the cost model's choice, with the forward just chosen
         const long long n_root = 1LL << (base.m - base.JF);
@@ -1587,7 +1608,7 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
             long long rpc = (long long)(base.roots_per_cta * fc + 0.5);
             rpc = std::max(2LL, (rpc + 1) / 2 * 2);
             if (rpc > n_root + 1) continue;
-            TuneVal tv{bestv.fwd_qpg, (int)rpc};
+            TuneVal tv{bestv.fwd_qpg, (int)rpc, bestv.coarse};
             float ms = 0.0f;
             st = time_it(tv, true, &ms);
             if (st != QMC_OK) break;
@@ -1619,8 +1640,10 @@ qmc_status qmc_tune_save(const char* path) {
     std::lock_guard<std::mutex> g(tc.mu);
     FILE* fh = fopen(path, "w");
     if (!fh) return fail(QMC_ERR_INVALID_ARG, "cannot write %s", path);
-    fprintf(fh, "# qmc_gb300 schedule cache: shape key | forward column quads per CTA | adjoint roots per CTA\n");
-    for (auto& kv : tc.m) fprintf(fh, "%s|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc);
+    fprintf(fh, "# qmc_gb300 schedule cache: shape key | forward column quads per CTA | adjoint roots per CTA | "
+                "coarse path (1 level passes, 2 block products)\n");
+    for (auto& kv : tc.m)
+        fprintf(fh, "%s|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc, kv.second.coarse);
     fclose(fh);
     return QMC_OK;
 }
@@ -1640,12 +1663,14 @@ qmc_status qmc_tune_load(const char* path, uint32_t* n_entries) {
         if (line[0] == '#' || line[0] == '\n') continue;
         char* a = strchr(line, '|');
         char* b = a ? strchr(a + 1, '|') : nullptr;
-        int q = 0, r = 0;
-        if (!a || !b || sscanf(a + 1, "%d", &q) != 1 || sscanf(b + 1, "%d", &r) != 1 || q < 0 || r < 0 || q > 128) {
+        char* c = b ? strchr(b + 1, '|') : nullptr;          // (the coarse path is optional)
+        int q = 0, r = 0, cp = 0;
+        if (!a || !b || sscanf(a + 1, "%d", &q) != 1 || sscanf(b + 1, "%d", &r) != 1 || q < 0 || r < 0 || q > 128 ||
+            (c && (sscanf(c + 1, "%d", &cp) != 1 || cp < 0 || cp > 2))) {
             st = fail(QMC_ERR_INVALID_ARG, "%s:%d: not a schedule entry", path, lineno);
             break;
         }
-        tc.m[std::string(line, a - line)] = TuneVal{q, r};
+        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp};
         ++n;
     }
     fclose(fh);

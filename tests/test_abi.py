@@ -346,9 +346,21 @@ def test_schedule_cache_file_and_planner(lib, tmp_path):
     assert st == L.QMC_OK and tuned != base                  # (the cost model takes 16 groups of 4 columns)
     out = tmp_path / "saved.txt"
     assert lib.qmc_tune_save(str(out).encode()) == L.QMC_OK
-    assert f"{key}|16|6" in out.read_text().splitlines()
+    assert f"{key}|16|6|0" in out.read_text().splitlines()      # (a missing coarse-path field reads as 0)
     assert lib.qmc_tune_clear() == L.QMC_OK
     assert ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)[1] == base
+    # the tensor-core tiers' coarse path is part of the schedule: this shape's coarse partial sums
+    # are small, so the model takes the block products; forcing the level passes adds their areas
+    q = I.c2(m=12, s=1024, dtype=np.float32)                 # (wide: the passes' A pieces dominate)
+    rq = Rule.from_problem(q)
+    fq = Integrand(I.F_CALL_MEAN_EXP, (0.2, 1.0))
+    st, products = ws_size(lib, L.QMC_OP_INTEGRATE, rq, 1024, fq, L.QMC_SPLIT)
+    kq = tune_key(q, L.QMC_SPLIT, I.F_CALL_MEAN_EXP, 1024)
+    path.write_text(f"{kq}|0|0|1\n{kq.replace('p2', 'p3')}|0|0|2\n")
+    assert lib.qmc_tune_load(str(path).encode(), ctypes.byref(n)) == L.QMC_OK and n.value == 2
+    st, passes = ws_size(lib, L.QMC_OP_INTEGRATE, rq, 1024, fq, L.QMC_SPLIT)
+    assert st == L.QMC_OK and passes != products
+    assert lib.qmc_tune_clear() == L.QMC_OK
     bad = tmp_path / "bad.txt"
     bad.write_text("no separators here\n")
     assert lib.qmc_tune_load(str(bad).encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
