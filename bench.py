@@ -42,7 +42,12 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
 # dram__bytes_read.sum + dram__bytes_write.sum per launch, scaled to the contract workload from
 # the ncu captures summarised under profiles/ (workload name, kernel name); a kernel missing
 # here has changed since its counters were taken and reports traffic null
-TRAFFIC_BYTES = {}
+TRAFFIC_BYTES = {
+    # profiles/net20_top_kernels.md: the 2-shift capture of the 16-shift contract workload, scaled by
+    # 16/2 (each shift's data are separate, so the DRAM bytes grow with the shifts)
+    ("net20", "k_fine_bwd_s4"): (594.804992e6 + 502.806272e6) * 8,
+    ("net20", "k_coarse_grad_tc"): (1318.091e6 + 13.10592e6) * 8,
+}
 
 
 def parse():
@@ -281,7 +286,7 @@ def alu_roofline(fp32_ops, mufu_ops, seconds, clock_mhz):
             "unit": "Gop/s", "frac": t_fp32 / seconds}
 
 
-def roofline_of(p, prec, name, ms_per_step, launches_per_step, clk, mp, peak_src):
+def roofline_of(p, prec, name, ms_per_step, launches_per_step, clk, mp, peak_src, workload=None):
     """Roofline of one kernel from its device time per step (the sum over its launches; its
     algorithmic work per step is the sum over the same launches)."""
     sec = ms_per_step / 1e3
@@ -297,8 +302,9 @@ def roofline_of(p, prec, name, ms_per_step, launches_per_step, clk, mp, peak_src
         r["peak_source"] = (f"derived: {SM_COUNT} SMs x pipe lanes (FP32 128, MUFU {MUFU_LANES}) x median SM "
                             f"clock {clk:.0f} MHz sampled during the timed region")
         r["work"] = {"fp32_ops_per_step": w32, "mufu_ops_per_step": wmu}
+    tb = TRAFFIC_BYTES.get((workload, name))
     r.update({"kernel": name, "ms_per_step": ms_per_step, "launches_per_step": launches_per_step,
-              "traffic": TRAFFIC_BYTES.get(name)})
+              "traffic": None if tb is None else tb / max(launches_per_step, 1.0)})
     return r
 
 
@@ -526,7 +532,8 @@ def run_ours(args, dist, rank, world):
     mp, peak_src = peaks()
     clk = clock_info["sm_mhz"] or mp.get("sm_max_mhz", 2070.0)
     top = max(kernels.items(), key=lambda kv: kv[1]["ms_per_step"])
-    roof = roofline_of(p, prec, top[0], top[1]["ms_per_step"], top[1]["launches_per_step"], clk, mp, peak_src)
+    roof = roofline_of(p, prec, top[0], top[1]["ms_per_step"], top[1]["launches_per_step"], clk, mp, peak_src,
+                       None if args.shifts else name)
     kernel_total = sum(k["ms_per_step"] for k in kernels.values())
     for k in kernels.values():
         k["share"] = k["ms_per_step"] / kernel_total
@@ -539,6 +546,22 @@ def run_ours(args, dist, rank, world):
         elif k.endswith("_tc"):
             per_kernel[k] = roofline_of(p, prec, k, v["ms_per_step"], v["launches_per_step"], clk, mp, peak_src)["frac"]
     roof["per_kernel_frac"] = per_kernel
+    # the whole step against its compute roofline: every fine-band FP32 operation at the FP32 pipe's
+    # peak plus every block-product flop at the sustained tensor peak (the HBM traffic of the root
+    # values and the folds is reported beside it, not added)
+    pieces = 3 if prec == "split" else 1
+    f32 = fine_work(p, "fwd")[0] + (fine_work(p, "bwd")[0] if backward else 0.0)
+    mma = coarse_mma_flops(p, pieces) * (2 if backward else 1) if prec in ("split", "bf16") else 0.0
+    t_f32 = f32 / (SM_COUNT * 128 * clk * 1e6)
+    t_mma = mma / (mp["bf16_tflops_sustained"] * 1e12)
+    jf, tau_I, chain = band_of(p)
+    root_bytes = p.R_eff * 2 ** (p.m - jf) * p.tau * 4.0
+    roof["step"] = {"fp32_ms": t_f32 * 1e3, "tensor_ms": t_mma * 1e3, "frac": (t_f32 + t_mma) / (ms / 1e3),
+                    "root_value_hbm_ms": (2 if not backward else 6) * root_bytes / (mp["hbm_gbs"] * 1e9) * 1e3,
+                    "note": "FP32 ops of the fine band at 152x128 lanes x clock plus block-product MMA flops at the "
+                            "measured sustained bf16 peak, over the graph-replayed step time; root_value_hbm_ms is "
+                            "the root values written and read (and, with the adjoint, the root gradients and their "
+                            "folds) at the measured copy bandwidth"}
 
     # end to end through the public API with host buffers: H2D of A, D2H of the estimates and dQ/dA
     A_host = torch.from_numpy(np.ascontiguousarray(p.A)).pin_memory()

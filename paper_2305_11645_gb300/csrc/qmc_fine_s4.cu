@@ -89,6 +89,10 @@ struct RowAcc2 {
             b.add(v.y, c0);
             s = f2(a.s, b.s);
             mx = f2(a.mx, b.mx);
+        } else if constexpr (F == F_GAUSS_NORM2) {
+            s = __ffma2_rn(v, v, s);                  // h(v) = v^2 and the row sum in one paired FMA
+        } else if constexpr (F == F_LINEAR_MEAN) {
+            s = __fadd2_rn(s, v);
         } else {
             s = __fadd2_rn(s, f2(Fn<F, float>::h(v.x, c0), Fn<F, float>::h(v.y, c0)));
         }
@@ -274,6 +278,8 @@ __device__ __forceinline__ float2 hp2(float2 v, float c0, float2 nax) {
     if constexpr (F == F_LOGSUMEXP) {
         const float2 w = __fadd2_rn(v, nax);
         return f2(ex2f(w.x), ex2f(w.y));
+    } else if constexpr (F == F_GAUSS_NORM2) {
+        return v;                                    // h' = 2 v: the 2 is in the staged row coefficient
     } else {
         return f2(Fn<F, float>::hp(v.x, c0, 0.0f), Fn<F, float>::hp(v.y, c0, 0.0f));
     }
@@ -292,6 +298,9 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
     const bool active = t < a.tau_pad;                          // then t + 1 < tau_pad too
     const float* tab = a.tab + (long long)r * a.tab_stride;
     const float upstream = (float)a.upstream[0];
+    // the row coefficients are staged times upstream (and times 2 for the Gaussian norm, whose
+    // h'(v) = 2 v then costs one multiply with the coefficient)
+    const float coef_scale = F == F_GAUSS_NORM2 ? 2.0f * upstream : upstream;
     const float kap = a.kappa, c0 = a.c0;
 
     // kappa * A of the thread's two columns and the band-gradient accumulators, as column pairs
@@ -329,7 +338,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
             if (!(code >> 31) && rho < rho_end) {
                 if (code >> 30) {
                     v = __ldg(rsave + (code & 0x3fffffffu) + 2 * rho);
-                    v = (code & 1u) ? -v : upstream * v;
+                    v = (code & 1u) ? -v : coef_scale * v;
                 } else {
                     v = __ldg(tab + code + rho);
                 }
