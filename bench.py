@@ -46,7 +46,6 @@ TRAFFIC_BYTES = {
     # profiles/net20_top_kernels.md: the 2-shift capture of the 16-shift contract workload, scaled by
     # 16/2 (each shift's data are separate, so the DRAM bytes grow with the shifts)
     ("net20", "k_fine_bwd_s4"): (594.804992e6 + 502.806272e6) * 8,
-    ("net20", "k_coarse_grad_tc"): (1318.091e6 + 13.10592e6) * 8,
 }
 
 

@@ -325,6 +325,10 @@ struct Plan {
     FoldLevels fold{};
     int root_blocks = 0, cg_count = 1, cr = 0;
     int groups = 0, roots_per_cta = 8, passes = 0, bwd_tiles = 0;
+    // tensor-core backward: entries staged by TMA (k_grad_tc; whole chunks of 32 rows, F materialised)
+    // and the rest on k_coarse_grad_tc (chl, its tiles bwd_tiles_l)
+    int gsel[kMaxGradTc] = {}, ngsel = 0, bwd_tiles_l = 0;
+    Chain chl{};
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
@@ -887,6 +891,26 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.chb.tile0[P.chb.count] = bt;
         P.bwd_tiles = bt;
         P.partc_elems = poff;
+        P.ngsel = 0;
+        P.chl = P.chb;
+        P.chl.count = 0;
+        int btl = 0;
+        for (int e = 0; e < P.chb.count; ++e) {
+            const bool tma = tc && P.chb.flog[e] == 0 && P.m - P.chb.lev[e] >= 5 && P.chb.tab[e] % 4 == 0 &&
+                             P.chb.foff[e] % 4 == 0 && P.tau_pad % 4 == 0 && P.tab_stride % 4 == 0 &&
+                             P.chb.kper[e] % 32 == 0 && P.ngsel < kMaxGradTc;
+            if (tma) { P.gsel[P.ngsel++] = e; continue; }
+            const int l = P.chl.count++;
+            P.chl.lev[l] = P.chb.lev[e];
+            P.chl.logn[l] = P.chb.logn[e]; P.chl.tau[l] = P.chb.tau[e]; P.chl.col0[l] = P.chb.col0[e];
+            P.chl.tab[l] = P.chb.tab[e]; P.chl.boff[l] = P.chb.boff[e];
+            P.chl.split[l] = P.chb.split[e]; P.chl.kper[l] = P.chb.kper[e]; P.chl.poff[l] = P.chb.poff[e];
+            P.chl.fsel[l] = P.chb.fsel[e]; P.chl.flog[l] = P.chb.flog[e]; P.chl.foff[l] = P.chb.foff[e];
+            P.chl.tile0[l] = btl;
+            btl += (P.chb.tau[e] + jcols - 1) / jcols * P.chb.split[e];
+        }
+        P.chl.tile0[P.chl.count] = btl;
+        P.bwd_tiles_l = btl;
     }
 
     // workspace layout
@@ -1249,9 +1273,15 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
                                                               P.tau_pad, P.reff, st));
         if (P.tc_pieces) {
             if constexpr (std::is_same<T, float>::value) {
-                QMC_LAUNCH(st, "k_coarse_grad_tc",
-                           launch_coarse_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
-                                                 P.tau_pad, P.chb, partc, P.reff, P.bwd_tiles, P.tc_pieces, P.xc, st));
+                if (P.ngsel)
+                    QMC_LAUNCH(st, "k_grad_tc",
+                               launch_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
+                                              P.tau_pad, P.chb, P.gsel, P.ngsel, partc, P.reff, P.tc_pieces, P.xc, st));
+                if (P.chl.count)
+                    QMC_LAUNCH(st, "k_coarse_grad_tc",
+                               launch_coarse_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
+                                                     P.tau_pad, P.chl, partc, P.reff, P.bwd_tiles_l, P.tc_pieces, P.xc,
+                                                     st));
                 if (P.xc != 0.0f) {
                     // 1^T G over every shift: the column sums of the top folded level (or of the roots)
                     const bool top = P.fold.depth > 0;
@@ -1302,6 +1332,8 @@ qmc_status qmc_device_status(int clear) {
     QMC_CUDA(cudaDeviceSynchronize());
     QMC_CUDA(tc_error_word(&word, clear != 0));
     QMC_CUDA(level_error_word(&lword, clear != 0));
+    word |= lword;
+    QMC_CUDA(grad_error_word(&lword, clear != 0));
     word |= lword;
     if (word)
         return fail(QMC_ERR_TIMEOUT, "a bounded device-side wait ran out (error word 0x%x: bit 0 a tensor-core "

@@ -232,6 +232,32 @@ struct FoldLevels {
 constexpr int kMaxCR = 256;          // columns per CTA of the fine forward kernel
 
 // ---------------------------------------------------------------------------------------------
+// Block gradients on the tensor cores (qmc_grad_tc.cu): the coarse entries with at least 32
+// distinct rows whose folded gradient is materialised, each with a TMA map of F (t, rows, shifts)
+// and of its table columns (rows, columns, shifts).
+// ---------------------------------------------------------------------------------------------
+}  // namespace qmc
+#include <cuda.h>
+namespace qmc {
+constexpr int kMaxGradTc = 24;
+struct GradTcEntry {
+    long long n, kper, poff;
+    int tau, split;
+};
+struct GradTcArgs {
+    CUtensorMap fmap[kMaxGradTc];
+    CUtensorMap xmap[kMaxGradTc];
+    GradTcEntry ent[kMaxGradTc];
+    long long unit0[kMaxGradTc + 1];
+    long long units;
+    int n, reff, t_tiles;
+};
+cudaError_t launch_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
+                           const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch, const int* sel,
+                           int nsel, float* part, int reff, int pieces, float xc, cudaStream_t st);
+cudaError_t grad_error_word(unsigned int* value, bool clear);
+
+// ---------------------------------------------------------------------------------------------
 // Base b > 2: one weight level of the top-down sum (qmc_base_b.cu).  Level I's n = b^(m-I)
 // distinct rows of its tau columns (A's rows col0 ..), written at n_out rows (n, or N for the
 // last level) on top of the coarser level's n_next rows.
