@@ -329,6 +329,14 @@ struct Plan {
     // and the rest on k_coarse_grad_tc (chl, its tiles bwd_tiles_l)
     int gsel[kMaxGradTc] = {}, ngsel = 0, bwd_tiles_l = 0;
     Chain chl{};
+    // tensor-core backward of the lowest fg_L coarse levels in one pass over the root gradients
+    // (k_fold_grad_tc, entries fg_ent[d] of level JF + d or -1), the folds above JF + fg_L from
+    // F_{JF+fg_L} (fold2), the levels' table columns pre-split at off_xt
+    int fg_L = 0, fg_ent[kMaxFoldLv] = {-1, -1, -1};
+    FoldGradArgs fga{};
+    SplitXtArgs sxa{};
+    FoldLevels fold2{};
+    size_t off_xt = 0, xt_bytes = 0;
     int nblk = 0;
     int tc_pieces = 0;             // 3: split tier, 1: bf16 tier, 0: FP32 / FP64 block products
     bool fine_s4 = false;          // S4 band in FP32 on the CUDA cores (every float tier)
@@ -846,6 +854,43 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             P.fold.off[I_mat - P.JF] = fchain;
             fchain += (1LL << (P.m - I_mat)) * P.tau_pad;
         }
+        // the lowest coarse levels fused with the fold: L levels JF .. JF+L-1, each with at most one
+        // entry of at most 64 columns (read from its materialised fold), F_{JF+L} materialised with
+        // at least 32 rows, at most 128 accumulator columns in all
+        P.fg_L = 0;
+        for (int d = 0; d < kMaxFoldLv; ++d) P.fg_ent[d] = -1;
+        if (P.tc_pieces != 0 && !P.nonper && precision != QMC_FP64) {
+            for (int L = kMaxFoldLv; L >= 1 && P.fg_L == 0; --L) {
+                if (P.JF + L > I_mat || P.m - (P.JF + L) < 5) continue;
+                int ent[kMaxFoldLv] = {-1, -1, -1}, ncols = 0, good = 1, any = 0;
+                for (int e = 0; e < P.chb.count; ++e) {
+                    const int d = P.chb.lev[e] - P.JF;
+                    if (d < 0 || d >= L) continue;
+                    if (ent[d] >= 0 || P.chb.tau[e] > 64 || P.chb.flog[e] != 0 || P.chb.tab[e] % 4 != 0) good = 0;
+                    ent[d] = e;
+                    ncols += (P.chb.tau[e] + 15) / 16 * 16;
+                    any = 1;
+                }
+                if (!good || !any || ncols > 128 || P.tab_stride % 4 != 0) continue;
+                P.fg_L = L;
+                for (int d = 0; d < L; ++d) P.fg_ent[d] = ent[d];
+            }
+        }
+        if (P.fg_L) {
+            const int L = P.fg_L;
+            if (!P.fold.want[L]) {          // F_{JF+L} is the fused kernel's output
+                P.fold.want[L] = 1;
+                P.fold.off[L] = fchain;
+                fchain += (1LL << (P.m - P.JF - L)) * P.tau_pad;
+            }
+            P.fold2 = FoldLevels{};
+            P.fold2.depth = P.fold.depth - L;
+            P.fold2.logn_top = P.fold.logn_top;
+            for (int d = 1; d <= P.fold2.depth; ++d) {
+                P.fold2.want[d] = P.fold.want[L + d];
+                P.fold2.off[d] = P.fold.off[L + d];
+            }
+        }
         P.Fchain_per_shift = fchain;
         // coarse gradient GEMMs: K = R n_e rows; splits balance the work over the GPU.  FP32/FP64
         // tiles: 16 columns j, 16 multiply-adds plus 4 fold loads per K row and column, ~4 CTAs
@@ -857,8 +902,18 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         const double fma_w = tc ? 2.0 : 16.0, fold_w = tc ? 1.0 : 4.0, target = tc ? 152.0 : 608.0;
         const long long kmin = tc ? 128 : 64;
         const int ttiles = (P.tau_pad + 127) / 128;
+        auto fused = [&](int e) {
+            for (int d = 0; d < P.fg_L; ++d)
+                if (P.fg_ent[d] == e) return true;
+            return false;
+        };
+        // the fused kernel: one CTA per SM, each on a column tile and a range of (shift, residue
+        // block) items; its partials are split over the CTAs of a column tile
+        const int fg_cpt = P.fg_L ? (int)std::max(1LL, std::min<long long>(152 / ttiles,
+                                         (long long)P.reff << (P.m - P.JF - P.fg_L - 5))) : 0;
         double wtot = 0.0;
         for (int e = 0; e < P.chb.count; ++e) {
+            if (fused(e)) continue;
             const long long K = (long long)P.reff << (P.m - P.chb.lev[e]);
             const double fold = (double)(1LL << P.chb.flog[e]);
             wtot += (double)((P.chb.tau[e] + jcols - 1) / jcols) * ttiles * K * (fma_w + fold_w * fold);
@@ -866,6 +921,14 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         long long poff = 0;
         int bt = 0;
         for (int e = 0; e < P.chb.count; ++e) {
+            if (fused(e)) {
+                P.chb.kper[e] = 0;
+                P.chb.split[e] = fg_cpt;
+                P.chb.poff[e] = poff;
+                poff += (long long)fg_cpt * P.chb.tau[e] * P.tau_pad;
+                P.chb.tile0[e] = bt;
+                continue;
+            }
             const long long K = (long long)P.reff << (P.m - P.chb.lev[e]);
             const double fold = (double)(1LL << P.chb.flog[e]);
             const int jt = (P.chb.tau[e] + jcols - 1) / jcols;
@@ -896,6 +959,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         P.chl.count = 0;
         int btl = 0;
         for (int e = 0; e < P.chb.count; ++e) {
+            if (fused(e)) continue;
             const bool tma = tc && P.chb.flog[e] == 0 && P.m - P.chb.lev[e] >= 5 && P.chb.tab[e] % 4 == 0 &&
                              P.chb.foff[e] % 4 == 0 && P.tau_pad % 4 == 0 && P.tab_stride % 4 == 0 &&
                              P.chb.kper[e] % 32 == 0 && P.ngsel < kMaxGradTc;
@@ -911,6 +975,42 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         }
         P.chl.tile0[P.chl.count] = btl;
         P.bwd_tiles_l = btl;
+        if (P.fg_L) {
+            const int L = P.fg_L;
+            FoldGradArgs& g = P.fga;
+            g = FoldGradArgs{};
+            g.log_out = P.m - P.JF - L;
+            g.items = (long long)P.reff << (g.log_out - 5);
+            g.tau_pad = P.tau_pad;
+            g.t_tiles = ttiles;
+            g.cpt = fg_cpt;
+            g.group = std::max(1, 32 >> L);            // level JF's chains: 32 2^L rows per item, <= 1024
+            g.fout_stride = P.Fchain_per_shift;
+            int acc = 0;
+            SplitXtArgs& sx = P.sxa;
+            sx = SplitXtArgs{};
+            long long xoff = 0;
+            for (int d = 0; d < L; ++d) {
+                const int e = P.fg_ent[d];
+                g.nd[d] = e >= 0 ? (P.chb.tau[e] + 15) / 16 * 16 : 0;
+                g.tau[d] = e >= 0 ? P.chb.tau[e] : 0;
+                g.acc[d] = acc;
+                g.poff[d] = e >= 0 ? P.chb.poff[e] : 0;
+                acc += g.nd[d];
+                if (e < 0) continue;
+                const int l = sx.n++;
+                sx.lev[l] = d;
+                sx.logn[l] = P.chb.logn[e];
+                sx.tau[l] = P.chb.tau[e];
+                sx.tab[l] = P.chb.tab[e];
+                sx.off[l] = xoff;
+                sx.blk0[l + 1] = sx.blk0[l] + ((long long)P.chb.tau[e] << (P.chb.logn[e] - 3));
+                xoff += (long long)P.tc_pieces * P.reff * P.chb.tau[e] << P.chb.logn[e];
+            }
+            g.nt = 32;
+            while (g.nt < acc) g.nt *= 2;
+            P.xt_bytes = (size_t)xoff * 2;
+        }
     }
 
     // workspace layout
@@ -990,6 +1090,8 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         o = align256(o + E * (size_t)std::max(P.partc_elems, 1LL));
         P.off_gsum = o;
         if (P.xc != 0.0f) o = align256(o + sizeof(double) * 65 * (size_t)P.tau_pad);
+        P.off_xt = o;
+        o = align256(o + P.xt_bytes);
         uend = std::max(uend, o);
     }
     P.total = uend;
@@ -1268,7 +1370,24 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
     if (P.chb.count)
     {
         T* Fchain = reinterpret_cast<T*>(ws + P.off_Fchain);
-        if (P.fold.depth > 0)
+        if (P.fg_L) {
+            if constexpr (std::is_same<T, float>::value) {
+                // levels JF .. JF+L-1 and their folds in one pass; the rest fold from F_{JF+L}
+                __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(ws + P.off_xt);
+                QMC_LAUNCH(st, "k_split_xt",
+                           launch_split_xt(tab, P.tab_stride, P.sxa, P.reff, P.tc_pieces, xt, P.xc, st));
+                FoldGradArgs ga = P.fga;
+                ga.fout = Fchain + P.fold.off[P.fg_L];
+                ga.part = partc;
+                QMC_LAUNCH(st, "k_fold_grad_tc",
+                           launch_fold_grad_tc(ga, P.fg_L, Froot, root_stride, n_root, xt, P.sxa, P.reff,
+                                               P.tc_pieces, st));
+                if (P.fold2.depth > 0)
+                    QMC_LAUNCH(st, "k_fold_tree",
+                               launch_fold_tree<T>(Fchain + P.fold.off[P.fg_L], P.Fchain_per_shift, Fchain,
+                                                   P.Fchain_per_shift, P.fold2, P.tau_pad, P.reff, st));
+            }
+        } else if (P.fold.depth > 0)
             QMC_LAUNCH(st, "k_fold_tree", launch_fold_tree<T>(Froot, root_stride, Fchain, P.Fchain_per_shift, P.fold,
                                                               P.tau_pad, P.reff, st));
         if (P.tc_pieces) {
@@ -1334,6 +1453,8 @@ qmc_status qmc_device_status(int clear) {
     QMC_CUDA(level_error_word(&lword, clear != 0));
     word |= lword;
     QMC_CUDA(grad_error_word(&lword, clear != 0));
+    word |= lword;
+    QMC_CUDA(foldgrad_error_word(&lword, clear != 0));
     word |= lword;
     if (word)
         return fail(QMC_ERR_TIMEOUT, "a bounded device-side wait ran out (error word 0x%x: bit 0 a tensor-core "

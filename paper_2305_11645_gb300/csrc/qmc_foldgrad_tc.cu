@@ -1,0 +1,490 @@
+// The adjoint of Algorithm 2's lowest coarse levels in one pass over the root gradients (split and
+// bf16 tiers).  The adjoint of the periodic tiling folds the root gradients F_JF onto every coarser
+// level, F_{I+1}[rho] = F_I[rho] + F_I[rho + n_{I+1}], and each level's block gradient is
+// dA_I = sum_r X_{r,I}^T F_{r,I} over its distinct rows.  For the L lowest levels JF .. JF+L-1
+// this kernel does both without writing the intermediate folds: F_JF is read once, the folds are
+// formed in registers, every level's rows go to the tensor cores as they appear, and only
+// F_{JF+L} (the input of the remaining levels' fold) is written.
+//
+// Work item: (shift r, column tile t0 .. t0+127, residue block rho0 .. rho0+31 of the n_out =
+// n_{JF+L} rows of level JF+L).  Its root rows are rho0 + k + q n_out (k < 32, q < 2^L); visiting
+// q in bit-reversed order, each pair of a fold is complete as soon as its second member arrives,
+// so a stack of L pending chunks is all the fold needs.  Level JF+d's chunk q_d (rows rho0 + k +
+// q_d n_out of that level) is the product D[t][j] += sum_k F[k][t] X_{JF+d}[k][j] with M = 128
+// columns t, N = the level's columns (rounded up to 16, at most 64), K = 32 rows.
+//
+// One CTA per SM, each on one column tile and a contiguous range of (shift, residue block) items:
+//   warp 0      TMA producer: the FP32 root chunk (128 t x 32 rows, a 3-D box over (t, rows,
+//               shifts)) into a ring of raw stages, and for every level chunk the pre-split bf16
+//               pieces of its point-table rows (k_split_xt) into the chunk's operand slot;
+//   warp 1      allocates tensor memory (two accumulator sets and one running total) and one
+//               thread issues every level chunk's MMAs into the accumulator of its level;
+//   warps 2-9   converters: fold in registers, split each level chunk's F^T into bf16 pieces
+//               (K-major, 64-byte swizzle) in its slot, write F_{JF+L}; after every group of
+//               items (level JF's chains at most 1024 rows) add the accumulators into the
+//               running total, one group behind the MMAs, and at the end store the CTA's
+//               partial gradient, which k_grad_reduce sums over the CTAs of the column tile.
+// Every wait is bounded; a run-out sets the error word (foldgrad_error_word) and the roles stop as
+// in the other tensor-core kernels.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "qmc_internal.cuh"
+#include "qmc_tc.cuh"
+
+namespace qmc {
+
+// sticky: bit 0 = a bounded wait of the fold-gradient kernel ran out
+__device__ unsigned int g_foldgrad_error;
+
+using namespace tc;
+
+namespace {
+
+constexpr int FG_M = 128;                      // columns t per item (MMA M)
+constexpr int FG_K = 32;                       // rows per chunk
+constexpr int FG_NMAX = 64;                    // columns j of one level (MMA N), at most
+constexpr int RS = 4;                          // raw root-chunk stages
+constexpr int CS = 4;                          // level-chunk operand slots
+constexpr uint32_t RAW = FG_K * FG_M * 4;      // [k][t] FP32, 16 KB
+constexpr uint32_t PF = FG_M * 64;             // one bf16 piece of F^T: 128 rows x 64 bytes
+constexpr uint32_t PXMAX = FG_NMAX * 64;       // one bf16 piece of X: up to 64 rows x 64 bytes
+constexpr int kThreads = 320;
+
+template <int P> constexpr uint32_t slot_bytes() { return P * (PF + PXMAX); }
+template <int P> constexpr size_t fg_smem() { return 1024 + RS * RAW + CS * slot_bytes<P>() + 256; }
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
+    for (long long it = 0; it < kWaitLimit; ++it)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
+                                       int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar) : "memory");
+}
+// 8 consecutive FP32 accumulator columns of this thread's lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                    "r"(r[7]) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+template <int L> __device__ __forceinline__ int bitrev(int i) {
+    int q = 0;
+#pragma unroll
+    for (int b = 0; b < L; ++b) q |= ((i >> b) & 1) << (L - 1 - b);
+    return q;
+}
+
+// the CTA's column tile, split index and item range
+struct CtaWork {
+    int tt, sp;
+    long long i0, i1;
+};
+__device__ __forceinline__ CtaWork cta_work(const FoldGradArgs& ga) {
+    CtaWork w;
+    w.tt = blockIdx.x / ga.cpt;
+    w.sp = blockIdx.x - w.tt * ga.cpt;
+    w.i0 = ga.items * w.sp / ga.cpt;
+    w.i1 = ga.items * (w.sp + 1) / ga.cpt;
+    return w;
+}
+
+// ---------------------------------------------------------------------------------------------
+// k_split_xt: the fused levels' point-table columns, centred, as bf16 pieces in [piece][shift][j]
+// [row] order (rows contiguous), which a TMA box of 32 rows x N columns with the 64-byte swizzle
+// places in shared memory as the MMA's K-major B operand.  Thread = 8 consecutive rows of one
+// column of one level.
+// ---------------------------------------------------------------------------------------------
+template <int P>
+__global__ void __launch_bounds__(256) k_split_xt(const float* __restrict__ tab, long long tab_stride,
+                                                  const __grid_constant__ SplitXtArgs sa, int reff,
+                                                  __nv_bfloat16* __restrict__ xp, float xc) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y;
+    if (i >= sa.blk0[sa.n]) return;
+    int l = 0;
+    while (l + 1 < sa.n && i >= sa.blk0[l + 1]) ++l;
+    const long long loc = i - sa.blk0[l];
+    const long long n = 1LL << sa.logn[l];
+    const long long row0 = (loc & ((n >> 3) - 1)) << 3;
+    const int j = (int)(loc >> (sa.logn[l] - 3));
+    const float4* src = reinterpret_cast<const float4*>(tab + (long long)r * tab_stride + sa.tab[l] +
+                                                        (long long)j * n + row0);
+    const float4 a = __ldg(src), b = __ldg(src + 1);
+    const float v[8] = {a.x - xc, a.y - xc, a.z - xc, a.w - xc, b.x - xc, b.y - xc, b.z - xc, b.w - xc};
+    uint32_t w[P][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t pc[P];
+        split_pair<P>(v[2 * q], v[2 * q + 1], pc);
+#pragma unroll
+        for (int p = 0; p < P; ++p) w[p][q] = pc[p];
+    }
+    const long long per_piece = (long long)reff * sa.tau[l] * n;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        __nv_bfloat16* dst = xp + sa.off[l] + p * per_piece + ((long long)r * sa.tau[l] + j) * n + row0;
+        *reinterpret_cast<uint4*>(dst) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
+}
+
+
+// ---------------------------------------------------------------------------------------------
+// k_fold_grad_tc<P, L>
+// ---------------------------------------------------------------------------------------------
+template <int P, int L>
+__global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_constant__ FoldGradArgs ga) {
+    constexpr int STEPS = 1 << L;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = align_1k(smem_raw);
+    unsigned char* raw = smem;                                    // RS raw stages
+    unsigned char* slots = smem + RS * RAW;                       // CS operand slots: F^T pieces, X pieces
+    uint64_t* rfull = reinterpret_cast<uint64_t*>(slots + CS * slot_bytes<P>());
+    uint64_t* rempty = rfull + RS;
+    uint64_t* sfull = rempty + RS;
+    uint64_t* sempty = sfull + CS;
+    uint64_t* tdone = sempty + CS;                                // [2]
+    uint64_t* tfree = tdone + 2;                                  // [2]
+    uint64_t* drain = tfree + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const CtaWork cw = cta_work(ga);
+    const long long nrb = (1LL << ga.log_out) >> 5;               // residue blocks per shift
+    const long long n_out = 1LL << ga.log_out;
+    const long long ngroups = (cw.i1 - cw.i0 + ga.group - 1) / ga.group;
+    const uint32_t ncols = 4 * (uint32_t)ga.nt > 256 ? 512u : 256u;
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.fmap)) : "memory");
+        for (int d = 0; d < L; ++d)
+            if (ga.nd[d]) asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.xmap[d])) : "memory");
+        for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], 8); }
+        for (int s = 0; s < CS; ++s) { bar_init(&sfull[s], 9); bar_init(&sempty[s], 1); }
+        for (int b = 0; b < 2; ++b) { bar_init(&tdone[b], 1); bar_init(&tfree[b], 8); }
+        bar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), ncols);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            long long itr = 0, slot = 0;
+            for (long long it = cw.i0; it < cw.i1 && ok; ++it) {
+                const int r = (int)(it / nrb);
+                const int rho0 = (int)((it - (long long)r * nrb) << 5);
+                for (int i = 0; i < STEPS && ok; ++i, ++itr) {
+                    const int q = bitrev<L>(i);
+                    const int rs = (int)(itr % RS);
+                    if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
+                    bar_expect_tx(smem_u32(&rfull[rs]), RAW);
+                    tma_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
+                           rho0 + q * (int)n_out, r);
+                    // level chunks completed at this step: levels 0 .. (trailing ones of i), below L
+                    for (int d = 0; d < L; ++d) {
+                        if (d > 0 && ((i >> (d - 1)) & 1) == 0) break;
+                        if (!ga.nd[d]) continue;
+                        const int cs = (int)(slot % CS);
+                        if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
+                        const uint32_t fb = smem_u32(&sfull[cs]);
+                        bar_expect_tx(fb, (uint32_t)(P * ga.nd[d] * 64));
+                        const int qd = q & ((1 << (L - d)) - 1);
+                        tma_4d(smem_u32(slots + cs * slot_bytes<P>() + P * PF), &ga.xmap[d], fb,
+                               rho0 + qd * (int)n_out, 0, r, 0);
+                        ++slot;
+                    }
+                }
+            }
+            if (!ok) atomicOr(&g_foldgrad_error, 1u);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            long long slot = 0;
+            for (long long g = 0; g < ngroups && ok; ++g) {
+                const int b = (int)(g & 1);
+                if (!bar_wait(smem_u32(&tfree[b]), (uint32_t)(((g >> 1) & 1) ^ 1))) { ok = false; break; }
+                fence_after_sync();
+                bool fresh[L];
+#pragma unroll
+                for (int d = 0; d < L; ++d) fresh[d] = true;
+                const long long ib = cw.i0 + g * ga.group, ie = min(cw.i1, ib + ga.group);
+                for (long long it = ib; it < ie && ok; ++it) {
+                    for (int i = 0; i < STEPS && ok; ++i) {
+#pragma unroll
+                        for (int d = 0; d < L; ++d) {
+                            if (d > 0 && ((i >> (d - 1)) & 1) == 0) break;
+                            const int nd = ga.nd[d];
+                            if (!nd) continue;
+                            const int cs = (int)(slot % CS);
+                            if (!bar_wait(smem_u32(&sfull[cs]), (uint32_t)((slot / CS) & 1))) { ok = false; break; }
+                            fence_after_sync();
+                            const uint32_t as = smem_u32(slots + cs * slot_bytes<P>()), xs = as + P * PF;
+                            const uint32_t idesc = idesc_bf16((uint32_t)nd);
+                            const uint32_t dst = tmem + (uint32_t)(b * ga.nt + ga.acc[d]);
+                            const uint32_t xpiece = (uint32_t)nd * 64;
+#pragma unroll
+                            for (int ks = 0; ks < 2; ++ks) {
+                                const uint64_t ad = smem_desc_sw64(as + 32 * ks), bd = smem_desc_sw64(xs + 32 * ks);
+                                constexpr int NP = P == 3 ? 6 : 1;
+                                constexpr int pi[6] = {2, 1, 0, 1, 0, 0};
+                                constexpr int pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+                                for (int pq = 0; pq < NP; ++pq) {
+                                    const int ia = P == 3 ? pi[pq] : 0, jb = P == 3 ? pj[pq] : 0;
+                                    mma_bf16(dst, desc_add(ad, ia * PF), desc_add(bd, jb * xpiece), idesc,
+                                             fresh[d] ? 0u : 1u);
+                                    fresh[d] = false;
+                                }
+                            }
+                            mma_commit(smem_u32(&sempty[cs]));
+                            ++slot;
+                        }
+                    }
+                }
+                if (ok) mma_commit(smem_u32(&tdone[b]));
+            }
+            if (!ok) atomicOr(&g_foldgrad_error, 1u);
+            mma_commit(smem_u32(drain));
+            bar_wait(smem_u32(drain), 0);
+        }
+    } else {
+        // ------------------------------------------------------------------ converters
+        const int ct = threadIdx.x - 64;                          // 0..255
+        const int tl = ct & 127, h = ct >> 7;                     // column t0 + tl, rows 16h .. 16h+15
+        const int quarter = warp & 3, half = (warp - 2) >> 2;     // accumulator lanes / column half
+        const int t = cw.tt * FG_M + tl;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        long long itr = 0, slot = 0;
+        bool have_total = false;
+        float stack[L][16];
+
+        // add accumulator set b into the running total (or start it)
+        auto drain_group = [&](long long g) -> bool {
+            const int b = (int)(g & 1);
+            // (the tensor-memory loads below are warp-collective: the whole warp takes one branch)
+            if (!__all_sync(0xffffffffu, bar_wait(smem_u32(&tdone[b]), (uint32_t)((g >> 1) & 1)))) return false;
+            fence_after_sync();
+            for (int d = 0; d < L; ++d) {
+                const int nh = ga.nd[d] >> 1;
+                for (int c = 0; c < nh; c += 8) {
+                    const uint32_t col = (uint32_t)(ga.acc[d] + half * nh + c);
+                    uint32_t a[8], s[8];
+                    tmem_ld8(lane_base + (uint32_t)(b * ga.nt) + col, a);
+                    if (have_total) tmem_ld8(lane_base + (uint32_t)(2 * ga.nt) + col, s);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int x = 0; x < 8; ++x)
+                        s[x] = have_total ? __float_as_uint(__uint_as_float(s[x]) + __uint_as_float(a[x])) : a[x];
+                    tmem_st8(lane_base + (uint32_t)(2 * ga.nt) + col, s);
+                }
+            }
+            tmem_wait_st();
+            have_total = true;
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) bar_arrive(smem_u32(&tfree[b]));
+            return true;
+        };
+
+        // split one level chunk's F^T rows into the next slot
+        auto emit = [&](const float (&v)[16]) -> bool {
+            const int cs = (int)(slot % CS);
+            if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) return false;
+            unsigned char* as = slots + cs * slot_bytes<P>();
+            store_group<P>(as, PF, tl, 2 * h, v);
+            store_group<P>(as, PF, tl, 2 * h + 1, v + 8);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) bar_arrive(smem_u32(&sfull[cs]));
+            ++slot;
+            return true;
+        };
+
+        for (long long g = 0; g < ngroups && ok; ++g) {
+            const long long ib = cw.i0 + g * ga.group, ie = min(cw.i1, ib + ga.group);
+            for (long long it = ib; it < ie && ok; ++it) {
+                const int r = (int)(it / nrb);
+                const long long rho0 = (it - (long long)r * nrb) << 5;
+#pragma unroll
+                for (int i = 0; i < STEPS; ++i, ++itr) {
+                    const int rs = (int)(itr % RS);
+                    if (!bar_wait(smem_u32(&rfull[rs]), (uint32_t)((itr / RS) & 1))) { ok = false; break; }
+                    float v[16];
+                    const float* rf = reinterpret_cast<const float*>(raw + rs * RAW);
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) v[k] = rf[(16 * h + k) * FG_M + tl];
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(smem_u32(&rempty[rs]));
+                    if (ga.nd[0] && !emit(v)) { ok = false; break; }
+#pragma unroll
+                    for (int d = 1; d <= L; ++d) {
+                        if (((i >> (d - 1)) & 1) == 0) {
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) stack[d - 1][k] = v[k];
+                            break;
+                        }
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) v[k] = stack[d - 1][k] + v[k];
+                        if (d < L) {
+                            if (ga.nd[d] && !emit(v)) { ok = false; break; }
+                        } else if (t < ga.tau_pad) {
+                            // F_{JF+L} rows rho0 + 16h + k (the residue block's only chunk)
+                            float* o = ga.fout + (long long)r * ga.fout_stride + (rho0 + 16 * h) * ga.tau_pad + t;
+#pragma unroll
+                            for (int k = 0; k < 16; ++k) o[(long long)k * ga.tau_pad] = v[k];
+                        }
+                    }
+                    if (!ok) break;
+                }
+            }
+            if (!ok) break;
+            if (g > 0 && !drain_group(g - 1)) { ok = false; break; }
+        }
+        if (ok && ngroups > 0 && !drain_group(ngroups - 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok && lane == 0) atomicOr(&g_foldgrad_error, 1u);
+        // the CTA's partial: level d, split sp, column j, t (loads by the whole warp, stores by the
+        // lanes whose column t exists)
+        // (tensor-memory lane quarter * 32 + lane is column te of the tile)
+        const int te = cw.tt * FG_M + quarter * 32 + lane;
+        if (ok) {
+            for (int d = 0; d < L; ++d) {
+                const int nh = ga.nd[d] >> 1;
+                float* pe = ga.part + ga.poff[d] + ((long long)cw.sp * ga.tau[d]) * ga.tau_pad + te;
+                for (int c = 0; c < nh; c += 8) {
+                    const int j0 = half * nh + c;
+                    uint32_t s[8];
+                    if (have_total) {
+                        tmem_ld8(lane_base + (uint32_t)(2 * ga.nt + ga.acc[d] + j0), s);
+                        tmem_wait_ld();
+                    }
+                    if (te < ga.tau_pad) {
+#pragma unroll
+                        for (int x = 0; x < 8; ++x)
+                            if (j0 + x < ga.tau[d])
+                                pe[(long long)(j0 + x) * ga.tau_pad] = have_total ? __uint_as_float(s[x]) : 0.0f;
+                    }
+                }
+            }
+        }
+    }
+
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after_sync();
+        tmem_dealloc(tmem, ncols);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
+    return fn;
+}
+
+}  // namespace
+
+cudaError_t foldgrad_error_word(unsigned int* value, bool clear) {
+    cudaError_t e = cudaMemcpyFromSymbol(value, g_foldgrad_error, sizeof(unsigned int));
+    if (e != cudaSuccess || !clear) return e;
+    const unsigned int zero = 0;
+    return cudaMemcpyToSymbol(g_foldgrad_error, &zero, sizeof(unsigned int));
+}
+
+cudaError_t launch_split_xt(const float* tab, long long tab_stride, const SplitXtArgs& sa, int reff, int pieces,
+                            __nv_bfloat16* xp, float xc, cudaStream_t st) {
+    const long long n = sa.blk0[sa.n];
+    if (n == 0) return cudaSuccess;
+    dim3 grid((unsigned)((n + 255) / 256), reff);
+    if (pieces == 3) k_split_xt<3><<<grid, 256, 0, st>>>(tab, tab_stride, sa, reff, xp, xc);
+    else k_split_xt<1><<<grid, 256, 0, st>>>(tab, tab_stride, sa, reff, xp, xc);
+    return cudaGetLastError();
+}
+
+// The tensor maps of one call: F_JF (FP32, dims t, rows, shifts; box 128 x 32 x 1, no swizzle) and
+// each level's pre-split pieces (bf16, dims rows, j, shifts, pieces; box 32 x N x 1 x P, 64-byte
+// swizzle); elements outside the arrays read as zero.
+cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, long long root_stride, long long n_root,
+                                const __nv_bfloat16* xp, const SplitXtArgs& sa, int reff, int pieces, cudaStream_t st) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)ga.tau_pad, (cuuint64_t)n_root, (cuuint64_t)reff};
+        const cuuint64_t strides[2] = {(cuuint64_t)ga.tau_pad * 4, (cuuint64_t)root_stride * 4};
+        const cuuint32_t box[3] = {FG_M, FG_K, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        if (fn(&ga.fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(Froot), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    for (int l = 0; l < sa.n; ++l) {
+        const int d = sa.lev[l];
+        const cuuint64_t n = 1ULL << sa.logn[l];
+        const cuuint64_t dims[4] = {n, (cuuint64_t)sa.tau[l], (cuuint64_t)reff, (cuuint64_t)pieces};
+        const cuuint64_t strides[3] = {n * 2, n * 2 * sa.tau[l], n * 2 * sa.tau[l] * reff};
+        const cuuint32_t box[4] = {FG_K, (cuuint32_t)ga.nd[d], 1, (cuuint32_t)pieces};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (fn(&ga.xmap[d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(xp + sa.off[l]), dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    const unsigned grid = (unsigned)(ga.t_tiles * ga.cpt);
+#define QMC_FG_LAUNCH(PP, LL)                                                                                   \
+    do {                                                                                                       \
+        cudaError_t e = cudaFuncSetAttribute(k_fold_grad_tc<PP, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)fg_smem<PP>());                                              \
+        if (e != cudaSuccess) return e;                                                                        \
+        k_fold_grad_tc<PP, LL><<<grid, kThreads, fg_smem<PP>(), st>>>(ga);                                     \
+    } while (0)
+    if (pieces == 3) {
+        if (L == 1) QMC_FG_LAUNCH(3, 1); else if (L == 2) QMC_FG_LAUNCH(3, 2); else if (L == 3) QMC_FG_LAUNCH(3, 3);
+        else return cudaErrorInvalidValue;
+    } else {
+        if (L == 1) QMC_FG_LAUNCH(1, 1); else if (L == 2) QMC_FG_LAUNCH(1, 2); else if (L == 3) QMC_FG_LAUNCH(1, 3);
+        else return cudaErrorInvalidValue;
+    }
+#undef QMC_FG_LAUNCH
+    return cudaGetLastError();
+}
+
+}  // namespace qmc

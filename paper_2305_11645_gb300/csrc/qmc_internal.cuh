@@ -238,6 +238,7 @@ constexpr int kMaxCR = 256;          // columns per CTA of the fine forward kern
 // ---------------------------------------------------------------------------------------------
 }  // namespace qmc
 #include <cuda.h>
+#include <cuda_bf16.h>
 namespace qmc {
 constexpr int kMaxGradTc = 24;
 struct GradTcEntry {
@@ -256,6 +257,40 @@ cudaError_t launch_grad_tc(const float* tab, long long tab_stride, const float* 
                            const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch, const int* sel,
                            int nsel, float* part, int reff, int pieces, float xc, cudaStream_t st);
 cudaError_t grad_error_word(unsigned int* value, bool clear);
+
+// ---------------------------------------------------------------------------------------------
+// Fold and block gradients of the lowest L <= 3 coarse levels in one pass over the root gradients
+// (qmc_foldgrad_tc.cu), with the levels' table columns pre-split into bf16 pieces (k_split_xt).
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxFoldLv = 3;
+struct SplitXtArgs {
+    int n;                           // levels with columns among the fused ones
+    int lev[kMaxFoldLv];             // d of each (level JF + d)
+    int logn[kMaxFoldLv], tau[kMaxFoldLv];
+    long long tab[kMaxFoldLv];       // table offset of the level's first column
+    long long off[kMaxFoldLv];       // bf16 element offset of its pieces in the split buffer
+    long long blk0[kMaxFoldLv + 1];  // prefix sums of tau x n / 8 threads
+};
+struct FoldGradArgs {
+    CUtensorMap fmap;                // F_JF: (t, rows, shifts)
+    CUtensorMap xmap[kMaxFoldLv];    // level JF + d pieces: (rows, j, shifts, pieces)
+    float* fout;                     // F_{JF+L}: n_out rows x tau_pad per shift, fout_stride apart
+    long long fout_stride;
+    float* part;
+    long long poff[kMaxFoldLv];      // partial offsets: [split][j][tau_pad] per level
+    long long items;                 // shifts x n_out / 32 (shift, residue block) items
+    int nd[kMaxFoldLv];              // MMA N of each level (0: no columns)
+    int tau[kMaxFoldLv];
+    int acc[kMaxFoldLv];             // accumulator column offsets
+    int nt;                          // columns of one accumulator set
+    int log_out;                     // log2 n_out
+    int tau_pad, cpt, t_tiles, group;
+};
+cudaError_t launch_split_xt(const float* tab, long long tab_stride, const SplitXtArgs& sa, int reff, int pieces,
+                            __nv_bfloat16* xp, float xc, cudaStream_t st);
+cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, long long root_stride, long long n_root,
+                                const __nv_bfloat16* xp, const SplitXtArgs& sa, int reff, int pieces, cudaStream_t st);
+cudaError_t foldgrad_error_word(unsigned int* value, bool clear);
 
 // ---------------------------------------------------------------------------------------------
 // Base b > 2: one weight level of the top-down sum (qmc_base_b.cu).  Level I's n = b^(m-I)
