@@ -1,29 +1,31 @@
 // The adjoint of Algorithm 2's lowest coarse levels in one pass over the root gradients (split and
-// bf16 tiers).  The adjoint of the periodic tiling folds the root gradients F_JF onto every coarser
-// level, F_{I+1}[rho] = F_I[rho] + F_I[rho + n_{I+1}], and each level's block gradient is
-// dA_I = sum_r X_{r,I}^T F_{r,I} over its distinct rows.  For the L lowest levels JF .. JF+L-1
-// this kernel does both without writing the intermediate folds: F_JF is read once, the folds are
-// formed in registers, every level's rows go to the tensor cores as they appear, and only
-// F_{JF+L} (the input of the remaining levels' fold) is written.
+// bf16 tiers).  The adjoint of the periodic tiling sends the root gradients F_JF to every coarser
+// level: level I's block gradient is dA_I = sum_r sum_rho X_{r,I}[rho mod n_I]^T F_{r,JF}[rho] over
+// the root rows rho (the same sum as over the folded gradient F_I[rho'] = sum_q F_JF[rho' + q n_I]
+// of Algorithm 2's distinct rows, taken before the fold).  For the L lowest levels JF .. JF+L-1
+// this kernel reads F_JF once: every root chunk goes to the tensor cores once, against the rows of
+// all L levels' point tables stacked into one B operand, and only the fold F_{JF+L} (the input of
+// the remaining levels) is written.
 //
 // Work item: (shift r, column tile t0 .. t0+127, residue block rho0 .. rho0+31 of the n_out =
-// n_{JF+L} rows of level JF+L).  Its root rows are rho0 + k + q n_out (k < 32, q < 2^L); visiting
-// q in bit-reversed order, each pair of a fold is complete as soon as its second member arrives,
-// so a stack of L pending chunks is all the fold needs.  Level JF+d's chunk q_d (rows rho0 + k +
-// q_d n_out of that level) is the product D[t][j] += sum_k F[k][t] X_{JF+d}[k][j] with M = 128
-// columns t, N = the level's columns (rounded up to 16, at most 64), K = 32 rows.
+// n_{JF+L} rows of level JF+L).  Its root rows are rho0 + k + q n_out (k < 32, q < 2^L); root chunk q
+// meets level JF+d's rows rho0 + k + (q mod 2^(L-d)) n_out.  One chunk's product is D[t][j] += sum_k
+// F[k][t] X[k][j] with M = 128 columns t, N = the levels' columns (each rounded up to 16, at most
+// 128 in all), K = 32 rows; D's columns are the levels' gradient columns side by side.
 //
 // One CTA per SM, each on one column tile and a contiguous range of (shift, residue block) items:
-//   warp 0      TMA producer: the FP32 root chunk (128 t x 32 rows, a 3-D box over (t, rows,
-//               shifts)) into a ring of raw stages, and for every level chunk the pre-split bf16
-//               pieces of its point-table rows (k_split_xt) into the chunk's operand slot;
-//   warp 1      allocates tensor memory (two accumulator sets and one running total) and one
-//               thread issues every level chunk's MMAs into the accumulator of its level;
-//   warps 2-9   converters: fold in registers, split each level chunk's F^T into bf16 pieces
-//               (K-major, 64-byte swizzle) in its slot, write F_{JF+L}; after every group of
-//               items (level JF's chains at most 1024 rows) add the accumulators into the
-//               running total, one group behind the MMAs, and at the end store the CTA's
-//               partial gradient, which k_grad_reduce sums over the CTAs of the column tile.
+//   warp 0      TMA producer: the FP32 root chunks (128 t x 32 rows, a 3-D box over (t, rows,
+//               shifts)) into a ring of raw stages;
+//   warp 2      TMA producer: for every root chunk the pre-split bf16 pieces (k_split_xt) of the
+//               levels' rows into the chunk's operand slot, one box per level and piece;
+//   warp 1      allocates the tensor memory and one thread issues every chunk's MMAs, with the
+//               chunk's F^T pieces read from tensor memory;
+//   warps 3-18  converters: split the chunk's F^T into bf16 pieces in tensor memory (lane = column
+//               t, two rows per 32-bit column), sum the chunks of an item into F_{JF+L} and write
+//               it; warps 3-10, after every group of items (chains of at most 1024 rows), add the
+//               accumulator into a running total in shared memory, one group behind the MMAs, and
+//               at the end store the CTA's partial gradient, which k_grad_reduce sums over the
+//               CTAs of the column tile.
 // Every wait is bounded; a run-out sets the error word (foldgrad_error_word) and the roles stop as
 // in the other tensor-core kernels.
 #include <cuda.h>
@@ -44,16 +46,36 @@ namespace {
 
 constexpr int FG_M = 128;                      // columns t per item (MMA M)
 constexpr int FG_K = 32;                       // rows per chunk
-constexpr int FG_NMAX = 64;                    // columns j of one level (MMA N), at most
+constexpr int FG_NMAX = 128;                   // gradient columns of all fused levels (MMA N), at most
 constexpr int RS = 4;                          // raw root-chunk stages
-constexpr int CS = 4;                          // level-chunk operand slots
+constexpr int CS = 4;                          // chunk operand slots
 constexpr uint32_t RAW = FG_K * FG_M * 4;      // [k][t] FP32, 16 KB
-constexpr uint32_t PF = FG_M * 64;             // one bf16 piece of F^T: 128 rows x 64 bytes
-constexpr uint32_t PXMAX = FG_NMAX * 64;       // one bf16 piece of X: up to 64 rows x 64 bytes
-constexpr int kThreads = 320;
+constexpr int kConv = 16;                      // converter warps
+constexpr int kThreads = 96 + 32 * kConv;
+// Tensor memory (512 columns): accumulator sets b = 0, 1 at columns 128 b, and the operand slots'
+// F^T pieces from column 256: slot s, piece p, K-step ks at 256 + 16 (P s + p) + 8 ks (one 32-bit
+// column holds two bf16 of consecutive rows k).
+constexpr uint32_t TM_SLOT0 = 256;
+static_assert(TM_SLOT0 + 16 * 3 * CS <= 512, "tensor-memory slots");
 
-template <int P> constexpr uint32_t slot_bytes() { return P * (PF + PXMAX); }
-template <int P> constexpr size_t fg_smem() { return 1024 + RS * RAW + CS * slot_bytes<P>() + 256; }
+// shared memory: raw stages, X slots (P pieces of ntot rows x 64 bytes), the running total
+// [ntot columns j][128 lanes] FP32, barriers
+__host__ __device__ constexpr uint32_t slot_bytes(int P, int ntot) { return (uint32_t)(P * ntot * 64); }
+__host__ __device__ constexpr size_t fg_smem(int P, int ntot) {
+    return 1024 + RS * RAW + CS * slot_bytes(P, ntot) + (size_t)ntot * 128 * 4 + 256;
+}
+
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
+}
 
 __device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
@@ -86,19 +108,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
-                    "r"(r[7]) : "memory");
-}
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-template <int L> __device__ __forceinline__ int bitrev(int i) {
-    int q = 0;
-#pragma unroll
-    for (int b = 0; b < L; ++b) q |= ((i >> b) & 1) << (L - 1 - b);
-    return q;
-}
 
 // the CTA's column tile, split index and item range
 struct CtaWork {
@@ -160,15 +171,19 @@ __global__ void __launch_bounds__(256) k_split_xt(const float* __restrict__ tab,
 template <int P, int L>
 __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_constant__ FoldGradArgs ga) {
     constexpr int STEPS = 1 << L;
+    const int ntot = ga.acc[L - 1] + ga.nd[L - 1];                // MMA N: every fused level's columns
+    const uint32_t sb = slot_bytes(P, ntot);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = align_1k(smem_raw);
     unsigned char* raw = smem;                                    // RS raw stages
-    unsigned char* slots = smem + RS * RAW;                       // CS operand slots: F^T pieces, X pieces
-    uint64_t* rfull = reinterpret_cast<uint64_t*>(slots + CS * slot_bytes<P>());
+    unsigned char* slots = smem + RS * RAW;                       // CS operand slots: X pieces
+    float* tot = reinterpret_cast<float*>(slots + CS * sb);       // running total [j][t]
+    uint64_t* rfull = reinterpret_cast<uint64_t*>(tot + ntot * 128);
     uint64_t* rempty = rfull + RS;
-    uint64_t* sfull = rempty + RS;
+    uint64_t* sfull = rempty + RS;                                // F^T pieces written
     uint64_t* sempty = sfull + CS;
-    uint64_t* tdone = sempty + CS;                                // [2]
+    uint64_t* xfull = sempty + CS;                                // X pieces landed
+    uint64_t* tdone = xfull + CS;                                 // [2]
     uint64_t* tfree = tdone + 2;                                  // [2]
     uint64_t* drain = tfree + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
@@ -178,18 +193,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
     const long long nrb = (1LL << ga.log_out) >> 5;               // residue blocks per shift
     const long long n_out = 1LL << ga.log_out;
     const long long ngroups = (cw.i1 - cw.i0 + ga.group - 1) / ga.group;
-    const uint32_t ncols = 4 * (uint32_t)ga.nt > 256 ? 512u : 256u;
     if (warp == 0 && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.fmap)) : "memory");
         for (int d = 0; d < L; ++d)
             if (ga.nd[d]) asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.xmap[d])) : "memory");
-        for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], 8); }
-        for (int s = 0; s < CS; ++s) { bar_init(&sfull[s], 9); bar_init(&sempty[s], 1); }
+        for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], kConv); }
+        for (int s = 0; s < CS; ++s) { bar_init(&sfull[s], kConv); bar_init(&sempty[s], 1); bar_init(&xfull[s], 1); }
         for (int b = 0; b < 2; ++b) { bar_init(&tdone[b], 1); bar_init(&tfree[b], 8); }
         bar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), ncols);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 512);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -197,80 +211,88 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
     bool ok = true;
 
     if (warp == 0) {
-        // ------------------------------------------------------------------ TMA producer
+        // ------------------------------------------------------------------ TMA producer of F_JF
         if (lane == 0) {
-            long long itr = 0, slot = 0;
+            long long itr = 0;
             for (long long it = cw.i0; it < cw.i1 && ok; ++it) {
                 const int r = (int)(it / nrb);
                 const int rho0 = (int)((it - (long long)r * nrb) << 5);
-                for (int i = 0; i < STEPS && ok; ++i, ++itr) {
-                    const int q = bitrev<L>(i);
+                for (int q = 0; q < STEPS && ok; ++q, ++itr) {
                     const int rs = (int)(itr % RS);
                     if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
                     bar_expect_tx(smem_u32(&rfull[rs]), RAW);
                     tma_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
                            rho0 + q * (int)n_out, r);
-                    // level chunks completed at this step: levels 0 .. (trailing ones of i), below L
+                }
+            }
+            if (!ok) {                                            // the copies still in flight land first
+                atomicOr(&g_foldgrad_error, 1u);
+                for (long long k = itr - 1; k >= 0 && k >= itr - RS; --k)
+                    bar_wait(smem_u32(&rfull[k % RS]), (uint32_t)((k / RS) & 1));
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------------ TMA producer of X pieces
+        if (lane == 0) {
+            long long slot = 0;
+            for (long long it = cw.i0; it < cw.i1 && ok; ++it) {
+                const int r = (int)(it / nrb);
+                const int rho0 = (int)((it - (long long)r * nrb) << 5);
+                for (int q = 0; q < STEPS && ok; ++q, ++slot) {
+                    const int cs = (int)(slot % CS);
+                    if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
+                    const uint32_t fb = smem_u32(&xfull[cs]);
+                    bar_expect_tx(fb, sb);
+                    const uint32_t xs = smem_u32(slots + cs * sb);
                     for (int d = 0; d < L; ++d) {
-                        if (d > 0 && ((i >> (d - 1)) & 1) == 0) break;
                         if (!ga.nd[d]) continue;
-                        const int cs = (int)(slot % CS);
-                        if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
-                        const uint32_t fb = smem_u32(&sfull[cs]);
-                        bar_expect_tx(fb, (uint32_t)(P * ga.nd[d] * 64));
-                        const int qd = q & ((1 << (L - d)) - 1);
-                        tma_4d(smem_u32(slots + cs * slot_bytes<P>() + P * PF), &ga.xmap[d], fb,
-                               rho0 + qd * (int)n_out, 0, r, 0);
-                        ++slot;
+                        const int row = rho0 + (q & ((1 << (L - d)) - 1)) * (int)n_out;
+                        for (int p = 0; p < P; ++p)
+                            tma_4d(xs + (uint32_t)((p * ntot + ga.acc[d]) * 64), &ga.xmap[d], fb, row, 0, r, p);
                     }
                 }
             }
-            if (!ok) atomicOr(&g_foldgrad_error, 1u);
+            if (!ok) {
+                atomicOr(&g_foldgrad_error, 1u);
+                for (long long k = slot - 1; k >= 0 && k >= slot - CS; --k)
+                    bar_wait(smem_u32(&xfull[k % CS]), (uint32_t)((k / CS) & 1));
+            }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             long long slot = 0;
+            const uint32_t idesc = idesc_bf16((uint32_t)ntot);
+            const uint32_t xpiece = (uint32_t)ntot * 64;
             for (long long g = 0; g < ngroups && ok; ++g) {
                 const int b = (int)(g & 1);
                 if (!bar_wait(smem_u32(&tfree[b]), (uint32_t)(((g >> 1) & 1) ^ 1))) { ok = false; break; }
                 fence_after_sync();
-                bool fresh[L];
-#pragma unroll
-                for (int d = 0; d < L; ++d) fresh[d] = true;
+                bool fresh = true;
+                const uint32_t dst = tmem + (uint32_t)(b * 128);
                 const long long ib = cw.i0 + g * ga.group, ie = min(cw.i1, ib + ga.group);
-                for (long long it = ib; it < ie && ok; ++it) {
-                    for (int i = 0; i < STEPS && ok; ++i) {
+                for (long long n = (ie - ib) * STEPS; n > 0 && ok; --n, ++slot) {
+                    const int cs = (int)(slot % CS);
+                    if (!bar_wait(smem_u32(&sfull[cs]), (uint32_t)((slot / CS) & 1)) ||
+                        !bar_wait(smem_u32(&xfull[cs]), (uint32_t)((slot / CS) & 1))) { ok = false; break; }
+                    fence_after_sync();
+                    const uint32_t xs = smem_u32(slots + cs * sb);
+                    const uint32_t ta = tmem + TM_SLOT0 + (uint32_t)(16 * P * cs);
 #pragma unroll
-                        for (int d = 0; d < L; ++d) {
-                            if (d > 0 && ((i >> (d - 1)) & 1) == 0) break;
-                            const int nd = ga.nd[d];
-                            if (!nd) continue;
-                            const int cs = (int)(slot % CS);
-                            if (!bar_wait(smem_u32(&sfull[cs]), (uint32_t)((slot / CS) & 1))) { ok = false; break; }
-                            fence_after_sync();
-                            const uint32_t as = smem_u32(slots + cs * slot_bytes<P>()), xs = as + P * PF;
-                            const uint32_t idesc = idesc_bf16((uint32_t)nd);
-                            const uint32_t dst = tmem + (uint32_t)(b * ga.nt + ga.acc[d]);
-                            const uint32_t xpiece = (uint32_t)nd * 64;
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t bd = smem_desc_sw64(xs + 32 * ks);
+                        constexpr int NP = P == 3 ? 6 : 1;
+                        constexpr int pi[6] = {2, 1, 0, 1, 0, 0};
+                        constexpr int pj[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
-                            for (int ks = 0; ks < 2; ++ks) {
-                                const uint64_t ad = smem_desc_sw64(as + 32 * ks), bd = smem_desc_sw64(xs + 32 * ks);
-                                constexpr int NP = P == 3 ? 6 : 1;
-                                constexpr int pi[6] = {2, 1, 0, 1, 0, 0};
-                                constexpr int pj[6] = {0, 1, 2, 0, 1, 0};
-#pragma unroll
-                                for (int pq = 0; pq < NP; ++pq) {
-                                    const int ia = P == 3 ? pi[pq] : 0, jb = P == 3 ? pj[pq] : 0;
-                                    mma_bf16(dst, desc_add(ad, ia * PF), desc_add(bd, jb * xpiece), idesc,
-                                             fresh[d] ? 0u : 1u);
-                                    fresh[d] = false;
-                                }
-                            }
-                            mma_commit(smem_u32(&sempty[cs]));
-                            ++slot;
+                        for (int pq = 0; pq < NP; ++pq) {
+                            const int ia = P == 3 ? pi[pq] : 0, jb = P == 3 ? pj[pq] : 0;
+                            mma_bf16_ts(dst, ta + (uint32_t)(16 * ia + 8 * ks), desc_add(bd, jb * xpiece), idesc,
+                                        fresh ? 0u : 1u);
+                            fresh = false;
                         }
                     }
+                    mma_commit(smem_u32(&sempty[cs]));
                 }
                 if (ok) mma_commit(smem_u32(&tdone[b]));
             }
@@ -280,54 +302,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
         }
     } else {
         // ------------------------------------------------------------------ converters
-        const int ct = threadIdx.x - 64;                          // 0..255
-        const int tl = ct & 127, h = ct >> 7;                     // column t0 + tl, rows 16h .. 16h+15
-        const int quarter = warp & 3, half = (warp - 2) >> 2;     // accumulator lanes / column half
+        // warp w takes tensor-memory lanes 32 (w % 4) .. + 31 (fixed by warp) = columns t, and
+        // rows 8h .. 8h+7 of every chunk, h = (w - 3) / 4; warps 3-10 also move the accumulator
+        // into the running total, column half (w - 3) / 4
+        const int quarter = warp & 3, h = (warp - 3) >> 2;
+        const int tl = quarter * 32 + lane;
         const int t = cw.tt * FG_M + tl;
+        const bool drainer = warp < 11;
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         long long itr = 0, slot = 0;
         bool have_total = false;
-        float stack[L][16];
+        const int nh = ntot >> 1, j0 = h * nh;                    // a drainer's columns (ntot % 16 == 0)
 
         // add accumulator set b into the running total (or start it)
         auto drain_group = [&](long long g) -> bool {
+            if (!drainer) return true;
             const int b = (int)(g & 1);
             // (the tensor-memory loads below are warp-collective: the whole warp takes one branch)
             if (!__all_sync(0xffffffffu, bar_wait(smem_u32(&tdone[b]), (uint32_t)((g >> 1) & 1)))) return false;
             fence_after_sync();
-            for (int d = 0; d < L; ++d) {
-                const int nh = ga.nd[d] >> 1;
-                for (int c = 0; c < nh; c += 8) {
-                    const uint32_t col = (uint32_t)(ga.acc[d] + half * nh + c);
-                    uint32_t a[8], s[8];
-                    tmem_ld8(lane_base + (uint32_t)(b * ga.nt) + col, a);
-                    if (have_total) tmem_ld8(lane_base + (uint32_t)(2 * ga.nt) + col, s);
-                    tmem_wait_ld();
+            for (int c = 0; c < nh; c += 8) {
+                uint32_t a[8];
+                tmem_ld8(lane_base + (uint32_t)(b * 128 + j0 + c), a);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int x = 0; x < 8; ++x)
-                        s[x] = have_total ? __float_as_uint(__uint_as_float(s[x]) + __uint_as_float(a[x])) : a[x];
-                    tmem_st8(lane_base + (uint32_t)(2 * ga.nt) + col, s);
+                for (int x = 0; x < 8; ++x) {
+                    float* o = tot + (j0 + c + x) * 128 + tl;
+                    *o = have_total ? *o + __uint_as_float(a[x]) : __uint_as_float(a[x]);
                 }
             }
-            tmem_wait_st();
             have_total = true;
             fence_before_sync();
             __syncwarp();
             if (lane == 0) bar_arrive(smem_u32(&tfree[b]));
-            return true;
-        };
-
-        // split one level chunk's F^T rows into the next slot
-        auto emit = [&](const float (&v)[16]) -> bool {
-            const int cs = (int)(slot % CS);
-            if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) return false;
-            unsigned char* as = slots + cs * slot_bytes<P>();
-            store_group<P>(as, PF, tl, 2 * h, v);
-            store_group<P>(as, PF, tl, 2 * h + 1, v + 8);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) bar_arrive(smem_u32(&sfull[cs]));
-            ++slot;
             return true;
         };
 
@@ -336,36 +343,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
             for (long long it = ib; it < ie && ok; ++it) {
                 const int r = (int)(it / nrb);
                 const long long rho0 = (it - (long long)r * nrb) << 5;
+                float fsum[8];
 #pragma unroll
-                for (int i = 0; i < STEPS; ++i, ++itr) {
-                    const int rs = (int)(itr % RS);
+                for (int k = 0; k < 8; ++k) fsum[k] = 0.0f;
+                for (int q = 0; q < STEPS; ++q, ++itr, ++slot) {
+                    const int rs = (int)(itr % RS), cs = (int)(slot % CS);
                     if (!bar_wait(smem_u32(&rfull[rs]), (uint32_t)((itr / RS) & 1))) { ok = false; break; }
-                    float v[16];
+                    float v[8];
                     const float* rf = reinterpret_cast<const float*>(raw + rs * RAW);
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) v[k] = rf[(16 * h + k) * FG_M + tl];
+                    for (int k = 0; k < 8; ++k) v[k] = rf[(8 * h + k) * FG_M + tl];
                     __syncwarp();
                     if (lane == 0) bar_arrive(smem_u32(&rempty[rs]));
-                    if (ga.nd[0] && !emit(v)) { ok = false; break; }
 #pragma unroll
-                    for (int d = 1; d <= L; ++d) {
-                        if (((i >> (d - 1)) & 1) == 0) {
+                    for (int k = 0; k < 8; ++k) fsum[k] += v[k];
+                    // the chunk's F^T rows as bf16 pieces in the slot's tensor memory
+                    if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
+                    fence_after_sync();
+                    uint32_t w[P][4];
 #pragma unroll
-                            for (int k = 0; k < 16; ++k) stack[d - 1][k] = v[k];
-                            break;
-                        }
+                    for (int x = 0; x < 4; ++x) {
+                        uint32_t pc[P];
+                        split_pair<P>(v[2 * x], v[2 * x + 1], pc);
 #pragma unroll
-                        for (int k = 0; k < 16; ++k) v[k] = stack[d - 1][k] + v[k];
-                        if (d < L) {
-                            if (ga.nd[d] && !emit(v)) { ok = false; break; }
-                        } else if (t < ga.tau_pad) {
-                            // F_{JF+L} rows rho0 + 16h + k (the residue block's only chunk)
-                            float* o = ga.fout + (long long)r * ga.fout_stride + (rho0 + 16 * h) * ga.tau_pad + t;
-#pragma unroll
-                            for (int k = 0; k < 16; ++k) o[(long long)k * ga.tau_pad] = v[k];
-                        }
+                        for (int p = 0; p < P; ++p) w[p][x] = pc[p];
                     }
-                    if (!ok) break;
+#pragma unroll
+                    for (int p = 0; p < P; ++p)
+                        tmem_st4(lane_base + TM_SLOT0 + (uint32_t)(16 * (P * cs + p) + 4 * h), w[p]);
+                    tmem_wait_st();
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(smem_u32(&sfull[cs]));
+                }
+                if (!ok) break;
+                if (t < ga.tau_pad) {
+                    // F_{JF+L} rows rho0 + 8h + k: the sum of the item's root chunks
+                    float* o = ga.fout + (long long)r * ga.fout_stride + (rho0 + 8 * h) * ga.tau_pad + t;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) o[(long long)k * ga.tau_pad] = fsum[k];
                 }
             }
             if (!ok) break;
@@ -374,27 +390,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
         if (ok && ngroups > 0 && !drain_group(ngroups - 1)) ok = false;
         ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) atomicOr(&g_foldgrad_error, 1u);
-        // the CTA's partial: level d, split sp, column j, t (loads by the whole warp, stores by the
-        // lanes whose column t exists)
-        // (tensor-memory lane quarter * 32 + lane is column te of the tile)
-        const int te = cw.tt * FG_M + quarter * 32 + lane;
-        if (ok) {
+        // the CTA's partial: level d, split sp, column j, t
+        if (ok && drainer && t < ga.tau_pad) {
             for (int d = 0; d < L; ++d) {
-                const int nh = ga.nd[d] >> 1;
-                float* pe = ga.part + ga.poff[d] + ((long long)cw.sp * ga.tau[d]) * ga.tau_pad + te;
-                for (int c = 0; c < nh; c += 8) {
-                    const int j0 = half * nh + c;
-                    uint32_t s[8];
-                    if (have_total) {
-                        tmem_ld8(lane_base + (uint32_t)(2 * ga.nt + ga.acc[d] + j0), s);
-                        tmem_wait_ld();
-                    }
-                    if (te < ga.tau_pad) {
-#pragma unroll
-                        for (int x = 0; x < 8; ++x)
-                            if (j0 + x < ga.tau[d])
-                                pe[(long long)(j0 + x) * ga.tau_pad] = have_total ? __uint_as_float(s[x]) : 0.0f;
-                    }
+                float* pe = ga.part + ga.poff[d] + ((long long)cw.sp * ga.tau[d]) * ga.tau_pad + t;
+                for (int j = 0; j < ga.tau[d]; ++j) {
+                    const int col = ga.acc[d] + j;
+                    if (col >= j0 && col < j0 + nh)
+                        pe[(long long)j * ga.tau_pad] = have_total ? tot[col * 128 + tl] : 0.0f;
                 }
             }
         }
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
     __syncthreads();
     if (warp == 1) {
         fence_after_sync();
-        tmem_dealloc(tmem, ncols);
+        tmem_dealloc(tmem, 512);
     }
 }
 
@@ -440,7 +443,7 @@ cudaError_t launch_split_xt(const float* tab, long long tab_stride, const SplitX
 }
 
 // The tensor maps of one call: F_JF (FP32, dims t, rows, shifts; box 128 x 32 x 1, no swizzle) and
-// each level's pre-split pieces (bf16, dims rows, j, shifts, pieces; box 32 x N x 1 x P, 64-byte
+// each level's pre-split pieces (bf16, dims rows, j, shifts, pieces; box 32 x N_d x 1 x 1, 64-byte
 // swizzle); elements outside the arrays read as zero.
 cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, long long root_stride, long long n_root,
                                 const __nv_bfloat16* xp, const SplitXtArgs& sa, int reff, int pieces, cudaStream_t st) {
@@ -461,20 +464,25 @@ cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, lon
         const cuuint64_t n = 1ULL << sa.logn[l];
         const cuuint64_t dims[4] = {n, (cuuint64_t)sa.tau[l], (cuuint64_t)reff, (cuuint64_t)pieces};
         const cuuint64_t strides[3] = {n * 2, n * 2 * sa.tau[l], n * 2 * sa.tau[l] * reff};
-        const cuuint32_t box[4] = {FG_K, (cuuint32_t)ga.nd[d], 1, (cuuint32_t)pieces};
+        const cuuint32_t box[4] = {FG_K, (cuuint32_t)ga.nd[d], 1, 1};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
         if (fn(&ga.xmap[d], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(xp + sa.off[l]), dims,
                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
+    int ntot = 0;
+    for (int d = 0; d < L; ++d) ntot = std::max(ntot, ga.acc[d] + ga.nd[d]);
+    if (ntot == 0 || ntot > FG_NMAX || ntot % 16 != 0 || ga.acc[L - 1] + ga.nd[L - 1] != ntot)
+        return cudaErrorInvalidValue;
+    const size_t smem = fg_smem(pieces, ntot);
     const unsigned grid = (unsigned)(ga.t_tiles * ga.cpt);
 #define QMC_FG_LAUNCH(PP, LL)                                                                                   \
     do {                                                                                                       \
         cudaError_t e = cudaFuncSetAttribute(k_fold_grad_tc<PP, LL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)fg_smem<PP>());                                              \
+                                             (int)smem);                                                       \
         if (e != cudaSuccess) return e;                                                                        \
-        k_fold_grad_tc<PP, LL><<<grid, kThreads, fg_smem<PP>(), st>>>(ga);                                     \
+        k_fold_grad_tc<PP, LL><<<grid, kThreads, smem, st>>>(ga);                                              \
     } while (0)
     if (pieces == 3) {
         if (L == 1) QMC_FG_LAUNCH(3, 1); else if (L == 2) QMC_FG_LAUNCH(3, 2); else if (L == 3) QMC_FG_LAUNCH(3, 3);
