@@ -328,6 +328,7 @@ struct Plan {
     // tensor-core backward: entries staged by TMA (k_grad_tc; whole chunks of 32 rows, F materialised)
     // and the rest on k_coarse_grad_tc (chl, its tiles bwd_tiles_l)
     int gsel[kMaxGradTc] = {}, ngsel = 0, bwd_tiles_l = 0;
+    long long gxoff[kMaxGradTc] = {};   // their pre-split table columns in the split buffer
     Chain chl{};
     // tensor-core backward of the lowest fg_L coarse levels in one pass over the root gradients
     // (k_fold_grad_tc, entries fg_ent[d] of level JF + d or -1), the folds above JF + fg_L from
@@ -820,6 +821,24 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         // level below m within kFoldDepth of the root; F of every coarse level up to I_mat is
         // materialised, the levels above it (the constant level m) fold from F_{I_mat} on the fly.
         P.chb = P.chf;
+        if (P.tc_pieces != 0) {
+            // the tensor-core gradients take up to 128 columns of a level per entry (MMA N)
+            Chain c{};
+            for (int e = 0; e < P.chf.count; ++e) {
+                const int I = P.chf.lev[e];
+                if (e > 0 && P.chf.lev[e - 1] == I) continue;      // the level's first entry only
+                const int parts = (P.lev_tau[I] + 127) / 128, width = (P.lev_tau[I] + parts - 1) / parts;
+                for (int pc = 0; pc < parts; ++pc) {
+                    const int c0 = pc * width, cw = std::min(width, P.lev_tau[I] - c0);
+                    if (cw <= 0) break;
+                    const int f = c.count++;
+                    c.lev[f] = I; c.logn[f] = P.m - I; c.tau[f] = cw; c.col0[f] = P.lev_col0[I] + c0;
+                    c.tab[f] = P.lev_tab[I] + ((long long)c0 << (P.m - I));
+                    c.split[f] = 1;
+                }
+            }
+            P.chb = c;
+        }
         const int max_depth = precision == QMC_FP64 ? 5 : 6;
         int I_mat = P.JF;
         for (int e = 0; e < P.chb.count; ++e)
@@ -866,7 +885,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
                 for (int e = 0; e < P.chb.count; ++e) {
                     const int d = P.chb.lev[e] - P.JF;
                     if (d < 0 || d >= L) continue;
-                    if (ent[d] >= 0 || P.chb.tau[e] > 64 || P.chb.flog[e] != 0 || P.chb.tab[e] % 4 != 0) good = 0;
+                    if (ent[d] >= 0 || P.chb.flog[e] != 0 || P.chb.tab[e] % 4 != 0) good = 0;
                     ent[d] = e;
                     ncols += (P.chb.tau[e] + 15) / 16 * 16;
                     any = 1;
@@ -937,7 +956,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             split = std::max(1LL, std::min(split, std::max(1LL, K / kmin)));
             // tensor-core splits of at most 4096 rows: an FP32 accumulator in tensor memory then sums
             // at most 1024 rows (four per CTA), and the splits are summed in double
-            if (tc) split = std::max(split, (K + 4095) / 4096);
+            if (tc) split = std::max(split, (K + 1023) / 1024);
             split = std::min(split, 4096LL);
             long long kper = (K + split - 1) / split;
             if (tc) {                       // whole chunks of 32 rows per split
@@ -961,6 +980,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         for (int e = 0; e < P.chb.count; ++e) {
             if (fused(e)) continue;
             const bool tma = tc && P.chb.flog[e] == 0 && P.m - P.chb.lev[e] >= 5 && P.chb.tab[e] % 4 == 0 &&
+                             P.chb.tau[e] <= 128 &&
                              P.chb.foff[e] % 4 == 0 && P.tau_pad % 4 == 0 && P.tab_stride % 4 == 0 &&
                              P.chb.kper[e] % 32 == 0 && P.ngsel < kMaxGradTc;
             if (tma) { P.gsel[P.ngsel++] = e; continue; }
@@ -975,6 +995,20 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         }
         P.chl.tile0[P.chl.count] = btl;
         P.bwd_tiles_l = btl;
+        SplitXtArgs& sx = P.sxa;
+        sx = SplitXtArgs{};
+        long long xoff = 0;
+        auto add_xt = [&](int e, int d) {
+            const int l = sx.n++;
+            sx.lev[l] = d;
+            sx.logn[l] = P.chb.logn[e];
+            sx.tau[l] = P.chb.tau[e];
+            sx.tab[l] = P.chb.tab[e];
+            sx.off[l] = xoff;
+            sx.blk0[l + 1] = sx.blk0[l] + ((long long)P.chb.tau[e] << (P.chb.logn[e] - 3));
+            xoff += (long long)P.tc_pieces * P.reff * P.chb.tau[e] << P.chb.logn[e];
+            return sx.off[l];
+        };
         if (P.fg_L) {
             const int L = P.fg_L;
             FoldGradArgs& g = P.fga;
@@ -987,9 +1021,6 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             g.group = std::max(1, 32 >> L);            // level JF's chains: 32 2^L rows per item, <= 1024
             g.fout_stride = P.Fchain_per_shift;
             int acc = 0;
-            SplitXtArgs& sx = P.sxa;
-            sx = SplitXtArgs{};
-            long long xoff = 0;
             for (int d = 0; d < L; ++d) {
                 const int e = P.fg_ent[d];
                 g.nd[d] = e >= 0 ? (P.chb.tau[e] + 15) / 16 * 16 : 0;
@@ -997,20 +1028,13 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
                 g.acc[d] = acc;
                 g.poff[d] = e >= 0 ? P.chb.poff[e] : 0;
                 acc += g.nd[d];
-                if (e < 0) continue;
-                const int l = sx.n++;
-                sx.lev[l] = d;
-                sx.logn[l] = P.chb.logn[e];
-                sx.tau[l] = P.chb.tau[e];
-                sx.tab[l] = P.chb.tab[e];
-                sx.off[l] = xoff;
-                sx.blk0[l + 1] = sx.blk0[l] + ((long long)P.chb.tau[e] << (P.chb.logn[e] - 3));
-                xoff += (long long)P.tc_pieces * P.reff * P.chb.tau[e] << P.chb.logn[e];
+                if (e >= 0) add_xt(e, d);
             }
             g.nt = 32;
             while (g.nt < acc) g.nt *= 2;
-            P.xt_bytes = (size_t)xoff * 2;
         }
+        for (int i = 0; i < P.ngsel; ++i) P.gxoff[i] = add_xt(P.gsel[i], -1);
+        P.xt_bytes = (size_t)xoff * 2;
     }
 
     // workspace layout
@@ -1370,12 +1394,14 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
     if (P.chb.count)
     {
         T* Fchain = reinterpret_cast<T*>(ws + P.off_Fchain);
+        __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(ws + P.off_xt);
+        if constexpr (std::is_same<T, float>::value) {
+            if (P.sxa.n)
+                QMC_LAUNCH(st, "k_split_xt", launch_split_xt(tab, P.tab_stride, P.sxa, P.reff, P.tc_pieces, xt, P.xc, st));
+        }
         if (P.fg_L) {
             if constexpr (std::is_same<T, float>::value) {
                 // levels JF .. JF+L-1 and their folds in one pass; the rest fold from F_{JF+L}
-                __nv_bfloat16* xt = reinterpret_cast<__nv_bfloat16*>(ws + P.off_xt);
-                QMC_LAUNCH(st, "k_split_xt",
-                           launch_split_xt(tab, P.tab_stride, P.sxa, P.reff, P.tc_pieces, xt, P.xc, st));
                 FoldGradArgs ga = P.fga;
                 ga.fout = Fchain + P.fold.off[P.fg_L];
                 ga.part = partc;
@@ -1394,8 +1420,8 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
             if constexpr (std::is_same<T, float>::value) {
                 if (P.ngsel)
                     QMC_LAUNCH(st, "k_grad_tc",
-                               launch_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,
-                                              P.tau_pad, P.chb, P.gsel, P.ngsel, partc, P.reff, P.tc_pieces, P.xc, st));
+                               launch_grad_tc(xt, Froot, root_stride, Fchain, P.Fchain_per_shift, P.tau_pad, P.chb,
+                                              P.gsel, P.gxoff, P.ngsel, partc, P.reff, P.tc_pieces, st));
                 if (P.chl.count)
                     QMC_LAUNCH(st, "k_coarse_grad_tc",
                                launch_coarse_grad_tc(tab, P.tab_stride, Froot, root_stride, Fchain, P.Fchain_per_shift,

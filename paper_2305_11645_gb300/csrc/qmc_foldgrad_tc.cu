@@ -461,6 +461,7 @@ cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, lon
     }
     for (int l = 0; l < sa.n; ++l) {
         const int d = sa.lev[l];
+        if (d < 0) continue;                      // (a k_grad_tc entry)
         const cuuint64_t n = 1ULL << sa.logn[l];
         const cuuint64_t dims[4] = {n, (cuuint64_t)sa.tau[l], (cuuint64_t)reff, (cuuint64_t)pieces};
         const cuuint64_t strides[3] = {n * 2, n * 2 * sa.tau[l], n * 2 * sa.tau[l] * reff};

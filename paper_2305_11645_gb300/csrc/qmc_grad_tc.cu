@@ -1,22 +1,23 @@
-// Block gradients of the coarse levels on the tensor cores (split and bf16 tiers): the adjoint of
-// Algorithm 2's block products, dA_e = sum_r X_{r,e}^T F_{r,e} over the level's distinct rows, with
-// F_e the root gradients folded onto the level (k_fold_tree).
+// Block gradients of the coarse levels above the fused ones on the tensor cores (split and bf16
+// tiers): the adjoint of Algorithm 2's block products, dA_e = sum_r X_{r,e}^T F_{r,e} over the
+// level's distinct rows, with F_e the root gradients folded onto the level (k_fold_grad_tc and
+// k_fold_tree).
 //
-// D[t][j] = sum_k F_e[k][t] (X_e[k][j] - xc): M = 128 columns t, N = 64 gradient columns j, K = the
-// level's rows over every shift, cut into splits of at most 4096 rows (a work unit = entry x j tile x
-// t tile x split).  One persistent CTA per SM, warp-specialised:
+// D[t][j] = sum_k F_e[k][t] (X_e[k][j] - xc): M = 128 columns t, N = 128 gradient columns j (an
+// entry has at most 128), K = the level's rows over every shift, cut into splits of at most 1024
+// rows (a work unit = entry x t tile x split).  One persistent CTA per SM, warp-specialised:
 //   warp 0      TMA producer: the raw FP32 chunk of F (32 rows k x 128 columns t, a 3-D box over
-//               (t, rows, shifts)) and of X (64 columns j x 32 rows k, from the point table) into a
-//               ring of raw stages;
-//   warp 1      allocates 256 tensor-memory columns (four 128 x 64 FP32 accumulators) and one thread
-//               issues each converted chunk's MMAs (M = 128, N = 64, K = 16) into accumulator
-//               chunk % 4, so that an FP32 accumulation chain in tensor memory is at most 1024 rows;
-//   warps 2-9   converters: split the raw chunk into bf16 pieces in the MMA's K-major, 64-byte-
-//               swizzled layout (F transposed to [t][k], X centred by xc, padding columns zero), and
-//               after a unit's last chunk read the four accumulators, sum them in a fixed order and
-//               store the unit's partial, which k_grad_reduce sums over the splits.
-// Every wait is bounded; a run-out sets the level kernels' error word and the CTA stops as in
-// k_level_tc (the MMA thread drains its commits before the tensor memory is released).
+//               (t, rows, shifts)) into a ring of raw stages;
+//   warp 2      TMA producer: the chunk's pre-split bf16 pieces of X (k_split_xt; 32 rows x 128
+//               columns, 64-byte swizzle, a 4-D box over (rows, j, shifts, pieces)) into its slot;
+//   warp 1      allocates the tensor memory (two accumulators, the slots' F^T pieces) and one
+//               thread issues every chunk's MMAs, with F^T read from tensor memory, into the
+//               accumulator of the unit's parity;
+//   warps 3-18  converters: split the chunk's F^T into bf16 pieces in tensor memory (lane = column
+//               t, two rows per 32-bit column); warps 3-10, one unit behind the MMAs, store the
+//               unit's accumulator as its partial, which k_grad_reduce sums over the splits.
+// Every wait is bounded; a run-out sets the error word (grad_error_word) and the roles stop as in
+// the other tensor-core kernels.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -34,20 +35,21 @@ using namespace tc;
 namespace {
 
 constexpr int GT_M = 128;                    // columns t per unit (MMA M)
-constexpr int GT_N = 64;                     // gradient columns j per unit (MMA N)
+constexpr int GT_N = 128;                    // gradient columns j per unit (MMA N)
 constexpr int GK = 32;                       // rows k per chunk
-constexpr int NACC = 4;
 constexpr int RS = 4;                        // raw stages
-constexpr int CS = 3;                        // converted stages
-constexpr uint32_t RAW_F = GK * GT_M * 4;    // [k][t] FP32, 16 KB
-constexpr uint32_t RAW_X = GT_N * GK * 4;    // [j][k] FP32, 8 KB
-constexpr uint32_t RAW_STAGE = RAW_F + RAW_X;
-constexpr uint32_t PF = GT_M * 64;           // one bf16 piece of F^T: 128 rows x 64 bytes
-constexpr uint32_t PX = GT_N * 64;           // one bf16 piece of X: 64 rows x 64 bytes
-constexpr int kThreads = 320;
+constexpr int CS = 4;                        // chunk slots
+constexpr uint32_t RAW = GK * GT_M * 4;      // [k][t] FP32, 16 KB
+constexpr uint32_t PX = GT_N * 64;           // one bf16 piece of X: 128 rows x 64 bytes
+constexpr int kConv = 16;
+constexpr int kThreads = 96 + 32 * kConv;
+// tensor memory: accumulators b = 0, 1 at columns 128 b; slot s's F^T piece p, K-step ks at
+// 256 + 16 (P s + p) + 8 ks
+constexpr uint32_t TM_SLOT0 = 256;
+static_assert(TM_SLOT0 + 16 * 3 * CS <= 512, "tensor-memory slots");
 
-template <int P> constexpr uint32_t cstage() { return P * (PF + PX); }
-template <int P> constexpr size_t grad_smem() { return 1024 + RS * RAW_STAGE + CS * cstage<P>() + 256; }
+template <int P> constexpr uint32_t slot_bytes() { return P * PX; }
+template <int P> constexpr size_t grad_smem() { return 1024 + RS * RAW + CS * slot_bytes<P>() + 256; }
 
 __device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
@@ -63,18 +65,41 @@ __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
         if (mbar_try(b, parity)) return true;
     return false;
 }
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
-                                            int c2) {
+__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
 }
+__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
+                                       int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar) : "memory");
+}
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
 
 struct UnitIdx {
-    int e, sp, j0, t0;
+    int e, sp, t0;
     long long kb, ke;
 };
 
+// unit u: entry e, then t tile fastest (concurrent CTAs share the entry's X chunks), then split
 __device__ __forceinline__ UnitIdx unit_of(const GradTcArgs& ga, long long u) {
     int e = 0;
     while (e + 1 < ga.n && u >= ga.unit0[e + 1]) ++e;
@@ -83,9 +108,7 @@ __device__ __forceinline__ UnitIdx unit_of(const GradTcArgs& ga, long long u) {
     UnitIdx ui;
     ui.e = e;
     ui.t0 = (int)(loc % ga.t_tiles) * GT_M;
-    const long long rest = loc / ga.t_tiles;
-    ui.sp = (int)(rest % en.split);
-    ui.j0 = (int)(rest / en.split) * GT_N;
+    ui.sp = (int)(loc / ga.t_tiles);
     ui.kb = (long long)ui.sp * en.kper;
     ui.ke = min((long long)ga.reff * en.n, ui.kb + en.kper);
     return ui;
@@ -93,18 +116,19 @@ __device__ __forceinline__ UnitIdx unit_of(const GradTcArgs& ga, long long u) {
 
 template <int P>
 __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__ GradTcArgs ga, float* __restrict__ part,
-                                                         int tau_pad, float xc) {
+                                                         int tau_pad) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = align_1k(smem_raw);
-    unsigned char* craw = smem;                                  // RS raw stages
-    unsigned char* cconv = smem + RS * RAW_STAGE;                // CS converted stages (1 KB aligned)
-    uint64_t* rfull = reinterpret_cast<uint64_t*>(cconv + CS * cstage<P>());
+    unsigned char* raw = smem;                                   // RS raw stages
+    unsigned char* slots = smem + RS * RAW;                      // CS X slots (1 KB aligned)
+    uint64_t* rfull = reinterpret_cast<uint64_t*>(slots + CS * slot_bytes<P>());
     uint64_t* rempty = rfull + RS;
-    uint64_t* cfull = rempty + RS;
-    uint64_t* cempty = cfull + CS;
-    uint64_t* tdone = cempty + CS;
-    uint64_t* tfree = tdone + 1;
-    uint64_t* drain = tfree + 1;
+    uint64_t* sfull = rempty + RS;
+    uint64_t* sempty = sfull + CS;
+    uint64_t* xfull = sempty + CS;
+    uint64_t* tdone = xfull + CS;                                // [2]
+    uint64_t* tfree = tdone + 2;                                 // [2]
+    uint64_t* drain = tfree + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -113,14 +137,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
             asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.fmap[e])) : "memory");
             asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.xmap[e])) : "memory");
         }
-        for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], 8); }
-        for (int s = 0; s < CS; ++s) { bar_init(&cfull[s], 8); bar_init(&cempty[s], 1); }
-        bar_init(tdone, 1);
-        bar_init(tfree, 8);
+        for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], kConv); }
+        for (int s = 0; s < CS; ++s) { bar_init(&sfull[s], kConv); bar_init(&sempty[s], 1); bar_init(&xfull[s], 1); }
+        for (int b = 0; b < 2; ++b) { bar_init(&tdone[b], 1); bar_init(&tfree[b], 8); }
         bar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NACC * GT_N);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), 512);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -128,134 +151,163 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
     bool ok = true;
 
     if (warp == 0) {
-        // ------------------------------------------------------------------ TMA producer
+        // ------------------------------------------------------------------ TMA producer of F
         if (lane == 0) {
-            long long it = 0;
+            long long itr = 0;
             for (long long u = blockIdx.x; u < ga.units && ok; u += gridDim.x) {
                 const UnitIdx ui = unit_of(ga, u);
-                const GradTcEntry& en = ga.ent[ui.e];
-                for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++it) {
-                    const int s = (int)(it % RS);
-                    if (!bar_wait(smem_u32(&rempty[s]), (uint32_t)(((it / RS) & 1) ^ 1))) { ok = false; break; }
-                    const uint32_t fb = smem_u32(&rfull[s]);
-                    bar_expect_tx(fb, RAW_STAGE);
-                    const int r = (int)(k0 / en.n), rho = (int)(k0 - (long long)r * en.n);
-                    unsigned char* st = craw + s * RAW_STAGE;
-                    // rows beyond the split's end (or the last shift) read as zero (out of range) or are
-                    // rows of the next split, whose F is multiplied by X rows that are zero-filled
-                    tma_load_3d(smem_u32(st), &ga.fmap[ui.e], fb, ui.t0, rho, r);
-                    tma_load_3d(smem_u32(st + RAW_F), &ga.xmap[ui.e], fb, rho, ui.j0, r);
+                const long long n = ga.ent[ui.e].n;
+                for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++itr) {
+                    const int rs = (int)(itr % RS);
+                    if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
+                    bar_expect_tx(smem_u32(&rfull[rs]), RAW);
+                    const int r = (int)(k0 / n), rho = (int)(k0 - (long long)r * n);
+                    tma_3d(smem_u32(raw + rs * RAW), &ga.fmap[ui.e], smem_u32(&rfull[rs]), ui.t0, rho, r);
+                }
+            }
+            if (!ok) {                                            // the copies still in flight land first
+                atomicOr(&g_grad_error, 1u);
+                for (long long k = itr - 1; k >= 0 && k >= itr - RS; --k)
+                    bar_wait(smem_u32(&rfull[k % RS]), (uint32_t)((k / RS) & 1));
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------------ TMA producer of X pieces
+        if (lane == 0) {
+            long long slot = 0;
+            for (long long u = blockIdx.x; u < ga.units && ok; u += gridDim.x) {
+                const UnitIdx ui = unit_of(ga, u);
+                const long long n = ga.ent[ui.e].n;
+                for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++slot) {
+                    const int cs = (int)(slot % CS);
+                    if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
+                    bar_expect_tx(smem_u32(&xfull[cs]), slot_bytes<P>());
+                    const int r = (int)(k0 / n), rho = (int)(k0 - (long long)r * n);
+                    tma_4d(smem_u32(slots + cs * slot_bytes<P>()), &ga.xmap[ui.e], smem_u32(&xfull[cs]), rho, 0, r, 0);
                 }
             }
             if (!ok) {
                 atomicOr(&g_grad_error, 1u);
-                for (long long k = it - 1; k >= 0 && k >= it - RS; --k)
-                    bar_wait(smem_u32(&rfull[k % RS]), (uint32_t)((k / RS) & 1));
+                for (long long k = slot - 1; k >= 0 && k >= slot - CS; --k)
+                    bar_wait(smem_u32(&xfull[k % CS]), (uint32_t)((k / CS) & 1));
             }
         }
     } else if (warp == 1) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(GT_N);
-            long long it = 0, n = 0;
-            for (long long u = blockIdx.x; u < ga.units && ok; u += gridDim.x, ++n) {
+            long long slot = 0, nu = 0;
+            for (long long u = blockIdx.x; u < ga.units && ok; u += gridDim.x, ++nu) {
                 const UnitIdx ui = unit_of(ga, u);
-                if (!bar_wait(smem_u32(tfree), (uint32_t)((n & 1) ^ 1))) { ok = false; break; }
+                const int b = (int)(nu & 1);
+                if (!bar_wait(smem_u32(&tfree[b]), (uint32_t)(((nu >> 1) & 1) ^ 1))) { ok = false; break; }
                 fence_after_sync();
-                int c = 0;
-                for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++it, ++c) {
-                    const int s = (int)(it % CS);
-                    if (!bar_wait(smem_u32(&cfull[s]), (uint32_t)((it / CS) & 1))) { ok = false; break; }
+                const uint32_t dst = tmem + (uint32_t)(b * GT_N);
+                bool fresh = true;
+                for (long long k0 = ui.kb; k0 < ui.ke && ok; k0 += GK, ++slot) {
+                    const int cs = (int)(slot % CS);
+                    if (!bar_wait(smem_u32(&sfull[cs]), (uint32_t)((slot / CS) & 1)) ||
+                        !bar_wait(smem_u32(&xfull[cs]), (uint32_t)((slot / CS) & 1))) { ok = false; break; }
                     fence_after_sync();
-                    const uint32_t fs = smem_u32(cconv + s * cstage<P>()), xs = fs + P * PF;
-                    bool fresh = c < NACC;
-                    for (int ks = 0; ks < 2; ++ks)
-                        issue_kstep<P, PF, PX>(tmem + (uint32_t)((c % NACC) * GT_N), smem_desc_sw64(fs + 32 * ks),
-                                               smem_desc_sw64(xs + 32 * ks), idesc, fresh);
-                    mma_commit(smem_u32(&cempty[s]));
+                    const uint32_t xs = smem_u32(slots + cs * slot_bytes<P>());
+                    const uint32_t ta = tmem + TM_SLOT0 + (uint32_t)(16 * P * cs);
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t bd = smem_desc_sw64(xs + 32 * ks);
+                        constexpr int NP = P == 3 ? 6 : 1;
+                        constexpr int pi[6] = {2, 1, 0, 1, 0, 0};
+                        constexpr int pj[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+                        for (int pq = 0; pq < NP; ++pq) {
+                            const int ia = P == 3 ? pi[pq] : 0, jb = P == 3 ? pj[pq] : 0;
+                            mma_bf16_ts(dst, ta + (uint32_t)(16 * ia + 8 * ks), desc_add(bd, jb * PX), idesc,
+                                        fresh ? 0u : 1u);
+                            fresh = false;
+                        }
+                    }
+                    mma_commit(smem_u32(&sempty[cs]));
                 }
-                if (ok) mma_commit(smem_u32(tdone));
+                if (ok) mma_commit(smem_u32(&tdone[b]));
             }
             if (!ok) atomicOr(&g_grad_error, 1u);
             mma_commit(smem_u32(drain));
             bar_wait(smem_u32(drain), 0);
         }
     } else {
-        // ------------------------------------------------------------------ converters and epilogue
-        const int ct = threadIdx.x - 64;                       // 0..255
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
-        long long itr = 0, itc = 0, n = 0;
-        for (long long u = blockIdx.x; u < ga.units && ok; u += gridDim.x, ++n) {
+        // ------------------------------------------------------------------ converters
+        // warp w: tensor-memory lanes 32 (w % 4) .. + 31 = columns t, rows 8h .. 8h+7 of every
+        // chunk, h = (w - 3) / 4; warps 3-10 store the partials, column half (w - 3) / 4
+        const int quarter = warp & 3, h = (warp - 3) >> 2;
+        const int tl = quarter * 32 + lane;
+        const bool drainer = warp < 11;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+        long long itr = 0, slot = 0;
+
+        // the partial of the CTA's nu-th unit u
+        auto store_unit = [&](long long u, long long nu) -> bool {
+            if (!drainer) return true;
             const UnitIdx ui = unit_of(ga, u);
             const GradTcEntry& en = ga.ent[ui.e];
-            const int nj = min(GT_N, en.tau - ui.j0);
-            for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++itr, ++itc) {
-                const int rs = (int)(itr % RS), cs = (int)(itc % CS);
-                if (!bar_wait(smem_u32(&rfull[rs]), (uint32_t)((itr / RS) & 1))) { ok = false; break; }
-                if (!bar_wait(smem_u32(&cempty[cs]), (uint32_t)(((itc / CS) & 1) ^ 1))) { ok = false; break; }
-                const float* rf = reinterpret_cast<const float*>(craw + rs * RAW_STAGE);
-                const float* rx = reinterpret_cast<const float*>(craw + rs * RAW_STAGE + RAW_F);
-                unsigned char* fs = cconv + cs * cstage<P>();
-                unsigned char* xs = fs + P * PF;
-                const long long nk = ui.ke - k0;               // valid rows of this chunk (may be < 32)
-                {   // F^T: row t = ct % 128, k = 16 (ct / 128) .. + 15
-                    const int t = ct & 127, h = ct >> 7;
-                    float v[16];
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int k = 16 * h + i;
-                        v[i] = k < nk ? rf[k * GT_M + t] : 0.0f;
-                    }
-                    store_group<P>(fs, PF, t, 2 * h, v);
-                    store_group<P>(fs, PF, t, 2 * h + 1, v + 8);
-                }
-                {   // X: row j = ct / 4, k = 8 (ct % 4) .. + 7 (the k group fastest, so that a quarter warp's
-                    // 16-byte loads span two rows), centred; padding rows j >= nj stay zero
-                    const int j = ct >> 2, q = ct & 3;
-                    const float4* xr = reinterpret_cast<const float4*>(rx + j * GK + 8 * q);
-                    const float4 a = xr[0], b = xr[1];
-                    const float d = j < nj ? xc : 0.0f;
-                    float v[8] = {a.x - d, a.y - d, a.z - d, a.w - d, b.x - d, b.y - d, b.z - d, b.w - d};
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        if (8 * q + i >= nk || j >= nj) v[i] = 0.0f;
-                    store_group<P>(xs, PX, j, q, v);
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                fence_before_sync();
-                __syncwarp();
-                if (lane == 0) {
-                    bar_arrive(smem_u32(&rempty[rs]));
-                    bar_arrive(smem_u32(&cfull[cs]));
-                }
-            }
-            if (!ok) break;
-            // the unit's partial: D[t][j] summed over the four accumulators in a fixed order
-            if (!bar_wait(smem_u32(tdone), (uint32_t)(n & 1))) { ok = false; break; }
+            const int b = (int)(nu & 1);
+            // (the tensor-memory loads below are warp-collective: the whole warp takes one branch)
+            if (!__all_sync(0xffffffffu, bar_wait(smem_u32(&tdone[b]), (uint32_t)((nu >> 1) & 1)))) return false;
             fence_after_sync();
-            const int chunks = (int)((ui.ke - ui.kb + GK - 1) / GK);
-            const int t = ui.t0 + quarter * 32 + lane;
-            float sum[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) sum[i] = 0.0f;
-            const uint32_t la = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
-            for (int a = 0; a < NACC && a < chunks; ++a) {
-                uint32_t d[32];
-                tmem_ld32(la + (uint32_t)(a * GT_N), d);
+            const int t = ui.t0 + tl;
+            float* pe = part + en.poff + (long long)ui.sp * en.tau * tau_pad + t;
+            for (int c = 0; c < 64; c += 8) {
+                const int j0 = h * 64 + c;
+                if (j0 >= en.tau) break;
+                uint32_t a[8];
+                tmem_ld8(lane_base + (uint32_t)(b * GT_N + j0), a);
                 tmem_wait_ld();
+                if (t < tau_pad) {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) sum[i] += __uint_as_float(d[i]);
+                    for (int x = 0; x < 8; ++x)
+                        if (j0 + x < en.tau) pe[(long long)(j0 + x) * tau_pad] = __uint_as_float(a[x]);
+                }
             }
             fence_before_sync();
             __syncwarp();
-            if (lane == 0) bar_arrive(smem_u32(tfree));
-            if (t < tau_pad) {
-                float* pe = part + en.poff + ((long long)ui.sp * en.tau + ui.j0 + half * 32) * tau_pad + t;
+            if (lane == 0) bar_arrive(smem_u32(&tfree[b]));
+            return true;
+        };
+
+        long long nu = 0, prev = -1;
+        for (long long u = blockIdx.x; u < ga.units && ok; u += gridDim.x, ++nu) {
+            const UnitIdx ui = unit_of(ga, u);
+            for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++itr, ++slot) {
+                const int rs = (int)(itr % RS), cs = (int)(slot % CS);
+                if (!bar_wait(smem_u32(&rfull[rs]), (uint32_t)((itr / RS) & 1))) { ok = false; break; }
+                float v[8];
+                const float* rf = reinterpret_cast<const float*>(raw + rs * RAW);
 #pragma unroll
-                for (int i = 0; i < 32; ++i)
-                    if (half * 32 + i < nj) pe[(long long)i * tau_pad] = sum[i];
+                for (int k = 0; k < 8; ++k) v[k] = rf[(8 * h + k) * GT_M + tl];
+                __syncwarp();
+                if (lane == 0) bar_arrive(smem_u32(&rempty[rs]));
+                if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
+                fence_after_sync();
+                uint32_t w[P][4];
+#pragma unroll
+                for (int x = 0; x < 4; ++x) {
+                    uint32_t pc[P];
+                    split_pair<P>(v[2 * x], v[2 * x + 1], pc);
+#pragma unroll
+                    for (int p = 0; p < P; ++p) w[p][x] = pc[p];
+                }
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    tmem_st4(lane_base + TM_SLOT0 + (uint32_t)(16 * (P * cs + p) + 4 * h), w[p]);
+                tmem_wait_st();
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) bar_arrive(smem_u32(&sfull[cs]));
             }
+            if (!ok) break;
+            if (prev >= 0 && !store_unit(prev, nu - 1)) { ok = false; break; }
+            prev = u;
         }
+        if (ok && prev >= 0 && !store_unit(prev, nu - 1)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
         if (!ok && lane == 0) atomicOr(&g_grad_error, 1u);
     }
 
@@ -263,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
     __syncthreads();
     if (warp == 1) {
         fence_after_sync();
-        tmem_dealloc(tmem, NACC * GT_N);
+        tmem_dealloc(tmem, 512);
     }
 }
 
@@ -279,22 +331,6 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// FP32 3-D tensor map, no swizzle: dims {d0, d1, d2}, strides (bytes) {s1, s2}, box {b0, b1, 1};
-// out-of-range elements read as zero
-cudaError_t map3(CUtensorMap* m, const void* base, long long d0, long long d1, long long d2, long long s1,
-                 long long s2, int b0, int b1) {
-    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
-    if (!fn) return cudaErrorNotSupported;
-    const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
-    const cuuint64_t strides[2] = {(cuuint64_t)s1, (cuuint64_t)s2};
-    const cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 }  // namespace
 
 cudaError_t grad_error_word(unsigned int* value, bool clear) {
@@ -304,13 +340,16 @@ cudaError_t grad_error_word(unsigned int* value, bool clear) {
     return cudaMemcpyToSymbol(g_grad_error, &zero, sizeof(unsigned int));
 }
 
-size_t grad_tc_smem(int pieces) { return pieces == 3 ? grad_smem<3>() : grad_smem<1>(); }
-
-cudaError_t launch_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
-                           const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch, const int* sel,
-                           int nsel, float* part, int reff, int pieces, float xc, cudaStream_t st) {
+// Tensor maps: F_e (FP32, dims t, rows, shifts; box 128 x 32 x 1, no swizzle) and the entry's
+// pre-split pieces (bf16, dims rows, j, shifts, pieces; box 32 x 128 x 1 x P, 64-byte swizzle);
+// elements outside the arrays (columns t >= tau_pad, j >= tau_e) read as zero.
+cudaError_t launch_grad_tc(const __nv_bfloat16* xp, const float* Froot, long long root_stride, const float* Fchain,
+                           long long chain_stride, int tau_pad, const Chain& ch, const int* sel, const long long* xoff,
+                           int nsel, float* part, int reff, int pieces, cudaStream_t st) {
     if (nsel == 0) return cudaSuccess;
-    if (nsel > kMaxGradTc) return cudaErrorInvalidValue;
+    if (nsel > kMaxGradTc || (pieces != 1 && pieces != 3)) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return cudaErrorNotSupported;
     GradTcArgs ga{};
     ga.n = nsel;
     ga.reff = reff;
@@ -324,16 +363,33 @@ cudaError_t launch_grad_tc(const float* tab, long long tab_stride, const float* 
         en.split = ch.split[e];
         en.kper = ch.kper[e];
         en.poff = ch.poff[e];
+        en.xoff = xoff[i];
+        if (en.tau > GT_N || en.n < GK || en.kper % GK != 0) return cudaErrorInvalidValue;
         ga.unit0[i] = units;
-        units += (long long)((en.tau + GT_N - 1) / GT_N) * en.split * ga.t_tiles;
+        units += (long long)en.split * ga.t_tiles;
         const float* Fb = (ch.fsel[e] ? Fchain : Froot) + ch.foff[e];
         const long long Fs = ch.fsel[e] ? chain_stride : root_stride;
-        // F: (t, rows rho < n_e, shifts), row stride tau_pad floats, shift stride Fs floats
-        cudaError_t err = map3(&ga.fmap[i], Fb, tau_pad, en.n, reff, 4LL * tau_pad, 4LL * Fs, GT_M, GK);
-        if (err != cudaSuccess) return err;
-        // X: (rows rho < n_e, columns j of the entry, shifts): the entry's table columns
-        err = map3(&ga.xmap[i], tab + ch.tab[e], en.n, en.tau, reff, 4LL * en.n, 4LL * tab_stride, GK, GT_N);
-        if (err != cudaSuccess) return err;
+        {
+            const cuuint64_t dims[3] = {(cuuint64_t)tau_pad, (cuuint64_t)en.n, (cuuint64_t)reff};
+            const cuuint64_t strides[2] = {(cuuint64_t)tau_pad * 4, (cuuint64_t)Fs * 4};
+            const cuuint32_t box[3] = {GT_M, GK, 1};
+            const cuuint32_t estr[3] = {1, 1, 1};
+            if (fn(&ga.fmap[i], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(Fb), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+        }
+        {
+            const cuuint64_t n = (cuuint64_t)en.n;
+            const cuuint64_t dims[4] = {n, (cuuint64_t)en.tau, (cuuint64_t)reff, (cuuint64_t)pieces};
+            const cuuint64_t strides[3] = {n * 2, n * 2 * en.tau, n * 2 * en.tau * reff};
+            const cuuint32_t box[4] = {GK, GT_N, 1, (cuuint32_t)pieces};
+            const cuuint32_t estr[4] = {1, 1, 1, 1};
+            if (fn(&ga.xmap[i], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(xp + en.xoff), dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+        }
     }
     ga.unit0[nsel] = units;
     ga.units = units;
@@ -344,11 +400,11 @@ cudaError_t launch_grad_tc(const float* tab, long long tab_stride, const float* 
     if (pieces == 3) {
         cudaError_t e = cudaFuncSetAttribute(k_grad_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem<3>());
         if (e != cudaSuccess) return e;
-        k_grad_tc<3><<<grid, kThreads, grad_smem<3>(), st>>>(ga, part, tau_pad, xc);
+        k_grad_tc<3><<<grid, kThreads, grad_smem<3>(), st>>>(ga, part, tau_pad);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_grad_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem<1>());
         if (e != cudaSuccess) return e;
-        k_grad_tc<1><<<grid, kThreads, grad_smem<1>(), st>>>(ga, part, tau_pad, xc);
+        k_grad_tc<1><<<grid, kThreads, grad_smem<1>(), st>>>(ga, part, tau_pad);
     }
     return cudaGetLastError();
 }

@@ -243,19 +243,20 @@ namespace qmc {
 constexpr int kMaxGradTc = 24;
 struct GradTcEntry {
     long long n, kper, poff;
+    long long xoff;                  // bf16 element offset of the entry's pre-split table columns
     int tau, split;
 };
 struct GradTcArgs {
-    CUtensorMap fmap[kMaxGradTc];
-    CUtensorMap xmap[kMaxGradTc];
+    CUtensorMap fmap[kMaxGradTc];    // F_e: (t, rows, shifts) FP32
+    CUtensorMap xmap[kMaxGradTc];    // the entry's pieces: (rows, j, shifts, pieces) bf16
     GradTcEntry ent[kMaxGradTc];
     long long unit0[kMaxGradTc + 1];
     long long units;
     int n, reff, t_tiles;
 };
-cudaError_t launch_grad_tc(const float* tab, long long tab_stride, const float* Froot, long long root_stride,
-                           const float* Fchain, long long chain_stride, int tau_pad, const Chain& ch, const int* sel,
-                           int nsel, float* part, int reff, int pieces, float xc, cudaStream_t st);
+cudaError_t launch_grad_tc(const __nv_bfloat16* xp, const float* Froot, long long root_stride, const float* Fchain,
+                           long long chain_stride, int tau_pad, const Chain& ch, const int* sel, const long long* xoff,
+                           int nsel, float* part, int reff, int pieces, cudaStream_t st);
 cudaError_t grad_error_word(unsigned int* value, bool clear);
 
 // ---------------------------------------------------------------------------------------------
@@ -263,13 +264,14 @@ cudaError_t grad_error_word(unsigned int* value, bool clear);
 // (qmc_foldgrad_tc.cu), with the levels' table columns pre-split into bf16 pieces (k_split_xt).
 // ---------------------------------------------------------------------------------------------
 constexpr int kMaxFoldLv = 3;
+constexpr int kMaxSplitXt = kMaxGradTc + kMaxFoldLv;
 struct SplitXtArgs {
-    int n;                           // levels with columns among the fused ones
-    int lev[kMaxFoldLv];             // d of each (level JF + d)
-    int logn[kMaxFoldLv], tau[kMaxFoldLv];
-    long long tab[kMaxFoldLv];       // table offset of the level's first column
-    long long off[kMaxFoldLv];       // bf16 element offset of its pieces in the split buffer
-    long long blk0[kMaxFoldLv + 1];  // prefix sums of tau x n / 8 threads
+    int n;                           // table column ranges pre-split (fused levels, then k_grad_tc entries)
+    int lev[kMaxSplitXt];            // d of a fused level JF + d, or -1
+    int logn[kMaxSplitXt], tau[kMaxSplitXt];
+    long long tab[kMaxSplitXt];      // table offset of the range's first column
+    long long off[kMaxSplitXt];      // bf16 element offset of its pieces in the split buffer
+    long long blk0[kMaxSplitXt + 1]; // prefix sums of tau x n / 8 threads
 };
 struct FoldGradArgs {
     CUtensorMap fmap;                // F_JF: (t, rows, shifts)
