@@ -46,6 +46,8 @@ TRAFFIC_BYTES = {
     # profiles/net20_top_kernels.md: the 2-shift capture of the 16-shift contract workload, scaled by
     # 16/2 (each shift's data are separate, so the DRAM bytes grow with the shifts)
     ("net20", "k_fine_bwd_s4"): (594.804992e6 + 502.806272e6) * 8,
+    ("net20", "k_fold_grad_tc"): (576.029696e6 + 60.704e6) * 8,
+    ("net20", "k_grad_tc"): (165.881088e6 + 3.455744e6) * 8,
 }
 
 
@@ -247,13 +249,46 @@ def fine_work(p, name):
     return outs * per, outs * mufu_h
 
 
-def coarse_mma_flops(p, pieces):
+def coarse_mma_flops(p, pieces, levels=None):
     """MMA flops of the coarse block products of one step (forward X_I A_I or adjoint X_I^T F_I, the
     same contraction sizes): 2 n_I tau tau_I per coarse level I (n_I = 2^(m-I) distinct rows), for
-    every shift, times the piece products (6 in the split tier, 1 in the bf16 tier)."""
+    every shift, times the piece products (6 in the split tier, 1 in the bf16 tier); every coarse
+    level, or the given ones."""
     jf, tau_I, chain = band_of(p)
     np_ = 6 if pieces == 3 else 1
-    return sum(2.0 * 2 ** (p.m - I) * p.tau * tau_I[I] for I in chain) * p.R_eff * np_
+    lv = chain if levels is None else levels
+    return sum(2.0 * 2 ** (p.m - I) * p.tau * tau_I[I] for I in lv) * p.R_eff * np_
+
+
+def coarse_kernel_levels(p, name):
+    """The coarse levels whose block products a tensor-core kernel computes, as the library's
+    planner assigns them: k_level_tc every coarse level (forward); k_fold_grad_tc the L <= 3 lowest
+    ones (adjoint, one entry of at most 128 columns each, 128 columns in all, at least 32 distinct
+    rows left at level JF+L, which lies within six folds of JF and below m); k_grad_tc the other
+    levels with at least 32 distinct rows whose folded gradient is materialised; k_coarse_grad_tc the
+    rest."""
+    jf, tau_I, chain = band_of(p)
+    if name == "k_level_tc":
+        return chain
+    below = [I for I in chain if I < p.m and I - jf <= 6]
+    i_mat = max(below) if below else jf
+    fused = []
+    for L in (3, 2, 1):
+        if jf + L > i_mat or p.m - (jf + L) < 5:
+            continue
+        lv = [I for I in range(jf, jf + L)]
+        cols = sum((tau_I[I] + 15) // 16 * 16 for I in lv)
+        if any(tau_I[I] > 128 for I in lv) or cols > 128 or cols == 0:
+            continue
+        fused = [I for I in lv if tau_I[I] > 0]
+        break
+    rest = [I for I in chain if I not in fused]
+    tma = [I for I in rest if p.m - I >= 5 and I <= i_mat]
+    if name == "k_fold_grad_tc":
+        return fused
+    if name == "k_grad_tc":
+        return tma
+    return [I for I in rest if I not in tma]
 
 
 def tensor_roofline(flops, seconds, peak_tflops):
@@ -290,7 +325,7 @@ def roofline_of(p, prec, name, ms_per_step, launches_per_step, clk, mp, peak_src
     algorithmic work per step is the sum over the same launches)."""
     sec = ms_per_step / 1e3
     if name.endswith("_tc"):
-        fl = coarse_mma_flops(p, 3 if prec == "split" else 1)
+        fl = coarse_mma_flops(p, 3 if prec == "split" else 1, coarse_kernel_levels(p, name))
         r = tensor_roofline(fl, sec, mp["bf16_tflops_sustained"])
         r["peak_source"] = (f"{peak_src} dense bf16 sustained peak (MEASURED_PEAKS.json bf16_tflops_sustained: "
                             f"the kernel runs inside a long step)")
