@@ -13,8 +13,8 @@
 //   warp 1      allocates the tensor memory (two accumulators, the slots' F^T pieces) and one
 //               thread issues every chunk's MMAs, with F^T read from tensor memory, into the
 //               accumulator of the unit's parity;
-//   warps 3-18  converters: split the chunk's F^T into bf16 pieces in tensor memory (lane = column
-//               t, two rows per 32-bit column); warps 3-10, one unit behind the MMAs, store the
+//   warps 3-10  converters: split the chunk's F^T into bf16 pieces in tensor memory (lane = column
+//               t, two rows per 32-bit column); one unit behind the MMAs, they store the
 //               unit's accumulator as its partial, which k_grad_reduce sums over the splits.
 // Every wait is bounded; a run-out sets the error word (grad_error_word) and the roles stop as in
 // the other tensor-core kernels.
@@ -41,7 +41,8 @@ constexpr int RS = 4;                        // raw stages
 constexpr int CS = 4;                        // chunk slots
 constexpr uint32_t RAW = GK * GT_M * 4;      // [k][t] FP32, 16 KB
 constexpr uint32_t PX = GT_N * 64;           // one bf16 piece of X: 128 rows x 64 bytes
-constexpr int kConv = 16;
+constexpr int kConv = 8;                     // converter warps, two per tensor-memory lane quarter
+constexpr int kRPT = GK * 4 / kConv;         // rows of a chunk per converter thread
 constexpr int kThreads = 96 + 32 * kConv;
 // tensor memory: accumulators b = 0, 1 at columns 128 b; slot s's F^T piece p, K-step ks at
 // 256 + 16 (P s + p) + 8 ks
@@ -83,9 +84,10 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
         :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&r)[4]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
+                    "r"(r[7]) : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
@@ -235,8 +237,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
         }
     } else {
         // ------------------------------------------------------------------ converters
-        // warp w: tensor-memory lanes 32 (w % 4) .. + 31 = columns t, rows 8h .. 8h+7 of every
-        // chunk, h = (w - 3) / 4; warps 3-10 store the partials, column half (w - 3) / 4
+        // warp w: tensor-memory lanes 32 (w % 4) .. + 31 = columns t, rows 16h .. 16h+15 of every
+        // chunk, h = (w - 3) / 4, which is also the column half of the partial it stores
         const int quarter = warp & 3, h = (warp - 3) >> 2;
         const int tl = quarter * 32 + lane;
         const bool drainer = warp < 11;
@@ -278,17 +280,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
             for (long long k0 = ui.kb; k0 < ui.ke; k0 += GK, ++itr, ++slot) {
                 const int rs = (int)(itr % RS), cs = (int)(slot % CS);
                 if (!bar_wait(smem_u32(&rfull[rs]), (uint32_t)((itr / RS) & 1))) { ok = false; break; }
-                float v[8];
+                float v[kRPT];
                 const float* rf = reinterpret_cast<const float*>(raw + rs * RAW);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) v[k] = rf[(8 * h + k) * GT_M + tl];
+                for (int k = 0; k < kRPT; ++k) v[k] = rf[(kRPT * h + k) * GT_M + tl];
                 __syncwarp();
                 if (lane == 0) bar_arrive(smem_u32(&rempty[rs]));
                 if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
                 fence_after_sync();
-                uint32_t w[P][4];
+                uint32_t w[P][kRPT / 2];
 #pragma unroll
-                for (int x = 0; x < 4; ++x) {
+                for (int x = 0; x < kRPT / 2; ++x) {
                     uint32_t pc[P];
                     split_pair<P>(v[2 * x], v[2 * x + 1], pc);
 #pragma unroll
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
                 }
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    tmem_st4(lane_base + TM_SLOT0 + (uint32_t)(16 * (P * cs + p) + 4 * h), w[p]);
+                    tmem_st8(lane_base + TM_SLOT0 + (uint32_t)(16 * (P * cs + p) + (kRPT / 2) * h), w[p]);
                 tmem_wait_st();
                 fence_before_sync();
                 __syncwarp();
