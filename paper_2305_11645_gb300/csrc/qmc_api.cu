@@ -400,9 +400,23 @@ void plan_levels(Plan& P) {
         group[ng++] = k;
         i += k;
     }
+    // The last pass writes S and is bound by that write; the lowest levels share it while their
+    // block products, taken over all n_root rows there, stay well inside the write time (at most
+    // 128 columns in the split tier's six piece products, 512 in the bf16 tier), at least two.
+    // Each level moved in saves its partial sum's write and read-back.
+    int k_last = 0;
+    {
+        const int kmax = P.tc_pieces == 3 ? 128 : 512;
+        int cols = 0;
+        for (int j = nl - 1; j >= i && k_last < kMaxPassSeg; --j) {
+            if (k_last >= 2 && cols + P.lev_tau[levs[j]] > kmax) break;
+            cols += P.lev_tau[levs[j]];
+            ++k_last;
+        }
+    }
     while (i < nl) {
         const int rest = nl - i;
-        const int k = rest == 2 ? 2 : 1;
+        const int k = rest <= k_last ? rest : 1;
         group[ng++] = k;
         i += k;
     }
