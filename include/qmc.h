@@ -99,8 +99,13 @@ typedef int qmc_status;
 /*
  * A reduced QMC rule (the point set).
  *  kind       QMC_LATTICE, QMC_DIGITAL_NET, QMC_REDUCED_MC or QMC_POLY_LATTICE.
- *  b          base; the GPU path supports b = 2 only (others: QMC_ERR_UNSUPPORTED).
- *  m          N = b^m points, 1 <= m <= 30.
+ *  b          base, a prime.  b = 2: every kind (the tensor-core block products and the binary fine band
+ *             of Sec. 3.2).  b > 2: QMC_LATTICE and QMC_REDUCED_MC (Sec. 1.3 lattices with N = b^m, and
+ *             Sec. 5; the other kinds return QMC_ERR_UNSUPPORTED), computed by the generic top-down
+ *             levels on the CUDA cores in every tier (FP32 in the tensor-core tiers).  A b > 2 lattice
+ *             point is u / b^q_j in double (u = k z_j mod b^q_j), shifted as {x + D 2^-32}, then
+ *             transformed; z_j must lie in U_{b^q_j} (not divisible by b, < b^q_j).
+ *  m          N = b^m points, 1 <= m <= 30 (b = 2), b^m <= 2^31 (b > 2; larger: QMC_ERR_UNSUPPORTED).
  *  s          dimension (rows of A), 1 <= s <= 65536.
  *  w          HOST uint32[s]: reduction indices, nondecreasing (Sec. 1.3: 0 = w_1 <= w_2 <= ...;
  *             any nondecreasing sequence is accepted).  Values >= m make column j constant.
