@@ -248,8 +248,11 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
 /*
  * Schedule autotuning (the paper has no counterpart: it picks launch shapes of this library's
  * kernels, never the arithmetic).  For a problem shape (m, the column counts per weight level,
- * tau, shifts, precision, integrand) the planner uses a cached schedule of the fine band
- * (forward: columns per CTA; adjoint: roots per CTA) when one exists, else its cost models.
+ * tau, shifts, precision, integrand) the planner uses a cached schedule when one exists, else its
+ * cost models: the fine band's forward columns per CTA and adjoint roots per CTA, and in the
+ * tensor-core tiers the coarse forward's path (1 level passes, 2 block products and chain sum)
+ * and the coarse adjoint's path (1 one fold of the root gradients and the cp.async block-gradient
+ * kernel, 2 the fused fold-gradient kernel and the TMA block-gradient kernel).
  *  qmc_autotune  times, with CUDA events on `stream`, the forward and the forward + backward of this
  *                problem under the cost model's schedule and a ladder of others, and caches the
  *                fastest.  d_est (R_eff + 1 doubles), d_gradA (s x tau) and d_ws are scratch: the
@@ -257,12 +260,20 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
  *                a tuned schedule can change qmc_workspace_size, so size workspaces after tuning.
  *                Synchronises the stream (not callable during stream capture).  *n_timed (may be
  *                NULL) receives the number of candidates timed.
+ *  qmc_tune_set  caches the given schedule for this problem's shape (host only, no CUDA call):
+ *                fwd_qpg (columns per CTA / 4, <= 128), bwd_rpc (roots per CTA), coarse (0-2) and
+ *                bwd_path (0-2); 0 keeps the cost model's choice of that value.  QMC_ERR_INVALID_ARG
+ *                for values out of range or an invalid rule; QMC_ERR_UNSUPPORTED for rules in a base
+ *                b > 2, whose plan takes no schedule.
  *  qmc_tune_save / qmc_tune_load   write / merge the cache as a text file, one line per shape
- *                ("key|columns per CTA / 4|roots per CTA"; 0 keeps the cost model's choice).
+ *                ("key|columns per CTA / 4|roots per CTA|coarse path|adjoint path"; the last two
+ *                are optional when loading; 0 keeps the cost model's choice).
  *  qmc_tune_clear  empties the cache.
  */
 qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, const qmc_integrand* f, int precision,
                         double* d_est, void* d_gradA, void* d_ws, size_t ws_bytes, void* stream, uint32_t* n_timed);
+qmc_status qmc_tune_set(const qmc_rule* rule, uint32_t tau, const qmc_integrand* f, int precision, int fwd_qpg,
+                        int bwd_rpc, int coarse, int bwd_path);
 qmc_status qmc_tune_save(const char* path);
 qmc_status qmc_tune_load(const char* path, uint32_t* n_entries);
 qmc_status qmc_tune_clear(void);

@@ -20,7 +20,8 @@ QMC_BWD_REUSE_FORWARD = 1
 EXPORTS = ["qmc_version", "qmc_last_error", "qmc_validate_rule", "qmc_workspace_size", "qmc_gen_points",
            "qmc_reduced_matmul", "qmc_integrate", "qmc_integrate_backward", "qmc_integrate_noalloc",
            "qmc_trace_enable", "qmc_trace_collect", "qmc_trace_entry", "qmc_device_status",
-           "qmc_selftest_wait_timeout", "qmc_autotune", "qmc_tune_save", "qmc_tune_load", "qmc_tune_clear"]
+           "qmc_selftest_wait_timeout", "qmc_autotune", "qmc_tune_set", "qmc_tune_save", "qmc_tune_load",
+           "qmc_tune_clear"]
 PRECISIONS = {"fp64": QMC_FP64, "fp32": QMC_FP32, "split": QMC_SPLIT, "bf16": QMC_BF16}
 
 
@@ -74,6 +75,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                               c_void_p, c_void_p]
         lib.qmc_autotune.argtypes = [POINTER(QmcRule), c_void_p, c_uint32, POINTER(QmcIntegrand), c_int, c_void_p,
                                      c_void_p, c_void_p, c_size_t, c_void_p, POINTER(c_uint32)]
+        lib.qmc_tune_set.argtypes = [POINTER(QmcRule), c_uint32, POINTER(QmcIntegrand), c_int, c_int, c_int, c_int,
+                                     c_int]
         lib.qmc_tune_save.argtypes = [ctypes.c_char_p]
         lib.qmc_tune_load.argtypes = [ctypes.c_char_p, POINTER(c_uint32)]
         lib.qmc_tune_clear.argtypes = []

@@ -285,6 +285,19 @@ def autotune(rule: Rule, A: torch.Tensor, f: Integrand, precision: Optional[str]
     return int(n.value)
 
 
+def tune_set(rule: Rule, tau: int, f: Integrand, precision: str, fwd_qpg: int = 0, bwd_rpc: int = 0,
+             coarse: int = 0, bwd_path: int = 0) -> None:
+    """Cache a schedule for this problem's shape (host only): forward columns per CTA / 4, adjoint
+    roots per CTA, the coarse forward's path (1 level passes, 2 block products) and the coarse
+    adjoint's path (1 one fold and the cp.async gradient kernel, 2 the fused fold-gradient and TMA
+    gradient kernels); 0 keeps the cost model's choice of that value."""
+    if precision not in L.PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(L.PRECISIONS)} (got {precision!r})")
+    r = rule.struct()
+    L.check(L.load().qmc_tune_set(ctypes.byref(r), int(tau), ctypes.byref(f.struct()), L.PRECISIONS[precision],
+                                  int(fwd_qpg), int(bwd_rpc), int(coarse), int(bwd_path)))
+
+
 def tune_save(path: str) -> None:
     L.check(L.load().qmc_tune_save(str(path).encode()))
 

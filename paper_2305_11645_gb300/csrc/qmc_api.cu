@@ -296,6 +296,8 @@ struct TuneVal {
     int fwd_qpg = 0;
     int bwd_rpc = 0;
     int coarse = 0;                // tensor-core tiers: 1 level passes, 2 block products + chain sum
+    int bwd = 0;                   // tensor-core adjoint: 1 one fold + k_coarse_grad_tc, 2 the fused
+                                   // fold-gradient and TMA gradient kernels (0: by size)
 };
 struct TuneCache {
     std::mutex mu;
@@ -329,6 +331,7 @@ struct Plan {
     // and the rest on k_coarse_grad_tc (chl, its tiles bwd_tiles_l)
     int gsel[kMaxGradTc] = {}, ngsel = 0, bwd_tiles_l = 0;
     long long gxoff[kMaxGradTc] = {};   // their pre-split table columns in the split buffer
+    bool bwd_tma = false;               // large enough for the fused and TMA gradient kernels
     Chain chl{};
     // tensor-core backward of the lowest fg_L coarse levels in one pass over the root gradients
     // (k_fold_grad_tc, entries fg_ent[d] of level JF + d or -1), the folds above JF + fg_L from
@@ -892,7 +895,12 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         // at least 32 rows, at most 128 accumulator columns in all
         P.fg_L = 0;
         for (int d = 0; d < kMaxFoldLv; ++d) P.fg_ent[d] = -1;
-        if (P.tc_pieces != 0 && !P.nonper && precision != QMC_FP64) {
+        // the fused kernel and k_grad_tc pay their fixed costs (tensor-memory set-up, two producer
+        // warps, the pre-split pass) once the root gradients reach 2^24 elements; below that one
+        // fold kernel and k_coarse_grad_tc take every level
+        P.bwd_tma = P.tc_pieces != 0 && (P.tuned.bwd == 2 ||
+                                         (P.tuned.bwd == 0 && (long long)P.reff * n_root * P.tau_pad >= (1LL << 24)));
+        if (P.bwd_tma && !P.nonper && precision != QMC_FP64) {
             for (int L = kMaxFoldLv; L >= 1 && P.fg_L == 0; --L) {
                 if (P.JF + L > I_mat || P.m - (P.JF + L) < 5) continue;
                 int ent[kMaxFoldLv] = {-1, -1, -1}, ncols = 0, good = 1, any = 0;
@@ -993,7 +1001,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         int btl = 0;
         for (int e = 0; e < P.chb.count; ++e) {
             if (fused(e)) continue;
-            const bool tma = tc && P.chb.flog[e] == 0 && P.m - P.chb.lev[e] >= 5 && P.chb.tab[e] % 4 == 0 &&
+            const bool tma = P.bwd_tma && P.chb.flog[e] == 0 && P.m - P.chb.lev[e] >= 5 && P.chb.tab[e] % 4 == 0 &&
                              P.chb.tau[e] <= 128 &&
                              P.chb.foff[e] % 4 == 0 && P.tau_pad % 4 == 0 && P.tab_stride % 4 == 0 &&
                              P.chb.kper[e] % 32 == 0 && P.ngsel < kMaxGradTc;
@@ -1777,7 +1785,7 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
         float bt = -1.0f;
         for (int qpg : ladder) {
             if (qpg < 1 || qpg > quads || qpg > 128) continue;
-            TuneVal tv{qpg, 0, 0};
+            TuneVal tv{qpg, 0, 0, 0};
             float ms = 0.0f;
             st = time_it(tv, false, &ms);
             if (st != QMC_OK) break;
@@ -1787,7 +1795,7 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
         // schedule just chosen
         if (base.tc_pieces && base.chf.count && st == QMC_OK) {
             float b1 = -1.0f, b2 = -1.0f;
-            TuneVal t1{bestv.fwd_qpg, 0, 1}, t2{bestv.fwd_qpg, 0, 2};
+            TuneVal t1{bestv.fwd_qpg, 0, 1, 0}, t2{bestv.fwd_qpg, 0, 2, 0};
             st = time_it(t1, false, &b1);
             if (st == QMC_OK) st = time_it(t2, false, &b2);
             if (st == QMC_OK && b1 > 0.0f && b2 > 0.0f) bestv.coarse = b1 <= b2 ? 1 : 2;
@@ -1801,11 +1809,21 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
             long long rpc = (long long)(base.roots_per_cta * fc + 0.5);
             rpc = std::max(2LL, (rpc + 1) / 2 * 2);
             if (rpc > n_root + 1) continue;
-            TuneVal tv{bestv.fwd_qpg, (int)rpc, bestv.coarse};
+            TuneVal tv{bestv.fwd_qpg, (int)rpc, bestv.coarse, 0};
             float ms = 0.0f;
             st = time_it(tv, true, &ms);
             if (st != QMC_OK) break;
             if (ms > 0.0f && (bb < 0.0f || ms < bb)) { bb = ms; bestv.bwd_rpc = (int)rpc; }
+        }
+        // tensor-core tiers: the coarse adjoint's path, with the schedules just chosen
+        if (base.tc_pieces && base.chb.count && st == QMC_OK) {
+            float b1 = -1.0f, b2 = -1.0f;
+            TuneVal t1 = bestv, t2 = bestv;
+            t1.bwd = 1;
+            t2.bwd = 2;
+            st = time_it(t1, true, &b1);
+            if (st == QMC_OK) st = time_it(t2, true, &b2);
+            if (st == QMC_OK && b1 > 0.0f && b2 > 0.0f) bestv.bwd = b1 <= b2 ? 1 : 2;
         }
     }
     cudaEventDestroy(e0);
@@ -1817,6 +1835,24 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
         tc.m[base.tune_key] = bestv;
     }
     if (n_timed) *n_timed = timed;
+    return QMC_OK;
+}
+
+qmc_status qmc_tune_set(const qmc_rule* rule, uint32_t tau, const qmc_integrand* f, int precision, int fwd_qpg,
+                        int bwd_rpc, int coarse, int bwd_path) {
+    if (!rule || !f) return fail(QMC_ERR_INVALID_ARG, "rule and f must be non-NULL");
+    if (fwd_qpg < 0 || fwd_qpg > 128 || bwd_rpc < 0 || coarse < 0 || coarse > 2 || bwd_path < 0 || bwd_path > 2)
+        return fail(QMC_ERR_INVALID_ARG, "schedule values out of range");
+    qmc_status st = validate(rule);
+    if (st != QMC_OK) return st;
+    Plan P;
+    t_hint = nullptr;
+    st = make_plan(QMC_OP_INTEGRATE_BWD, rule, tau, f, precision, nullptr, P);
+    if (st != QMC_OK) return st;
+    if (P.tune_key.empty()) return fail(QMC_ERR_UNSUPPORTED, "this rule's plan takes no schedule");
+    TuneCache& tc = tune_cache();
+    std::lock_guard<std::mutex> g(tc.mu);
+    tc.m[P.tune_key] = TuneVal{fwd_qpg, bwd_rpc, coarse, bwd_path};
     return QMC_OK;
 }
 
@@ -1834,9 +1870,10 @@ qmc_status qmc_tune_save(const char* path) {
     FILE* fh = fopen(path, "w");
     if (!fh) return fail(QMC_ERR_INVALID_ARG, "cannot write %s", path);
     fprintf(fh, "# qmc_gb300 schedule cache: shape key | forward column quads per CTA | adjoint roots per CTA | "
-                "coarse path (1 level passes, 2 block products)\n");
+                "coarse path (1 level passes, 2 block products) | adjoint path (1 one fold, 2 fused)\n");
     for (auto& kv : tc.m)
-        fprintf(fh, "%s|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc, kv.second.coarse);
+        fprintf(fh, "%s|%d|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc, kv.second.coarse,
+                kv.second.bwd);
     fclose(fh);
     return QMC_OK;
 }
@@ -1856,14 +1893,16 @@ qmc_status qmc_tune_load(const char* path, uint32_t* n_entries) {
         if (line[0] == '#' || line[0] == '\n') continue;
         char* a = strchr(line, '|');
         char* b = a ? strchr(a + 1, '|') : nullptr;
-        char* c = b ? strchr(b + 1, '|') : nullptr;          // (the coarse path is optional)
-        int q = 0, r = 0, cp = 0;
+        char* c = b ? strchr(b + 1, '|') : nullptr;          // (the coarse and adjoint paths are optional)
+        char* d = c ? strchr(c + 1, '|') : nullptr;
+        int q = 0, r = 0, cp = 0, bp = 0;
         if (!a || !b || sscanf(a + 1, "%d", &q) != 1 || sscanf(b + 1, "%d", &r) != 1 || q < 0 || r < 0 || q > 128 ||
-            (c && (sscanf(c + 1, "%d", &cp) != 1 || cp < 0 || cp > 2))) {
+            (c && (sscanf(c + 1, "%d", &cp) != 1 || cp < 0 || cp > 2)) ||
+            (d && (sscanf(d + 1, "%d", &bp) != 1 || bp < 0 || bp > 2))) {
             st = fail(QMC_ERR_INVALID_ARG, "%s:%d: not a schedule entry", path, lineno);
             break;
         }
-        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp};
+        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp, bp};
         ++n;
     }
     fclose(fh);

@@ -346,7 +346,7 @@ def test_schedule_cache_file_and_planner(lib, tmp_path):
     assert st == L.QMC_OK and tuned != base                  # (the cost model takes 16 groups of 4 columns)
     out = tmp_path / "saved.txt"
     assert lib.qmc_tune_save(str(out).encode()) == L.QMC_OK
-    assert f"{key}|16|6|0" in out.read_text().splitlines()      # (a missing coarse-path field reads as 0)
+    assert f"{key}|16|6|0|0" in out.read_text().splitlines()    # (missing path fields read as 0)
     assert lib.qmc_tune_clear() == L.QMC_OK
     assert ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)[1] == base
     # the tensor-core tiers' coarse path is part of the schedule: this shape's coarse partial sums
@@ -366,6 +366,32 @@ def test_schedule_cache_file_and_planner(lib, tmp_path):
     assert lib.qmc_tune_load(str(bad).encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
     assert lib.qmc_tune_load(str(tmp_path / "missing.txt").encode(), ctypes.byref(n)) == L.QMC_ERR_INVALID_ARG
     assert lib.qmc_tune_clear() == L.QMC_OK
+
+
+def test_schedule_set_adjoint_path(lib, tmp_path):
+    """qmc_tune_set caches a schedule for a problem's shape without a GPU: forcing the fused
+    fold-gradient and TMA gradient kernels on a small split-tier problem (the model takes the one-fold
+    path below 2^24 root-gradient elements) adds their pre-split table buffer to the backward's
+    workspace; the entry is what qmc_tune_save writes; values out of range are rejected."""
+    p = I.c5(m=14, s=256, R=2)
+    r = Rule.from_problem(p)
+    f = Integrand(I.F_LOGSUMEXP, ())
+    tau = int(p.A.shape[1])
+    assert lib.qmc_tune_clear() == L.QMC_OK
+    st, compact = ws_size(lib, L.QMC_OP_INTEGRATE_BWD, r, tau, f, L.QMC_SPLIT)
+    assert st == L.QMC_OK
+    assert lib.qmc_tune_set(ctypes.byref(r.struct()), tau, ctypes.byref(f.struct()), L.QMC_SPLIT, 0, 0, 0, 2) == L.QMC_OK
+    st, fused = ws_size(lib, L.QMC_OP_INTEGRATE_BWD, r, tau, f, L.QMC_SPLIT)
+    assert st == L.QMC_OK and fused > compact
+    out = tmp_path / "saved.txt"
+    assert lib.qmc_tune_save(str(out).encode()) == L.QMC_OK
+    key = tune_key(p, L.QMC_SPLIT, I.F_LOGSUMEXP, tau)
+    assert f"{key}|0|0|0|2" in out.read_text().splitlines()
+    for bad in ((129, 0, 0, 0), (0, -1, 0, 0), (0, 0, 3, 0), (0, 0, 0, 3)):
+        assert lib.qmc_tune_set(ctypes.byref(r.struct()), tau, ctypes.byref(f.struct()), L.QMC_SPLIT,
+                                *bad) == L.QMC_ERR_INVALID_ARG
+    assert lib.qmc_tune_clear() == L.QMC_OK
+    assert ws_size(lib, L.QMC_OP_INTEGRATE_BWD, r, tau, f, L.QMC_SPLIT)[1] == compact
 
 
 def test_base_b_rules_checked_on_the_host(lib):

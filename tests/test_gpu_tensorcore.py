@@ -122,6 +122,34 @@ def test_integrate_and_backward(precision, fk, shape):
 
 
 @pytest.mark.parametrize("precision", ["split", "bf16"])
+@pytest.mark.parametrize("shape", [0, 4, 5, 6, FOLD_SHAPE])
+@pytest.mark.parametrize("path", [1, 2])
+def test_backward_adjoint_paths(precision, shape, path):
+    """Both coarse adjoints of the tensor-core tiers, pinned by the schedule: 1 (one fold of the root
+    gradients, the cp.async block-gradient kernel; the model's choice for these small shapes) and 2
+    (the fused fold-gradient kernel on the lowest coarse levels, then the TMA block-gradient kernel,
+    the rest on the first path).  The shapes cover one, two and three fused levels, fused levels
+    without columns, entries cut at 128 columns and levels folded on the fly."""
+    kind = I.LATTICE if shape % 2 == 0 else I.DIGITAL_NET
+    p = shaped_problem(TC_SHAPES[shape], kind, 900 + 11 * shape + path, R=3, dtype=np.float32,
+                       f_kind=I.F_LOGSUMEXP)
+    rule = api.Rule.from_problem(p)
+    A = torch.from_numpy(p.A).to(DEV)
+    f = integrand(p)
+    api.tune_clear()
+    try:
+        api.tune_set(rule, A.shape[1], f, precision, bwd_path=path)
+        up = torch.tensor([0.7], dtype=torch.float64, device=DEV)
+        G = api.integrate_backward(rule, A, f, up, precision=precision)[0].cpu().numpy()
+        assert np.all(np.isfinite(G))
+        assert norm_rel(G, 0.7 * O.grad(p)) <= (2e-5 if precision == "split" else 2e-2)
+        G2 = api.integrate_backward(rule, A, f, up, precision=precision)[0].cpu().numpy()
+        assert np.array_equal(G, G2)
+    finally:
+        api.tune_clear()
+
+
+@pytest.mark.parametrize("precision", ["split", "bf16"])
 @pytest.mark.parametrize("shape", [0, FOLD_SHAPE])
 @pytest.mark.parametrize("kind", [I.REDUCED_MC, I.POLY_LATTICE])
 def test_mc_and_poly_lattice_tiers(precision, shape, kind):
