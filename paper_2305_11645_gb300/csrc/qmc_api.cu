@@ -332,6 +332,7 @@ struct Plan {
     int gsel[kMaxGradTc] = {}, ngsel = 0, bwd_tiles_l = 0;
     long long gxoff[kMaxGradTc] = {};   // their pre-split table columns in the split buffer
     bool bwd_tma = false;               // large enough for the fused and TMA gradient kernels
+    bool froot_tiled = false;           // root gradients in 128-column tiles (the fused kernel reads them)
     Chain chl{};
     // tensor-core backward of the lowest fg_L coarse levels in one pass over the root gradients
     // (k_fold_grad_tc, entries fg_ent[d] of level JF + d or -1), the folds above JF + fg_L from
@@ -385,6 +386,9 @@ size_t gen_words(const Plan& P) {
 // (which writes the root values S): that pass then multiplies the second level on twice its
 // distinct rows, but the level's partial sum (half the size of S) is never written or read.
 // Falls back to the block products and chain sum when a limit below is exceeded.
+// columns of a root-gradient row as stored: tau_pad, or whole 128-column tiles when tiled
+long long root_cols(const Plan& P) { return P.froot_tiled ? (long long)(P.tau_pad + 127) / 128 * 128 : P.tau_pad; }
+
 void plan_levels(Plan& P) {
     LevelPlan& L = P.lvp;
     L = LevelPlan{};
@@ -917,6 +921,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
                 for (int d = 0; d < L; ++d) P.fg_ent[d] = ent[d];
             }
         }
+        P.froot_tiled = P.fg_L > 0 && P.fine_s4;
         if (P.fg_L) {
             const int L = P.fg_L;
             if (!P.fold.want[L]) {          // F_{JF+L} is the fused kernel's output
@@ -1042,6 +1047,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             g.cpt = fg_cpt;
             g.group = std::max(1, 32 >> L);            // level JF's chains: 32 2^L rows per item, <= 1024
             g.fout_stride = P.Fchain_per_shift;
+            g.froot_tiled = P.froot_tiled ? 1 : 0;
             int acc = 0;
             for (int d = 0; d < L; ++d) {
                 const int e = P.fg_ent[d];
@@ -1127,7 +1133,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     if (op == QMC_OP_INTEGRATE_BWD) {
         size_t o = u0;
         P.off_F = o;
-        o = align256(o + E * (size_t)P.reff * (size_t)n_root * P.tau_pad);
+        o = align256(o + E * (size_t)P.reff * (size_t)n_root * root_cols(P));
         P.off_Fchain = o;
         o = align256(o + E * (size_t)P.reff * (size_t)std::max(P.Fchain_per_shift, 1LL));
         P.off_gradpart = o;
@@ -1392,12 +1398,14 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
         ldA = P.need_pad ? P.tau_pad : P.tau;
     }
     const long long n_root = 1LL << (P.m - P.JF);
-    const long long root_stride = n_root * P.tau_pad;
+    const long long root_stride = n_root * root_cols(P);
     T* Froot = reinterpret_cast<T*>(ws + P.off_F);
     FineArgs<T> a = fine_args<T>(P, ws, A, ldA, f);
     a.rowsave = reinterpret_cast<const T*>(ws + P.off_rowsave);
     a.upstream = upstream;
     a.Froot = Froot;
+    a.froot_tiled = P.froot_tiled ? 1 : 0;
+    a.froot_stride = root_stride;
     a.gradpart = reinterpret_cast<T*>(ws + P.off_gradpart);
     a.roots_per_cta = P.roots_per_cta;
     a.groups = P.groups;

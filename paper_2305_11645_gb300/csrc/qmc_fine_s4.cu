@@ -354,7 +354,11 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
     // root values S_4 (layout [t/4][rho][4]) of the thread's columns, and its root-gradient column
     const float* Sb = (a.S && active) ? a.S + (long long)r * a.S_stride + ((long long)(t >> 2) << a.logn_root) * 4 + (t & 3)
                                       : nullptr;
-    float* Fb = a.Froot + (long long)r * n_root * a.tau_pad + t;
+    // root-gradient rows: row-major [rho][tau_pad], or 128-column tiles [t / 128][rho][128] (then a
+    // 32-row TMA box of one tile is contiguous for the fused fold-gradient kernel)
+    float* Fb = a.froot_tiled ? a.Froot + (long long)r * a.froot_stride + (((long long)(t >> 7) << a.logn_root) << 7) + (t & 127)
+                              : a.Froot + (long long)r * n_root * a.tau_pad + t;
+    const long long frow = a.froot_tiled ? 128 : a.tau_pad;
     auto lds2 = [&](long long rho) -> float2 {
         return Sb ? __ldg(reinterpret_cast<const float2*>(Sb + rho * 4)) : make_float2(0.0f, 0.0f);
     };
@@ -444,7 +448,7 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
             }
             if (active) {
                 // columns at or beyond tau carry no gradient
-                *reinterpret_cast<float2*>(Fb + rho * a.tau_pad) =
+                *reinterpret_cast<float2*>(Fb + rho * frow) =
                     make_float2(t < a.tau ? Fr.x : 0.0f, t + 1 < a.tau ? Fr.y : 0.0f);
             }
         }

@@ -230,8 +230,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
                     const int rs = (int)(itr % RS);
                     if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
                     bar_expect_tx(smem_u32(&rfull[rs]), RAW);
-                    tma_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
-                           rho0 + q * (int)n_out, r);
+                    if (ga.froot_tiled)
+                        tma_4d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), 0, rho0 + q * (int)n_out,
+                               cw.tt, r);
+                    else
+                        tma_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
+                               rho0 + q * (int)n_out, r);
                 }
             }
             if (!ok) {                                            // the copies still in flight land first
@@ -459,7 +463,17 @@ cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, lon
                                 const __nv_bfloat16* xp, const SplitXtArgs& sa, int reff, int pieces, cudaStream_t st) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
-    {
+    if (ga.froot_tiled) {
+        // [r][t / 128][rows][128]: dims (128 columns, rows, column tiles, shifts)
+        const cuuint64_t dims[4] = {FG_M, (cuuint64_t)n_root, (cuuint64_t)ga.t_tiles, (cuuint64_t)reff};
+        const cuuint64_t strides[3] = {FG_M * 4, (cuuint64_t)n_root * FG_M * 4, (cuuint64_t)root_stride * 4};
+        const cuuint32_t box[4] = {FG_M, FG_K, 1, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        if (fn(&ga.fmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(Froot), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    } else {
         const cuuint64_t dims[3] = {(cuuint64_t)ga.tau_pad, (cuuint64_t)n_root, (cuuint64_t)reff};
         const cuuint64_t strides[2] = {(cuuint64_t)ga.tau_pad * 4, (cuuint64_t)root_stride * 4};
         const cuuint32_t box[3] = {FG_M, FG_K, 1};

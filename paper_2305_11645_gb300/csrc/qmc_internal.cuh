@@ -287,6 +287,7 @@ struct FoldGradArgs {
     int nt;                          // columns of one accumulator set
     int log_out;                     // log2 n_out
     int tau_pad, cpt, t_tiles, group;
+    int froot_tiled;                 // F_JF in 128-column tiles, [r][t / 128][rows][128]
 };
 cudaError_t launch_split_xt(const float* tab, long long tab_stride, const SplitXtArgs& sa, int reff, int pieces,
                             __nv_bfloat16* xp, float xc, cudaStream_t st);
@@ -408,7 +409,10 @@ template <class T> struct FineArgs {
     const T* rowsave;        // per row: {g'(u_k) gfac/(R_eff N), log2 e * u_k} from the forward finalisation
     const double* upstream;
     double tau_d, K_d;
-    T* Froot;                                  // [r][n_root][tau_pad]
+    T* Froot;                                  // [r][n_root][tau_pad], or with froot_tiled
+                                               // [r][t / 128][n_root][128] (froot_stride per shift)
+    int froot_tiled;
+    long long froot_stride;
     T* gradpart;                               // [r][group][KF][tau_pad]
     int roots_per_cta, groups, kf_actual;
     int fkind;
