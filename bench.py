@@ -45,7 +45,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
 TRAFFIC_BYTES = {
     # profiles/net20_top_kernels.md: the 2-shift capture of the 16-shift contract workload, scaled by
     # 16/2 (each shift's data are separate, so the DRAM bytes grow with the shifts)
-    ("net20", "k_fine_bwd_s4"): (594.804992e6 + 502.806272e6) * 8,
+    ("net20", "k_fine_bwd_s4"): (596.494592e6 + 503.741184e6) * 8,
+    ("net20", "k_fine_fwd_s4"): (602.550528e6 + 16.719616e6) * 8,
     ("net20", "k_fold_grad_tc"): (576.02432e6 + 60.26112e6) * 8,
     ("net20", "k_grad_tc"): (166.872576e6 + 3.574784e6) * 8,
 }
