@@ -69,55 +69,7 @@ __host__ __device__ constexpr size_t fg_smem(int P, int ntot) {
     return 1024 + RS * RAW + CS * slot_bytes(P, ntot) + (size_t)ntot * 128 * 4 + 256;
 }
 
-__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
-        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[4]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]) : "memory");
-}
-__device__ __forceinline__ void tmem_st(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
-                    "r"(r[7]) : "memory");
-}
 
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint32_t b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
-}
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
-    for (long long it = 0; it < kWaitLimit; ++it)
-        if (mbar_try(b, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
-                                       int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar) : "memory");
-}
-// 8 consecutive FP32 accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 
 // the CTA's column tile, split index and item range
@@ -203,9 +155,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
     const long long n_out = 1LL << ga.log_out;
     const long long ngroups = (cw.i1 - cw.i0 + ga.group - 1) / ga.group;
     if (warp == 0 && lane == 0) {
-        asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.fmap)) : "memory");
+        tma_prefetch(&ga.fmap);
         for (int d = 0; d < L; ++d)
-            if (ga.nd[d]) asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.xmap[d])) : "memory");
+            if (ga.nd[d]) tma_prefetch(&ga.xmap[d]);
         for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], kConv); }
         for (int s = 0; s < CS; ++s) { bar_init(&sfull[s], kConv); bar_init(&sempty[s], 1); bar_init(&xfull[s], 1); }
         for (int b = 0; b < 2; ++b) { bar_init(&tdone[b], 1); bar_init(&tfree[b], 8); }
@@ -231,10 +183,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
                     if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
                     bar_expect_tx(smem_u32(&rfull[rs]), RAW);
                     if (ga.froot_tiled)
-                        tma_4d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), 0, rho0 + q * (int)n_out,
+                        tma_load_4d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), 0, rho0 + q * (int)n_out,
                                cw.tt, r);
                     else
-                        tma_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
+                        tma_load_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
                                rho0 + q * (int)n_out, r);
                 }
             }
@@ -261,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
                         if (!ga.nd[d]) continue;
                         const int row = rho0 + (q & ((1 << (L - d)) - 1)) * (int)n_out;
                         for (int p = 0; p < P; ++p)
-                            tma_4d(xs + (uint32_t)((p * ntot + ga.acc[d]) * 64), &ga.xmap[d], fb, row, 0, r, p);
+                            tma_load_4d(xs + (uint32_t)((p * ntot + ga.acc[d]) * 64), &ga.xmap[d], fb, row, 0, r, p);
                     }
                 }
             }

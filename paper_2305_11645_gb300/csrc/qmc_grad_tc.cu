@@ -52,49 +52,6 @@ static_assert(TM_SLOT0 + 16 * 3 * CS <= 512, "tensor-memory slots");
 template <int P> constexpr uint32_t slot_bytes() { return P * PX; }
 template <int P> constexpr size_t grad_smem() { return 1024 + RS * RAW + CS * slot_bytes<P>() + 256; }
 
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint32_t b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
-}
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
-    for (long long it = 0; it < kWaitLimit; ++it)
-        if (mbar_try(b, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1, int c2,
-                                       int c3) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
-        :: "r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-                 :: "r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]),
-                    "r"(r[7]) : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-}
 
 struct UnitIdx {
     int e, sp, t0;
@@ -136,8 +93,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0 && lane == 0) {
         for (int e = 0; e < ga.n; ++e) {
-            asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.fmap[e])) : "memory");
-            asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(&ga.xmap[e])) : "memory");
+            tma_prefetch(&ga.fmap[e]);
+            tma_prefetch(&ga.xmap[e]);
         }
         for (int s = 0; s < RS; ++s) { bar_init(&rfull[s], 1); bar_init(&rempty[s], kConv); }
         for (int s = 0; s < CS; ++s) { bar_init(&sfull[s], kConv); bar_init(&sempty[s], 1); bar_init(&xfull[s], 1); }
@@ -164,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
                     if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
                     bar_expect_tx(smem_u32(&rfull[rs]), RAW);
                     const int r = (int)(k0 / n), rho = (int)(k0 - (long long)r * n);
-                    tma_3d(smem_u32(raw + rs * RAW), &ga.fmap[ui.e], smem_u32(&rfull[rs]), ui.t0, rho, r);
+                    tma_load_3d(smem_u32(raw + rs * RAW), &ga.fmap[ui.e], smem_u32(&rfull[rs]), ui.t0, rho, r);
                 }
             }
             if (!ok) {                                            // the copies still in flight land first
@@ -185,7 +142,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
                     if (!bar_wait(smem_u32(&sempty[cs]), (uint32_t)(((slot / CS) & 1) ^ 1))) { ok = false; break; }
                     bar_expect_tx(smem_u32(&xfull[cs]), slot_bytes<P>());
                     const int r = (int)(k0 / n), rho = (int)(k0 - (long long)r * n);
-                    tma_4d(smem_u32(slots + cs * slot_bytes<P>()), &ga.xmap[ui.e], smem_u32(&xfull[cs]), rho, 0, r, 0);
+                    tma_load_4d(smem_u32(slots + cs * slot_bytes<P>()), &ga.xmap[ui.e], smem_u32(&xfull[cs]), rho, 0, r, 0);
                 }
             }
             if (!ok) {
@@ -298,7 +255,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_grad_tc(const __grid_constant__
                 }
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    tmem_st8(lane_base + TM_SLOT0 + (uint32_t)(16 * (P * cs + p) + (kRPT / 2) * h), w[p]);
+                    tmem_st(lane_base + TM_SLOT0 + (uint32_t)(16 * (P * cs + p) + (kRPT / 2) * h), w[p]);
                 tmem_wait_st();
                 fence_before_sync();
                 __syncwarp();

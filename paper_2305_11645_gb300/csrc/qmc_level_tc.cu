@@ -61,38 +61,6 @@ template <int P> constexpr size_t level_smem() {
     return 1024 + (size_t)stages<P>() * stage_bytes<P>() + 256;
 }
 
-// ------------------------------------------------------------------------------------------
-// TMA and mbarrier helpers
-// ------------------------------------------------------------------------------------------
-__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(b), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint32_t b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(b) : "memory");
-}
-// bounded wait for the completion of the phase with the given parity
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity) {
-    for (long long it = 0; it < kWaitLimit; ++it)
-        if (mbar_try(b, parity)) return true;
-    return false;
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1,
-                                            int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void tma_prefetch(const CUtensorMap* map) {
-    asm volatile("prefetch.tensormap [%0];" :: "l"(reinterpret_cast<uint64_t>(map)) : "memory");
-}
 
 // ------------------------------------------------------------------------------------------
 // k_split_x: the coarse levels' point-table entries as bf16 pieces.  Thread (row, g) of block
