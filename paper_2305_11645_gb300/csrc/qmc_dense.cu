@@ -8,8 +8,9 @@
 //                  and fixed-order block sums of f for the mean (eq. (2)).
 //                  The last block to finish forms Q_r = N^-1 sum_k f and the
 //                  mean over shifts.
-//  k_fold_tree     the root gradients folded level by level onto the distinct
-//                  rows of every coarse level.
+//  k_fold_tree     the root gradients (or, after the fused adjoint, the fold it
+//                  wrote) folded level by level onto the distinct rows of every
+//                  coarse level.
 //  k_chain_sum     S_JF[rho] = sum_e B_e[rho mod n_e]: the root values of the
 //                  fine band (Algorithm 2's tiling of the coarse levels).
 //  k_coarse_grad   dA_e = sum_r X_{r,e}^T F_{r,e}, with F_e[rho] = sum_q

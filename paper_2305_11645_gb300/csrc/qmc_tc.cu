@@ -1,7 +1,11 @@
 // Tensor-core block products for the split and bf16 tiers: the coarse block products
 // B_e = X_e A_e of Algorithm 2 (X~_I A~_I on the b^(m-I) distinct rows of weight block I)
 // and the block gradients dA_e = X_e^T F_e of the adjoint, on tcgen05.mma (kind::f16,
-// bf16 operands, FP32 accumulation in tensor memory).
+// bf16 operands, FP32 accumulation in tensor memory).  These compact kernels serve the
+// problems below the level passes' and the fused adjoint's size thresholds, and the
+// adjoint's levels that the TMA kernels do not take (fewer than 32 distinct rows, or
+// folded from a materialised level on the fly); large problems run qmc_level_tc.cu,
+// qmc_foldgrad_tc.cu and qmc_grad_tc.cu.
 //
 // Split tier.  Every FP32 operand v is written exactly as three bf16 pieces
 //     v = v0 + v1 + v2,   v0 = bf16(v) (nearest), v1 = the top 8 bits of v - v0,
