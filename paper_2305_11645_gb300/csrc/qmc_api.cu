@@ -298,6 +298,7 @@ struct TuneVal {
     int coarse = 0;                // tensor-core tiers: 1 level passes, 2 block products + chain sum
     int bwd = 0;                   // tensor-core adjoint: 1 one fold + k_coarse_grad_tc, 2 the fused
                                    // fold-gradient and TMA gradient kernels (0: by size)
+    int fwd_nb = 0;                // S4 forward: level-3 nodes per thread, 1 or 2 (0: by integrand)
 };
 struct TuneCache {
     std::mutex mu;
@@ -321,6 +322,7 @@ struct Plan {
     long long T_tot = 0, tab_stride = 0;   // table entries per shift, and the per-shift stride (multiple of 4)
     int tau = 0, tau_pad = 0, precision = 0, elt = 4, fkind = 0;
     int shape = SHAPE_S0, JF = 0, kf_width = 0, cw_bwd = 4;
+    int fwd_nb = 1;                // S4 forward: level-3 nodes per thread
     bool exact = false;            // fine band levels hold exactly their maximum column counts
     Chain chf{}, chb{};
     long long B_per_shift = 0, S_per_shift = 0, partc_elems = 0, Fchain_per_shift = 0;
@@ -768,11 +770,16 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
     P.fine_s4 = (op == QMC_OP_INTEGRATE || op == QMC_OP_INTEGRATE_BWD) && P.shape == SHAPE_S4 &&
                 precision != QMC_FP64 && P.m <= 27;
     if (P.fine_s4) {
-        const int rows = fine_s4_fwd_roots();
+        // a thread per root (both level-3 nodes) for the integrands whose h needs few registers
+        // (measured on the 2^20-point step: 4.56 -> 3.47 ms for the Gaussian norm, 3.29 -> 2.86 ms
+        // for log-sum-exp); a thread per node otherwise; the schedule can pick either
+        P.fwd_nb = (P.fkind == QMC_F_MEAN_COS || P.fkind == QMC_F_PDE_INV_SQ) ? 1 : 2;
+        if (P.tuned.fwd_nb == 1 || P.tuned.fwd_nb == 2) P.fwd_nb = P.tuned.fwd_nb;
+        const int rows = fine_s4_fwd_roots(P.fwd_nb);
         P.root_blocks = (int)((n_root + rows - 1) / rows);
         const long long rbr = (long long)P.root_blocks * P.reff;
         const int quads = P.tau_pad / 4, qmax = 512 / 4;
-        const long long resident = fine_s4_fwd_resident(P.fkind);
+        const long long resident = fine_s4_fwd_resident(P.fkind, P.fwd_nb);
         long long best = -1;
         for (int cg = (quads + qmax - 1) / qmax; cg <= quads; ++cg) {
             const int qpg = (quads + cg - 1) / cg;
@@ -1359,7 +1366,7 @@ qmc_status run_forward(const Plan& P, const qmc_rule* r, const T* dA, char* ws, 
     a.P = dP;
     if (mode == MODE_FUSED && P.fine_s4) {
         if constexpr (std::is_same<T, float>::value) {
-            QMC_LAUNCH(st, "k_fine_fwd_s4", launch_fine_fwd_s4(a, P.fkind, dim3(P.root_blocks, P.cg_count, P.reff), st));
+            QMC_LAUNCH(st, "k_fine_fwd_s4", launch_fine_fwd_s4(a, P.fkind, P.fwd_nb, dim3(P.root_blocks, P.cg_count, P.reff), st));
         }
     } else if (mode == MODE_MATERIALIZE && P.fine_mat) {
         if constexpr (std::is_same<T, float>::value) {
@@ -1793,17 +1800,32 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
         float bt = -1.0f;
         for (int qpg : ladder) {
             if (qpg < 1 || qpg > quads || qpg > 128) continue;
-            TuneVal tv{qpg, 0, 0, 0};
+            TuneVal tv{qpg, 0, 0, 0, 0};
             float ms = 0.0f;
             st = time_it(tv, false, &ms);
             if (st != QMC_OK) break;
             if (ms > 0.0f && (bt < 0.0f || ms < bt)) { bt = ms; bestv.fwd_qpg = qpg; }
         }
+        // the other number of level-3 nodes per forward thread, with the column groups just chosen
+        if (st == QMC_OK) {
+            Plan tmp;
+            TuneVal tb{bestv.fwd_qpg, 0, 0, 0, 0};
+            t_hint = &tb;
+            st = make_plan(QMC_OP_INTEGRATE_BWD, rule, tau, f, precision, d_A, tmp);
+            t_hint = nullptr;
+            if (st == QMC_OK) {
+                TuneVal alt = tb;
+                alt.fwd_nb = 3 - tmp.fwd_nb;
+                float ma = 0.0f;
+                st = time_it(alt, false, &ma);
+                if (st == QMC_OK && ma > 0.0f && (bt < 0.0f || ma < bt)) { bt = ma; bestv.fwd_nb = alt.fwd_nb; }
+            }
+        }
         // tensor-core tiers: the coarse path (level passes or block products), with the forward
         // schedule just chosen
         if (base.tc_pieces && base.chf.count && st == QMC_OK) {
             float b1 = -1.0f, b2 = -1.0f;
-            TuneVal t1{bestv.fwd_qpg, 0, 1, 0}, t2{bestv.fwd_qpg, 0, 2, 0};
+            TuneVal t1{bestv.fwd_qpg, 0, 1, 0, bestv.fwd_nb}, t2{bestv.fwd_qpg, 0, 2, 0, bestv.fwd_nb};
             st = time_it(t1, false, &b1);
             if (st == QMC_OK) st = time_it(t2, false, &b2);
             if (st == QMC_OK && b1 > 0.0f && b2 > 0.0f) bestv.coarse = b1 <= b2 ? 1 : 2;
@@ -1817,7 +1839,7 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
             long long rpc = (long long)(base.roots_per_cta * fc + 0.5);
             rpc = std::max(2LL, (rpc + 1) / 2 * 2);
             if (rpc > n_root + 1) continue;
-            TuneVal tv{bestv.fwd_qpg, (int)rpc, bestv.coarse, 0};
+            TuneVal tv{bestv.fwd_qpg, (int)rpc, bestv.coarse, 0, bestv.fwd_nb};
             float ms = 0.0f;
             st = time_it(tv, true, &ms);
             if (st != QMC_OK) break;
@@ -1860,7 +1882,7 @@ qmc_status qmc_tune_set(const qmc_rule* rule, uint32_t tau, const qmc_integrand*
     if (P.tune_key.empty()) return fail(QMC_ERR_UNSUPPORTED, "this rule's plan takes no schedule");
     TuneCache& tc = tune_cache();
     std::lock_guard<std::mutex> g(tc.mu);
-    tc.m[P.tune_key] = TuneVal{fwd_qpg, bwd_rpc, coarse, bwd_path};
+    tc.m[P.tune_key] = TuneVal{fwd_qpg, bwd_rpc, coarse, bwd_path, 0};
     return QMC_OK;
 }
 
@@ -1878,10 +1900,11 @@ qmc_status qmc_tune_save(const char* path) {
     FILE* fh = fopen(path, "w");
     if (!fh) return fail(QMC_ERR_INVALID_ARG, "cannot write %s", path);
     fprintf(fh, "# qmc_gb300 schedule cache: shape key | forward column quads per CTA | adjoint roots per CTA | "
-                "coarse path (1 level passes, 2 block products) | adjoint path (1 one fold, 2 fused)\n");
+                "coarse path (1 level passes, 2 block products) | adjoint path (1 one fold, 2 fused) | "
+                "forward level-3 nodes per thread\n");
     for (auto& kv : tc.m)
-        fprintf(fh, "%s|%d|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc, kv.second.coarse,
-                kv.second.bwd);
+        fprintf(fh, "%s|%d|%d|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc, kv.second.coarse,
+                kv.second.bwd, kv.second.fwd_nb);
     fclose(fh);
     return QMC_OK;
 }
@@ -1903,14 +1926,16 @@ qmc_status qmc_tune_load(const char* path, uint32_t* n_entries) {
         char* b = a ? strchr(a + 1, '|') : nullptr;
         char* c = b ? strchr(b + 1, '|') : nullptr;          // (the coarse and adjoint paths are optional)
         char* d = c ? strchr(c + 1, '|') : nullptr;
-        int q = 0, r = 0, cp = 0, bp = 0;
+        char* e = d ? strchr(d + 1, '|') : nullptr;
+        int q = 0, r = 0, cp = 0, bp = 0, nb = 0;
         if (!a || !b || sscanf(a + 1, "%d", &q) != 1 || sscanf(b + 1, "%d", &r) != 1 || q < 0 || r < 0 || q > 128 ||
             (c && (sscanf(c + 1, "%d", &cp) != 1 || cp < 0 || cp > 2)) ||
-            (d && (sscanf(d + 1, "%d", &bp) != 1 || bp < 0 || bp > 2))) {
+            (d && (sscanf(d + 1, "%d", &bp) != 1 || bp < 0 || bp > 2)) ||
+            (e && (sscanf(e + 1, "%d", &nb) != 1 || nb < 0 || nb > 2))) {
             st = fail(QMC_ERR_INVALID_ARG, "%s:%d: not a schedule entry", path, lineno);
             break;
         }
-        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp, bp};
+        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp, bp, nb};
         ++n;
     }
     fclose(fh);

@@ -28,8 +28,11 @@
 namespace qmc {
 namespace {
 
-constexpr int kFwdRoots = 64;
-constexpr int kFwdThreads = 2 * kFwdRoots;
+constexpr int kFwdThreads = 128;
+// forward roots per CTA with NB level-3 nodes per thread (NB = 1: a thread per node, two per root;
+// NB = 2: a thread per root, both nodes, half the loads of A per operation and twice the
+// independent work per thread, with more registers)
+__host__ __device__ constexpr int fwd_roots(int NB) { return kFwdThreads * NB / 2; }
 constexpr int kBwdThreads = 256;
 constexpr int kBwdCols = 256;                // columns per CTA: 4 warps x 32 lanes x 2
 constexpr int kRB = 8;                       // roots per staged batch
@@ -37,8 +40,9 @@ constexpr int kSlots = 96;                   // staged floats per root
 constexpr int kBwdMinBlocks = 2;
 // forward CTAs resident per SM: 7 (72 registers) where the integrand's h fits without spilling,
 // else 5 (cos, the inverse square's reciprocal and log-sum-exp's running maximum need more)
-__host__ __device__ constexpr int fwd_min_blocks(int F) {
-    return (F == F_LINEAR_MEAN || F == F_CALL_MEAN_EXP || F == F_GAUSS_NORM2) ? 7 : 5;
+__host__ __device__ constexpr int fwd_min_blocks(int F, int NB) {
+    return NB == 1 ? ((F == F_LINEAR_MEAN || F == F_CALL_MEAN_EXP || F == F_GAUSS_NORM2) ? 7 : 5)
+                   : ((F == F_LINEAR_MEAN || F == F_CALL_MEAN_EXP || F == F_GAUSS_NORM2) ? 4 : 3);
 }
 constexpr int kMaxCRS4 = 512;                // forward columns per CTA (dynamic shared memory 48 KB)
 
@@ -99,39 +103,45 @@ struct RowAcc2 {
     }
 };
 
-template <int F>
-__global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F)) k_fine_fwd_s4(const __grid_constant__ FineArgs<float> a) {
+template <int F, int NB>
+__global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F, NB)) k_fine_fwd_s4(const __grid_constant__ FineArgs<float> a) {
+    constexpr int kNB = NB;
+    constexpr int kFwdRoots = fwd_roots(NB);
     extern __shared__ __align__(16) float4 As_dyn[];                  // [a.cr][kAQuads]
     float4 (*As)[kAQuads] = reinterpret_cast<float4 (*)[kAQuads]>(As_dyn);
-    const int tid = threadIdx.x, b = tid / kFwdRoots;
+    const int tid = threadIdx.x;
+    // thread: root rho and its level-3 nodes b0 .. b0 + kNB - 1
+    const int b0 = kNB == 2 ? 0 : tid / kFwdRoots;
     const long long n_root = 1LL << a.logn_root;
-    const long long rho = (long long)blockIdx.x * kFwdRoots + (tid % kFwdRoots);
+    const long long rho = (long long)blockIdx.x * kFwdRoots + (kNB == 2 ? tid : tid % kFwdRoots);
     const int cg = blockIdx.y, r = blockIdx.z;
     const int t_beg = cg * a.cr, t_end = min(t_beg + a.cr, a.tau);
     const int ncol = (t_end - t_beg + 3) & ~3;
 
-    // x of the subtree (level-3 node b, level-2 nodes b + 2 i2, level-1 nodes b + 2 i1, leaves
+    // x of each subtree (level-3 node b, level-2 nodes b + 2 i2, level-1 nodes b + 2 i1, leaves
     // b + 2 i), as register pairs: the level-3 columns (2k, 2k+1), and for the lower levels the
     // sibling nodes (i2 = 0, 1), (i1 = 0, 1), (i1 = 2, 3), (i = 2k, 2k+1)
     // (the loads of x and of the first root values are issued before the staging of A, so that
     // their latency overlaps it)
     const bool valid = rho < n_root;
-    const float* tab = a.tab + (long long)r * a.tab_stride + (valid ? rho : 0) + ((long long)b << a.logn_root);
     const long long step2 = 2LL << a.logn_root;                  // from node c to node c + 2
-    float2 x3p[4], x2p[4], x1p[2][2], x0p[4];
-    {
+    float2 x3p[kNB][4], x2p[kNB][4], x1p[kNB][2][2], x0p[kNB][4];
+#pragma unroll
+    for (int nb = 0; nb < kNB; ++nb) {
+        const int b = b0 + nb;
+        const float* tab = a.tab + (long long)r * a.tab_stride + (valid ? rho : 0) + ((long long)b << a.logn_root);
         const float* p3 = tab + a.lev_tab[3];
         float x3[8];
 #pragma unroll
         for (int jj = 0; jj < 8; ++jj) x3[jj] = jj < a.lev_tau[3] ? __ldg(p3 + ((long long)jj << a.lev_logn[3])) : 0.0f;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) x3p[k] = f2(x3[2 * k], x3[2 * k + 1]);
+        for (int k = 0; k < 4; ++k) x3p[nb][k] = f2(x3[2 * k], x3[2 * k + 1]);
         const float* p2 = tab + a.lev_tab[2];
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj) {
             const bool on = jj < a.lev_tau[2];
             const float* q = p2 + ((long long)jj << a.lev_logn[2]);
-            x2p[jj] = on ? f2(__ldg(q), __ldg(q + step2)) : f2(0.0f, 0.0f);
+            x2p[nb][jj] = on ? f2(__ldg(q), __ldg(q + step2)) : f2(0.0f, 0.0f);
         }
         const float* p1 = tab + a.lev_tab[1];
 #pragma unroll
@@ -140,40 +150,45 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F)) k_fine_fwd_s4(
             const float* q = p1 + ((long long)jj << a.lev_logn[1]);
 #pragma unroll
             for (int p = 0; p < 2; ++p)
-                x1p[p][jj] = on ? f2(__ldg(q + (2 * p) * step2), __ldg(q + (2 * p + 1) * step2)) : f2(0.0f, 0.0f);
+                x1p[nb][p][jj] = on ? f2(__ldg(q + (2 * p) * step2), __ldg(q + (2 * p + 1) * step2)) : f2(0.0f, 0.0f);
         }
         const float* p0 = tab + a.lev_tab[0];
         const bool on0 = a.lev_tau[0] > 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            x0p[k] = on0 ? f2(__ldg(p0 + (2 * k) * step2), __ldg(p0 + (2 * k + 1) * step2)) : f2(0.0f, 0.0f);
+            x0p[nb][k] = on0 ? f2(__ldg(p0 + (2 * k) * step2), __ldg(p0 + (2 * k + 1) * step2)) : f2(0.0f, 0.0f);
     }
 
-    RowAcc2<F> acc[4];                                    // leaves (2k, 2k+1)
+    RowAcc2<F> acc[kNB][4];                               // leaves (2k, 2k+1) of each subtree
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k].init();
+    for (int nb = 0; nb < kNB; ++nb)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[nb][k].init();
     const float kap = a.kappa, c0 = a.c0;
-    // one column: the subtree's 8 outputs and their row accumulators
+    // one column: every subtree's 8 outputs and their row accumulators
     auto column = [&](const float4* ac, float vroot) {
         const float4 A0 = ac[0], A1 = ac[1], A2 = ac[2], A3 = ac[3], A4 = ac[4], A5 = ac[5];
-        float2 s3 = ffma2(x3p[0], f2(A0.x, A0.y), f2(vroot, 0.0f));
-        s3 = ffma2(x3p[1], f2(A0.z, A0.w), s3);
-        s3 = ffma2(x3p[2], f2(A1.x, A1.y), s3);
-        s3 = ffma2(x3p[3], f2(A1.z, A1.w), s3);
-        const float v3 = s3.x + s3.y;
-        float2 v2 = ffma2(x2p[0], f2(A2.x, A2.y), f2(v3, v3));            // level-2 nodes i2 = 0, 1
-        v2 = ffma2(x2p[1], f2(A2.z, A2.w), v2);
-        v2 = ffma2(x2p[2], f2(A3.x, A3.y), v2);
-        v2 = ffma2(x2p[3], f2(A3.z, A3.w), v2);
-        // level-1 nodes (0, 1) and (2, 3): parents (0, 1), i.e. v2 itself
-        const float2 v1a = ffma2(x1p[0][1], f2(A4.z, A4.w), ffma2(x1p[0][0], f2(A4.x, A4.y), v2));
-        const float2 v1b = ffma2(x1p[1][1], f2(A4.z, A4.w), ffma2(x1p[1][0], f2(A4.x, A4.y), v2));
-        // leaves (0, 1), (4, 5) below (0, 1) and (2, 3), (6, 7) below (2, 3)
-        const float2 a0 = f2(A5.x, A5.y);
-        acc[0].add(ffma2(x0p[0], a0, v1a), c0);
-        acc[1].add(ffma2(x0p[1], a0, v1b), c0);
-        acc[2].add(ffma2(x0p[2], a0, v1a), c0);
-        acc[3].add(ffma2(x0p[3], a0, v1b), c0);
+#pragma unroll
+        for (int nb = 0; nb < kNB; ++nb) {
+            float2 s3 = ffma2(x3p[nb][0], f2(A0.x, A0.y), f2(vroot, 0.0f));
+            s3 = ffma2(x3p[nb][1], f2(A0.z, A0.w), s3);
+            s3 = ffma2(x3p[nb][2], f2(A1.x, A1.y), s3);
+            s3 = ffma2(x3p[nb][3], f2(A1.z, A1.w), s3);
+            const float v3 = s3.x + s3.y;
+            float2 v2 = ffma2(x2p[nb][0], f2(A2.x, A2.y), f2(v3, v3));        // level-2 nodes i2 = 0, 1
+            v2 = ffma2(x2p[nb][1], f2(A2.z, A2.w), v2);
+            v2 = ffma2(x2p[nb][2], f2(A3.x, A3.y), v2);
+            v2 = ffma2(x2p[nb][3], f2(A3.z, A3.w), v2);
+            // level-1 nodes (0, 1) and (2, 3): parents (0, 1), i.e. v2 itself
+            const float2 v1a = ffma2(x1p[nb][0][1], f2(A4.z, A4.w), ffma2(x1p[nb][0][0], f2(A4.x, A4.y), v2));
+            const float2 v1b = ffma2(x1p[nb][1][1], f2(A4.z, A4.w), ffma2(x1p[nb][1][0], f2(A4.x, A4.y), v2));
+            // leaves (0, 1), (4, 5) below (0, 1) and (2, 3), (6, 7) below (2, 3)
+            const float2 a0 = f2(A5.x, A5.y);
+            acc[nb][0].add(ffma2(x0p[nb][0], a0, v1a), c0);
+            acc[nb][1].add(ffma2(x0p[nb][1], a0, v1b), c0);
+            acc[nb][2].add(ffma2(x0p[nb][2], a0, v1a), c0);
+            acc[nb][3].add(ffma2(x0p[nb][3], a0, v1b), c0);
+        }
     };
     // root values S_4 (layout [t/4][rho][4]), two quads of columns ahead
     const float* S = (a.S && valid) ? a.S + (long long)r * a.S_stride + rho * 4 : nullptr;
@@ -225,11 +240,13 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F)) k_fine_fwd_s4(
     // row partials of this column group: rowpart[r][cg][k] (log-sum-exp: also rowmax)
     if (valid) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const long long o = ((long long)r * gridDim.y + cg) * a.N + rho + ((long long)(b + 2 * i) << a.logn_root);
-            a.rowpart[o] = (i & 1) ? acc[i >> 1].s.y : acc[i >> 1].s.x;
-            if constexpr (F == F_LOGSUMEXP) a.rowmax[o] = (i & 1) ? acc[i >> 1].mx.y : acc[i >> 1].mx.x;
-        }
+        for (int nb = 0; nb < kNB; ++nb)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const long long o = ((long long)r * gridDim.y + cg) * a.N + rho + ((long long)(b0 + nb + 2 * i) << a.logn_root);
+                a.rowpart[o] = (i & 1) ? acc[nb][i >> 1].s.y : acc[nb][i >> 1].s.x;
+                if constexpr (F == F_LOGSUMEXP) a.rowmax[o] = (i & 1) ? acc[nb][i >> 1].mx.y : acc[nb][i >> 1].mx.x;
+            }
     }
 }
 
@@ -632,8 +649,8 @@ __global__ void __launch_bounds__(kMatThreads, 5) k_fine_mat_s4(const __grid_con
 
 }  // namespace
 
-int fine_s4_fwd_roots() { return kFwdRoots; }
-int fine_s4_fwd_resident(int F) { return fwd_min_blocks(F); }
+int fine_s4_fwd_roots(int nb) { return fwd_roots(nb); }
+int fine_s4_fwd_resident(int F, int nb) { return fwd_min_blocks(F, nb); }
 int fine_s4_bwd_cols() { return kBwdCols; }
 int fine_s4_bwd_batch() { return kRB; }
 int fine_s4_mat_cols() { return kMatCols; }
@@ -644,29 +661,36 @@ cudaError_t launch_fine_mat_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t
     return cudaGetLastError();
 }
 
-template <int F>
+template <int F, int NB>
 static cudaError_t fwd_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {
     const size_t smem = (size_t)a.cr * kAQuads * sizeof(float4);
     // dynamic + static shared memory may exceed 48 KB; the attribute belongs to the current device,
     // so it is set on every launch (as for the tensor-core kernels), not once per process
-    const cudaError_t e = cudaFuncSetAttribute(k_fine_fwd_s4<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const cudaError_t e = cudaFuncSetAttribute(k_fine_fwd_s4<F, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)(kMaxCRS4 * kAQuads * sizeof(float4)));
     if (e != cudaSuccess) return e;
-    k_fine_fwd_s4<F><<<grid, kFwdThreads, smem, st>>>(a);
+    k_fine_fwd_s4<F, NB><<<grid, kFwdThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
-    if (a.cr < 4 || a.cr > kMaxCRS4 || (a.cr & 3)) return cudaErrorInvalidValue;
+template <int NB>
+static cudaError_t fwd_s4_nb(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
     switch (F) {
-        case F_LINEAR_MEAN: return fwd_s4<F_LINEAR_MEAN>(a, grid, st);
-        case F_MEAN_COS: return fwd_s4<F_MEAN_COS>(a, grid, st);
-        case F_CALL_MEAN_EXP: return fwd_s4<F_CALL_MEAN_EXP>(a, grid, st);
-        case F_GAUSS_NORM2: return fwd_s4<F_GAUSS_NORM2>(a, grid, st);
-        case F_PDE_INV_SQ: return fwd_s4<F_PDE_INV_SQ>(a, grid, st);
-        case F_LOGSUMEXP: return fwd_s4<F_LOGSUMEXP>(a, grid, st);
+        case F_LINEAR_MEAN: return fwd_s4<F_LINEAR_MEAN, NB>(a, grid, st);
+        case F_MEAN_COS: return fwd_s4<F_MEAN_COS, NB>(a, grid, st);
+        case F_CALL_MEAN_EXP: return fwd_s4<F_CALL_MEAN_EXP, NB>(a, grid, st);
+        case F_GAUSS_NORM2: return fwd_s4<F_GAUSS_NORM2, NB>(a, grid, st);
+        case F_PDE_INV_SQ: return fwd_s4<F_PDE_INV_SQ, NB>(a, grid, st);
+        case F_LOGSUMEXP: return fwd_s4<F_LOGSUMEXP, NB>(a, grid, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, int nb, dim3 grid, cudaStream_t st) {
+    if (a.cr < 4 || a.cr > kMaxCRS4 || (a.cr & 3)) return cudaErrorInvalidValue;
+    if (nb == 2) return fwd_s4_nb<2>(a, F, grid, st);
+    if (nb == 1) return fwd_s4_nb<1>(a, F, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
