@@ -11,11 +11,12 @@
 // plus the root per output, six times over in the three-piece split, and its adjoint is bounded
 // by the tensor pipe well above the 11 FP32 operations per output the tree takes here.
 //
-// Forward: a CTA holds 64 roots x 2 branches.  Thread (rho, b) owns the 8 leaves q = b + 2i under
-// level-3 node b (the tree splits there without shared work), keeps their 32 x values in
-// registers (as pairs of sibling nodes) and walks the CTA's columns; the kappa-scaled fine
-// columns of A are staged in shared memory and read as six broadcast 16-byte loads per column,
-// and the paired FP32 instructions (FFMA2, FADD2) take two siblings per instruction.
+// Forward: a thread owns the 8 leaves q = b + 2i under level-3 node b of a root (the tree
+// splits there without shared work) for NB = 1 (a CTA of 64 roots x 2 branches), or both nodes'
+// 16 leaves for NB = 2 (a CTA of 128 roots); it keeps their x values in registers (as pairs of
+// sibling nodes) and walks the CTA's columns; the kappa-scaled fine columns of A are staged in
+// shared memory and read as six broadcast 16-byte loads per column, which serve NB subtrees, and
+// the paired FP32 instructions (FFMA2, FADD2) take two siblings per instruction.
 //
 // Backward: a CTA covers 256 columns (4 warps x 32 lanes x 2 columns) of a range of roots, in
 // two halves of 4 warps that take alternate roots.  The x values and row coefficients of 8 roots
