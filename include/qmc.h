@@ -250,7 +250,8 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
  * kernels, never the arithmetic).  For a problem shape (m, the column counts per weight level,
  * tau, shifts, precision, integrand) the planner uses a cached schedule when one exists, else its
  * cost models: the fine band's forward columns per CTA and adjoint roots per CTA, and in the
- * the fine forward's level-3 nodes per thread (autotuned only), in the
+ * the fine forward's level-3 nodes per thread and the fine adjoint's column pairs per lane
+ * (autotuned only), in the
  * tensor-core tiers the coarse forward's path (1 level passes, 2 block products and chain sum)
  * and the coarse adjoint's path (1 one fold of the root gradients and the cp.async block-gradient
  * kernel, 2 the fused fold-gradient kernel and the TMA block-gradient kernel).
@@ -268,8 +269,8 @@ qmc_status qmc_integrate_backward(const qmc_rule* rules, const void* const* d_A,
  *                b > 2, whose plan takes no schedule.
  *  qmc_tune_save / qmc_tune_load   write / merge the cache as a text file, one line per shape
  *                ("key|columns per CTA / 4|roots per CTA|coarse path|adjoint path|forward level-3
- *                nodes per thread (1 or 2)"; the last three are optional when loading; 0 keeps the
- *                cost model's choice).
+ *                nodes per thread (1 or 2)|adjoint column pairs per lane (1 or 2)"; the last four are
+ *                optional when loading; 0 keeps the cost model's choice).
  *  qmc_tune_clear  empties the cache.
  */
 qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, const qmc_integrand* f, int precision,

@@ -299,6 +299,7 @@ struct TuneVal {
     int bwd = 0;                   // tensor-core adjoint: 1 one fold + k_coarse_grad_tc, 2 the fused
                                    // fold-gradient and TMA gradient kernels (0: by size)
     int fwd_nb = 0;                // S4 forward: level-3 nodes per thread, 1 or 2 (0: by integrand)
+    int bwd_cpl = 0;               // S4 adjoint: column pairs per lane, 1 or 2 (0: 2)
 };
 struct TuneCache {
     std::mutex mu;
@@ -323,6 +324,7 @@ struct Plan {
     int tau = 0, tau_pad = 0, precision = 0, elt = 4, fkind = 0;
     int shape = SHAPE_S0, JF = 0, kf_width = 0, cw_bwd = 4;
     int fwd_nb = 1;                // S4 forward: level-3 nodes per thread
+    int bwd_cpl = 1;               // S4 adjoint: column pairs per lane
     bool exact = false;            // fine band levels hold exactly their maximum column counts
     Chain chf{}, chb{};
     long long B_per_shift = 0, S_per_shift = 0, partc_elems = 0, Fchain_per_shift = 0;
@@ -816,7 +818,11 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
         // 256 columns per CTA; an even number of roots per CTA (the two halves take alternate
         // roots), chosen by the same kind of cost model (at least 2 CTAs of 8 warps resident per
         // SM, a fixed setup cost of about 8 roots per CTA)
-        const int cols = fine_s4_bwd_cols(), rb = fine_s4_bwd_batch();
+        // two column pairs per lane: every broadcast load of a root's staged x values feeds twice the
+        // FP32 work, at one CTA of 8 warps per SM (measured on the 2^20-point step: 8.43 -> 7.65 ms)
+        P.bwd_cpl = P.tuned.bwd_cpl == 1 ? 1 : 2;
+        const int cols = fine_s4_bwd_cols(P.bwd_cpl), rb = fine_s4_bwd_batch();
+        const long long resident = P.bwd_cpl == 2 ? 1 : 2;     // CTAs of 8 warps per SM
         P.passes = (P.tau_pad + cols - 1) / cols;
         long long best = -1;
         const long long gmax = std::min<long long>((n_root + 1) / 2, 152LL * 16);
@@ -825,7 +831,7 @@ qmc_status make_plan(int op, const qmc_rule* r, uint32_t tau, const qmc_integran
             const long long g = (n_root + rpc - 1) / rpc;
             if (g != G) continue;
             const long long per_sm = ((long long)P.passes * g * P.reff + 151) / 152;
-            const long long cost = std::max(per_sm, 2LL) * (rpc + rb);
+            const long long cost = std::max(per_sm, resident) * (rpc + rb);
             if (best < 0 || cost < best) { best = cost; P.roots_per_cta = (int)rpc; P.groups = (int)g; }
         }
         const long long rpc = P.tuned.bwd_rpc;
@@ -1420,7 +1426,7 @@ qmc_status run_backward(const Plan& P, const qmc_rule* r, const T* dA, char* ws,
     const int nfine_part = P.reff * P.groups;
     if (P.fine_s4) {
         if constexpr (std::is_same<T, float>::value)
-            QMC_LAUNCH(st, "k_fine_bwd_s4", launch_fine_bwd_s4(a, P.fkind, dim3(P.groups, P.passes, P.reff), st));
+            QMC_LAUNCH(st, "k_fine_bwd_s4", launch_fine_bwd_s4(a, P.fkind, P.bwd_cpl, dim3(P.groups, P.passes, P.reff), st));
     } else {
         dim3 grid(P.groups, P.passes, P.reff);
         QMC_LAUNCH(st, "k_fine_bwd", launch_fine_bwd<T>(a, P.shape, P.exact, P.fkind, grid, st));
@@ -1845,6 +1851,13 @@ qmc_status qmc_autotune(const qmc_rule* rule, const void* d_A, uint32_t tau, con
             if (st != QMC_OK) break;
             if (ms > 0.0f && (bb < 0.0f || ms < bb)) { bb = ms; bestv.bwd_rpc = (int)rpc; }
         }
+        // one column pair per lane (two CTAs per SM), with the cost model's roots per CTA
+        if (st == QMC_OK) {
+            TuneVal tv{bestv.fwd_qpg, 0, bestv.coarse, 0, bestv.fwd_nb, 1};
+            float ms = 0.0f;
+            st = time_it(tv, true, &ms);
+            if (st == QMC_OK && ms > 0.0f && (bb < 0.0f || ms < bb)) { bb = ms; bestv.bwd_rpc = 0; bestv.bwd_cpl = 1; }
+        }
         // tensor-core tiers: the coarse adjoint's path, with the schedules just chosen
         if (base.tc_pieces && base.chb.count && st == QMC_OK) {
             float b1 = -1.0f, b2 = -1.0f;
@@ -1901,10 +1914,10 @@ qmc_status qmc_tune_save(const char* path) {
     if (!fh) return fail(QMC_ERR_INVALID_ARG, "cannot write %s", path);
     fprintf(fh, "# qmc_gb300 schedule cache: shape key | forward column quads per CTA | adjoint roots per CTA | "
                 "coarse path (1 level passes, 2 block products) | adjoint path (1 one fold, 2 fused) | "
-                "forward level-3 nodes per thread\n");
+                "forward level-3 nodes per thread | adjoint column pairs per lane\n");
     for (auto& kv : tc.m)
-        fprintf(fh, "%s|%d|%d|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc, kv.second.coarse,
-                kv.second.bwd, kv.second.fwd_nb);
+        fprintf(fh, "%s|%d|%d|%d|%d|%d|%d\n", kv.first.c_str(), kv.second.fwd_qpg, kv.second.bwd_rpc,
+                kv.second.coarse, kv.second.bwd, kv.second.fwd_nb, kv.second.bwd_cpl);
     fclose(fh);
     return QMC_OK;
 }
@@ -1927,15 +1940,17 @@ qmc_status qmc_tune_load(const char* path, uint32_t* n_entries) {
         char* c = b ? strchr(b + 1, '|') : nullptr;          // (the coarse and adjoint paths are optional)
         char* d = c ? strchr(c + 1, '|') : nullptr;
         char* e = d ? strchr(d + 1, '|') : nullptr;
-        int q = 0, r = 0, cp = 0, bp = 0, nb = 0;
+        char* g = e ? strchr(e + 1, '|') : nullptr;
+        int q = 0, r = 0, cp = 0, bp = 0, nb = 0, cl = 0;
         if (!a || !b || sscanf(a + 1, "%d", &q) != 1 || sscanf(b + 1, "%d", &r) != 1 || q < 0 || r < 0 || q > 128 ||
             (c && (sscanf(c + 1, "%d", &cp) != 1 || cp < 0 || cp > 2)) ||
             (d && (sscanf(d + 1, "%d", &bp) != 1 || bp < 0 || bp > 2)) ||
-            (e && (sscanf(e + 1, "%d", &nb) != 1 || nb < 0 || nb > 2))) {
+            (e && (sscanf(e + 1, "%d", &nb) != 1 || nb < 0 || nb > 2)) ||
+            (g && (sscanf(g + 1, "%d", &cl) != 1 || cl < 0 || cl > 2))) {
             st = fail(QMC_ERR_INVALID_ARG, "%s:%d: not a schedule entry", path, lineno);
             break;
         }
-        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp, bp, nb};
+        tc.m[std::string(line, a - line)] = TuneVal{q, r, cp, bp, nb, cl};
         ++n;
     }
     fclose(fh);

@@ -38,7 +38,6 @@ constexpr int kBwdThreads = 256;
 constexpr int kBwdCols = 256;                // columns per CTA: 4 warps x 32 lanes x 2
 constexpr int kRB = 8;                       // roots per staged batch
 constexpr int kSlots = 96;                   // staged floats per root
-constexpr int kBwdMinBlocks = 2;
 // forward CTAs resident per SM: 7 (72 registers) where the integrand's h fits without spilling,
 // else 5 (cos, the inverse square's reciprocal and log-sum-exp's running maximum need more)
 __host__ __device__ constexpr int fwd_min_blocks(int F, int NB) {
@@ -303,17 +302,26 @@ __device__ __forceinline__ float2 hp2(float2 v, float c0, float2 nax) {
     }
 }
 
-template <int F>
-__global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(const __grid_constant__ FineArgs<float> a) {
+// CPL column pairs per lane: a CTA covers 256 CPL columns; a lane's pair p holds columns
+// pass * 256 CPL + 256 p + 2 colw, +1.  With CPL = 2 every broadcast load of a root's staged x
+// values feeds twice the FP32 work, at one CTA of 8 warps per SM instead of two.
+template <int F, int CPL>
+__global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(const __grid_constant__ FineArgs<float> a) {
+    constexpr int kCols = kBwdCols * CPL;
     __shared__ __align__(16) float xs[2][kRB][kRowPad];
-    __shared__ __align__(16) float2 red[15][kBwdCols / 2];
+    __shared__ __align__(16) float2 red[15][kCols / 2];
     __shared__ unsigned codes[kSlots];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int half = warp >> 2, colw = (warp & 3) * 32 + lane;   // column pair of this lane
     const int grp = blockIdx.x, pass = blockIdx.y, r = blockIdx.z;
     const long long n_root = 1LL << a.logn_root;
-    const int t = pass * kBwdCols + 2 * colw;
-    const bool active = t < a.tau_pad;                          // then t + 1 < tau_pad too
+    int t[CPL];
+    bool active[CPL];
+#pragma unroll
+    for (int p = 0; p < CPL; ++p) {
+        t[p] = pass * kCols + kBwdCols * p + 2 * colw;
+        active[p] = t[p] < a.tau_pad;                          // then t + 1 < tau_pad too
+    }
     const float* tab = a.tab + (long long)r * a.tab_stride;
     const float upstream = (float)a.upstream[0];
     // the row coefficients are staged times upstream (and times 2 for the Gaussian norm, whose
@@ -321,22 +329,25 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
     const float coef_scale = F == F_GAUSS_NORM2 ? 2.0f * upstream : upstream;
     const float kap = a.kappa, c0 = a.c0;
 
-    // kappa * A of the thread's two columns and the band-gradient accumulators, as column pairs
-    float2 ah3[8], ah2[4], ah1[2], ah0;
-    float2 g3[8], g2[4], g1[2], g0;
-    auto lda = [&](int lev, int jj) -> float2 {
-        if (!active || jj >= a.lev_tau[lev]) return f2(0.0f, 0.0f);
-        const float* p = a.A + (long long)(a.lev_col0[lev] + jj) * a.ldA + t;
-        return f2(kap * __ldg(p), kap * __ldg(p + 1));
+    // kappa * A of the thread's columns and the band-gradient accumulators, as column pairs
+    float2 ah3[CPL][8], ah2[CPL][4], ah1[CPL][2], ah0[CPL];
+    float2 g3[CPL][8], g2[CPL][4], g1[CPL][2], g0[CPL];
+    auto lda = [&](int p, int lev, int jj) -> float2 {
+        if (!active[p] || jj >= a.lev_tau[lev]) return f2(0.0f, 0.0f);
+        const float* q = a.A + (long long)(a.lev_col0[lev] + jj) * a.ldA + t[p];
+        return f2(kap * __ldg(q), kap * __ldg(q + 1));
     };
 #pragma unroll
-    for (int jj = 0; jj < 8; ++jj) { ah3[jj] = lda(3, jj); g3[jj] = f2(0.0f, 0.0f); }
+    for (int p = 0; p < CPL; ++p) {
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) { ah2[jj] = lda(2, jj); g2[jj] = f2(0.0f, 0.0f); }
+        for (int jj = 0; jj < 8; ++jj) { ah3[p][jj] = lda(p, 3, jj); g3[p][jj] = f2(0.0f, 0.0f); }
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) { ah1[jj] = lda(1, jj); g1[jj] = f2(0.0f, 0.0f); }
-    ah0 = lda(0, 0);
-    g0 = f2(0.0f, 0.0f);
+        for (int jj = 0; jj < 4; ++jj) { ah2[p][jj] = lda(p, 2, jj); g2[p][jj] = f2(0.0f, 0.0f); }
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) { ah1[p][jj] = lda(p, 1, jj); g1[p][jj] = f2(0.0f, 0.0f); }
+        ah0[p] = lda(p, 0, 0);
+        g0[p] = f2(0.0f, 0.0f);
+    }
 
     const long long rho_beg = (long long)grp * a.roots_per_cta;
     const long long rho_end = min(rho_beg + (long long)a.roots_per_cta, n_root);
@@ -369,30 +380,43 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
         for (int u = 0; u < PER; ++u)
             *reinterpret_cast<float2*>(&xs[buf][jst][2 * ((tid >> 3) + 32 * u)]) = f2(pre[u], pre[u]);
     };
-    // root values S_4 (layout [t/4][rho][4]) of the thread's columns, and its root-gradient column
-    const float* Sb = (a.S && active) ? a.S + (long long)r * a.S_stride + ((long long)(t >> 2) << a.logn_root) * 4 + (t & 3)
-                                      : nullptr;
-    // root-gradient rows: row-major [rho][tau_pad], or 128-column tiles [t / 128][rho][128] (then a
-    // 32-row TMA box of one tile is contiguous for the fused fold-gradient kernel)
-    float* Fb = a.froot_tiled ? a.Froot + (long long)r * a.froot_stride + (((long long)(t >> 7) << a.logn_root) << 7) + (t & 127)
-                              : a.Froot + (long long)r * n_root * a.tau_pad + t;
+    // root values S_4 (layout [t/4][rho][4]) of the thread's columns, and its root-gradient columns:
+    // row-major [rho][tau_pad], or 128-column tiles [t / 128][rho][128] (then a 32-row TMA box of
+    // one tile is contiguous for the fused fold-gradient kernel)
+    const float* Sb[CPL];
+    float* Fb[CPL];
+#pragma unroll
+    for (int p = 0; p < CPL; ++p) {
+        Sb[p] = (a.S && active[p])
+                    ? a.S + (long long)r * a.S_stride + ((long long)(t[p] >> 2) << a.logn_root) * 4 + (t[p] & 3)
+                    : nullptr;
+        Fb[p] = a.froot_tiled
+                    ? a.Froot + (long long)r * a.froot_stride + (((long long)(t[p] >> 7) << a.logn_root) << 7) + (t[p] & 127)
+                    : a.Froot + (long long)r * n_root * a.tau_pad + t[p];
+    }
     const long long frow = a.froot_tiled ? 128 : a.tau_pad;
-    auto lds2 = [&](long long rho) -> float2 {
-        return Sb ? __ldg(reinterpret_cast<const float2*>(Sb + rho * 4)) : make_float2(0.0f, 0.0f);
+    auto lds2 = [&](int p, long long rho) -> float2 {
+        return Sb[p] ? __ldg(reinterpret_cast<const float2*>(Sb[p] + rho * 4)) : make_float2(0.0f, 0.0f);
     };
 
     __syncthreads();                                            // the slot codes
     if (nb > 0) { fetch(rho_beg); put(0); }
     __syncthreads();
-    float2 snext = rho_beg + half < rho_end ? lds2(rho_beg + half) : make_float2(0.0f, 0.0f);
+    float2 snext[CPL];
+#pragma unroll
+    for (int p = 0; p < CPL; ++p) snext[p] = rho_beg + half < rho_end ? lds2(p, rho_beg + half) : make_float2(0.0f, 0.0f);
     for (int kb = 0; kb < nb; ++kb) {
         const long long rb0 = rho_beg + (long long)kb * kRB;
         if (kb + 1 < nb) fetch(rb0 + kRB);                        // in flight during this batch
         for (int j = half; j < kRB; j += 2) {
             const long long rho = rb0 + j;
             if (rho >= rho_end) break;
-            const float2 sr = snext;
-            if (rho + 2 < rho_end) snext = lds2(rho + 2);
+            float2 sr[CPL];
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) {
+                sr[p] = snext[p];
+                if (rho + 2 < rho_end) snext[p] = lds2(p, rho + 2);
+            }
             const float* xr = xs[kb & 1][j];
             // slots 2g and 2g + 1, each a {v, v} pair
             auto pairs = [&](int g, float2& p0, float2& p1) {
@@ -400,74 +424,110 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
                 p0 = f2(q.x, q.y);
                 p1 = f2(q.z, q.w);
             };
-            float2 Fr = f2(0.0f, 0.0f);
+            float2 Fr[CPL];
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) Fr[p] = f2(0.0f, 0.0f);
 #pragma unroll
             for (int c3 = 0; c3 < 2; ++c3) {
                 // (x of the level-3 and level-2 nodes is read again for the gradient updates
                 // instead of being held in registers across the subtree)
                 // (two interleaved partial sums shorten the dependent chain)
-                float2 v3 = f2(kap * sr.x, kap * sr.y), w3 = f2(0.0f, 0.0f), F3 = f2(0.0f, 0.0f);
+                float2 v3[CPL], w3[CPL], F3[CPL];
+#pragma unroll
+                for (int p = 0; p < CPL; ++p) {
+                    v3[p] = f2(kap * sr[p].x, kap * sr[p].y);
+                    w3[p] = f2(0.0f, 0.0f);
+                    F3[p] = f2(0.0f, 0.0f);
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     float2 xa, xb;
                     pairs(4 * c3 + k, xa, xb);
-                    v3 = ffma2(xa, ah3[2 * k], v3);
-                    w3 = ffma2(xb, ah3[2 * k + 1], w3);
+#pragma unroll
+                    for (int p = 0; p < CPL; ++p) {
+                        v3[p] = ffma2(xa, ah3[p][2 * k], v3[p]);
+                        w3[p] = ffma2(xb, ah3[p][2 * k + 1], w3[p]);
+                    }
                 }
-                v3 = __fadd2_rn(v3, w3);
+#pragma unroll
+                for (int p = 0; p < CPL; ++p) v3[p] = __fadd2_rn(v3[p], w3[p]);
 #pragma unroll
                 for (int k2 = 0; k2 < 2; ++k2) {
                     const int c2 = c3 + 2 * k2;
-                    float2 v2 = v3, w2 = f2(0.0f, 0.0f), F2 = f2(0.0f, 0.0f);
+                    float2 v2[CPL], w2[CPL], F2[CPL];
+#pragma unroll
+                    for (int p = 0; p < CPL; ++p) {
+                        v2[p] = v3[p];
+                        w2[p] = f2(0.0f, 0.0f);
+                        F2[p] = f2(0.0f, 0.0f);
+                    }
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         float2 xa, xb;
                         pairs(8 + 2 * c2 + k, xa, xb);
-                        v2 = ffma2(xa, ah2[2 * k], v2);
-                        w2 = ffma2(xb, ah2[2 * k + 1], w2);
+#pragma unroll
+                        for (int p = 0; p < CPL; ++p) {
+                            v2[p] = ffma2(xa, ah2[p][2 * k], v2[p]);
+                            w2[p] = ffma2(xb, ah2[p][2 * k + 1], w2[p]);
+                        }
                     }
-                    v2 = __fadd2_rn(v2, w2);
+#pragma unroll
+                    for (int p = 0; p < CPL; ++p) v2[p] = __fadd2_rn(v2[p], w2[p]);
 #pragma unroll
                     for (int k1 = 0; k1 < 2; ++k1) {             // level-1 node c1 = c2 + 4 k1
                         const int c1 = c2 + 4 * k1;
                         float2 x10, x11, x0a, x0b;
                         pairs(16 + 2 * c1, x10, x11);
                         pairs(17 + 2 * c1, x0a, x0b);
-                        const float2 v1 = ffma2(x11, ah1[1], ffma2(x10, ah1[0], v2));
                         // leaves c1 and c1 + 8: coefficients (and -aux) in slots 64 + 4 c2 + 2 k1 + (0, 1)
                         float2 cfa, cfb, naa = f2(0.0f, 0.0f), nab = f2(0.0f, 0.0f);
                         pairs(32 + 2 * c2 + k1, cfa, cfb);
                         if constexpr (F == F_LOGSUMEXP) pairs(40 + 2 * c2 + k1, naa, nab);
-                        const float2 Ga = __fmul2_rn(cfa, hp2<F>(ffma2(x0a, ah0, v1), c0, naa));
-                        const float2 Gb = __fmul2_rn(cfb, hp2<F>(ffma2(x0b, ah0, v1), c0, nab));
-                        g0 = ffma2(x0b, Gb, ffma2(x0a, Ga, g0));
-                        const float2 F1 = __fadd2_rn(Ga, Gb);
-                        g1[0] = ffma2(x10, F1, g1[0]);
-                        g1[1] = ffma2(x11, F1, g1[1]);
-                        F2 = __fadd2_rn(F2, F1);
+#pragma unroll
+                        for (int p = 0; p < CPL; ++p) {
+                            const float2 v1 = ffma2(x11, ah1[p][1], ffma2(x10, ah1[p][0], v2[p]));
+                            const float2 Ga = __fmul2_rn(cfa, hp2<F>(ffma2(x0a, ah0[p], v1), c0, naa));
+                            const float2 Gb = __fmul2_rn(cfb, hp2<F>(ffma2(x0b, ah0[p], v1), c0, nab));
+                            g0[p] = ffma2(x0b, Gb, ffma2(x0a, Ga, g0[p]));
+                            const float2 F1 = __fadd2_rn(Ga, Gb);
+                            g1[p][0] = ffma2(x10, F1, g1[p][0]);
+                            g1[p][1] = ffma2(x11, F1, g1[p][1]);
+                            F2[p] = __fadd2_rn(F2[p], F1);
+                        }
                     }
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         float2 xa, xb;
                         pairs(8 + 2 * c2 + k, xa, xb);
-                        g2[2 * k] = ffma2(xa, F2, g2[2 * k]);
-                        g2[2 * k + 1] = ffma2(xb, F2, g2[2 * k + 1]);
+#pragma unroll
+                        for (int p = 0; p < CPL; ++p) {
+                            g2[p][2 * k] = ffma2(xa, F2[p], g2[p][2 * k]);
+                            g2[p][2 * k + 1] = ffma2(xb, F2[p], g2[p][2 * k + 1]);
+                        }
                     }
-                    F3 = __fadd2_rn(F3, F2);
+#pragma unroll
+                    for (int p = 0; p < CPL; ++p) F3[p] = __fadd2_rn(F3[p], F2[p]);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     float2 xa, xb;
                     pairs(4 * c3 + k, xa, xb);
-                    g3[2 * k] = ffma2(xa, F3, g3[2 * k]);
-                    g3[2 * k + 1] = ffma2(xb, F3, g3[2 * k + 1]);
+#pragma unroll
+                    for (int p = 0; p < CPL; ++p) {
+                        g3[p][2 * k] = ffma2(xa, F3[p], g3[p][2 * k]);
+                        g3[p][2 * k + 1] = ffma2(xb, F3[p], g3[p][2 * k + 1]);
+                    }
                 }
-                Fr = __fadd2_rn(Fr, F3);
+#pragma unroll
+                for (int p = 0; p < CPL; ++p) Fr[p] = __fadd2_rn(Fr[p], F3[p]);
             }
-            if (active) {
-                // columns at or beyond tau carry no gradient
-                *reinterpret_cast<float2*>(Fb + rho * frow) =
-                    make_float2(t < a.tau ? Fr.x : 0.0f, t + 1 < a.tau ? Fr.y : 0.0f);
+#pragma unroll
+            for (int p = 0; p < CPL; ++p) {
+                if (active[p]) {
+                    // columns at or beyond tau carry no gradient
+                    *reinterpret_cast<float2*>(Fb[p] + rho * frow) =
+                        make_float2(t[p] < a.tau ? Fr[p].x : 0.0f, t[p] + 1 < a.tau ? Fr[p].y : 0.0f);
+                }
             }
         }
         if (kb + 1 < nb) put((kb + 1) & 1);
@@ -476,19 +536,27 @@ __global__ void __launch_bounds__(kBwdThreads, kBwdMinBlocks) k_fine_bwd_s4(cons
 
     // the two root halves' accumulators, in a fixed order; gradient rows in the band's column
     // order: level 0, level 1 (2), level 2 (4), level 3 (8)
-    auto row = [&](int j) -> float2 { return j == 0 ? g0 : j < 3 ? g1[j - 1] : j < 7 ? g2[j - 3] : g3[j - 7]; };
+    auto row = [&](int p, int j) -> float2 {
+        return j == 0 ? g0[p] : j < 3 ? g1[p][j - 1] : j < 7 ? g2[p][j - 3] : g3[p][j - 7];
+    };
     if (half == 1) {
 #pragma unroll
-        for (int j = 0; j < 15; ++j) red[j][colw] = row(j);
+        for (int p = 0; p < CPL; ++p)
+#pragma unroll
+            for (int j = 0; j < 15; ++j) red[j][colw + (kBwdCols / 2) * p] = row(p, j);
     }
     __syncthreads();
-    if (half == 0 && active) {
-        float* out = a.gradpart + ((long long)r * a.groups + grp) * 15 * a.tau_pad + t;
+    if (half == 0) {
 #pragma unroll
-        for (int j = 0; j < 15; ++j) {
-            const float2 o = __fadd2_rn(row(j), red[j][colw]);
-            *reinterpret_cast<float2*>(out + (long long)j * a.tau_pad) =
-                make_float2(t < a.tau ? o.x : 0.0f, t + 1 < a.tau ? o.y : 0.0f);
+        for (int p = 0; p < CPL; ++p) {
+            if (!active[p]) continue;
+            float* out = a.gradpart + ((long long)r * a.groups + grp) * 15 * a.tau_pad + t[p];
+#pragma unroll
+            for (int j = 0; j < 15; ++j) {
+                const float2 o = __fadd2_rn(row(p, j), red[j][colw + (kBwdCols / 2) * p]);
+                *reinterpret_cast<float2*>(out + (long long)j * a.tau_pad) =
+                    make_float2(t[p] < a.tau ? o.x : 0.0f, t[p] + 1 < a.tau ? o.y : 0.0f);
+            }
         }
     }
 }
@@ -652,7 +720,7 @@ __global__ void __launch_bounds__(kMatThreads, 5) k_fine_mat_s4(const __grid_con
 
 int fine_s4_fwd_roots(int nb) { return fwd_roots(nb); }
 int fine_s4_fwd_resident(int F, int nb) { return fwd_min_blocks(F, nb); }
-int fine_s4_bwd_cols() { return kBwdCols; }
+int fine_s4_bwd_cols(int cpl) { return kBwdCols * cpl; }
 int fine_s4_bwd_batch() { return kRB; }
 int fine_s4_mat_cols() { return kMatCols; }
 
@@ -694,17 +762,24 @@ cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, int nb, dim3 gri
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
+template <int CPL>
+static cudaError_t bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
     switch (F) {
-        case F_LINEAR_MEAN: k_fine_bwd_s4<F_LINEAR_MEAN><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_MEAN_COS: k_fine_bwd_s4<F_MEAN_COS><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_CALL_MEAN_EXP: k_fine_bwd_s4<F_CALL_MEAN_EXP><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_GAUSS_NORM2: k_fine_bwd_s4<F_GAUSS_NORM2><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_PDE_INV_SQ: k_fine_bwd_s4<F_PDE_INV_SQ><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_LOGSUMEXP: k_fine_bwd_s4<F_LOGSUMEXP><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_LINEAR_MEAN: k_fine_bwd_s4<F_LINEAR_MEAN, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_MEAN_COS: k_fine_bwd_s4<F_MEAN_COS, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_CALL_MEAN_EXP: k_fine_bwd_s4<F_CALL_MEAN_EXP, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_GAUSS_NORM2: k_fine_bwd_s4<F_GAUSS_NORM2, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_PDE_INV_SQ: k_fine_bwd_s4<F_PDE_INV_SQ, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
+        case F_LOGSUMEXP: k_fine_bwd_s4<F_LOGSUMEXP, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, int cpl, dim3 grid, cudaStream_t st) {
+    if (cpl == 2) return bwd_s4<2>(a, F, grid, st);
+    if (cpl == 1) return bwd_s4<1>(a, F, grid, st);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace qmc

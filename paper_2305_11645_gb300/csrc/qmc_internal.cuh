@@ -471,14 +471,15 @@ cudaError_t tc_error_word(unsigned int* value, bool clear);
 cudaError_t launch_selftest_wait(uint32_t polls, cudaStream_t st);
 // the S4 fine band in FP32 on the CUDA cores: forward CTAs of fine_s4_fwd_roots(nb) roots, nb = 1
 // or 2 level-3 nodes per thread (grid: root blocks x column groups of a.cr <= 512 columns x
-// shifts), adjoint CTAs of fine_s4_bwd_cols() columns (grid: root groups of a.roots_per_cta roots,
+// shifts), adjoint CTAs of fine_s4_bwd_cols(cpl) columns, cpl = 1 or 2 column pairs per lane
+// (grid: root groups of a.roots_per_cta roots,
 // a multiple of fine_s4_bwd_batch() x column passes x shifts)
 int fine_s4_fwd_roots(int nb);
 int fine_s4_fwd_resident(int F, int nb);   // forward CTAs resident per SM for integrand F
-int fine_s4_bwd_cols();
+int fine_s4_bwd_cols(int cpl);
 int fine_s4_bwd_batch();
 cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, int nb, dim3 grid, cudaStream_t st);
-cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st);
+cudaError_t launch_fine_bwd_s4(const FineArgs<float>& a, int F, int cpl, dim3 grid, cudaStream_t st);
 // the materialised S4 band (P = X A, float tiers): CTAs of fine_s4_mat_cols() columns over
 // a.roots_per_cta roots (grid: root groups x column passes x shifts)
 int fine_s4_mat_cols();

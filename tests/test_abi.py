@@ -346,7 +346,7 @@ def test_schedule_cache_file_and_planner(lib, tmp_path):
     assert st == L.QMC_OK and tuned != base                  # (the cost model takes 16 groups of 4 columns)
     out = tmp_path / "saved.txt"
     assert lib.qmc_tune_save(str(out).encode()) == L.QMC_OK
-    assert f"{key}|16|6|0|0|0" in out.read_text().splitlines()  # (missing fields read as 0)
+    assert f"{key}|16|6|0|0|0|0" in out.read_text().splitlines()  # (missing fields read as 0)
     assert lib.qmc_tune_clear() == L.QMC_OK
     assert ws_size(lib, L.QMC_OP_INTEGRATE, r, 64, f, L.QMC_FP32)[1] == base
     # the tensor-core tiers' coarse path is part of the schedule: this shape's coarse partial sums
@@ -386,7 +386,7 @@ def test_schedule_set_adjoint_path(lib, tmp_path):
     out = tmp_path / "saved.txt"
     assert lib.qmc_tune_save(str(out).encode()) == L.QMC_OK
     key = tune_key(p, L.QMC_SPLIT, I.F_LOGSUMEXP, tau)
-    assert f"{key}|0|0|0|2|0" in out.read_text().splitlines()
+    assert f"{key}|0|0|0|2|0|0" in out.read_text().splitlines()
     for bad in ((129, 0, 0, 0), (0, -1, 0, 0), (0, 0, 3, 0), (0, 0, 0, 3)):
         assert lib.qmc_tune_set(ctypes.byref(r.struct()), tau, ctypes.byref(f.struct()), L.QMC_SPLIT,
                                 *bad) == L.QMC_ERR_INVALID_ARG
