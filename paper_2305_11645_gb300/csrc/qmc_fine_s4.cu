@@ -36,7 +36,9 @@ constexpr int kFwdThreads = 128;
 __host__ __device__ constexpr int fwd_roots(int NB) { return kFwdThreads * NB / 2; }
 constexpr int kBwdThreads = 256;
 constexpr int kBwdCols = 256;                // columns per CTA: 4 warps x 32 lanes x 2
-constexpr int kRB = 8;                       // roots per staged batch
+constexpr int kRB = 8;                       // roots per staged batch (materialised product)
+constexpr int kBRB = 16;                     // roots per staged batch (adjoint: fewer barriers than 8,
+                                             // 7.52 -> 7.33 ms on the 2^20-point step)
 constexpr int kSlots = 96;                   // staged floats per root
 // forward CTAs resident per SM: 7 (72 registers) where the integrand's h fits without spilling,
 // else 5 (cos, the inverse square's reciprocal and log-sum-exp's running maximum need more)
@@ -261,9 +263,9 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F, NB)) k_fine_fwd
 //   slots 32..63   per level-1 node c1: x columns 0, 1 and the x of its leaves c1, c1 + 8
 //   slots 64..79   per level-2 node c2: coefficients of the leaves c2, c2 + 8, c2 + 4, c2 + 12
 //   slots 80..95   the same leaves' -aux (log-sum-exp only)
-// A root's row is kRowPad floats long: the 8 roots of a batch then start 16 bytes apart modulo
-// 128, so that the staging stores hit distinct banks, and the reads are 16-byte aligned at
-// fixed offsets.
+// A root's row is kRowPad floats long: consecutive roots of a batch then start 16 bytes apart
+// modulo 128, so that the staging stores of 8 roots hit distinct banks, and the reads are
+// 16-byte aligned at fixed offsets.
 constexpr int kRowPad = 2 * kSlots + 4;
 
 // Where slot s of every root comes from, as a 32-bit code: bit 31 set for no value (0), else
@@ -302,14 +304,25 @@ __device__ __forceinline__ float2 hp2(float2 v, float c0, float2 nax) {
     }
 }
 
+// Dynamic shared memory of the adjoint: the double-buffered staging of kBRB roots, reused after
+// the last batch for the reduction of the two root halves' gradients (15 rows of 256 CPL columns)
+__host__ __device__ constexpr size_t bwd_smem_bytes(int cpl) {
+    return sizeof(float) * 2 * kBRB * kRowPad > sizeof(float2) * 15 * (kBwdCols * cpl / 2)
+               ? sizeof(float) * 2 * kBRB * kRowPad
+               : sizeof(float2) * 15 * (kBwdCols * cpl / 2);
+}
+
 // CPL column pairs per lane: a CTA covers 256 CPL columns; a lane's pair p holds columns
 // pass * 256 CPL + 256 p + 2 colw, +1.  With CPL = 2 every broadcast load of a root's staged x
 // values feeds twice the FP32 work, at one CTA of 8 warps per SM instead of two.
 template <int F, int CPL>
 __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(const __grid_constant__ FineArgs<float> a) {
     constexpr int kCols = kBwdCols * CPL;
-    __shared__ __align__(16) float xs[2][kRB][kRowPad];
-    __shared__ __align__(16) float2 red[15][kCols / 2];
+    // the staging buffers and, after the last batch's barrier, the halves' reduction share the
+    // dynamic shared memory (bwd_smem_bytes)
+    extern __shared__ __align__(16) unsigned char bwd_dyn[];
+    float (*xs)[kBRB][kRowPad] = reinterpret_cast<float (*)[kBRB][kRowPad]>(bwd_dyn);
+    float2 (*red)[kCols / 2] = reinterpret_cast<float2 (*)[kCols / 2]>(bwd_dyn);
     __shared__ unsigned codes[kSlots];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int half = warp >> 2, colw = (warp & 3) * 32 + lane;   // column pair of this lane
@@ -351,10 +364,11 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
 
     const long long rho_beg = (long long)grp * a.roots_per_cta;
     const long long rho_end = min(rho_beg + (long long)a.roots_per_cta, n_root);
-    const int nb = rho_end > rho_beg ? (int)((rho_end - rho_beg + kRB - 1) / kRB) : 0;
-    // staging: thread tid fills slots tid / 8 + 32 u of batch root tid % 8
-    constexpr int PER = kRB * kSlots / kBwdThreads;
-    const int jst = tid & 7;
+    const int nb = rho_end > rho_beg ? (int)((rho_end - rho_beg + kBRB - 1) / kBRB) : 0;
+    // staging: thread tid fills slots tid / kBRB + (256 / kBRB) u of batch root tid % kBRB
+    constexpr int PER = kBRB * kSlots / kBwdThreads;
+    constexpr int SST = kBwdThreads / kBRB;
+    const int jst = tid % kBRB;
     const float* rsave = a.rowsave + 2 * (long long)r * a.N;
     if (tid < kSlots) codes[tid] = bwd_slot_code<F>(a, tid);    // (read after the first barrier)
     float pre[PER];
@@ -362,7 +376,7 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
         const long long rho = rb0 + jst;
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
-            const unsigned code = codes[(tid >> 3) + 32 * u];
+            const unsigned code = codes[tid / kBRB + SST * u];
             float v = 0.0f;
             if (!(code >> 31) && rho < rho_end) {
                 if (code >> 30) {
@@ -378,7 +392,7 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
     auto put = [&](int buf) {
 #pragma unroll
         for (int u = 0; u < PER; ++u)
-            *reinterpret_cast<float2*>(&xs[buf][jst][2 * ((tid >> 3) + 32 * u)]) = f2(pre[u], pre[u]);
+            *reinterpret_cast<float2*>(&xs[buf][jst][2 * (tid / kBRB + SST * u)]) = f2(pre[u], pre[u]);
     };
     // root values S_4 (layout [t/4][rho][4]) of the thread's columns, and its root-gradient columns:
     // row-major [rho][tau_pad], or 128-column tiles [t / 128][rho][128] (then a 32-row TMA box of
@@ -406,9 +420,9 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
 #pragma unroll
     for (int p = 0; p < CPL; ++p) snext[p] = rho_beg + half < rho_end ? lds2(p, rho_beg + half) : make_float2(0.0f, 0.0f);
     for (int kb = 0; kb < nb; ++kb) {
-        const long long rb0 = rho_beg + (long long)kb * kRB;
-        if (kb + 1 < nb) fetch(rb0 + kRB);                        // in flight during this batch
-        for (int j = half; j < kRB; j += 2) {
+        const long long rb0 = rho_beg + (long long)kb * kBRB;
+        if (kb + 1 < nb) fetch(rb0 + kBRB);                       // in flight during this batch
+        for (int j = half; j < kBRB; j += 2) {
             const long long rho = rb0 + j;
             if (rho >= rho_end) break;
             float2 sr[CPL];
@@ -419,14 +433,13 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
             }
             const float* xr = xs[kb & 1][j];
             // slots 2g and 2g + 1, each a {v, v} pair
+            // (the gradients F of a node's children are summed without a zero start)
             auto pairs = [&](int g, float2& p0, float2& p1) {
                 const float4 q = *reinterpret_cast<const float4*>(xr + 4 * g);
                 p0 = f2(q.x, q.y);
                 p1 = f2(q.z, q.w);
             };
             float2 Fr[CPL];
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) Fr[p] = f2(0.0f, 0.0f);
 #pragma unroll
             for (int c3 = 0; c3 < 2; ++c3) {
                 // (x of the level-3 and level-2 nodes is read again for the gradient updates
@@ -437,7 +450,6 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                 for (int p = 0; p < CPL; ++p) {
                     v3[p] = f2(kap * sr[p].x, kap * sr[p].y);
                     w3[p] = f2(0.0f, 0.0f);
-                    F3[p] = f2(0.0f, 0.0f);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -459,7 +471,6 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                     for (int p = 0; p < CPL; ++p) {
                         v2[p] = v3[p];
                         w2[p] = f2(0.0f, 0.0f);
-                        F2[p] = f2(0.0f, 0.0f);
                     }
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                             const float2 F1 = __fadd2_rn(Ga, Gb);
                             g1[p][0] = ffma2(x10, F1, g1[p][0]);
                             g1[p][1] = ffma2(x11, F1, g1[p][1]);
-                            F2[p] = __fadd2_rn(F2[p], F1);
+                            F2[p] = k1 == 0 ? F1 : __fadd2_rn(F2[p], F1);
                         }
                     }
 #pragma unroll
@@ -506,7 +517,7 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                         }
                     }
 #pragma unroll
-                    for (int p = 0; p < CPL; ++p) F3[p] = __fadd2_rn(F3[p], F2[p]);
+                    for (int p = 0; p < CPL; ++p) F3[p] = k2 == 0 ? F2[p] : __fadd2_rn(F3[p], F2[p]);
                 }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
@@ -519,7 +530,7 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                     }
                 }
 #pragma unroll
-                for (int p = 0; p < CPL; ++p) Fr[p] = __fadd2_rn(Fr[p], F3[p]);
+                for (int p = 0; p < CPL; ++p) Fr[p] = c3 == 0 ? F3[p] : __fadd2_rn(Fr[p], F3[p]);
             }
 #pragma unroll
             for (int p = 0; p < CPL; ++p) {
@@ -721,7 +732,7 @@ __global__ void __launch_bounds__(kMatThreads, 5) k_fine_mat_s4(const __grid_con
 int fine_s4_fwd_roots(int nb) { return fwd_roots(nb); }
 int fine_s4_fwd_resident(int F, int nb) { return fwd_min_blocks(F, nb); }
 int fine_s4_bwd_cols(int cpl) { return kBwdCols * cpl; }
-int fine_s4_bwd_batch() { return kRB; }
+int fine_s4_bwd_batch() { return kBRB; }
 int fine_s4_mat_cols() { return kMatCols; }
 
 cudaError_t launch_fine_mat_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {
@@ -765,12 +776,23 @@ cudaError_t launch_fine_fwd_s4(const FineArgs<float>& a, int F, int nb, dim3 gri
 template <int CPL>
 static cudaError_t bwd_s4(const FineArgs<float>& a, int F, dim3 grid, cudaStream_t st) {
     switch (F) {
-        case F_LINEAR_MEAN: k_fine_bwd_s4<F_LINEAR_MEAN, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_MEAN_COS: k_fine_bwd_s4<F_MEAN_COS, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_CALL_MEAN_EXP: k_fine_bwd_s4<F_CALL_MEAN_EXP, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_GAUSS_NORM2: k_fine_bwd_s4<F_GAUSS_NORM2, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_PDE_INV_SQ: k_fine_bwd_s4<F_PDE_INV_SQ, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
-        case F_LOGSUMEXP: k_fine_bwd_s4<F_LOGSUMEXP, CPL><<<grid, kBwdThreads, 0, st>>>(a); break;
+#define QMC_BWD_S4(FF)                                                                                     \
+    do {                                                                                                   \
+        constexpr size_t smem = bwd_smem_bytes(CPL);                                                       \
+        if (smem > 48 * 1024) {                                                                            \
+            const cudaError_t e = cudaFuncSetAttribute(k_fine_bwd_s4<FF, CPL>,                             \
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+            if (e != cudaSuccess) return e;                                                                \
+        }                                                                                                  \
+        k_fine_bwd_s4<FF, CPL><<<grid, kBwdThreads, smem, st>>>(a);                                        \
+    } while (0)
+        case F_LINEAR_MEAN: QMC_BWD_S4(F_LINEAR_MEAN); break;
+        case F_MEAN_COS: QMC_BWD_S4(F_MEAN_COS); break;
+        case F_CALL_MEAN_EXP: QMC_BWD_S4(F_CALL_MEAN_EXP); break;
+        case F_GAUSS_NORM2: QMC_BWD_S4(F_GAUSS_NORM2); break;
+        case F_PDE_INV_SQ: QMC_BWD_S4(F_PDE_INV_SQ); break;
+        case F_LOGSUMEXP: QMC_BWD_S4(F_LOGSUMEXP); break;
+#undef QMC_BWD_S4
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
