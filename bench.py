@@ -45,8 +45,8 @@ GOLDEN = os.path.join(ROOT, "tests", "golden", "full_size_oracle.json")
 TRAFFIC_BYTES = {
     # profiles/net20_top_kernels.md: the 2-shift capture of the 16-shift contract workload, scaled by
     # 16/2 (each shift's data are separate, so the DRAM bytes grow with the shifts)
-    ("net20", "k_fine_bwd_s4"): (590.476032e6 + 500.617216e6) * 8,
-    ("net20", "k_fine_fwd_s4"): (608.797184e6 + 30.578688e6) * 8,
+    ("net20", "k_fine_bwd_s4"): (590.064384e6 + 500.344064e6) * 8,
+    ("net20", "k_fine_fwd_s4"): (608.503808e6 + 30.661376e6) * 8,
     ("net20", "k_fold_grad_tc"): (576.100352e6 + 60.806656e6) * 8,
     ("net20", "k_grad_tc"): (166.677504e6 + 3.560448e6) * 8,
 }

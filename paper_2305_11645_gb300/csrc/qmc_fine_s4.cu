@@ -46,7 +46,8 @@ __host__ __device__ constexpr int fwd_min_blocks(int F, int NB) {
     return NB == 1 ? ((F == F_LINEAR_MEAN || F == F_CALL_MEAN_EXP || F == F_GAUSS_NORM2) ? 7 : 5)
                    : ((F == F_LINEAR_MEAN || F == F_CALL_MEAN_EXP || F == F_GAUSS_NORM2) ? 4 : 3);
 }
-constexpr int kMaxCRS4 = 512;                // forward columns per CTA (dynamic shared memory 48 KB)
+constexpr int kMaxCRS4 = 512;                // forward columns per CTA (dynamic shared memory 56 KB with
+                                             // the root-value ring: 4 CTAs fill an SM's 228 KB)
 
 // ------------------------------------------------------------------------------------------
 // Forward
@@ -59,7 +60,25 @@ constexpr int kMaxCRS4 = 512;                // forward columns per CTA (dynamic
 // partial sums over (a3 2k, a3 2k+1), and the two sibling nodes of each lower level share an a.
 constexpr int kAQuads = 6;
 
+// The forward's root values S_4 pass through a ring of kSRing slots of 16 bytes per thread in
+// shared memory, copied kSDist quads of columns ahead of their use
+constexpr int kSDist = 3;
+constexpr int kSRing = kSDist + 1;           // the slot refilled is the one read a quad earlier
+__host__ __device__ constexpr size_t fwd_smem_bytes(int cr) {
+    return (size_t)cr * kAQuads * 16 + (size_t)kSRing * kFwdThreads * 16;
+}
+
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+// 16-byte asynchronous copy global -> shared (zero-filled when !valid; src must still be a
+// valid address), and the per-thread copy groups
+__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(saddr), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 // Row accumulator of u = sum_t h(v_t); log-sum-exp keeps (max, sum 2^(v - max)) and takes one
@@ -109,8 +128,9 @@ template <int F, int NB>
 __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F, NB)) k_fine_fwd_s4(const __grid_constant__ FineArgs<float> a) {
     constexpr int kNB = NB;
     constexpr int kFwdRoots = fwd_roots(NB);
-    extern __shared__ __align__(16) float4 As_dyn[];                  // [a.cr][kAQuads]
+    extern __shared__ __align__(16) float4 As_dyn[];        // [a.cr][kAQuads], then [kSRing][threads]
     float4 (*As)[kAQuads] = reinterpret_cast<float4 (*)[kAQuads]>(As_dyn);
+    float4* ring = As_dyn + (size_t)a.cr * kAQuads;
     const int tid = threadIdx.x;
     // thread: root rho and its level-3 nodes b0 .. b0 + kNB - 1
     const int b0 = kNB == 2 ? 0 : tid / kFwdRoots;
@@ -192,14 +212,20 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F, NB)) k_fine_fwd
             acc[nb][3].add(ffma2(x0p[nb][3], a0, v1b), c0);
         }
     };
-    // root values S_4 (layout [t/4][rho][4]), two quads of columns ahead
+    // root values S_4 (layout [t/4][rho][4]): quad q of the group (columns t_beg + 4q ..) into ring
+    // slot q % kSRing, kSDist quads ahead (no registers held by the copies in flight; register loads
+    // two quads ahead left 10% of the kernel's time waiting on them), zeros without root values
     const float* S = (a.S && valid) ? a.S + (long long)r * a.S_stride + rho * 4 : nullptr;
     const long long squad = 4LL << a.logn_root;
-    auto lds4 = [&](int t) -> float4 {
-        return (S && t < t_end) ? __ldg(reinterpret_cast<const float4*>(S + (long long)(t >> 2) * squad))
-                                : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    auto issue_s = [&](int q) {
+        const int t = t_beg + 4 * q;
+        const bool on = S && t < t_end;
+        cp_async16((uint32_t)__cvta_generic_to_shared(ring + (q % kSRing) * kFwdThreads + tid),
+                   on ? S + (long long)(t >> 2) * squad : a.tab, on);
+        cp_async_commit();                                    // (one group per quad, possibly empty)
     };
-    float4 snext = lds4(t_beg), snext2 = lds4(t_beg + 4);
+#pragma unroll
+    for (int q = 0; q < kSDist; ++q) issue_s(q);
     {
         // threads tid < 120 stage position jp = tid % 24 of the columns tid / 24, tid / 24 + 5, ...
         constexpr int W = 4 * kAQuads, STEP = kFwdThreads / W;
@@ -219,25 +245,28 @@ __global__ void __launch_bounds__(kFwdThreads, fwd_min_blocks(F, NB)) k_fine_fwd
                 Asf[c * W + jp] = (on && t_beg + c < a.tau) ? a.kappa * __ldg(arow + t_beg + c) : 0.0f;
     }
     __syncthreads();
-    const int t_full = t_beg + ((t_end - t_beg) & ~3);
-    int t0 = valid ? t_beg : t_end;
-    for (; t0 < t_full; t0 += 4) {                        // whole quads: four independent columns
-        const float4 sq = snext;
-        snext = snext2;
-        snext2 = lds4(t0 + 8);
-        const float4* ac = As[t0 - t_beg];
+    const int nfull = (t_end - t_beg) >> 2;
+    int q = 0;
+    for (; valid && q < nfull; ++q) {                     // whole quads: four independent columns
+        cp_async_wait<kSDist - 1>();                      // this thread's copy of quad q has landed
+        const float4 sq = ring[(q % kSRing) * kFwdThreads + tid];
+        issue_s(q + kSDist);
+        const float4* ac = As[4 * q];
         column(ac, kap * sq.x);
         column(ac + kAQuads, kap * sq.y);
         asm volatile("" ::: "memory");                 // (caps the columns' loads held at once)
         column(ac + 2 * kAQuads, kap * sq.z);
         column(ac + 3 * kAQuads, kap * sq.w);
     }
-    if (t0 < t_end) {                                     // the ragged last quad
-        const float sv[4] = {snext.x, snext.y, snext.z, snext.w};
+    if (valid && t_beg + 4 * q < t_end) {                 // the ragged last quad
+        cp_async_wait<kSDist - 1>();
+        const float4 sq = ring[(q % kSRing) * kFwdThreads + tid];
+        const float sv[4] = {sq.x, sq.y, sq.z, sq.w};
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            if (t0 + c < t_end) column(As[t0 - t_beg + c], kap * sv[c]);
+            if (t_beg + 4 * q + c < t_end) column(As[4 * q + c], kap * sv[c]);
     }
+    cp_async_wait<0>();                                   // (no copy outlives the CTA)
 
     // row partials of this column group: rowpart[r][cg][k] (log-sum-exp: also rowmax)
     if (valid) {
@@ -743,11 +772,11 @@ cudaError_t launch_fine_mat_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t
 
 template <int F, int NB>
 static cudaError_t fwd_s4(const FineArgs<float>& a, dim3 grid, cudaStream_t st) {
-    const size_t smem = (size_t)a.cr * kAQuads * sizeof(float4);
+    const size_t smem = fwd_smem_bytes(a.cr);
     // dynamic + static shared memory may exceed 48 KB; the attribute belongs to the current device,
     // so it is set on every launch (as for the tensor-core kernels), not once per process
     const cudaError_t e = cudaFuncSetAttribute(k_fine_fwd_s4<F, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)(kMaxCRS4 * kAQuads * sizeof(float4)));
+                                               (int)fwd_smem_bytes(kMaxCRS4));
     if (e != cudaSuccess) return e;
     k_fine_fwd_s4<F, NB><<<grid, kFwdThreads, smem, st>>>(a);
     return cudaGetLastError();
