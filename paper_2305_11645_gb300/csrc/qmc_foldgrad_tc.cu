@@ -182,9 +182,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_fold_grad_tc(const __grid_const
                     const int rs = (int)(itr % RS);
                     if (!bar_wait(smem_u32(&rempty[rs]), (uint32_t)(((itr / RS) & 1) ^ 1))) { ok = false; break; }
                     bar_expect_tx(smem_u32(&rfull[rs]), RAW);
-                    if (ga.froot_tiled)
-                        tma_load_4d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), 0, rho0 + q * (int)n_out,
-                               cw.tt, r);
+                    if (ga.froot_tiled)                       // 32 rows of one tile: 16 KB in one copy
+                        bulk_load(smem_u32(raw + rs * RAW),
+                                  ga.froot + (long long)r * ga.froot_stride +
+                                      ((long long)cw.tt * ga.n_root + rho0 + (long long)q * n_out) * FG_M,
+                                  RAW, smem_u32(&rfull[rs]));
                     else
                         tma_load_3d(smem_u32(raw + rs * RAW), &ga.fmap, smem_u32(&rfull[rs]), cw.tt * FG_M,
                                rho0 + q * (int)n_out, r);
@@ -415,6 +417,11 @@ cudaError_t launch_fold_grad_tc(FoldGradArgs& ga, int L, const float* Froot, lon
                                 const __nv_bfloat16* xp, const SplitXtArgs& sa, int reff, int pieces, cudaStream_t st) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return cudaErrorNotSupported;
+    ga.froot = Froot;
+    ga.froot_stride = root_stride;
+    ga.n_root = n_root;
+    if (ga.froot_tiled && (reinterpret_cast<uintptr_t>(Froot) % 16 != 0 || root_stride % 4 != 0 || n_root % FG_K != 0))
+        return cudaErrorInvalidValue;                     // (the bulk copies' alignment and whole chunks)
     if (ga.froot_tiled) {
         // [r][t / 128][rows][128]: dims (128 columns, rows, column tiles, shifts)
         const cuuint64_t dims[4] = {FG_M, (cuuint64_t)n_root, (cuuint64_t)ga.t_tiles, (cuuint64_t)reff};

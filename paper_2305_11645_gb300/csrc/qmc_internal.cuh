@@ -288,6 +288,9 @@ struct FoldGradArgs {
     int log_out;                     // log2 n_out
     int tau_pad, cpt, t_tiles, group;
     int froot_tiled;                 // F_JF in 128-column tiles, [r][t / 128][rows][128]
+    const float* froot;              // F_JF (the tiled layout: a chunk of 32 rows is 16 KB contiguous)
+    long long froot_stride;          // floats per shift
+    long long n_root;
 };
 cudaError_t launch_split_xt(const float* tab, long long tab_stride, const SplitXtArgs& sa, int reff, int pieces,
                             __nv_bfloat16* xp, float xc, cudaStream_t st);
