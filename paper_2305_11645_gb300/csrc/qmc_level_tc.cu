@@ -66,7 +66,10 @@ template <int P> constexpr size_t level_smem() {
 // k_split_x: the coarse levels' point-table entries as bf16 pieces.  Thread (row, g) of block
 // (level s, piece-chunk kc) writes the 8 columns 32 kc + 8 g .. + 7 of row rho of the level
 // (zero beyond its tau_I columns) for every piece; row rho < n'_I reads table row rho mod n_I.
-// Consecutive threads take consecutive rows, so the table reads of a warp are contiguous.
+// Four consecutive threads take the four 16-byte groups of one row, so a warp writes 8 whole
+// 64-byte rows of a piece (512 contiguous bytes) and reads 8 consecutive table rows (one 32-byte
+// sector) of each of 4 columns per load (with consecutive rows per thread, each 16-byte store
+// filled a quarter of a different row: 0.28 ms against 0.21 ms on the 2^20-point step).
 // ------------------------------------------------------------------------------------------
 struct SplitXArgs {
     int nlev;
@@ -86,9 +89,9 @@ __global__ void __launch_bounds__(256) k_split_x(const float* __restrict__ tab, 
     const LevelSeg& sg = sa.seg[l];
     const long long loc = i - sa.blk0[l];
     const long long nrep = 1LL << sg.logn_rep;
-    const long long rho = loc & (nrep - 1);
-    const long long rest = loc >> sg.logn_rep;           // = kc * 4 + g
-    const int g = (int)(rest & 3), kc = (int)(rest >> 2);
+    const int g = (int)(loc & 3);
+    const long long rho = (loc >> 2) & (nrep - 1);
+    const int kc = (int)(loc >> (2 + sg.logn_rep));
     const float* src = tab + (long long)r * tab_stride + sg.tab + (rho & ((1LL << sg.logn) - 1));
     float v[8];
 #pragma unroll
