@@ -46,6 +46,7 @@ __global__ void k_table(const __grid_constant__ DevRule R, T* __restrict__ tab, 
         const int j = R.lev_col0[I] + (int)(idx >> q);
         const uint32_t row = (uint32_t)(idx & ((1LL << q) - 1));
         const uint32_t x0 = unshifted_x32(R, j, row, q);
+#pragma unroll 4
         for (int r = 0; r < reff; ++r) {
             const uint32_t x = R.shift ? apply_shift(R.kind, x0, R.shift[(size_t)r * R.s + j]) : x0;
             tab[(long long)r * stride + g] = Tr<T>::apply(x, R.transform);
