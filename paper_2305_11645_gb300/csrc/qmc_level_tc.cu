@@ -22,7 +22,7 @@
 //               from one thread, the chunk's MMAs (M = 128, N = 256, K = 16, bf16 -> FP32), then
 //               commits the stage back to the producer and, after a tile's last chunk, the
 //               accumulator to the epilogue;
-//   warps 2-9   epilogue: each reads its 32 rows x 128 columns of the accumulator, adds the
+//   warps 2-13  epilogue: each reads its 32 rows x 96 or 64 columns of the accumulator, adds the
 //               coarser pass's rows (rho mod n_next) and stores the tile, in the [t/4][rho][4]
 //               layout of the root values, while the MMAs of the next tile fill the other
 //               accumulator.
@@ -53,7 +53,8 @@ constexpr int LT_M = 128;               // tile rows (MMA M, tensor-memory lanes
 constexpr int LT_N = 256;               // tile columns t (MMA N)
 constexpr uint32_t XPIECE = LT_M * 64;  // one piece of the X tile: 128 rows x 64 bytes
 constexpr uint32_t APIECE = LT_N * 64;  // one piece of the A tile: 256 rows x 64 bytes
-constexpr int kThreads = 320;           // producer, MMA, 8 epilogue warps
+constexpr int kEpi = 12;                // epilogue warps: 3 per tensor-memory lane quarter
+constexpr int kThreads = 64 + 32 * kEpi;   // producer, MMA, epilogue
 
 template <int P> constexpr int stages() { return P == 3 ? 3 : 6; }
 template <int P> constexpr uint32_t stage_bytes() { return P * (XPIECE + APIECE); }
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
         tma_prefetch(&xmap);
         tma_prefetch(&amap);
         for (int s = 0; s < ST; ++s) { bar_init(&full[s], 1); bar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { bar_init(&tfull[a], 1); bar_init(&tempty[a], 8); }
+        for (int a = 0; a < 2; ++a) { bar_init(&tfull[a], 1); bar_init(&tempty[a], kEpi); }
         bar_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -277,7 +278,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
         }
     } else {
         // ------------------------------------------------------------------ epilogue
-        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        // warp: lanes 32 quarter of the accumulator, its 32-column groups part, part + 3, ...
+        const int quarter = warp & 3, part = (warp - 2) >> 2;
+        const int ng = (LT_N / 32 - part + kEpi / 4 - 1) / (kEpi / 4);
         const long long n_out = 1LL << ps.logn_out;
         const bool has_next = ps.logn_next >= 0;
         const long long nmask = has_next ? (1LL << ps.logn_next) - 1 : 0;
@@ -289,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
             const bool row_ok = rho < n_out;
             const float* nx = has_next ? wsf + ps.next_off + (long long)ti.r * ps.next_stride + (rho & nmask) * 4
                                        : nullptr;
-            const int tb = ti.t0 + half * 128 + cg * 32;
+            const int tb = ti.t0 + (part + (kEpi / 4) * cg) * 32;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const int t = tb + 4 * q;
@@ -309,17 +312,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_level_tc(const __grid_constant_
             const long long rho = ti.rho0 + quarter * 32 + lane;
             const bool row_ok = rho < n_out;
             float* out = wsf + ps.out_off + (long long)ti.r * ps.out_stride + rho * 4;
-            const uint32_t lane_addr = tmem + (uint32_t)(a * LT_N + half * 128) + ((uint32_t)(quarter * 32) << 16);
+            const uint32_t lane_addr = tmem + (uint32_t)(a * LT_N) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
-            for (int cg = 0; cg < 4; ++cg) {
-                const int tb = ti.t0 + half * 128 + cg * 32;        // first column of the group
+            for (int cg = 0; cg < ng; ++cg) {
+                const int col = (part + (kEpi / 4) * cg) * 32;       // the group's first column in the tile
+                const int tb = ti.t0 + col;
                 float4 pv[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) pv[q] = pn[q];
-                if (cg < 3) load_group(ti, cg + 1, pn);
+                if (cg + 1 < ng) load_group(ti, cg + 1, pn);
                 else if (tile + gridDim.x < ps.ntiles) load_group(tile_of(ps, tile + gridDim.x), 0, pn);
                 uint32_t d[32];
-                tmem_ld32(lane_addr + cg * 32, d);
+                tmem_ld32(lane_addr + col, d);
                 tmem_wait_ld();
                 if (row_ok) {
 #pragma unroll
