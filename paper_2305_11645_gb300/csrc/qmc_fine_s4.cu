@@ -372,7 +372,6 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
     // h'(v) = 2 v then costs one multiply with the coefficient)
     const float coef_scale = F == F_GAUSS_NORM2 ? 2.0f * upstream : upstream;
     const float kap = a.kappa, c0 = a.c0;
-    const float2 kap2 = f2(kap, kap);
 
     // kappa * A of the thread's columns and the band-gradient accumulators, as column pairs
     float2 ah3[CPL][8], ah2[CPL][4], ah1[CPL][2], ah0[CPL];
@@ -472,25 +471,25 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                 p1 = f2(q.z, q.w);
             };
             float2 Fr[CPL];
-            float2 v4[CPL];                                     // kappa S_4 of the root
-#pragma unroll
-            for (int p = 0; p < CPL; ++p) v4[p] = __fmul2_rn(sr[p], kap2);
 #pragma unroll
             for (int c3 = 0; c3 < 2; ++c3) {
                 // (x of the level-3 and level-2 nodes is read again for the gradient updates
                 // instead of being held in registers across the subtree)
                 // (two interleaved partial sums shorten the dependent chain)
-                // (each second partial sum starts with a multiply: a zero pair to add to would cost
-                // register moves)
                 float2 v3[CPL], w3[CPL], F3[CPL];
+#pragma unroll
+                for (int p = 0; p < CPL; ++p) {
+                    v3[p] = f2(kap * sr[p].x, kap * sr[p].y);
+                    w3[p] = f2(0.0f, 0.0f);
+                }
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     float2 xa, xb;
                     pairs(4 * c3 + k, xa, xb);
 #pragma unroll
                     for (int p = 0; p < CPL; ++p) {
-                        v3[p] = ffma2(xa, ah3[p][2 * k], k == 0 ? v4[p] : v3[p]);
-                        w3[p] = k == 0 ? __fmul2_rn(xb, ah3[p][1]) : ffma2(xb, ah3[p][2 * k + 1], w3[p]);
+                        v3[p] = ffma2(xa, ah3[p][2 * k], v3[p]);
+                        w3[p] = ffma2(xb, ah3[p][2 * k + 1], w3[p]);
                     }
                 }
 #pragma unroll
@@ -500,13 +499,18 @@ __global__ void __launch_bounds__(kBwdThreads, CPL == 1 ? 2 : 1) k_fine_bwd_s4(c
                     const int c2 = c3 + 2 * k2;
                     float2 v2[CPL], w2[CPL], F2[CPL];
 #pragma unroll
+                    for (int p = 0; p < CPL; ++p) {
+                        v2[p] = v3[p];
+                        w2[p] = f2(0.0f, 0.0f);
+                    }
+#pragma unroll
                     for (int k = 0; k < 2; ++k) {
                         float2 xa, xb;
                         pairs(8 + 2 * c2 + k, xa, xb);
 #pragma unroll
                         for (int p = 0; p < CPL; ++p) {
-                            v2[p] = ffma2(xa, ah2[p][2 * k], k == 0 ? v3[p] : v2[p]);
-                            w2[p] = k == 0 ? __fmul2_rn(xb, ah2[p][1]) : ffma2(xb, ah2[p][2 * k + 1], w2[p]);
+                            v2[p] = ffma2(xa, ah2[p][2 * k], v2[p]);
+                            w2[p] = ffma2(xb, ah2[p][2 * k + 1], w2[p]);
                         }
                     }
 #pragma unroll
