@@ -46,7 +46,6 @@ TRAFFIC_BYTES = {
     # profiles/net20_top_kernels.md: the 2-shift capture of the 16-shift contract workload, scaled by
     # 16/2 (each shift's data are separate, so the DRAM bytes grow with the shifts)
     ("net20", "k_fine_bwd_s4"): (590.064384e6 + 500.344064e6) * 8,
-    ("net20", "k_fine_fwd_s4"): (608.503808e6 + 30.661376e6) * 8,
     ("net20", "k_fold_grad_tc"): (576.025088e6 + 60.776704e6) * 8,
     ("net20", "k_grad_tc"): (166.576384e6 + 3.463936e6) * 8,
 }
