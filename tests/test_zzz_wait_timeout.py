@@ -1,7 +1,8 @@
 """The failure path of the bounded device-side waits, exercised without a GPU fault: a kernel's
 wait on an mbarrier that nothing completes runs out after a fixed number of polls, the library
 reports QMC_ERR_TIMEOUT through its sticky error word, and the context stays usable (a small
-estimate afterwards still matches the oracle).  Runs last, so that nothing else shares the word."""
+estimate afterwards still matches the oracle).  Runs after every other kernel test but the
+allocation-free entry point's (collected last), so that nothing else shares the word."""
 import numpy as np
 import pytest
 import torch
