@@ -49,3 +49,21 @@ def test_coarse_tensor_work(net20):
     # six levels of 2 * 2^20 * 1024 * 96 flops each, and level 10's single column
     assert np.isclose(flops(range(4, 11)), 6 * 2.0 * 2**20 * TAU * 16 * 6 + 2.0 * 2**10 * TAU * 16 * 6)
     assert bench.coarse_mma_flops(net20, 1) * 6 == bench.coarse_mma_flops(net20, 3)
+
+
+def test_roofline_fractions(net20):
+    # the dominant kernel at the measured 7.315 ms per step and a 2070 MHz clock: 11 FP32 operations
+    # per output against 152 SMs x 128 lanes x clock; a tensor-core kernel against the sustained peak
+    mp = {"bf16_tflops_sustained": 1684.4}
+    r = bench.roofline_of(net20, "split", "k_fine_bwd_s4", 7.315, 1.0, 2070.0, mp, "measured", "net20")
+    assert r["bound"] == "alu" and r["pipe"] == "fp32" and r["unit"] == "Gop/s"
+    assert np.isclose(r["peak"], 152 * 128 * 2070e6 / 1e9)
+    assert np.isclose(r["frac"], OUTPUTS * 11.0 / (7.315e-3 * 152 * 128 * 2070e6))
+    assert np.isclose(r["achieved"] / r["peak"], r["frac"])
+    assert r["traffic"] == bench.TRAFFIC_BYTES[("net20", "k_fine_bwd_s4")]
+    t = bench.roofline_of(net20, "split", "k_grad_tc", 0.5, 1.0, 2070.0, mp, "measured", "net20")
+    fl = sum(2.0 * (1 << (M - l)) * TAU * tau_of(l) for l in (7, 8, 9, 10)) * R * 6
+    assert t["bound"] == "tensor" and np.isclose(t["frac"], fl / 0.5e-3 / 1e12 / 1684.4)
+    # a kernel without counters of its current code reports no traffic
+    f = bench.roofline_of(net20, "split", "k_fine_fwd_s4", 3.2, 1.0, 2070.0, mp, "measured", "net20")
+    assert f["traffic"] is None
